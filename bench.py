@@ -1,0 +1,384 @@
+#!/usr/bin/env python
+"""Benchmark: exact lexicographic enumeration of one large factorization set.
+
+Workload (single GPU): d = 6 generators drawn from seed 0 uniformly in
+[50, 200] (distinct, sorted, gcd 1) and n the smallest element with
+|Z(n)| >= 5e8 (found with the library's own device counting) -- about 12 GB
+of int32 tuples per step.  One step is the whole path on the device: the
+counting table, the memo build (elementwise batches of copy-and-increment),
+and the rank-sliced enumeration writing every tuple to HBM.
+
+Printed: one JSON line (rank 0).  `value` is factorizations/s with the
+generators already on the device side; `e2e` is the same metric through
+fz_enumerate_host (plan, enumeration and the device->host copy of every tuple
+into pinned host memory inside the timed region); `roofline` is the
+enumeration kernel's written bytes per launch over its CUDA-event time
+against the measured HBM copy bandwidth; `cpu_baseline` is the oracle (plain
+C recursion) on a bounded sample of the same workload on the host cores.
+
+`--impl reference` times that oracle alone, on the same workload and metric.
+Under torchrun each rank runs its own replica of the workload (weak scaling,
+no data exchange); times are the max over ranks.
+"""
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "Factorizations/s (exact, lex order) vs HBM roofline; served p50/p99 latency"
+UNIT = "factorizations/s"
+WORKLOAD = ("single large element: d=6 generators uniform in [50,200] (seed 0, distinct, "
+            "sorted, gcd 1), n = smallest with |Z(n)| >= 5e8, int32 tuples, memo depth "
+            "autotuned")
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--seed", type=int, default=0)
+    ap.add_argument("--e2e-steps", type=int, default=2)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--k", type=int, default=-1, help="memo depth (default: autotune)")
+    ap.add_argument("--slice-rows", type=int, default=0)
+    ap.add_argument("--cpu-seconds", type=float, default=15.0,
+                    help="target duration of the bounded oracle sample")
+    return ap.parse_args()
+
+
+# ---------------------------------------------------------------- workload
+def resolve_instance(count_upto, seed):
+    from paper_2407_20474_gb300 import workloads
+    g = workloads.config2_generators(seed)
+    n = workloads.find_n(count_upto, g, workloads.CONFIG2_TARGET, 4096)
+    return g, n
+
+
+# ---------------------------------------------------------- clock sampling
+class ClockSampler:
+    """nvidia-smi clocks / throttle reasons sampled in the background."""
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index=0, period_ms=50):
+        self.path = tempfile.mktemp(suffix=".csv")
+        self.proc = None
+        try:
+            self.fh = open(self.path, "w")
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(gpu_index), "--query-gpu=" + self.FIELDS,
+                 "--format=csv,noheader,nounits", "-lms", str(period_ms)],
+                stdout=self.fh, stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+        self.t0 = self.t1 = None
+
+    def mark_start(self):
+        self.t0 = time.time()
+
+    def mark_end(self):
+        self.t1 = time.time()
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        time.sleep(0.15)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.fh.close()
+        sms, maxes, reasons = [], [], set()
+        with open(self.path) as f:
+            for line in f:
+                p = [x.strip() for x in line.split(",")]
+                if len(p) < 9:
+                    continue
+                try:
+                    sm = float(p[1])
+                    mx = float(p[2])
+                except ValueError:
+                    continue
+                sms.append(sm)
+                maxes.append(mx)
+                names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown",
+                         "sw_power_cap"]
+                for name, flag in zip(names, p[5:9]):
+                    if flag.lower() == "active":
+                        reasons.add(name)
+        os.unlink(self.path)
+        if not sms:
+            return None
+        return {"sm_mhz": statistics.median(sms), "sm_max_mhz": max(maxes),
+                "reasons": sorted(reasons), "samples": len(sms)}
+
+
+# ------------------------------------------------------------ distributed
+def dist_setup(args):
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    pg = None
+    if world > 1:
+        import torch.distributed as dist
+        backend = "nccl" if args.impl == "ours" else "gloo"
+        if backend == "nccl":
+            import torch
+            torch.cuda.set_device(local)
+        dist.init_process_group(backend=backend)
+        pg = dist
+    return world, rank, local, pg
+
+
+def barrier(pg, torch=None):
+    if pg is not None:
+        if torch is not None:
+            pg.barrier(device_ids=[torch.cuda.current_device()])
+        else:
+            pg.barrier()
+
+
+def max_over_ranks(pg, value, torch=None):
+    if pg is None:
+        return value
+    if torch is not None:
+        t = torch.tensor([value], dtype=torch.float64, device="cuda")
+    else:
+        import torch as _t
+        t = _t.tensor([value], dtype=_t.float64)
+    pg.all_reduce(t, op=pg.ReduceOp.MAX)
+    return float(t.item())
+
+
+# ------------------------------------------------------------ cpu baseline
+def cpu_baseline(g, n, seconds, count_table=None):
+    """The oracle (plain C recursion, unchanged) on a bounded sample of the
+    same workload: the subtrees of every s-th value of a_1, walked on all host
+    cores; s is chosen so the run lasts about `seconds`."""
+    import numpy as np
+    import oracle
+    T = count_table if count_table is not None else oracle.count_table(g, n)
+    vals = np.arange(n // g[0], -1, -1, dtype=np.int64)
+    sizes = np.asarray(T[1][n - g[0] * vals], dtype=np.float64)
+    total = float(sizes.sum())
+    threads = os.cpu_count() or 1
+    # calibration on a small strided sample
+    stride = 64
+    t0 = time.perf_counter()
+    rows, _, used = oracle.sample_a1(g, n, vals[::stride], threads=threads)
+    dt = max(time.perf_counter() - t0, 1e-6)
+    rate = rows / dt
+    want_rows = rate * seconds
+    stride = max(1, int(round(total / max(want_rows, 1.0))))
+    sample = vals[::stride]
+    t0 = time.perf_counter()
+    rows, digest, used = oracle.sample_a1(g, n, sample, threads=threads)
+    dt = time.perf_counter() - t0
+    return {"value": rows / dt, "unit": UNIT, "cores": used, "kind": "oracle",
+            "sample": "rows of Z(n) whose a_1 is every %d-th value (%d of %d values, "
+                      "%d rows = %.2f%% of |Z|), plain recursion on %d threads, %.1f s"
+                      % (stride, sample.size, vals.size, rows, 100.0 * rows / total,
+                         used, dt),
+            "rows": rows, "seconds": dt}
+
+
+# --------------------------------------------------------------- our impl
+def kernel_traffic(d):
+    """dram bytes per launch of the enumeration kernel from the committed ncu
+    summary, if it was taken on the current kernel source; else None."""
+    path = os.path.join(ROOT, "profiles", "enum_kernel_traffic.json")
+    if not os.path.exists(path):
+        return None
+    try:
+        rec = json.load(open(path))
+    except ValueError:
+        return None
+    src = open(os.path.join(ROOT, "paper_2407_20474_gb300", "csrc", "fz_enum.cu"), "rb").read()
+    if rec.get("source_sha256") != hashlib.sha256(src).hexdigest():
+        return None
+    return rec.get("bytes_per_full_launch")
+
+
+def run_ours(args):
+    import torch
+    import __graft_entry__
+    world, rank, local, pg = dist_setup(args)
+    __graft_entry__.build()
+    import paper_2407_20474_gb300 as fz
+    torch.cuda.set_device(local)
+    dev = torch.cuda.current_device()
+    g, n = resolve_instance(lambda gg, nm: fz.fz_count_upto(gg, nm), args.seed)
+    d = len(g)
+    plan = fz.Plan(g, n, k=args.k, slice_rows=args.slice_rows)
+    count = plan.count
+    out = torch.empty(count * d, dtype=torch.int32, device="cuda")
+    stream = torch.cuda.current_stream()
+
+    def step(ev=None):
+        plan.rebuild()
+        if ev is not None:
+            ev[0].record(stream)
+        plan.enumerate(out)
+        if ev is not None:
+            ev[1].record(stream)
+
+    for _ in range(max(args.warmup, 0)):
+        step()
+    plan.sync()
+    torch.cuda.synchronize()
+
+    K = max(args.steps, 1)
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+           for _ in range(K)]
+    start, end = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    sampler = ClockSampler(dev) if rank == 0 else None
+    if sampler:
+        time.sleep(0.3)
+    launches0 = fz.fz_kernel_launches()
+    barrier(pg, torch)
+    torch.cuda.synchronize()
+    if sampler:
+        sampler.mark_start()
+    start.record(stream)
+    for i in range(K):
+        step(evs[i])
+    end.record(stream)
+    torch.cuda.synchronize()
+    if sampler:
+        sampler.mark_end()
+    barrier(pg, torch)
+    launches = fz.fz_kernel_launches() - launches0
+    plan.sync()
+    ms = start.elapsed_time(end)
+    ms = max_over_ranks(pg, ms, torch)
+    enum_ms = statistics.mean(a.elapsed_time(b) for a, b in evs)
+    clocks = sampler.stop() if sampler else None
+
+    value = world * K * count / (ms / 1e3)
+    bytes_per_launch = count * d * 4
+    achieved = bytes_per_launch / (enum_ms / 1e3) / 1e9
+    peaks = {}
+    pp = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(pp):
+        peaks = json.load(open(pp))
+    peak = peaks.get("hbm_gbs")
+    peak_src = "measured" if peak else "fallback"
+    if not peak:
+        peak = 6800.0
+
+    # end to end through the public host-buffer call
+    e2e = None
+    if not args.no_e2e:
+        host = torch.empty(count * d, dtype=torch.int32, pin_memory=True)
+        fz.fz_enumerate_host(g, n, host)   # warm-up (allocations, page-in)
+        torch.cuda.synchronize()
+        E = max(args.e2e_steps, 1)
+        barrier(pg, torch)
+        t0 = time.perf_counter()
+        for _ in range(E):
+            fz.fz_enumerate_host(g, n, host)
+        torch.cuda.synchronize()
+        t = time.perf_counter() - t0
+        t = max_over_ranks(pg, t, torch)
+        e2e = {"value": world * E * count / t, "unit": UNIT, "h2d_bytes_per_step": 4 * d,
+               "d2h_bytes_per_step": count * d * 4,
+               "note": "fz_enumerate_host: plan (count + memo), enumeration and D2H of "
+                       "every tuple into pinned host memory, %d steps" % E}
+        del host
+
+    base = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        base = cpu_baseline(g, n, args.cpu_seconds)
+        base = {k: v for k, v in base.items() if k not in ("rows", "seconds")}
+
+    if rank == 0:
+        rec = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": K,
+            "warmup": args.warmup, "ms_per_step": ms / K, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "int32", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "g": list(g), "n": n, "count": count,
+                       "k": plan.k, "top": plan.top, "memo_rows": plan.memo_rows,
+                       "slice_rows": plan.slice_rows, "bytes_per_step": bytes_per_launch,
+                       "parallelism": "replicas (one instance per GPU)",
+                       "l2": "output %.1f GB per step >> 129 MB L2; count table and memo "
+                             "rebuilt every step" % (bytes_per_launch / 1e9)},
+            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                         "frac": achieved / peak, "traffic": kernel_traffic(d),
+                         "kernel": "fz_enum_kernel<%d>" % d,
+                         "kernel_ms": enum_ms, "peak_source": peak_src,
+                         "algorithmic_bytes_per_launch": bytes_per_launch},
+            "cpu_baseline": base,
+            "e2e": e2e,
+            "clocks": clocks,
+            "gpu_launches": launches,
+        }
+        print(json.dumps(rec))
+    plan.close()
+    if pg is not None:
+        pg.destroy_process_group()
+
+
+# --------------------------------------------------------- reference arm
+def run_reference(args):
+    world, rank, local, pg = dist_setup(args)
+    if rank != 0:
+        if pg is not None:
+            pg.destroy_process_group()
+        return
+    import oracle
+    from oracle import build as ob
+    ob.build_oracle()
+    g, n = resolve_instance(oracle.count_upto, args.seed)
+    T = oracle.count_table(g, n)
+    count = int(T[0][n])
+    K = max(args.steps, 1)
+    W = max(args.warmup, 0)
+    # each step: a bounded sample of the workload; keep the whole run short
+    per_step = max(0.5, min(args.cpu_seconds, 120.0 / (K + W)))
+    res = []
+    for i in range(W + K):
+        r = cpu_baseline(g, n, per_step, count_table=T)
+        if i >= W:
+            res.append(r)
+    rows = sum(r["rows"] for r in res)
+    secs = sum(r["seconds"] for r in res)
+    value = rows / secs
+    rec = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+        "steps": K, "warmup": W, "ms_per_step": 1e3 * secs / K, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "int32", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "g": list(g), "n": n, "count": count},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": res[-1]["cores"],
+                         "kind": "oracle", "sample": res[-1]["sample"]},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0,
+                "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(rec))
+    if pg is not None:
+        pg.destroy_process_group()
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

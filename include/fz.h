@@ -1,0 +1,229 @@
+/*
+ * fz.h -- C ABI of the GB300 (sm_103a) library for exact, lexicographically
+ * ordered factorization sets in numerical semigroups (arXiv 2407.20474).
+ *
+ *   Z(n, (g_1..g_d)) = { a in N^d : sum_i a_i g_i = n }            (Section 1)
+ *
+ * Every list this library writes is in DESCENDING lexicographic order: a_1
+ * first, greatest first (Lemma "disjlex" and its corollary, Section 2.1; the
+ * lexicographically greatest next-candidate step of Algorithm 3.1, Section 3).
+ * Rank 0 is the greatest tuple.  Tuples are int32, row-major: row t of an
+ * output holds a_1..a_d at out[t*d + 0 .. t*d + d-1].
+ *
+ * Conventions shared by every call
+ * --------------------------------
+ * - Return value: FZ_OK (0) or a negative fz_status.  No call traps, aborts
+ *   or exits; device-side failures are reported through status words that
+ *   the library reads back at its next synchronising call.
+ * - Generators: 1 <= d <= FZ_MAX_D, every g_i >= 1.  The caller's order is
+ *   kept (never sorted): it defines the lexicographic order.  Repeated values
+ *   and a gcd > 1 are allowed (they give distinct tuples / empty sets).
+ * - Elements: 0 <= n <= INT32_MAX.  Z(0) = {0}; an n that is not a
+ *   combination of the generators has |Z(n)| = 0 (not an error).
+ * - Counts and offsets are uint64.  A count that does not fit (>= 2^64 - 1)
+ *   gives FZ_EOVERFLOW.
+ * - `stream` is a cudaStream_t passed as void* (NULL = the legacy default
+ *   stream).  Calls documented as asynchronous only enqueue work on it.
+ * - Pointers ending in _dev are device memory owned by the caller; the
+ *   library never frees caller memory.  Handles (fz_plan_t, fz_memo_t) own
+ *   library-allocated device memory until destroyed.
+ * - Output buffers (out_dev) should be 16-byte aligned: that enables the
+ *   bulk (TMA) store path.  Other 4-byte aligned pointers are accepted and
+ *   use plain stores.
+ * - Thread safety: distinct handles may be used from distinct host threads;
+ *   one handle must not be used by two threads at once.
+ */
+#ifndef FZ_H
+#define FZ_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define FZ_MAX_D 16
+#define FZ_AUTO (-1)
+
+typedef enum fz_status {
+    FZ_OK = 0,
+    FZ_EINVAL = -1,     /* bad argument: d, g_i, n, k, top, null pointer, alignment */
+    FZ_EOVERFLOW = -2,  /* a count or a byte size does not fit in 64 bits */
+    FZ_ENOSPC = -3,     /* output capacity smaller than needed (*written/*rows_needed still set) */
+    FZ_ENOMEM = -4,     /* device or host allocation failed */
+    FZ_EAGAIN = -5,     /* serving: request deferred, queue full */
+    FZ_ETIMEOUT = -6,   /* a bounded device-side wait gave up */
+    FZ_ECUDA = -7,      /* other CUDA failure; see fz_last_error_string() */
+    FZ_ENOTFOUND = -8,  /* unknown ticket or handle */
+    FZ_EINTERNAL = -9   /* a device-side consistency check failed */
+} fz_status;
+
+/* Implementation options.  Every field accepts FZ_AUTO (or 0 for slice_rows). */
+typedef struct fz_opts {
+    int32_t k;          /* memo depth, the paper's memoDim (Section 3.1): the
+                           last k coordinates are copied from the memo.
+                           0 = no memo (plain next-candidate walk of
+                           Algorithm 3.1); 1..d; FZ_AUTO = autotuned. */
+    int32_t top;        /* memo covers remainders p in [0, top) (the paper's
+                           topOfMemo); larger p take the ordinary step.
+                           FZ_AUTO = n + 1 (fully populated memo). */
+    int32_t slice_rows; /* output rows per warp work item (rounded up to a
+                           multiple of 4); 0 = default */
+    int32_t flags;      /* reserved, must be 0 */
+} fz_opts_t;
+
+/* Library version as 10000*major + 100*minor + patch. */
+int fz_version(void);
+
+/* Human-readable text of the last error raised on the calling host thread. */
+const char *fz_last_error_string(void);
+
+/* Static name of a status code ("FZ_EINVAL", ...). */
+const char *fz_status_string(int status);
+
+/* Number of CUDA kernels this library has enqueued in this process, over
+ * all threads and devices (a tracing counter; memsets and copies are not
+ * counted). */
+uint64_t fz_kernel_launches(void);
+
+/* ------------------------------------------------------------------------
+ * Counting (the saved subset cardinalities of Section 2.3, generalised).
+ *
+ * C[j][r] = |Z(r, (g_{j+1}..g_d))| for j = 0..d, r = 0..n (0-based j), with
+ * C[d][r] = [r == 0] and C[j][r] = C[j+1][r] + C[j][r - g_{j+1}].  By the
+ * disjoint recurrence of Section 2 (Lemma "disjdyn"), C[i-1][r] = |Z_{>=i}(r)|
+ * is the size of the block incr_i(Z_{>=i}(r)) = Z_{=i}(r + g_i).
+ * ---------------------------------------------------------------------- */
+
+/* |Z(n, g)| into *count (host).  `g` is host memory.  Synchronises `stream`.
+ * Errors: FZ_EINVAL, FZ_EOVERFLOW, FZ_ENOMEM, FZ_ECUDA. */
+int fz_count(const int32_t *g, int d, int32_t n, uint64_t *count, void *stream);
+
+/* counts[r] = |Z(r, g)| for r = 0..n_max into a host array of n_max + 1
+ * entries.  Entries that do not fit are UINT64_MAX (saturated).
+ * Synchronises `stream`.  Errors: FZ_EINVAL, FZ_ENOMEM, FZ_ECUDA. */
+int fz_count_upto(const int32_t *g, int d, int32_t n_max, uint64_t *counts,
+                  void *stream);
+
+/* The full table C (layout [d+1][n+1], row-major, uint64) into caller device
+ * memory `table_dev`.  Asynchronous; saturating at UINT64_MAX.
+ * Errors: FZ_EINVAL, FZ_ECUDA. */
+int fz_count_table(const int32_t *g, int d, int32_t n, uint64_t *table_dev,
+                   void *stream);
+
+/* ------------------------------------------------------------------------
+ * Memo of tail sets, built by the dynamic FactorizationsUpToElement pass:
+ * the lists Z(r, tail), r = 0..top-1, each in descending order, computed
+ * elementwise in batches of min(tail) elements (Section 2.2), every batch a
+ * set of copy-and-increment steps incr_i(Z_{>=i}(r - t_i)) written to
+ * pre-assigned offsets (Sections 2.3 and 2.4).  The layout is a CSR:
+ * offsets[r] .. offsets[r+1] are the rows of Z(r, tail), k int32 per row.
+ * ---------------------------------------------------------------------- */
+
+/* Number of memo rows sum_{r<top} |Z(r, tail)| into *rows (host).
+ * Synchronises `stream`.  Errors: FZ_EINVAL, FZ_EOVERFLOW, FZ_ENOMEM, FZ_ECUDA. */
+int fz_memo_rows(const int32_t *tail, int k, int32_t top, uint64_t *rows,
+                 void *stream);
+
+/* Build the memo into caller memory: offsets_dev (top + 1 uint64) and
+ * rows_dev (rows_capacity rows of k int32).  *rows_needed receives the row
+ * count; if it exceeds rows_capacity nothing is written and FZ_ENOSPC is
+ * returned.  Synchronises `stream`.  Errors: FZ_EINVAL, FZ_ENOSPC,
+ * FZ_EOVERFLOW, FZ_ENOMEM, FZ_ETIMEOUT, FZ_ECUDA. */
+int fz_build_memo_into(const int32_t *tail, int k, int32_t top,
+                       uint64_t *offsets_dev, int32_t *rows_dev,
+                       uint64_t rows_capacity, uint64_t *rows_needed,
+                       void *stream);
+
+typedef struct fz_memo_s *fz_memo_t;
+typedef struct fz_memo_info {
+    int32_t k, top;
+    uint64_t rows;                /* total rows */
+    const uint64_t *offsets_dev;  /* top + 1 entries, owned by the memo */
+    const int32_t *rows_dev;      /* rows * k entries, owned by the memo */
+} fz_memo_info_t;
+
+/* Library-owned memo (same contents as fz_build_memo_into).  Synchronises.
+ * Release with fz_memo_release. */
+int fz_build_memo(const int32_t *tail, int k, int32_t top, fz_memo_t *memo,
+                  void *stream);
+int fz_memo_info(fz_memo_t memo, fz_memo_info_t *info);
+int fz_memo_release(fz_memo_t memo);
+
+/* ------------------------------------------------------------------------
+ * Plans: one instance Z(n, g) with its count table and memo resident on the
+ * device, enumerated by rank ranges.
+ *
+ * The enumeration is the dynamic next-candidate walk (Section 3.1): leading
+ * coordinates a_1..a_{d-k} are walked in descending order; each prefix with
+ * p = n - phi(prefix) < top emits Memo[p] with the prefix prepended, and the
+ * state is left at (prefix, 0, ..., 0); prefixes with p >= top continue with
+ * the ordinary step of Algorithm 3.1.  Work is split by exact rank ranges
+ * from the count table (each warp unranks the start of its range), which
+ * plays the role of the paper's splitWork.
+ * ---------------------------------------------------------------------- */
+typedef struct fz_plan_s *fz_plan_t;
+typedef struct fz_plan_info {
+    uint64_t count;         /* |Z(n, g)| */
+    int32_t d, n, k, top;   /* resolved memo depth and top */
+    uint64_t memo_rows;     /* rows in the memo (0 if k == 0) */
+    uint64_t device_bytes;  /* device memory held by the plan */
+    int32_t slice_rows;     /* resolved rows per warp work item */
+    int32_t reserved;
+} fz_plan_info_t;
+
+/* Count (device), choose k and top (opts or autotune), allocate, build the
+ * memo.  `g` is host memory.  Synchronises `stream`.
+ * Errors: FZ_EINVAL, FZ_EOVERFLOW, FZ_ENOMEM, FZ_ETIMEOUT, FZ_ECUDA. */
+int fz_plan_create(const int32_t *g, int d, int32_t n, const fz_opts_t *opt,
+                   fz_plan_t *plan, void *stream);
+int fz_plan_info(fz_plan_t plan, fz_plan_info_t *info);
+
+/* Recompute the count table and rebuild the memo in the plan's buffers.
+ * Asynchronous (no host synchronisation), so it can be captured in a CUDA
+ * graph.  Errors surface at fz_plan_sync. */
+int fz_plan_rebuild(fz_plan_t plan, void *stream);
+
+/* Rows with rank in [rank_begin, min(rank_end, count)) into out_dev (row 0
+ * of out_dev is rank rank_begin).  rank_end = UINT64_MAX means "to the end".
+ * *written (host) is set before launching.  Asynchronous.
+ * Errors: FZ_EINVAL, FZ_ENOSPC (capacity < *written; nothing launched),
+ * FZ_ECUDA. */
+int fz_plan_enumerate(fz_plan_t plan, uint64_t rank_begin, uint64_t rank_end,
+                      int32_t *out_dev, uint64_t out_capacity_rows,
+                      uint64_t *written, void *stream);
+
+/* Tuples of the given ranks: ranks_dev[m] (device, each < count) ->
+ * out_dev[m*d ..].  Asynchronous.  Errors: FZ_EINVAL, FZ_ECUDA. */
+int fz_plan_unrank(fz_plan_t plan, const uint64_t *ranks_dev, uint64_t m,
+                   int32_t *out_dev, void *stream);
+
+/* Synchronise `stream` and report device-side errors of earlier calls on
+ * this plan (FZ_ETIMEOUT, FZ_EINTERNAL, FZ_ECUDA), clearing them. */
+int fz_plan_sync(fz_plan_t plan, void *stream);
+int fz_plan_destroy(fz_plan_t plan);
+
+/* ------------------------------------------------------------------------
+ * One-shot calls.
+ * ---------------------------------------------------------------------- */
+
+/* fz_plan_create + fz_plan_enumerate + fz_plan_sync + fz_plan_destroy.
+ * `opt` may be NULL (autotune).  Synchronises.  Errors: as those calls. */
+int fz_enumerate(const int32_t *g, int d, int32_t n, const fz_opts_t *opt,
+                 uint64_t rank_begin, uint64_t rank_end, int32_t *out_dev,
+                 uint64_t out_capacity_rows, uint64_t *written, void *stream);
+
+/* As fz_enumerate, but out_host is host memory (pinned memory is fastest).
+ * The rows are produced on the device in chunks and copied back while the
+ * next chunk is produced.  Synchronises. */
+int fz_enumerate_host(const int32_t *g, int d, int32_t n, const fz_opts_t *opt,
+                      uint64_t rank_begin, uint64_t rank_end, int32_t *out_host,
+                      uint64_t out_capacity_rows, uint64_t *written,
+                      void *stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* FZ_H */

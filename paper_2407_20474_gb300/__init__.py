@@ -1,0 +1,353 @@
+"""Python binding of the fz C ABI (``include/fz.h``): argument marshalling only.
+
+Every step of the path -- counting table, memo build, unranking, enumeration
+-- runs in the CUDA kernels of ``libfz.so`` (built in-tree by
+``paper_2407_20474_gb300._build.build()``).  There is no CPU fallback: if the
+library is missing or cannot be loaded, every call raises ``FzError``.
+
+Device buffers are passed as torch CUDA tensors (or raw integer device
+addresses); streams default to torch's current stream when torch is present.
+Tuples are int32, row-major, in descending lexicographic order.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from typing import Optional, Sequence
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libfz.so")
+
+FZ_MAX_D = 16
+FZ_AUTO = -1
+
+FZ_OK = 0
+FZ_EINVAL = -1
+FZ_EOVERFLOW = -2
+FZ_ENOSPC = -3
+FZ_ENOMEM = -4
+FZ_EAGAIN = -5
+FZ_ETIMEOUT = -6
+FZ_ECUDA = -7
+FZ_ENOTFOUND = -8
+FZ_EINTERNAL = -9
+
+# Every symbol include/fz.h declares (checked by the CPU tests).
+EXPORTS = (
+    "fz_version", "fz_last_error_string", "fz_status_string", "fz_kernel_launches",
+    "fz_count", "fz_count_upto", "fz_count_table",
+    "fz_memo_rows", "fz_build_memo_into", "fz_build_memo", "fz_memo_info",
+    "fz_memo_release",
+    "fz_plan_create", "fz_plan_info", "fz_plan_rebuild", "fz_plan_enumerate",
+    "fz_plan_unrank", "fz_plan_sync", "fz_plan_destroy",
+    "fz_enumerate", "fz_enumerate_host",
+)
+
+
+class FzError(RuntimeError):
+    def __init__(self, status: int, message: str):
+        super().__init__("%s: %s" % (status_string(status), message))
+        self.status = status
+
+
+class fz_opts_t(ctypes.Structure):
+    _fields_ = [("k", ctypes.c_int32), ("top", ctypes.c_int32),
+                ("slice_rows", ctypes.c_int32), ("flags", ctypes.c_int32)]
+
+
+class fz_plan_info_t(ctypes.Structure):
+    _fields_ = [("count", ctypes.c_uint64), ("d", ctypes.c_int32), ("n", ctypes.c_int32),
+                ("k", ctypes.c_int32), ("top", ctypes.c_int32),
+                ("memo_rows", ctypes.c_uint64), ("device_bytes", ctypes.c_uint64),
+                ("slice_rows", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+
+
+class fz_memo_info_t(ctypes.Structure):
+    _fields_ = [("k", ctypes.c_int32), ("top", ctypes.c_int32), ("rows", ctypes.c_uint64),
+                ("offsets_dev", ctypes.c_void_p), ("rows_dev", ctypes.c_void_p)]
+
+
+_lib = None
+_P = ctypes.c_void_p
+_I32P = ctypes.POINTER(ctypes.c_int32)
+_U64P = ctypes.POINTER(ctypes.c_uint64)
+
+_SIGS = {
+    "fz_version": (ctypes.c_int, []),
+    "fz_last_error_string": (ctypes.c_char_p, []),
+    "fz_status_string": (ctypes.c_char_p, [ctypes.c_int]),
+    "fz_kernel_launches": (ctypes.c_uint64, []),
+    "fz_count": (ctypes.c_int, [_I32P, ctypes.c_int, ctypes.c_int32, _U64P, _P]),
+    "fz_count_upto": (ctypes.c_int, [_I32P, ctypes.c_int, ctypes.c_int32, _U64P, _P]),
+    "fz_count_table": (ctypes.c_int, [_I32P, ctypes.c_int, ctypes.c_int32, _P, _P]),
+    "fz_memo_rows": (ctypes.c_int, [_I32P, ctypes.c_int, ctypes.c_int32, _U64P, _P]),
+    "fz_build_memo_into": (ctypes.c_int, [_I32P, ctypes.c_int, ctypes.c_int32, _P, _P,
+                                          ctypes.c_uint64, _U64P, _P]),
+    "fz_build_memo": (ctypes.c_int, [_I32P, ctypes.c_int, ctypes.c_int32,
+                                     ctypes.POINTER(_P), _P]),
+    "fz_memo_info": (ctypes.c_int, [_P, ctypes.POINTER(fz_memo_info_t)]),
+    "fz_memo_release": (ctypes.c_int, [_P]),
+    "fz_plan_create": (ctypes.c_int, [_I32P, ctypes.c_int, ctypes.c_int32,
+                                      ctypes.POINTER(fz_opts_t), ctypes.POINTER(_P), _P]),
+    "fz_plan_info": (ctypes.c_int, [_P, ctypes.POINTER(fz_plan_info_t)]),
+    "fz_plan_rebuild": (ctypes.c_int, [_P, _P]),
+    "fz_plan_enumerate": (ctypes.c_int, [_P, ctypes.c_uint64, ctypes.c_uint64, _P,
+                                         ctypes.c_uint64, _U64P, _P]),
+    "fz_plan_unrank": (ctypes.c_int, [_P, _P, ctypes.c_uint64, _P, _P]),
+    "fz_plan_sync": (ctypes.c_int, [_P, _P]),
+    "fz_plan_destroy": (ctypes.c_int, [_P]),
+    "fz_enumerate": (ctypes.c_int, [_I32P, ctypes.c_int, ctypes.c_int32,
+                                    ctypes.POINTER(fz_opts_t), ctypes.c_uint64,
+                                    ctypes.c_uint64, _P, ctypes.c_uint64, _U64P, _P]),
+    "fz_enumerate_host": (ctypes.c_int, [_I32P, ctypes.c_int, ctypes.c_int32,
+                                         ctypes.POINTER(fz_opts_t), ctypes.c_uint64,
+                                         ctypes.c_uint64, _P, ctypes.c_uint64, _U64P, _P]),
+}
+
+
+def lib():
+    """The loaded ``libfz.so`` (raises FzError if it is missing)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise FzError(FZ_ECUDA, "libfz.so not built (run __graft_entry__.build())")
+        try:
+            L = ctypes.CDLL(LIB_PATH)
+        except OSError as e:
+            raise FzError(FZ_ECUDA, "cannot load libfz.so: %s" % e)
+        for name, (res, args) in _SIGS.items():
+            fn = getattr(L, name)
+            fn.restype = res
+            fn.argtypes = args
+        _lib = L
+    return _lib
+
+
+def status_string(status: int) -> str:
+    try:
+        return lib().fz_status_string(int(status)).decode()
+    except FzError:
+        return "FZ_STATUS_%d" % status
+
+
+def _check(rc: int):
+    if rc != FZ_OK:
+        msg = lib().fz_last_error_string().decode(errors="replace")
+        raise FzError(rc, msg)
+
+
+def _gens(g: Sequence[int]):
+    arr = (ctypes.c_int32 * len(g))(*[int(x) for x in g])
+    return arr, len(g)
+
+
+def _stream(stream) -> Optional[int]:
+    if stream is None:
+        try:
+            import torch
+            if torch.cuda.is_available():
+                return torch.cuda.current_stream().cuda_stream
+        except ImportError:
+            pass
+        return None
+    if hasattr(stream, "cuda_stream"):
+        return stream.cuda_stream
+    return int(stream)
+
+
+def _ptr(x) -> Optional[int]:
+    if x is None:
+        return None
+    if hasattr(x, "data_ptr"):
+        return x.data_ptr()
+    return int(x)
+
+
+def _opts(k=FZ_AUTO, top=FZ_AUTO, slice_rows=0):
+    return fz_opts_t(int(k), int(top), int(slice_rows), 0)
+
+
+# ---------------------------------------------------------------- counting
+def fz_version() -> int:
+    return int(lib().fz_version())
+
+
+def fz_kernel_launches() -> int:
+    """Kernels the library has enqueued in this process (tracing counter)."""
+    return int(lib().fz_kernel_launches())
+
+
+def fz_count(g: Sequence[int], n: int, stream=None) -> int:
+    """|Z(n, g)| (device counting table)."""
+    ga, d = _gens(g)
+    out = ctypes.c_uint64(0)
+    _check(lib().fz_count(ga, d, int(n), ctypes.byref(out), _stream(stream)))
+    return int(out.value)
+
+
+def fz_count_upto(g: Sequence[int], n_max: int, stream=None) -> np.ndarray:
+    """|Z(r, g)| for r = 0..n_max (uint64; saturated entries are 2^64 - 1)."""
+    ga, d = _gens(g)
+    out = np.zeros(int(n_max) + 1, dtype=np.uint64)
+    _check(lib().fz_count_upto(ga, d, int(n_max),
+                               out.ctypes.data_as(_U64P), _stream(stream)))
+    return out
+
+
+def fz_count_table(g: Sequence[int], n: int, table, stream=None) -> None:
+    """Fill a device uint64 buffer of (d+1)*(n+1) entries with the count table."""
+    ga, d = _gens(g)
+    _check(lib().fz_count_table(ga, d, int(n), _ptr(table), _stream(stream)))
+
+
+# -------------------------------------------------------------------- memo
+def fz_memo_rows(tail: Sequence[int], top: int, stream=None) -> int:
+    ga, k = _gens(tail)
+    out = ctypes.c_uint64(0)
+    _check(lib().fz_memo_rows(ga, k, int(top), ctypes.byref(out), _stream(stream)))
+    return int(out.value)
+
+
+def fz_build_memo_into(tail: Sequence[int], top: int, offsets, rows, rows_capacity: int,
+                       stream=None) -> int:
+    """Build Memo[r] = Z(r, tail), r < top, into caller device buffers
+    (offsets: top+1 uint64; rows: rows_capacity*k int32).  Returns the rows."""
+    ga, k = _gens(tail)
+    need = ctypes.c_uint64(0)
+    _check(lib().fz_build_memo_into(ga, k, int(top), _ptr(offsets), _ptr(rows),
+                                    int(rows_capacity), ctypes.byref(need), _stream(stream)))
+    return int(need.value)
+
+
+class Memo:
+    """Library-owned memo (fz_build_memo / fz_memo_release)."""
+
+    def __init__(self, tail: Sequence[int], top: int, stream=None):
+        ga, k = _gens(tail)
+        h = _P()
+        _check(lib().fz_build_memo(ga, k, int(top), ctypes.byref(h), _stream(stream)))
+        self._h = h
+        info = fz_memo_info_t()
+        _check(lib().fz_memo_info(h, ctypes.byref(info)))
+        self.k, self.top, self.rows = info.k, info.top, int(info.rows)
+        self.offsets_dev, self.rows_dev = info.offsets_dev, info.rows_dev
+
+    def close(self):
+        if getattr(self, "_h", None):
+            lib().fz_memo_release(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def fz_build_memo(tail: Sequence[int], top: int, stream=None) -> Memo:
+    return Memo(tail, top, stream)
+
+
+# ------------------------------------------------------------------- plans
+class Plan:
+    """One instance Z(n, g) with its count table and memo resident on the device."""
+
+    def __init__(self, g: Sequence[int], n: int, k: int = FZ_AUTO, top: int = FZ_AUTO,
+                 slice_rows: int = 0, stream=None):
+        ga, d = _gens(g)
+        h = _P()
+        o = _opts(k, top, slice_rows)
+        _check(lib().fz_plan_create(ga, d, int(n), ctypes.byref(o), ctypes.byref(h),
+                                    _stream(stream)))
+        self._h = h
+        self.g = tuple(int(x) for x in g)
+        self.n = int(n)
+        info = fz_plan_info_t()
+        _check(lib().fz_plan_info(h, ctypes.byref(info)))
+        self.count = int(info.count)
+        self.d, self.k, self.top = int(info.d), int(info.k), int(info.top)
+        self.memo_rows = int(info.memo_rows)
+        self.device_bytes = int(info.device_bytes)
+        self.slice_rows = int(info.slice_rows)
+
+    def rebuild(self, stream=None):
+        _check(lib().fz_plan_rebuild(self._h, _stream(stream)))
+
+    def enumerate(self, out, rank_begin: int = 0, rank_end: Optional[int] = None,
+                  capacity_rows: Optional[int] = None, stream=None) -> int:
+        """Asynchronously write ranks [rank_begin, rank_end) into ``out``."""
+        end = (1 << 64) - 1 if rank_end is None else int(rank_end)
+        if capacity_rows is None:
+            capacity_rows = (out.numel() // self.d) if hasattr(out, "numel") else 0
+        w = ctypes.c_uint64(0)
+        _check(lib().fz_plan_enumerate(self._h, int(rank_begin), end, _ptr(out),
+                                       int(capacity_rows), ctypes.byref(w), _stream(stream)))
+        return int(w.value)
+
+    def unrank(self, ranks, out, stream=None):
+        """Asynchronously write the tuples of device uint64 ``ranks`` into ``out``."""
+        m = ranks.numel() if hasattr(ranks, "numel") else len(ranks)
+        _check(lib().fz_plan_unrank(self._h, _ptr(ranks), int(m), _ptr(out), _stream(stream)))
+
+    def sync(self, stream=None):
+        _check(lib().fz_plan_sync(self._h, _stream(stream)))
+
+    def close(self):
+        if getattr(self, "_h", None):
+            lib().fz_plan_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+
+def fz_plan_create(g, n, k=FZ_AUTO, top=FZ_AUTO, slice_rows=0, stream=None) -> Plan:
+    return Plan(g, n, k, top, slice_rows, stream)
+
+
+# --------------------------------------------------------------- one-shot
+def fz_enumerate(g: Sequence[int], n: int, out, rank_begin: int = 0,
+                 rank_end: Optional[int] = None, k: int = FZ_AUTO, top: int = FZ_AUTO,
+                 slice_rows: int = 0, capacity_rows: Optional[int] = None,
+                 stream=None) -> int:
+    """Rows of ranks [rank_begin, rank_end) into device buffer ``out``; returns rows."""
+    ga, d = _gens(g)
+    o = _opts(k, top, slice_rows)
+    end = (1 << 64) - 1 if rank_end is None else int(rank_end)
+    if capacity_rows is None:
+        capacity_rows = (out.numel() // d) if hasattr(out, "numel") else 0
+    w = ctypes.c_uint64(0)
+    _check(lib().fz_enumerate(ga, d, int(n), ctypes.byref(o), int(rank_begin), end,
+                              _ptr(out), int(capacity_rows), ctypes.byref(w),
+                              _stream(stream)))
+    return int(w.value)
+
+
+def fz_enumerate_host(g: Sequence[int], n: int, out, rank_begin: int = 0,
+                      rank_end: Optional[int] = None, k: int = FZ_AUTO, top: int = FZ_AUTO,
+                      slice_rows: int = 0, stream=None) -> int:
+    """As fz_enumerate into host memory ``out`` (numpy int32 array or pinned
+    torch CPU tensor, at least rows*d entries)."""
+    ga, d = _gens(g)
+    o = _opts(k, top, slice_rows)
+    end = (1 << 64) - 1 if rank_end is None else int(rank_end)
+    if isinstance(out, np.ndarray):
+        assert out.dtype == np.int32 and out.flags.c_contiguous
+        ptr, cap = out.ctypes.data, out.size // d
+    else:
+        ptr, cap = out.data_ptr(), out.numel() // d
+    w = ctypes.c_uint64(0)
+    _check(lib().fz_enumerate_host(ga, d, int(n), ctypes.byref(o), int(rank_begin), end,
+                                   ptr, int(cap), ctypes.byref(w), _stream(stream)))
+    return int(w.value)

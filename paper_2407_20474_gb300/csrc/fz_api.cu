@@ -1,0 +1,703 @@
+// fz_api.cu -- the C ABI declared in include/fz.h: error state, counting,
+// memo construction, plans (resident count table + memo per instance) and
+// the one-shot enumeration calls.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <atomic>
+#include <cstring>
+#include <mutex>
+#include <string>
+#include <vector>
+
+#include "fz_internal.cuh"
+
+namespace fz {
+
+namespace {
+thread_local std::string g_last_error;
+std::atomic<uint64_t> g_launches{0};
+}
+
+void note_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
+
+int set_error(int status, const std::string &msg) {
+    g_last_error = msg;
+    return status;
+}
+
+int cuda_error(cudaError_t e, const char *what) {
+    std::string m = std::string(what) + ": " + cudaGetErrorName(e) + " (" +
+                    cudaGetErrorString(e) + ")";
+    if (e == cudaErrorMemoryAllocation) return set_error(FZ_ENOMEM, m);
+    return set_error(FZ_ECUDA, m);
+}
+
+int device_props(DeviceProps *out) {
+    static std::mutex mu;
+    static DeviceProps cache[64];
+    int dev = 0;
+    FZ_CUDA_TRY(cudaGetDevice(&dev));
+    std::lock_guard<std::mutex> lk(mu);
+    if (dev >= 0 && dev < 64 && cache[dev].device == dev) {
+        *out = cache[dev];
+        return FZ_OK;
+    }
+    DeviceProps p;
+    p.device = dev;
+    FZ_CUDA_TRY(cudaDeviceGetAttribute(&p.sms, cudaDevAttrMultiProcessorCount, dev));
+    FZ_CUDA_TRY(cudaDeviceGetAttribute(&p.max_smem_optin,
+                                       cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
+    if (dev >= 0 && dev < 64) cache[dev] = p;
+    *out = p;
+    return FZ_OK;
+}
+
+int validate_gens(const int32_t *g, int d) {
+    if (!g) return set_error(FZ_EINVAL, "generators: null pointer");
+    if (d < 1 || d > FZ_MAX_D) return set_error(FZ_EINVAL, "d must be in 1..16");
+    for (int i = 0; i < d; ++i)
+        if (g[i] < 1) return set_error(FZ_EINVAL, "generators must be >= 1");
+    return FZ_OK;
+}
+
+namespace {
+
+// RAII device buffer (cudaMalloc / cudaFree).
+struct DevBuf {
+    void *p = nullptr;
+    size_t bytes = 0;
+    DevBuf() = default;
+    DevBuf(const DevBuf &) = delete;
+    DevBuf &operator=(const DevBuf &) = delete;
+    ~DevBuf() { release(); }
+    int alloc(size_t b) {
+        release();
+        if (b == 0) b = 16;
+        cudaError_t e = cudaMalloc(&p, b);
+        if (e != cudaSuccess) {
+            p = nullptr;
+            return cuda_error(e, "cudaMalloc");
+        }
+        bytes = b;
+        return FZ_OK;
+    }
+    void release() {
+        if (p) cudaFree(p);
+        p = nullptr;
+        bytes = 0;
+    }
+    template <class T>
+    T *as() const {
+        return static_cast<T *>(p);
+    }
+};
+
+int status_to_fz(int dev_status) {
+    switch (dev_status) {
+        case DEV_OK: return FZ_OK;
+        case DEV_TIMEOUT: return set_error(FZ_ETIMEOUT, "a bounded device wait expired");
+        default: return set_error(FZ_EINTERNAL, "device-side consistency check failed");
+    }
+}
+
+bool mul_overflows(uint64_t a, uint64_t b, uint64_t *out) {
+    if (a != 0 && b > ~0ull / a) return true;
+    *out = a * b;
+    return false;
+}
+
+cudaStream_t as_stream(void *s) { return static_cast<cudaStream_t>(s); }
+
+}  // namespace
+}  // namespace fz
+
+using namespace fz;
+
+// ---------------------------------------------------------------------------
+// plan
+// ---------------------------------------------------------------------------
+struct fz_plan_s {
+    int d = 0;
+    int32_t n = 0;
+    int32_t g[FZ_MAX_D] = {};
+    int K = 0;
+    int32_t top = 0;
+    uint64_t count = 0;
+    uint64_t memo_rows = 0;
+    uint64_t slice_rows = 0;
+    int64_t tmp_words = 0;
+    DevBuf base;   // C, tmp, O, status, bar, counter
+    DevBuf memo;   // map + rows
+    uint64_t *C = nullptr, *tmp = nullptr, *O = nullptr, *map = nullptr;
+    int32_t *rows = nullptr;
+    int *status = nullptr;
+    unsigned *bar = nullptr;
+    unsigned long long *counter = nullptr;
+};
+
+struct fz_memo_s {
+    int k = 0;
+    int32_t top = 0;
+    uint64_t rows = 0;
+    DevBuf buf;       // offsets
+    DevBuf rows_buf;  // rows
+    uint64_t *O = nullptr;
+    int32_t *R = nullptr;
+};
+
+namespace fz {
+namespace {
+
+size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
+
+// Enqueue the memo of plan p (offsets scan, gather map, fill).
+int plan_enqueue_memo(fz_plan_s *p, cudaStream_t s) {
+    if (p->K < 1 || p->top < 1) return FZ_OK;
+    const int64_t cs = (int64_t)p->n + 1;
+    const uint64_t *crow = p->C + (int64_t)(p->d - p->K) * cs;
+    int rc = launch_exclusive_scan_tmp(crow, p->O, p->top, p->tmp, s);
+    if (rc != FZ_OK) return rc;
+    if (p->memo_rows == 0) return FZ_OK;
+    MemoBuffers mb;
+    mb.Ct = crow;
+    mb.cs = cs;
+    mb.O = p->O;
+    mb.map = p->map;
+    mb.rows = p->rows;
+    mb.status = p->status;
+    mb.bar = p->bar;
+    return launch_memo_build(p->g + (p->d - p->K), p->K, p->top, p->memo_rows, mb, s);
+}
+
+int read_status(int *status_dev, cudaStream_t s) {
+    int h = 0;
+    FZ_CUDA_TRY(cudaMemcpyAsync(&h, status_dev, sizeof(int), cudaMemcpyDeviceToHost, s));
+    FZ_CUDA_TRY(cudaStreamSynchronize(s));
+    if (h != 0) {
+        FZ_CUDA_TRY(cudaMemsetAsync(status_dev, 0, sizeof(int), s));
+        FZ_CUDA_TRY(cudaStreamSynchronize(s));
+    }
+    return status_to_fz(h);
+}
+
+// Memo rows of depth k with full top = n + 1, from row d - k of the table
+// (exclusive scan into p->O, then one 8-byte read).  Synchronises.
+int memo_rows_for(fz_plan_s *p, int k, int32_t top, uint64_t *rows, cudaStream_t s) {
+    const int64_t cs = (int64_t)p->n + 1;
+    const uint64_t *crow = p->C + (int64_t)(p->d - k) * cs;
+    int rc = launch_exclusive_scan_tmp(crow, p->O, top, p->tmp, s);
+    if (rc != FZ_OK) return rc;
+    FZ_CUDA_TRY(cudaMemcpyAsync(rows, p->O + top, sizeof(uint64_t), cudaMemcpyDeviceToHost, s));
+    FZ_CUDA_TRY(cudaStreamSynchronize(s));
+    return FZ_OK;
+}
+
+// Memo depth chosen automatically: the deepest k in 2..min(d-1, 4) whose full
+// memo stays small next to the output and needs a bounded number of
+// elementwise batches; k = 0 (plain walk) when none qualifies.
+int choose_k(fz_plan_s *p, cudaStream_t s, int *k_out) {
+    *k_out = 0;
+    const uint64_t out_bytes = p->count * (uint64_t)p->d * 4ull;
+    const uint64_t budget = std::max<uint64_t>(8ull << 20, out_bytes / 8);
+    for (int k = std::min(p->d - 1, 4); k >= 2; --k) {
+        int32_t tmin = p->g[p->d - k];
+        for (int i = p->d - k; i < p->d; ++i) tmin = std::min(tmin, p->g[i]);
+        const int64_t batches = ((int64_t)p->n + 1 + tmin - 1) / tmin;
+        if (batches > 4096) continue;
+        uint64_t rows = 0;
+        int rc = memo_rows_for(p, k, p->n + 1, &rows, s);
+        if (rc != FZ_OK) return rc;
+        if (rows == ~0ull || rows > MEMO_MAX_ROWS) continue;
+        const uint64_t bytes = rows * (uint64_t)(4 * k + 8);
+        if (bytes > budget) continue;
+        *k_out = k;
+        return FZ_OK;
+    }
+    return FZ_OK;
+}
+
+int plan_create_impl(const int32_t *g, int d, int32_t n, const fz_opts_t *opt, fz_plan_s *p,
+                     cudaStream_t s) {
+    int rc = validate_gens(g, d);
+    if (rc != FZ_OK) return rc;
+    if (n < 0) return set_error(FZ_EINVAL, "n must be >= 0");
+    if (opt && opt->flags != 0) return set_error(FZ_EINVAL, "opts.flags must be 0");
+    if (opt && (opt->k != FZ_AUTO && (opt->k < 0 || opt->k > d)))
+        return set_error(FZ_EINVAL, "opts.k must be FZ_AUTO or in 0..d");
+    if (opt && opt->top != FZ_AUTO && opt->top < 0)
+        return set_error(FZ_EINVAL, "opts.top must be FZ_AUTO or >= 0");
+    if (opt && opt->slice_rows < 0) return set_error(FZ_EINVAL, "opts.slice_rows must be >= 0");
+    p->d = d;
+    p->n = n;
+    for (int i = 0; i < d; ++i) p->g[i] = g[i];
+    const int64_t cs = (int64_t)n + 1;
+    uint64_t table_words;
+    if (mul_overflows((uint64_t)(d + 1), (uint64_t)cs, &table_words))
+        return set_error(FZ_EOVERFLOW, "count table size");
+    p->tmp_words = std::max(count_table_tmp_words(g, d, n), exclusive_scan_tmp_words(cs));
+    const size_t off_C = 0;
+    const size_t off_tmp = align256(off_C + table_words * 8);
+    const size_t off_O = align256(off_tmp + (size_t)p->tmp_words * 8);
+    const size_t off_status = align256(off_O + (size_t)(cs + 1) * 8);
+    const size_t off_bar = off_status + 256;
+    const size_t off_counter = off_bar + 256;
+    const size_t total = off_counter + 256;
+    rc = p->base.alloc(total);
+    if (rc != FZ_OK) return rc;
+    char *b = p->base.as<char>();
+    p->C = reinterpret_cast<uint64_t *>(b + off_C);
+    p->tmp = reinterpret_cast<uint64_t *>(b + off_tmp);
+    p->O = reinterpret_cast<uint64_t *>(b + off_O);
+    p->status = reinterpret_cast<int *>(b + off_status);
+    p->bar = reinterpret_cast<unsigned *>(b + off_bar);
+    p->counter = reinterpret_cast<unsigned long long *>(b + off_counter);
+    FZ_CUDA_TRY(cudaMemsetAsync(b + off_status, 0, 768, s));
+
+    rc = launch_count_table_tmp(g, d, n, p->C, p->tmp, s);
+    if (rc != FZ_OK) return rc;
+    FZ_CUDA_TRY(cudaMemcpyAsync(&p->count, p->C + n, sizeof(uint64_t), cudaMemcpyDeviceToHost,
+                                s));
+    FZ_CUDA_TRY(cudaStreamSynchronize(s));
+    if (p->count == ~0ull) return set_error(FZ_EOVERFLOW, "|Z(n)| does not fit in 64 bits");
+
+    // memo depth and top
+    int k = opt ? opt->k : FZ_AUTO;
+    if (k == FZ_AUTO) {
+        rc = choose_k(p, s, &k);
+        if (rc != FZ_OK) return rc;
+    }
+    int64_t top = (opt && opt->top != FZ_AUTO) ? opt->top : (int64_t)n + 1;
+    if (top > (int64_t)n + 1) top = (int64_t)n + 1;
+    if (k == 0) top = 0;
+    p->K = k;
+    p->top = (int32_t)top;
+    if (k >= 1 && top >= 1) {
+        rc = memo_rows_for(p, k, p->top, &p->memo_rows, s);
+        if (rc != FZ_OK) return rc;
+        if (p->memo_rows == ~0ull || p->memo_rows > MEMO_MAX_ROWS)
+            return set_error(FZ_EINVAL, "memo too large (more than 2^30 rows); lower k or top");
+        const size_t off_rows = align256(p->memo_rows * 8);
+        rc = p->memo.alloc(off_rows + p->memo_rows * (size_t)k * 4 + 16);
+        if (rc != FZ_OK) return rc;
+        p->map = p->memo.as<uint64_t>();
+        p->rows = reinterpret_cast<int32_t *>(p->memo.as<char>() + off_rows);
+        rc = plan_enqueue_memo(p, s);
+        if (rc != FZ_OK) return rc;
+        rc = read_status(p->status, s);
+        if (rc != FZ_OK) return rc;
+    }
+    DeviceProps dp;
+    rc = device_props(&dp);
+    if (rc != FZ_OK) return rc;
+    if (opt && opt->slice_rows > 0)
+        p->slice_rows = ((uint64_t)opt->slice_rows + 3) & ~3ull;
+    else
+        p->slice_rows = default_slice_rows(p->count, dp.sms);
+    return FZ_OK;
+}
+
+EnumLaunch launch_of(const fz_plan_s *p) {
+    EnumLaunch L;
+    L.C = p->C;
+    L.cs = (int64_t)p->n + 1;
+    L.O = p->O;
+    L.memo = p->rows;
+    L.memo_rows = p->memo_rows;
+    L.status = p->status;
+    L.slice_counter = p->counter;
+    L.n = p->n;
+    L.d = p->d;
+    L.K = p->K;
+    L.top = p->top;
+    L.g = p->g;
+    return L;
+}
+
+uint64_t rows_in(const fz_plan_s *p, uint64_t b, uint64_t e) {
+    if (e > p->count) e = p->count;
+    return b < e ? e - b : 0;
+}
+
+}  // namespace
+}  // namespace fz
+
+extern "C" {
+
+int fz_version(void) { return 100; }
+
+uint64_t fz_kernel_launches(void) { return fz::g_launches.load(std::memory_order_relaxed); }
+
+const char *fz_last_error_string(void) { return fz::g_last_error.c_str(); }
+
+const char *fz_status_string(int status) {
+    switch (status) {
+        case FZ_OK: return "FZ_OK";
+        case FZ_EINVAL: return "FZ_EINVAL";
+        case FZ_EOVERFLOW: return "FZ_EOVERFLOW";
+        case FZ_ENOSPC: return "FZ_ENOSPC";
+        case FZ_ENOMEM: return "FZ_ENOMEM";
+        case FZ_EAGAIN: return "FZ_EAGAIN";
+        case FZ_ETIMEOUT: return "FZ_ETIMEOUT";
+        case FZ_ECUDA: return "FZ_ECUDA";
+        case FZ_ENOTFOUND: return "FZ_ENOTFOUND";
+        case FZ_EINTERNAL: return "FZ_EINTERNAL";
+        default: return "FZ_UNKNOWN";
+    }
+}
+
+// ----------------------------------------------------------------- counting
+int fz_count_upto(const int32_t *g, int d, int32_t n_max, uint64_t *counts, void *stream) {
+    int rc = validate_gens(g, d);
+    if (rc != FZ_OK) return rc;
+    if (n_max < 0) return set_error(FZ_EINVAL, "n must be >= 0");
+    if (!counts) return set_error(FZ_EINVAL, "counts: null pointer");
+    cudaStream_t s = as_stream(stream);
+    const int64_t len = (int64_t)n_max + 1;
+    int64_t tmpw = count_table_tmp_words(g, d, n_max);
+    DevBuf buf;
+    rc = buf.alloc((size_t)(2 * len + tmpw) * 8);
+    if (rc != FZ_OK) return rc;
+    uint64_t *a = buf.as<uint64_t>(), *b = a + len, *tmp = b + len, *res = nullptr;
+    rc = launch_count_rolling(g, d, n_max, a, b, tmp, &res, s);
+    if (rc != FZ_OK) return rc;
+    FZ_CUDA_TRY(cudaMemcpyAsync(counts, res, (size_t)len * 8, cudaMemcpyDeviceToHost, s));
+    FZ_CUDA_TRY(cudaStreamSynchronize(s));
+    return FZ_OK;
+}
+
+int fz_count(const int32_t *g, int d, int32_t n, uint64_t *count, void *stream) {
+    int rc = validate_gens(g, d);
+    if (rc != FZ_OK) return rc;
+    if (n < 0) return set_error(FZ_EINVAL, "n must be >= 0");
+    if (!count) return set_error(FZ_EINVAL, "count: null pointer");
+    cudaStream_t s = as_stream(stream);
+    const int64_t len = (int64_t)n + 1;
+    int64_t tmpw = count_table_tmp_words(g, d, n);
+    DevBuf buf;
+    rc = buf.alloc((size_t)(2 * len + tmpw) * 8);
+    if (rc != FZ_OK) return rc;
+    uint64_t *a = buf.as<uint64_t>(), *b = a + len, *tmp = b + len, *res = nullptr;
+    rc = launch_count_rolling(g, d, n, a, b, tmp, &res, s);
+    if (rc != FZ_OK) return rc;
+    uint64_t h = 0;
+    FZ_CUDA_TRY(cudaMemcpyAsync(&h, res + n, 8, cudaMemcpyDeviceToHost, s));
+    FZ_CUDA_TRY(cudaStreamSynchronize(s));
+    *count = h;
+    if (h == ~0ull) return set_error(FZ_EOVERFLOW, "|Z(n)| does not fit in 64 bits");
+    return FZ_OK;
+}
+
+int fz_count_table(const int32_t *g, int d, int32_t n, uint64_t *table_dev, void *stream) {
+    int rc = validate_gens(g, d);
+    if (rc != FZ_OK) return rc;
+    if (n < 0) return set_error(FZ_EINVAL, "n must be >= 0");
+    if (!table_dev) return set_error(FZ_EINVAL, "table: null pointer");
+    cudaStream_t s = as_stream(stream);
+    int64_t tmpw = count_table_tmp_words(g, d, n);
+    uint64_t *tmp = nullptr;
+    if (tmpw > 0) FZ_CUDA_TRY(cudaMallocAsync((void **)&tmp, (size_t)tmpw * 8, s));
+    rc = launch_count_table_tmp(g, d, n, table_dev, tmp, s);
+    if (tmp) cudaFreeAsync(tmp, s);
+    return rc;
+}
+
+// --------------------------------------------------------------------- memo
+static int memo_common(const int32_t *tail, int k, int32_t top, cudaStream_t s, DevBuf &table,
+                       uint64_t **C, int64_t *tmpw_out) {
+    int rc = validate_gens(tail, k);
+    if (rc != FZ_OK) return rc;
+    if (top < 0) return set_error(FZ_EINVAL, "top must be >= 0");
+    const int32_t n = top > 0 ? top - 1 : 0;
+    const int64_t cs = (int64_t)n + 1;
+    int64_t tmpw = std::max(count_table_tmp_words(tail, k, n), exclusive_scan_tmp_words(cs));
+    rc = table.alloc((size_t)((k + 1) * cs + tmpw + 64) * 8);
+    if (rc != FZ_OK) return rc;
+    *C = table.as<uint64_t>();
+    *tmpw_out = tmpw;
+    rc = launch_count_table_tmp(tail, k, n, *C, *C + (k + 1) * cs, s);
+    return rc;
+}
+
+int fz_memo_rows(const int32_t *tail, int k, int32_t top, uint64_t *rows, void *stream) {
+    if (!rows) return set_error(FZ_EINVAL, "rows: null pointer");
+    cudaStream_t s = as_stream(stream);
+    if (top == 0) {
+        int rc = validate_gens(tail, k);
+        if (rc == FZ_OK) *rows = 0;
+        return rc;
+    }
+    DevBuf table, off;
+    uint64_t *C = nullptr;
+    int64_t tmpw = 0;
+    int rc = memo_common(tail, k, top, s, table, &C, &tmpw);
+    if (rc != FZ_OK) return rc;
+    rc = off.alloc((size_t)(top + 1) * 8);
+    if (rc != FZ_OK) return rc;
+    const int64_t cs = (int64_t)top;
+    rc = launch_exclusive_scan_tmp(C, off.as<uint64_t>(), top, C + (k + 1) * cs, s);
+    if (rc != FZ_OK) return rc;
+    uint64_t h = 0;
+    FZ_CUDA_TRY(cudaMemcpyAsync(&h, off.as<uint64_t>() + top, 8, cudaMemcpyDeviceToHost, s));
+    FZ_CUDA_TRY(cudaStreamSynchronize(s));
+    *rows = h;
+    if (h == ~0ull) return set_error(FZ_EOVERFLOW, "memo rows do not fit in 64 bits");
+    return FZ_OK;
+}
+
+static int build_memo_to(const int32_t *tail, int k, int32_t top, uint64_t *O, int32_t **R,
+                         uint64_t rows_capacity, uint64_t *rows_needed, DevBuf *own_rows,
+                         cudaStream_t s) {
+    DevBuf table, work;
+    uint64_t *C = nullptr;
+    int64_t tmpw = 0;
+    int rc = memo_common(tail, k, top, s, table, &C, &tmpw);
+    if (rc != FZ_OK) return rc;
+    const int64_t cs = (int64_t)top;
+    uint64_t *tmp = C + (k + 1) * cs;
+    rc = launch_exclusive_scan_tmp(C, O, top, tmp, s);
+    if (rc != FZ_OK) return rc;
+    uint64_t rows = 0;
+    FZ_CUDA_TRY(cudaMemcpyAsync(&rows, O + top, 8, cudaMemcpyDeviceToHost, s));
+    FZ_CUDA_TRY(cudaStreamSynchronize(s));
+    if (rows_needed) *rows_needed = rows;
+    if (rows == ~0ull) return set_error(FZ_EOVERFLOW, "memo rows do not fit in 64 bits");
+    if (own_rows) {
+        rc = own_rows->alloc(rows * (size_t)k * 4 + 16);
+        if (rc != FZ_OK) return rc;
+        *R = own_rows->as<int32_t>();
+    } else if (rows > rows_capacity) {
+        return set_error(FZ_ENOSPC, "memo rows exceed rows_capacity");
+    }
+    if (rows == 0) return FZ_OK;
+    // gather map + status + barrier words
+    const size_t map_bytes = align256(rows * 8);
+    rc = work.alloc(map_bytes + 512);
+    if (rc != FZ_OK) return rc;
+    MemoBuffers mb;
+    mb.Ct = C;
+    mb.cs = cs;
+    mb.O = O;
+    mb.map = work.as<uint64_t>();
+    mb.status = reinterpret_cast<int *>(work.as<char>() + map_bytes);
+    mb.bar = reinterpret_cast<unsigned *>(work.as<char>() + map_bytes + 256);
+    FZ_CUDA_TRY(cudaMemsetAsync(work.as<char>() + map_bytes, 0, 512, s));
+    rc = launch_memo_build(tail, k, top, rows, mb, s);
+    if (rc != FZ_OK) return rc;
+    return read_status(mb.status, s);
+}
+
+int fz_build_memo_into(const int32_t *tail, int k, int32_t top, uint64_t *offsets_dev,
+                       int32_t *rows_dev, uint64_t rows_capacity, uint64_t *rows_needed,
+                       void *stream) {
+    if (!offsets_dev || (!rows_dev && rows_capacity > 0))
+        return set_error(FZ_EINVAL, "memo buffers: null pointer");
+    if (top == 0) {
+        int rc = validate_gens(tail, k);
+        if (rc != FZ_OK) return rc;
+        if (rows_needed) *rows_needed = 0;
+        FZ_CUDA_TRY(cudaMemsetAsync(offsets_dev, 0, 8, as_stream(stream)));
+        FZ_CUDA_TRY(cudaStreamSynchronize(as_stream(stream)));
+        return FZ_OK;
+    }
+    int32_t *R = rows_dev;
+    return build_memo_to(tail, k, top, offsets_dev, &R, rows_capacity, rows_needed, nullptr,
+                         as_stream(stream));
+}
+
+int fz_build_memo(const int32_t *tail, int k, int32_t top, fz_memo_t *memo, void *stream) {
+    if (!memo) return set_error(FZ_EINVAL, "memo: null pointer");
+    int rc = validate_gens(tail, k);
+    if (rc != FZ_OK) return rc;
+    if (top < 0) return set_error(FZ_EINVAL, "top must be >= 0");
+    fz_memo_s *m = new (std::nothrow) fz_memo_s;
+    if (!m) return set_error(FZ_ENOMEM, "host allocation");
+    m->k = k;
+    m->top = top;
+    cudaStream_t s = as_stream(stream);
+    rc = m->buf.alloc((size_t)(top + 1) * 8);
+    if (rc == FZ_OK) {
+        m->O = m->buf.as<uint64_t>();
+        if (top == 0) {
+            if (cudaMemsetAsync(m->O, 0, 8, s) != cudaSuccess ||
+                cudaStreamSynchronize(s) != cudaSuccess)
+                rc = set_error(FZ_ECUDA, "memset");
+        } else {
+            rc = build_memo_to(tail, k, top, m->O, &m->R, 0, &m->rows, &m->rows_buf, s);
+        }
+    }
+    if (rc != FZ_OK) {
+        delete m;
+        return rc;
+    }
+    *memo = m;
+    return FZ_OK;
+}
+
+int fz_memo_info(fz_memo_t memo, fz_memo_info_t *info) {
+    if (!memo || !info) return set_error(FZ_EINVAL, "null pointer");
+    info->k = memo->k;
+    info->top = memo->top;
+    info->rows = memo->rows;
+    info->offsets_dev = memo->O;
+    info->rows_dev = memo->R;
+    return FZ_OK;
+}
+
+int fz_memo_release(fz_memo_t memo) {
+    if (!memo) return set_error(FZ_EINVAL, "null pointer");
+    delete memo;
+    return FZ_OK;
+}
+
+// -------------------------------------------------------------------- plans
+int fz_plan_create(const int32_t *g, int d, int32_t n, const fz_opts_t *opt, fz_plan_t *plan,
+                   void *stream) {
+    if (!plan) return set_error(FZ_EINVAL, "plan: null pointer");
+    fz_plan_s *p = new (std::nothrow) fz_plan_s;
+    if (!p) return set_error(FZ_ENOMEM, "host allocation");
+    int rc = plan_create_impl(g, d, n, opt, p, as_stream(stream));
+    if (rc != FZ_OK) {
+        cudaStreamSynchronize(as_stream(stream));
+        delete p;
+        return rc;
+    }
+    *plan = p;
+    return FZ_OK;
+}
+
+int fz_plan_info(fz_plan_t p, fz_plan_info_t *info) {
+    if (!p || !info) return set_error(FZ_EINVAL, "null pointer");
+    info->count = p->count;
+    info->d = p->d;
+    info->n = p->n;
+    info->k = p->K;
+    info->top = p->top;
+    info->memo_rows = p->memo_rows;
+    info->device_bytes = p->base.bytes + p->memo.bytes;
+    info->slice_rows = (int32_t)p->slice_rows;
+    info->reserved = 0;
+    return FZ_OK;
+}
+
+int fz_plan_rebuild(fz_plan_t p, void *stream) {
+    if (!p) return set_error(FZ_EINVAL, "plan: null pointer");
+    cudaStream_t s = as_stream(stream);
+    int rc = launch_count_table_tmp(p->g, p->d, p->n, p->C, p->tmp, s);
+    if (rc != FZ_OK) return rc;
+    return plan_enqueue_memo(p, s);
+}
+
+int fz_plan_enumerate(fz_plan_t p, uint64_t rank_begin, uint64_t rank_end, int32_t *out_dev,
+                      uint64_t out_capacity_rows, uint64_t *written, void *stream) {
+    if (!p) return set_error(FZ_EINVAL, "plan: null pointer");
+    const uint64_t rows = rows_in(p, rank_begin, rank_end);
+    if (written) *written = rows;
+    if (rows == 0) return FZ_OK;
+    if (!out_dev) return set_error(FZ_EINVAL, "out: null pointer");
+    if (((uintptr_t)out_dev & 3u) != 0) return set_error(FZ_EINVAL, "out must be 4-byte aligned");
+    if (out_capacity_rows < rows) return set_error(FZ_ENOSPC, "output capacity too small");
+    return launch_enumerate(launch_of(p), rank_begin, rows, out_dev, p->slice_rows,
+                            as_stream(stream));
+}
+
+int fz_plan_unrank(fz_plan_t p, const uint64_t *ranks_dev, uint64_t m, int32_t *out_dev,
+                   void *stream) {
+    if (!p) return set_error(FZ_EINVAL, "plan: null pointer");
+    if (m == 0) return FZ_OK;
+    if (!ranks_dev || !out_dev) return set_error(FZ_EINVAL, "null pointer");
+    return launch_unrank(launch_of(p), ranks_dev, m, out_dev, as_stream(stream));
+}
+
+int fz_plan_sync(fz_plan_t p, void *stream) {
+    if (!p) return set_error(FZ_EINVAL, "plan: null pointer");
+    cudaStream_t s = as_stream(stream);
+    FZ_CUDA_TRY(cudaStreamSynchronize(s));
+    return read_status(p->status, s);
+}
+
+int fz_plan_destroy(fz_plan_t p) {
+    if (!p) return set_error(FZ_EINVAL, "plan: null pointer");
+    delete p;
+    return FZ_OK;
+}
+
+// ---------------------------------------------------------------- one-shot
+int fz_enumerate(const int32_t *g, int d, int32_t n, const fz_opts_t *opt, uint64_t rank_begin,
+                 uint64_t rank_end, int32_t *out_dev, uint64_t out_capacity_rows,
+                 uint64_t *written, void *stream) {
+    fz_plan_t p = nullptr;
+    int rc = fz_plan_create(g, d, n, opt, &p, stream);
+    if (rc != FZ_OK) return rc;
+    rc = fz_plan_enumerate(p, rank_begin, rank_end, out_dev, out_capacity_rows, written, stream);
+    if (rc == FZ_OK) rc = fz_plan_sync(p, stream);
+    fz_plan_destroy(p);
+    return rc;
+}
+
+int fz_enumerate_host(const int32_t *g, int d, int32_t n, const fz_opts_t *opt,
+                      uint64_t rank_begin, uint64_t rank_end, int32_t *out_host,
+                      uint64_t out_capacity_rows, uint64_t *written, void *stream) {
+    fz_plan_t p = nullptr;
+    int rc = fz_plan_create(g, d, n, opt, &p, stream);
+    if (rc != FZ_OK) return rc;
+    const uint64_t rows = rows_in(p, rank_begin, rank_end);
+    if (written) *written = rows;
+    if (rows > 0 && !out_host) rc = set_error(FZ_EINVAL, "out: null pointer");
+    if (rc == FZ_OK && out_capacity_rows < rows)
+        rc = set_error(FZ_ENOSPC, "output capacity too small");
+    if (rc != FZ_OK || rows == 0) {
+        fz_plan_destroy(p);
+        return rc;
+    }
+    cudaStream_t s = as_stream(stream);
+    // two device chunks: enumerate chunk i while chunk i-1 is copied back
+    const uint64_t chunk = std::min<uint64_t>(rows, std::max<uint64_t>(1ull << 20,
+                                                  (256ull << 20) / (4ull * d)));
+    DevBuf bufs;
+    rc = bufs.alloc(2 * align256(chunk * (size_t)d * 4));
+    cudaStream_t copy = nullptr;
+    cudaEvent_t made[2] = {nullptr, nullptr}, copied[2] = {nullptr, nullptr};
+    if (rc == FZ_OK && cudaStreamCreateWithFlags(&copy, cudaStreamNonBlocking) != cudaSuccess)
+        rc = set_error(FZ_ECUDA, "stream create");
+    for (int i = 0; i < 2 && rc == FZ_OK; ++i) {
+        if (cudaEventCreateWithFlags(&made[i], cudaEventDisableTiming) != cudaSuccess ||
+            cudaEventCreateWithFlags(&copied[i], cudaEventDisableTiming) != cudaSuccess)
+            rc = set_error(FZ_ECUDA, "event create");
+    }
+    const size_t half = align256(chunk * (size_t)d * 4);
+    uint64_t done = 0;
+    int i = 0;
+    while (rc == FZ_OK && done < rows) {
+        const uint64_t now = std::min(chunk, rows - done);
+        int32_t *dbuf = reinterpret_cast<int32_t *>(bufs.as<char>() + (size_t)(i & 1) * half);
+        if (i >= 2 && cudaStreamWaitEvent(s, copied[i & 1], 0) != cudaSuccess) {
+            rc = set_error(FZ_ECUDA, "stream wait");
+            break;
+        }
+        uint64_t w = 0;
+        rc = fz_plan_enumerate(p, rank_begin + done, rank_begin + done + now, dbuf, now, &w, s);
+        if (rc != FZ_OK) break;
+        if (cudaEventRecord(made[i & 1], s) != cudaSuccess ||
+            cudaStreamWaitEvent(copy, made[i & 1], 0) != cudaSuccess ||
+            cudaMemcpyAsync(out_host + done * (uint64_t)d, dbuf, now * (size_t)d * 4,
+                            cudaMemcpyDeviceToHost, copy) != cudaSuccess ||
+            cudaEventRecord(copied[i & 1], copy) != cudaSuccess) {
+            rc = set_error(FZ_ECUDA, "chunk copy");
+            break;
+        }
+        done += now;
+        ++i;
+    }
+    if (copy) cudaStreamSynchronize(copy);
+    if (rc == FZ_OK) rc = fz_plan_sync(p, stream);
+    for (int j = 0; j < 2; ++j) {
+        if (made[j]) cudaEventDestroy(made[j]);
+        if (copied[j]) cudaEventDestroy(copied[j]);
+    }
+    if (copy) cudaStreamDestroy(copy);
+    fz_plan_destroy(p);
+    return rc;
+}
+
+}  // extern "C"

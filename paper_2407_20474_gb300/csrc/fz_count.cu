@@ -1,0 +1,198 @@
+// fz_count.cu -- the exact counting table of the factorization sets.
+//
+//   C[j][r] = |Z(r, (g_{j+1}, ..., g_d))|,  j = 0..d (0-based), r = 0..n,
+//   C[d][r] = [r == 0],   C[j][r] = sum_{t >= 0} C[j+1][r - t g_{j+1}].
+//
+// By the disjoint recurrence of Section 2 (Lemma "disjdyn") C[i-1][r] is
+// |Z_{>=i}(r)|, the size of the block incr_i(Z_{>=i}(r)) = Z_{=i}(r + g_i)
+// whose saving the paper describes in Section 2.3.  It gives every block's
+// size and start, hence exact output offsets for every warp.
+//
+// Each row is a strided inclusive prefix sum of the row below it (stride
+// g_{j+1}): for every residue class rho mod g the entries rho, rho + g, ...
+// are summed in order.  Short chains are scanned by one warp each; long
+// chains are cut into blocks of RB entries, the block sums are scanned by the
+// same routine (they form a strided array of the same shape), and the blocks
+// are then re-walked with their carries.  All sums saturate at 2^64 - 1.
+#include "fz_internal.cuh"
+
+namespace fz {
+
+namespace {
+
+constexpr int64_t DIRECT_T = 4096;  // chains up to this length: one warp each
+constexpr int RB = 32;              // entries per block in the blocked scan
+constexpr int THREADS = 256;
+
+__global__ void row_delta_kernel(uint64_t *__restrict__ row, int64_t len) {
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (; i < len; i += stride) row[i] = (i == 0) ? 1ull : 0ull;
+}
+
+// One warp per residue chain; 4 x 32 entries loaded ahead of the scan.
+__global__ void __launch_bounds__(THREADS)
+chain_scan_direct_kernel(const uint64_t *__restrict__ in, uint64_t *__restrict__ out,
+                         int64_t len, int64_t g) {
+    const int lane = threadIdx.x & 31;
+    const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    const int64_t chains = g < len ? g : len;
+    for (int64_t rho = warp; rho < chains; rho += nwarps) {
+        const int64_t T = (len - rho + g - 1) / g;
+        uint64_t carry = 0;
+        for (int64_t t0 = 0; t0 < T; t0 += 128) {
+            uint64_t v[4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                int64_t t = t0 + u * 32 + lane;
+                v[u] = t < T ? __ldg(in + rho + t * g) : 0ull;
+            }
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                int64_t t = t0 + u * 32 + lane;
+                uint64_t s = sat_add(warp_incl_scan_sat(v[u], lane), carry);
+                if (t < T) out[rho + t * g] = s;
+                carry = shfl_u64(s, 31);
+            }
+        }
+    }
+}
+
+// S[b*g + rho] = sum of the RB entries of chain rho in block b.
+__global__ void __launch_bounds__(THREADS)
+block_sum_kernel(const uint64_t *__restrict__ in, uint64_t *__restrict__ S, int64_t len,
+                 int64_t g, int64_t slen) {
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (; i < slen; i += stride) {
+        const int64_t b = i / g, rho = i - b * g;
+        const int64_t r0 = (b * RB) * g + rho;
+        uint64_t acc = 0;
+#pragma unroll 8
+        for (int t = 0; t < RB; ++t) {
+            int64_t r = r0 + (int64_t)t * g;
+            if (r < len) acc = sat_add(acc, __ldg(in + r));
+        }
+        S[i] = acc;
+    }
+}
+
+// out[r] = carry(block) + running sum inside the block.
+__global__ void __launch_bounds__(THREADS)
+block_apply_kernel(const uint64_t *__restrict__ in, uint64_t *__restrict__ out,
+                   const uint64_t *__restrict__ Sincl, int64_t len, int64_t g, int64_t slen) {
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (; i < slen; i += stride) {
+        const int64_t b = i / g, rho = i - b * g;
+        uint64_t acc = b > 0 ? Sincl[i - g] : 0ull;
+        const int64_t r0 = (b * RB) * g + rho;
+#pragma unroll 8
+        for (int t = 0; t < RB; ++t) {
+            int64_t r = r0 + (int64_t)t * g;
+            if (r < len) {
+                acc = sat_add(acc, __ldg(in + r));
+                out[r] = acc;
+            }
+        }
+    }
+}
+
+int grid_for(int64_t work, int per_block) {
+    int64_t b = (work + per_block - 1) / per_block;
+    if (b < 1) b = 1;
+    if (b > 65535LL * 16) b = 65535LL * 16;
+    return (int)b;
+}
+
+// Scratch words the blocked scan needs for an array of `len` entries, stride g.
+int64_t scan_tmp_words(int64_t len, int64_t g) {
+    int64_t T = (len + g - 1) / g;
+    if (len <= 0 || T <= DIRECT_T) return 0;
+    int64_t nrb = (T + RB - 1) / RB;
+    int64_t slen = nrb * g;
+    return 2 * slen + scan_tmp_words(slen, g);
+}
+
+// out[r] = sum_{t >= 0, r - t g >= 0} in[r - t g], for r < len.
+int strided_scan(const uint64_t *in, uint64_t *out, int64_t len, int64_t g, uint64_t *tmp,
+                 cudaStream_t s) {
+    if (len <= 0) return FZ_OK;
+    const int64_t T = (len + g - 1) / g;
+    if (T <= DIRECT_T) {
+        int64_t chains = g < len ? g : len;
+        int blocks = grid_for(chains * 32, THREADS);
+        chain_scan_direct_kernel<<<blocks, THREADS, 0, s>>>(in, out, len, g);
+        note_launch();
+        FZ_CUDA_TRY(cudaGetLastError());
+        return FZ_OK;
+    }
+    const int64_t nrb = (T + RB - 1) / RB;
+    const int64_t slen = nrb * g;
+    uint64_t *S = tmp, *Sincl = tmp + slen;
+    block_sum_kernel<<<grid_for(slen, THREADS), THREADS, 0, s>>>(in, S, len, g, slen);
+    note_launch();
+    FZ_CUDA_TRY(cudaGetLastError());
+    int rc = strided_scan(S, Sincl, slen, g, tmp + 2 * slen, s);
+    if (rc != FZ_OK) return rc;
+    block_apply_kernel<<<grid_for(slen, THREADS), THREADS, 0, s>>>(in, out, Sincl, len, g, slen);
+    note_launch();
+    FZ_CUDA_TRY(cudaGetLastError());
+    return FZ_OK;
+}
+
+}  // namespace
+
+int64_t count_table_tmp_words(const int32_t *g, int d, int32_t n) {
+    int64_t w = 0;
+    for (int j = 0; j < d; ++j) {
+        int64_t t = scan_tmp_words((int64_t)n + 1, g[j]);
+        if (t > w) w = t;
+    }
+    return w;
+}
+
+int64_t exclusive_scan_tmp_words(int64_t len) { return scan_tmp_words(len, 1); }
+
+int launch_count_table_tmp(const int32_t *g, int d, int32_t n, uint64_t *table, uint64_t *tmp,
+                           cudaStream_t s) {
+    const int64_t len = (int64_t)n + 1;
+    uint64_t *last = table + (int64_t)d * len;
+    row_delta_kernel<<<grid_for(len, THREADS), THREADS, 0, s>>>(last, len);
+    note_launch();
+    FZ_CUDA_TRY(cudaGetLastError());
+    for (int j = d - 1; j >= 0; --j) {
+        int rc = strided_scan(table + (int64_t)(j + 1) * len, table + (int64_t)j * len, len,
+                              g[j], tmp, s);
+        if (rc != FZ_OK) return rc;
+    }
+    return FZ_OK;
+}
+
+int launch_count_rolling(const int32_t *g, int d, int32_t n, uint64_t *a, uint64_t *b,
+                         uint64_t *tmp, uint64_t **result, cudaStream_t s) {
+    const int64_t len = (int64_t)n + 1;
+    row_delta_kernel<<<grid_for(len, THREADS), THREADS, 0, s>>>(a, len);
+    note_launch();
+    FZ_CUDA_TRY(cudaGetLastError());
+    uint64_t *below = a, *cur = b;
+    for (int j = d - 1; j >= 0; --j) {
+        int rc = strided_scan(below, cur, len, g[j], tmp, s);
+        if (rc != FZ_OK) return rc;
+        uint64_t *t = below;
+        below = cur;
+        cur = t;
+    }
+    *result = below;
+    return FZ_OK;
+}
+
+// in: len entries; out: len + 1 entries, out[0] = 0, out[r+1] = sum_{r' <= r} in[r'].
+int launch_exclusive_scan_tmp(const uint64_t *in, uint64_t *out, int64_t len, uint64_t *tmp,
+                              cudaStream_t s) {
+    FZ_CUDA_TRY(cudaMemsetAsync(out, 0, sizeof(uint64_t), s));
+    return strided_scan(in, out + 1, len, 1, tmp, s);
+}
+
+}  // namespace fz

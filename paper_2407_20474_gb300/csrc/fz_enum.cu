@@ -1,0 +1,640 @@
+// fz_enum.cu -- lexicographic enumeration of Z(n, g) with low-dimension
+// tabulation (Section 3.1), sliced by exact ranks.
+//
+// The output list (descending lexicographic order) is the depth-first walk of
+// the tree whose depth-c nodes are prefixes (a_0..a_{c-1}) with remainder
+// rem = n - phi(prefix) >= 0; the children of a node are a_c = floor(rem/g_c)
+// down to 0 (the order in which the next-candidate step of Algorithm 3.1
+// visits them).  The subtree of the child a_c = v holds C[c+1][rem - v g_c]
+// rows, and the rows of all children with a_c >= v number C[c][rem - v g_c]
+// (count table, fz_count.cu), so any rank is located by searching one table
+// row per level.
+//
+// Leaves ("blocks"), as in the dynamic next-candidate step:
+//  * memo leaf: a prefix of length L = d - K whose remainder p is < top;
+//    its rows are Memo[p] = Z(p, (g_L..g_{d-1})) with the prefix prepended
+//    (the block copy of Section 3.1; the walk then continues from
+//    (prefix, 0, ..., 0), the observation of Section 3.1);
+//  * walk leaf: a prefix of length d - 1 (reached when no memo applies);
+//    its one row, if g_{d-1} divides p, is the candidate of Algorithm 3.1's
+//    ordinary step with a_d = p / g_d.
+//
+// Work split: each warp takes slices of S consecutive ranks (an atomic
+// counter hands them out), finds the leaf holding its first rank by table
+// search (this replaces the paper's splitWork with exact bounds), and walks
+// from there.  A run of sibling leaves is processed 32 at a time: every lane
+// evaluates one candidate, the table gives each lane its cumulative row end
+// directly, and lanes then fill rows: each lane finds the leaf of its row by
+// a 5-step shuffle search.  Rows are assembled in a per-warp shared-memory
+// ring of two halves and each full half is written to HBM with one bulk
+// (TMA) store, so the stream is written with 16-byte aligned, fully
+// coalesced transactions while the warp generates the next half.
+#include "fz_internal.cuh"
+
+namespace fz {
+
+constexpr int ENUM_WARPS = 8;
+constexpr int ENUM_THREADS = ENUM_WARPS * 32;
+constexpr int RING_BYTES_PER_WARP = 12 * 1024;  // two halves
+constexpr uint32_t CAP32 = 0xffffffffu;
+
+struct EnumParams {
+    const uint64_t *C;     // count table rows 0..d, stride cs
+    int64_t cs;
+    const uint64_t *O;     // memo CSR offsets (top + 1), or null
+    const int32_t *memo;   // memo rows, K int32 each, or null
+    uint64_t memo_rows;    // rows in memo (bounds guard)
+    int32_t *out;          // row 0 = rank rank_begin
+    int *status;
+    unsigned long long *slice_counter;
+    uint64_t rank_begin;   // absolute rank of out row 0
+    uint64_t nrows;        // rows to write
+    uint64_t slice_rows;   // S (multiple of 4)
+    uint64_t nslices;
+    int n, d, K, top;
+    int lam_m;             // coordinate whose children are memo leaves (d-K-1), or -1
+    int lam_w;             // coordinate whose children are walk leaves (d-2)
+    int half_rows;         // B: rows per ring half (multiple of 32)
+    int aligned;           // out is 16-byte aligned
+    int g[FZ_MAX_D];
+};
+
+struct WarpPath {
+    int a[FZ_MAX_D];      // a_0..a_{lam-1}
+    int r[FZ_MAX_D + 1];  // r[0] = n, r[c+1] = r[c] - a[c] g[c]
+};
+
+enum LeafType : int { T_NONE = 0, T_MEMO = 1, T_WALK = 2, T_INTERNAL = 3 };
+
+// Largest u in [0, umax] with F(u) <= R, F(u) = C[c][rem - (umax + 1 - u) g_c]
+// (rows in the children with a_c > umax - u), searched 32 probes at a time.
+// Returns the child a_c = umax - u holding relative rank R and the rows
+// before it.  Requires R < C[c][rem].
+__device__ __forceinline__ void find_child(const EnumParams &P, int c, int rem, uint64_t R,
+                                           int lane, int &v_out, uint64_t &before_out) {
+    const long long g = P.g[c];
+    const long long umax = rem / g;
+    const long long base = (long long)rem - (umax + 1) * g;
+    const uint64_t *row = P.C + (long long)c * P.cs;
+    long long lo = 0, hi = umax + 1;
+    uint64_t flo = 0;
+    while (hi - lo > 1) {
+        const long long step = (hi - lo + 31) >> 5;
+        const long long u = lo + (long long)(lane + 1) * step;
+        bool ok = false;
+        uint64_t fu = 0;
+        if (u < hi) {
+            const long long idx = base + u * g;
+            fu = idx >= 0 ? __ldg(row + idx) : 0ull;
+            ok = fu <= R;
+        }
+        const unsigned m = __ballot_sync(FULL, ok);
+        const int cnt = __popc(m);
+        const uint64_t fsel = shfl_u64(fu, cnt > 0 ? cnt - 1 : 0);
+        if (cnt > 0) {
+            flo = fsel;
+            lo += (long long)cnt * step;
+        }
+        const long long nh = lo + step;
+        if (nh < hi) hi = nh;
+    }
+    v_out = (int)(umax - lo);
+    before_out = flo;
+}
+
+// Walk state of one warp (warp-uniform).
+struct RunState {
+    int lam;          // coordinate of the current run of sibling leaves
+    int inwalk;       // inside the subtree of a memo-level child with p >= top
+    long long vcur;   // next candidate value of a_lam (descending)
+    uint64_t base;    // rows in the siblings before vcur
+};
+
+// Choose the first live child at depths c_from..c_to-1 (path stored by lane 0).
+__device__ __forceinline__ void descend(const EnumParams &P, WarpPath *wp, int c_from,
+                                        int c_to, int lane) {
+    int rem = wp->r[c_from];
+    for (int c = c_from; c < c_to; ++c) {
+        int v;
+        uint64_t before;
+        find_child(P, c, rem, 0ull, lane, v, before);
+        rem -= v * P.g[c];
+        if (lane == 0) {
+            wp->a[c] = v;
+            wp->r[c + 1] = rem;
+        }
+    }
+    __syncwarp();
+}
+
+// Position the warp on the leaf holding absolute rank R.  Returns the offset
+// of R inside that leaf.  Sets *ok = false if the table is inconsistent.
+__device__ uint64_t unrank_to_leaf(const EnumParams &P, WarpPath *wp, uint64_t R, int lane,
+                                   RunState &st, bool *ok) {
+    int rem = P.n;
+    if (lane == 0) wp->r[0] = rem;
+    int inwalk = 0;
+    const bool memo = P.lam_m >= 0;
+    *ok = true;
+    for (int c = 0; c < P.d; ++c) {
+        const int runlev = (memo && !inwalk) ? P.lam_m : P.lam_w;
+        const uint64_t total = __ldg(P.C + (long long)c * P.cs + rem);
+        if (R >= total) {
+            *ok = false;
+            break;
+        }
+        int v;
+        uint64_t before;
+        find_child(P, c, rem, R, lane, v, before);
+        R -= before;
+        const int p = rem - v * P.g[c];
+        if (c == runlev) {
+            if (memo && !inwalk && p >= P.top && P.lam_m < P.lam_w) {
+                // memo-level child beyond the memo: walk its subtree
+                if (lane == 0) {
+                    wp->a[c] = v;
+                    wp->r[c + 1] = p;
+                }
+                rem = p;
+                inwalk = 1;
+                continue;
+            }
+            st.lam = c;
+            st.inwalk = inwalk;
+            st.vcur = v;
+            st.base = before;
+            __syncwarp();
+            return R;
+        }
+        if (lane == 0) {
+            wp->a[c] = v;
+            wp->r[c + 1] = p;
+        }
+        rem = p;
+    }
+    __syncwarp();
+    *ok = false;
+    return 0;
+}
+
+// Move to the next run after the current one is exhausted.  Returns false at
+// the end of the stream.
+__device__ bool advance(const EnumParams &P, WarpPath *wp, int lane, RunState &st) {
+    const bool memo = P.lam_m >= 0;
+    for (int j = st.lam - 1; j >= 0; --j) {
+        const int rem = wp->r[j];
+        const int aj = wp->a[j];
+        const uint64_t *row = P.C + (long long)j * P.cs;
+        const uint64_t R = __ldg(row + (rem - aj * P.g[j]));  // rows in children >= aj
+        const uint64_t total = __ldg(row + rem);
+        if (R >= total) continue;
+        int v;
+        uint64_t before;
+        find_child(P, j, rem, R, lane, v, before);
+        const int p = rem - v * P.g[j];
+        if (lane == 0) {
+            wp->a[j] = v;
+            wp->r[j + 1] = p;
+        }
+        __syncwarp();
+        int nw;
+        if (memo && j < P.lam_m)
+            nw = 0;
+        else if (memo)
+            nw = 1;  // at or below the memo level: inside a walked subtree
+        else
+            nw = 0;
+        const int newlam = (memo && !nw) ? P.lam_m : P.lam_w;
+        descend(P, wp, j + 1, newlam, lane);
+        st.lam = newlam;
+        st.inwalk = nw;
+        st.vcur = wp->r[newlam] / P.g[newlam];
+        st.base = 0;
+        return true;
+    }
+    return false;
+}
+
+template <int D>
+__device__ __forceinline__ void flush_rows(const EnumParams &P, const int32_t *src,
+                                           uint64_t out_row, uint32_t nrows, int lane,
+                                           uint64_t pol) {
+    int32_t *gdst = P.out + out_row * (uint64_t)D;
+    const uint32_t words = nrows * (uint32_t)D;
+    if (P.aligned) {
+        const uint32_t bytes = words * 4u;
+        const uint32_t bulk = bytes & ~15u;
+        fence_proxy_async_smem();
+        __syncwarp();
+        if (lane == 0 && bulk) {
+            bulk_store(gdst, src, bulk, pol);
+            bulk_commit();
+        }
+        const uint32_t rem_words = (bytes - bulk) >> 2;
+        if ((uint32_t)lane < rem_words) gdst[(bulk >> 2) + lane] = src[(bulk >> 2) + lane];
+    } else {
+        __syncwarp();
+        for (uint32_t w = lane; w < words; w += 32) gdst[w] = src[w];
+        __syncwarp();
+    }
+}
+
+template <int D>
+__global__ void __launch_bounds__(ENUM_THREADS, 2)
+    fz_enum_kernel(const __grid_constant__ EnumParams P) {
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    const int lane = threadIdx.x & 31;
+    const int wid = threadIdx.x >> 5;
+    const uint32_t B = (uint32_t)P.half_rows;
+    int32_t *ring = reinterpret_cast<int32_t *>(smem_raw) + (size_t)wid * 2 * B * D;
+    WarpPath *wp = reinterpret_cast<WarpPath *>(smem_raw + (size_t)ENUM_WARPS * 2 * B * D * 4) + wid;
+    const uint64_t pol = policy_evict_first();
+    const int g_last = P.g[D - 1];
+
+    for (;;) {
+        unsigned long long s = 0;
+        if (lane == 0) s = atomicAdd(P.slice_counter, 1ull);
+        s = __shfl_sync(FULL, s, 0);
+        if (s >= P.nslices) break;
+        const uint64_t row0 = s * P.slice_rows;  // relative to out
+        uint64_t left64 = P.nrows - row0;
+        uint32_t rows_left = (uint32_t)(left64 < P.slice_rows ? left64 : P.slice_rows);
+
+        RunState st;
+        bool ok;
+        uint64_t skip = unrank_to_leaf(P, wp, P.rank_begin + row0, lane, st, &ok);
+        if (!ok) {
+            if (lane == 0) atomicExch(P.status, (int)DEV_INTERNAL);
+            break;
+        }
+
+        // ring bookkeeping: rows go to half `half` at position hpos; `nfull`
+        // halves of this slice have been flushed already
+        uint32_t hpos = 0, half = 0, nfull = 0;
+
+        int pre[D];
+#pragma unroll
+        for (int c = 0; c < D; ++c) pre[c] = (c < st.lam) ? wp->a[c] : 0;
+
+        while (rows_left > 0) {
+            const int lam = st.lam;
+            const int rem = wp->r[lam];
+            const int glam = P.g[lam];
+            const bool memo_run = (P.lam_m >= 0) && !st.inwalk && lam == P.lam_m;
+            const long long vl = st.vcur - lane;
+            const bool valid = vl >= 0;
+            int p = 0;
+            uint64_t incl = 0;
+            int type = T_NONE;
+            if (valid) {
+                p = (int)((long long)rem - vl * glam);
+                if (p < 0 || p > P.n) {  // cannot happen for 0 <= vl <= rem / glam
+                    atomicExch(P.status, (int)DEV_INTERNAL);
+                    p = 0;
+                }
+                incl = __ldg(P.C + (long long)lam * P.cs + p);
+                if (memo_run && p < P.top)
+                    type = T_MEMO;
+                else if (lam == P.lam_w)
+                    type = T_WALK;
+                else
+                    type = T_INTERNAL;
+            }
+            uint64_t prev = __shfl_up_sync(FULL, incl, 1);
+            if (lane == 0) prev = st.base;
+            const uint64_t size = valid ? incl - prev : 0ull;
+            const unsigned im = __ballot_sync(FULL, type == T_INTERNAL && size > 0);
+            const int first_int = im ? __ffs(im) - 1 : 32;
+            const int nvalid = st.vcur + 1 < 32 ? (int)(st.vcur + 1) : 32;
+            const int consumed = first_int < nvalid ? first_int : nvalid;
+            const uint64_t last_incl = consumed > 0 ? shfl_u64(incl, consumed - 1) : st.base;
+            const uint64_t batch_rows = last_incl - st.base;
+            uint32_t E32 = CAP32, X32 = 0;
+            if (lane < consumed) {
+                const uint64_t e = incl - st.base;
+                E32 = e < (uint64_t)CAP32 ? (uint32_t)e : CAP32;
+                if (type == T_MEMO)
+                    X32 = (uint32_t)__ldg(P.O + p);
+                else if (type == T_WALK)
+                    X32 = (uint32_t)(p / g_last);
+            }
+            // rows [skip, q_end) of this batch
+            uint64_t q_end64 = skip + rows_left;
+            if (q_end64 > batch_rows) q_end64 = batch_rows;
+            const uint32_t q_begin = (uint32_t)skip;
+            const uint32_t q_end = (uint32_t)q_end64;
+            for (uint32_t q0 = q_begin; q0 < q_end;) {
+                uint32_t cnt = q_end - q0;
+                if (cnt > 32u) cnt = 32u;
+                if (cnt > B - hpos) cnt = B - hpos;  // rounds never cross a half boundary
+                if (hpos == 0 && nfull >= 2) {
+                    // this half was last stored two flushes ago; the most recent
+                    // flush (the other half) may still be reading
+                    if (lane == 0) asm volatile("cp.async.bulk.wait_group.read 1;" ::: "memory");
+                    __syncwarp();
+                }
+                const bool act = (uint32_t)lane < cnt;
+                const uint32_t q = act ? q0 + lane : q_end - 1;
+                int l = 0;
+#pragma unroll
+                for (int sft = 16; sft >= 1; sft >>= 1) {
+                    const uint32_t e = __shfl_sync(FULL, E32, l + sft - 1);
+                    if (e <= q) l += sft;
+                }
+                uint32_t eprev = __shfl_sync(FULL, E32, l > 0 ? l - 1 : 0);
+                if (l == 0) eprev = 0;
+                const uint32_t o = q - eprev;
+                const int pl = __shfl_sync(FULL, p, l);
+                const uint32_t xl = __shfl_sync(FULL, X32, l);
+                const int vrow = (int)(st.vcur - l);
+                bool mleaf = memo_run && pl < P.top;
+                if (mleaf && (uint64_t)xl + o >= P.memo_rows) {  // bounds guard
+                    atomicExch(P.status, (int)DEV_INTERNAL);
+                    mleaf = false;
+                }
+                if (act) {
+                    int32_t *dst = ring + (size_t)(half * B + hpos + lane) * D;
+                    const int32_t *mrow = mleaf ? P.memo + (size_t)(xl + o) * (size_t)P.K : nullptr;
+                    int vals[D];
+#pragma unroll
+                    for (int c = 0; c < D; ++c) {
+                        int x;
+                        if (c < lam)
+                            x = pre[c];
+                        else if (c == lam)
+                            x = vrow;
+                        else if (mleaf)
+                            x = __ldg(mrow + (c - lam - 1));
+                        else
+                            x = (int)xl;
+                        vals[c] = x;
+                    }
+                    if constexpr ((D & 1) == 0) {
+#pragma unroll
+                        for (int c = 0; c < D; c += 2)
+                            *reinterpret_cast<int2 *>(dst + c) = make_int2(vals[c], vals[c + 1]);
+                    } else {
+#pragma unroll
+                        for (int c = 0; c < D; ++c) dst[c] = vals[c];
+                    }
+                }
+                hpos += cnt;
+                q0 += cnt;
+                if (hpos == B) {
+                    flush_rows<D>(P, ring + (size_t)half * B * D, row0 + (uint64_t)nfull * B, B,
+                                  lane, pol);
+                    ++nfull;
+                    half ^= 1u;
+                    hpos = 0;
+                }
+            }
+            const uint32_t emitted = q_end > q_begin ? q_end - q_begin : 0u;
+            rows_left -= emitted;
+            if (rows_left == 0) break;
+            skip = 0;
+            if (first_int < nvalid) {
+                // the next child is a memo-level prefix beyond the memo: walk it
+                const int ve = (int)(st.vcur - first_int);
+                const int pe = rem - ve * glam;
+                if (lane == 0) {
+                    wp->a[lam] = ve;
+                    wp->r[lam + 1] = pe;
+                }
+                __syncwarp();
+                descend(P, wp, lam + 1, P.lam_w, lane);
+                st.lam = P.lam_w;
+                st.inwalk = 1;
+                st.vcur = wp->r[P.lam_w] / P.g[P.lam_w];
+                st.base = 0;
+            } else {
+                st.base = last_incl;
+                st.vcur -= consumed;
+                if (st.vcur < 0 && !advance(P, wp, lane, st)) {
+                    if (lane == 0) atomicExch(P.status, (int)DEV_INTERNAL);
+                    break;
+                }
+            }
+#pragma unroll
+            for (int c = 0; c < D; ++c) pre[c] = (c < st.lam) ? wp->a[c] : 0;
+        }
+        if (hpos > 0)
+            flush_rows<D>(P, ring + (size_t)half * B * D, row0 + (uint64_t)nfull * B, hpos,
+                          lane, pol);
+        if (lane == 0) bulk_wait_read_all();
+        __syncwarp();
+    }
+    if (lane == 0) bulk_wait_all();
+    __syncwarp();
+}
+
+// Tuples of given ranks (one warp per rank).
+template <int D>
+__global__ void __launch_bounds__(ENUM_THREADS)
+    fz_unrank_kernel(const __grid_constant__ EnumParams P,
+                                                                 const uint64_t *ranks,
+                                                                 uint64_t m) {
+    __shared__ WarpPath paths[ENUM_WARPS];
+    const int lane = threadIdx.x & 31;
+    const int wid = threadIdx.x >> 5;
+    WarpPath *wp = &paths[wid];
+    const uint64_t nw = (uint64_t)gridDim.x * ENUM_WARPS;
+    for (uint64_t i = (uint64_t)blockIdx.x * ENUM_WARPS + wid; i < m; i += nw) {
+        const uint64_t R = ranks[i];
+        RunState st;
+        bool ok;
+        const uint64_t off = unrank_to_leaf(P, wp, R, lane, st, &ok);
+        if (!ok) {
+            if (lane < D) P.out[i * D + lane] = -1;
+            if (lane == 0) atomicExch(P.status, (int)DEV_INTERNAL);
+            continue;
+        }
+        const int lam = st.lam;
+        const int v = (int)st.vcur;
+        const int p = wp->r[lam] - v * P.g[lam];
+        bool mleaf = (P.lam_m >= 0) && !st.inwalk && lam == P.lam_m && p < P.top;
+        if (mleaf && __ldg(P.O + p) + off >= P.memo_rows) {  // bounds guard
+            if (lane == 0) atomicExch(P.status, (int)DEV_INTERNAL);
+            mleaf = false;
+        }
+        if (lane < D) {
+            int x;
+            if (lane < lam)
+                x = wp->a[lane];
+            else if (lane == lam)
+                x = v;
+            else if (mleaf)
+                x = __ldg(P.memo + (size_t)(__ldg(P.O + p) + off) * P.K + (lane - lam - 1));
+            else
+                x = p / P.g[D - 1];
+            P.out[i * D + lane] = x;
+        }
+        __syncwarp();
+    }
+}
+
+// Whole output taken from one place: d == 1 (one candidate) or k == d (the
+// output is Memo[n] itself).  mode 1: copy memo rows; mode 2: single row.
+__global__ void fz_direct_kernel(const EnumParams P, int mode) {
+    const uint64_t tid = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const uint64_t nt = (uint64_t)gridDim.x * blockDim.x;
+    if (mode == 1) {
+        const uint64_t src0 = (__ldg(P.O + P.n) + P.rank_begin) * (uint64_t)P.d;
+        const uint64_t words = P.nrows * (uint64_t)P.d;
+        if (src0 + words > P.memo_rows * (uint64_t)P.d) {  // bounds guard
+            if (tid == 0) atomicExch(P.status, (int)DEV_INTERNAL);
+            return;
+        }
+        for (uint64_t w = tid; w < words; w += nt) P.out[w] = __ldg(P.memo + src0 + w);
+    } else if (tid == 0 && P.nrows > 0) {
+        P.out[0] = P.n / P.g[0];
+    }
+}
+
+// ---------------------------------------------------------------------------
+// host launchers
+// ---------------------------------------------------------------------------
+static int half_rows_for(int d) {
+    int b = RING_BYTES_PER_WARP / (8 * d);
+    b = (b / 32) * 32;
+    return b < 32 ? 32 : b;
+}
+
+static size_t enum_smem_bytes(int d) {
+    return (size_t)ENUM_WARPS * 2 * half_rows_for(d) * d * 4 +
+           (size_t)ENUM_WARPS * sizeof(WarpPath);
+}
+
+template <int D>
+static int launch_enum_d(const EnumParams &P, cudaStream_t s, int sms) {
+    const size_t smem = enum_smem_bytes(D);
+    static bool attr_set[64] = {};
+    int dev = 0;
+    cudaGetDevice(&dev);
+    if (dev < 64 && !attr_set[dev]) {
+        FZ_CUDA_TRY(cudaFuncSetAttribute(fz_enum_kernel<D>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)smem));
+        attr_set[dev] = true;
+    }
+    int per_sm = 0;
+    FZ_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fz_enum_kernel<D>,
+                                                              ENUM_THREADS, smem));
+    if (per_sm < 1) per_sm = 1;
+    uint64_t want = (P.nslices + ENUM_WARPS - 1) / ENUM_WARPS;
+    uint64_t grid = (uint64_t)per_sm * sms;
+    if (want < grid) grid = want;
+    if (grid < 1) grid = 1;
+    FZ_CUDA_TRY(cudaMemsetAsync(P.slice_counter, 0, sizeof(unsigned long long), s));
+    fz_enum_kernel<D><<<(unsigned)grid, ENUM_THREADS, smem, s>>>(P);
+    note_launch();
+    FZ_CUDA_TRY(cudaGetLastError());
+    return FZ_OK;
+}
+
+template <int D>
+static int launch_unrank_d(const EnumParams &P, const uint64_t *ranks, uint64_t m,
+                           cudaStream_t s) {
+    uint64_t blocks = (m + ENUM_WARPS - 1) / ENUM_WARPS;
+    if (blocks > 4096) blocks = 4096;
+    if (blocks < 1) blocks = 1;
+    fz_unrank_kernel<D><<<(unsigned)blocks, ENUM_THREADS, 0, s>>>(P, ranks, m);
+    note_launch();
+    FZ_CUDA_TRY(cudaGetLastError());
+    return FZ_OK;
+}
+
+static EnumParams make_params(const EnumLaunch &L) {
+    EnumParams P{};
+    P.C = L.C;
+    P.cs = L.cs;
+    P.O = L.O;
+    P.memo = L.memo;
+    P.memo_rows = L.memo_rows;
+    P.status = L.status;
+    P.slice_counter = L.slice_counter;
+    P.n = L.n;
+    P.d = L.d;
+    P.K = L.K;
+    P.top = L.top;
+    for (int i = 0; i < L.d; ++i) P.g[i] = L.g[i];
+    const bool memo = L.K >= 1 && L.K <= L.d - 1 && L.top > 0;
+    P.lam_m = memo ? L.d - L.K - 1 : -1;
+    P.lam_w = L.d - 2;
+    if (!memo) {
+        P.K = 0;
+        P.top = 0;
+    }
+    return P;
+}
+
+#define FZ_DISPATCH_D(d, FN, ...)                 \
+    switch (d) {                                  \
+        case 2: return FN<2>(__VA_ARGS__);        \
+        case 3: return FN<3>(__VA_ARGS__);        \
+        case 4: return FN<4>(__VA_ARGS__);        \
+        case 5: return FN<5>(__VA_ARGS__);        \
+        case 6: return FN<6>(__VA_ARGS__);        \
+        case 7: return FN<7>(__VA_ARGS__);        \
+        case 8: return FN<8>(__VA_ARGS__);        \
+        case 9: return FN<9>(__VA_ARGS__);        \
+        case 10: return FN<10>(__VA_ARGS__);      \
+        case 11: return FN<11>(__VA_ARGS__);      \
+        case 12: return FN<12>(__VA_ARGS__);      \
+        case 13: return FN<13>(__VA_ARGS__);      \
+        case 14: return FN<14>(__VA_ARGS__);      \
+        case 15: return FN<15>(__VA_ARGS__);      \
+        case 16: return FN<16>(__VA_ARGS__);      \
+        default: return set_error(FZ_EINVAL, "d out of range"); \
+    }
+
+// Enumerate ranks [rank_begin, rank_begin + nrows) into out.  Asynchronous.
+int launch_enumerate(const EnumLaunch &L, uint64_t rank_begin, uint64_t nrows, int32_t *out,
+                     uint64_t slice_rows, cudaStream_t s) {
+    if (nrows == 0) return FZ_OK;
+    EnumParams P = make_params(L);
+    P.out = out;
+    P.rank_begin = rank_begin;
+    P.nrows = nrows;
+    P.aligned = ((uintptr_t)out & 15u) == 0;
+    if (L.d == 1 || (L.K == L.d && L.top > L.n)) {
+        const int mode = (L.d == 1 && !(L.K == 1 && L.top > L.n)) ? 2 : 1;
+        uint64_t words = nrows * (uint64_t)L.d;
+        uint64_t blocks = (words + 255) / 256;
+        if (blocks > 4096) blocks = 4096;
+        if (blocks < 1) blocks = 1;
+        fz_direct_kernel<<<(unsigned)blocks, 256, 0, s>>>(P, mode);
+        note_launch();
+        FZ_CUDA_TRY(cudaGetLastError());
+        return FZ_OK;
+    }
+    DeviceProps dp;
+    int rc = device_props(&dp);
+    if (rc != FZ_OK) return rc;
+    if (slice_rows < 4) slice_rows = 4;
+    slice_rows = (slice_rows + 3) & ~3ull;
+    P.slice_rows = slice_rows;
+    P.nslices = (nrows + slice_rows - 1) / slice_rows;
+    P.half_rows = half_rows_for(L.d);
+    FZ_DISPATCH_D(L.d, launch_enum_d, P, s, dp.sms);
+}
+
+int launch_unrank(const EnumLaunch &L, const uint64_t *ranks, uint64_t m, int32_t *out,
+                  cudaStream_t s) {
+    if (m == 0) return FZ_OK;
+    EnumParams P = make_params(L);
+    P.out = out;
+    if (L.d == 1 || (L.K == L.d && L.top > L.n))
+        return set_error(FZ_EINVAL, "unrank: d == 1 or k == d has a single block; use enumerate");
+    FZ_DISPATCH_D(L.d, launch_unrank_d, P, ranks, m, s);
+}
+
+uint64_t default_slice_rows(uint64_t nrows, int sms) {
+    // about eight work items per resident warp, between 1024 and 65536 rows
+    uint64_t warps = (uint64_t)sms * 2 * ENUM_WARPS;
+    uint64_t s = nrows / (warps * 8 + 1);
+    if (s < 1024) s = 1024;
+    if (s > 65536) s = 65536;
+    return (s + 3) & ~3ull;
+}
+
+}  // namespace fz

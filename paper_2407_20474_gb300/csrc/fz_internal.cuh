@@ -1,0 +1,255 @@
+// fz_internal.cuh -- device helpers and host utilities shared by the fz
+// library's translation units (count DP, memo build, enumeration, C ABI).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+
+#include "../../include/fz.h"
+
+namespace fz {
+
+constexpr unsigned FULL = 0xffffffffu;
+constexpr uint64_t SAT = ~0ull;
+
+// ---------------------------------------------------------------------------
+// Error reporting (host).  The message is thread-local; see fz_api.cu.
+// ---------------------------------------------------------------------------
+int set_error(int status, const std::string &msg);
+// Count one kernel launch (fz_kernel_launches).
+void note_launch();
+int cuda_error(cudaError_t e, const char *what);
+#define FZ_CUDA_TRY(expr)                                   \
+    do {                                                    \
+        cudaError_t fz_e_ = (expr);                         \
+        if (fz_e_ != cudaSuccess) return ::fz::cuda_error(fz_e_, #expr); \
+    } while (0)
+
+// Device-side status codes written into a per-handle status word.
+enum DevStatus : int {
+    DEV_OK = 0,
+    DEV_TIMEOUT = 1,    // a bounded wait gave up
+    DEV_INTERNAL = 2,   // a consistency check failed
+};
+
+// ---------------------------------------------------------------------------
+// Saturating 64-bit arithmetic and warp scans.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ uint64_t sat_add(uint64_t a, uint64_t b) {
+    uint64_t s = a + b;
+    return s < a ? SAT : s;
+}
+
+__device__ __forceinline__ uint64_t shfl_u64(uint64_t v, int src) {
+    return __shfl_sync(FULL, v, src);
+}
+
+// Inclusive warp scan with saturation (min(sum, 2^64-1) is associative).
+__device__ __forceinline__ uint64_t warp_incl_scan_sat(uint64_t v, int lane) {
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        uint64_t t = __shfl_up_sync(FULL, v, o);
+        if (lane >= o) v = sat_add(v, t);
+    }
+    return v;
+}
+
+__device__ __forceinline__ uint64_t warp_incl_scan(uint64_t v, int lane) {
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        uint64_t t = __shfl_up_sync(FULL, v, o);
+        if (lane >= o) v += t;
+    }
+    return v;
+}
+
+// ---------------------------------------------------------------------------
+// Memory-model helpers.
+// ---------------------------------------------------------------------------
+// L2-only load (bypasses L1, which is not coherent with writes made by other
+// SMs during the same kernel).
+__device__ __forceinline__ int32_t ld_cg_s32(const int32_t *p) {
+    int32_t v;
+    asm volatile("ld.global.cg.s32 %0, [%1];" : "=r"(v) : "l"(p));
+    return v;
+}
+
+__device__ __forceinline__ uint64_t ld_cg_u64(const uint64_t *p) {
+    uint64_t v;
+    asm volatile("ld.global.cg.u64 %0, [%1];" : "=l"(v) : "l"(p));
+    return v;
+}
+
+__device__ __forceinline__ unsigned ld_acquire_u32(const unsigned *p) {
+    unsigned v;
+    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+
+__device__ __forceinline__ void st_release_u32(unsigned *p, unsigned v) {
+    asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+
+__device__ __forceinline__ uint64_t globaltimer_ns() {
+    uint64_t t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+// ---------------------------------------------------------------------------
+// Bulk (TMA) stores from shared to global memory.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ uint32_t smem_addr(const void *p) {
+    return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+// Makes this thread's generic-proxy writes to shared memory visible to the
+// async proxy (the bulk copy engine).
+__device__ __forceinline__ void fence_proxy_async_smem() {
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+
+__device__ __forceinline__ uint64_t policy_evict_first() {
+    uint64_t pol;
+    asm volatile("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(pol));
+    return pol;
+}
+
+// dst and src 16-byte aligned, bytes a positive multiple of 16.
+__device__ __forceinline__ void bulk_store(void *gdst, const void *ssrc, uint32_t bytes,
+                                           uint64_t pol) {
+    asm volatile(
+        "cp.async.bulk.global.shared::cta.bulk_group.L2::cache_hint [%0], [%1], %2, %3;" ::"l"(
+            gdst),
+        "r"(smem_addr(ssrc)), "r"(bytes), "l"(pol)
+        : "memory");
+}
+
+__device__ __forceinline__ void bulk_commit() {
+    asm volatile("cp.async.bulk.commit_group;" ::: "memory");
+}
+
+// Wait until every committed bulk group of this thread has finished reading
+// its shared-memory source.
+__device__ __forceinline__ void bulk_wait_read_all() {
+    asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory");
+}
+
+// Wait until every committed bulk group of this thread has completed.
+__device__ __forceinline__ void bulk_wait_all() {
+    asm volatile("cp.async.bulk.wait_group 0;" ::: "memory");
+}
+
+// ---------------------------------------------------------------------------
+// Bounded grid barrier for cooperative launches.  Every block calls it the
+// same number of times.  The wait polls a generation word with an iteration
+// and wall-clock limit; when the limit is hit the block records DEV_TIMEOUT
+// in *status and the barrier returns false (the caller then returns).
+// ---------------------------------------------------------------------------
+struct GridBarrier {
+    unsigned *count;  // arrivals in the current generation (left at 0)
+    unsigned *gen;    // generation number
+};
+
+constexpr uint64_t BARRIER_TIMEOUT_NS = 2000000000ull;  // 2 s
+constexpr uint32_t BARRIER_MAX_POLLS = 1u << 26;
+
+__device__ __forceinline__ bool grid_barrier(GridBarrier b, int *status) {
+    __shared__ int ok_flag;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        int ok = 1;
+        unsigned my_gen = ld_acquire_u32(b.gen);
+        __threadfence();
+        unsigned arrived = atomicAdd(b.count, 1u) + 1u;
+        if (arrived == gridDim.x * gridDim.y * gridDim.z) {
+            atomicExch(b.count, 0u);
+            __threadfence();
+            st_release_u32(b.gen, my_gen + 1u);
+        } else {
+            uint64_t t0 = globaltimer_ns();
+            uint32_t polls = 0;
+            while (ld_acquire_u32(b.gen) == my_gen) {
+                if (++polls >= BARRIER_MAX_POLLS ||
+                    ((polls & 255u) == 0 && globaltimer_ns() - t0 > BARRIER_TIMEOUT_NS)) {
+                    atomicExch(status, (int)DEV_TIMEOUT);
+                    ok = 0;
+                    break;
+                }
+                __nanosleep(32);
+            }
+        }
+        // a timeout anywhere stops every block at its next barrier
+        if (ok && *((volatile int *)status) == (int)DEV_TIMEOUT) ok = 0;
+        ok_flag = ok;
+    }
+    __syncthreads();
+    return ok_flag != 0;
+}
+
+// ---------------------------------------------------------------------------
+// Host helpers.
+// ---------------------------------------------------------------------------
+struct DeviceProps {
+    int device = -1;
+    int sms = 0;
+    int max_smem_optin = 0;
+};
+int device_props(DeviceProps *out);
+
+int validate_gens(const int32_t *g, int d);
+
+// Count DP (fz_count.cu).  Writes C[j][r], j = 0..d, r = 0..n, row stride
+// n + 1, into table (device), using `tmp` (count_table_tmp_words words) as
+// scratch.  Asynchronous; saturates at 2^64 - 1.
+int64_t count_table_tmp_words(const int32_t *g, int d, int32_t n);
+int launch_count_table_tmp(const int32_t *g, int d, int32_t n, uint64_t *table, uint64_t *tmp,
+                           cudaStream_t s);
+// Only row 0 (|Z(r, g)|, r = 0..n) with two rolling rows a, b (n + 1 words
+// each); returns which of them holds the result.
+int launch_count_rolling(const int32_t *g, int d, int32_t n, uint64_t *a, uint64_t *b,
+                         uint64_t *tmp, uint64_t **result, cudaStream_t s);
+
+// out[0] = 0, out[r + 1] = in[0] + ... + in[r] for r < len (saturating).
+int64_t exclusive_scan_tmp_words(int64_t len);
+int launch_exclusive_scan_tmp(const uint64_t *in, uint64_t *out, int64_t len, uint64_t *tmp,
+                              cudaStream_t s);
+
+// Memo build (fz_memo.cu).
+struct MemoBuffers {
+    const uint64_t *Ct = nullptr;  // count table rows 0..k of the tail, stride cs
+    int64_t cs = 0;
+    const uint64_t *O = nullptr;   // top + 1 offsets (already scanned)
+    uint64_t *map = nullptr;       // rows entries (gather map)
+    int32_t *rows = nullptr;       // rows * k
+    int *status = nullptr;         // device status word
+    unsigned *bar = nullptr;       // 2 words: barrier count, generation
+};
+// Gather map + batched copy-and-increment fill.  Asynchronous.
+int launch_memo_build(const int32_t *tail, int k, int32_t top, uint64_t rows,
+                      const MemoBuffers &mb, cudaStream_t s);
+
+// Enumeration (fz_enum.cu).
+struct EnumLaunch {
+    const uint64_t *C = nullptr;   // count table rows 0..d, stride cs = n + 1
+    int64_t cs = 0;
+    const uint64_t *O = nullptr;   // memo offsets
+    const int32_t *memo = nullptr; // memo rows
+    uint64_t memo_rows = 0;
+    int *status = nullptr;
+    unsigned long long *slice_counter = nullptr;
+    int n = 0, d = 0, K = 0, top = 0;
+    const int32_t *g = nullptr;    // host generators
+};
+int launch_enumerate(const EnumLaunch &L, uint64_t rank_begin, uint64_t nrows, int32_t *out,
+                     uint64_t slice_rows, cudaStream_t s);
+int launch_unrank(const EnumLaunch &L, const uint64_t *ranks, uint64_t m, int32_t *out,
+                  cudaStream_t s);
+uint64_t default_slice_rows(uint64_t nrows, int sms);
+
+// Largest memo the library builds (rows); keeps memo row indices in 32 bits.
+constexpr uint64_t MEMO_MAX_ROWS = 1ull << 30;
+
+}  // namespace fz
