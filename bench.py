@@ -55,14 +55,17 @@ def parse():
     ap.add_argument("--slice-rows", type=int, default=0)
     ap.add_argument("--cpu-seconds", type=float, default=15.0,
                     help="target duration of the bounded oracle sample")
+    ap.add_argument("--target", type=int, default=0,
+                    help="|Z(n)| target of the workload (default 5e8; smaller values give "
+                         "the small profiling case)")
     return ap.parse_args()
 
 
 # ---------------------------------------------------------------- workload
-def resolve_instance(count_upto, seed):
+def resolve_instance(count_upto, seed, target=0):
     from paper_2407_20474_gb300 import workloads
     g = workloads.config2_generators(seed)
-    n = workloads.find_n(count_upto, g, workloads.CONFIG2_TARGET, 4096)
+    n = workloads.find_n(count_upto, g, target or workloads.CONFIG2_TARGET, 4096)
     return g, n
 
 
@@ -221,7 +224,7 @@ def run_ours(args):
     import paper_2407_20474_gb300 as fz
     torch.cuda.set_device(local)
     dev = torch.cuda.current_device()
-    g, n = resolve_instance(lambda gg, nm: fz.fz_count_upto(gg, nm), args.seed)
+    g, n = resolve_instance(lambda gg, nm: fz.fz_count_upto(gg, nm), args.seed, args.target)
     d = len(g)
     plan = fz.Plan(g, n, k=args.k, slice_rows=args.slice_rows)
     count = plan.count
@@ -342,7 +345,7 @@ def run_reference(args):
     import oracle
     from oracle import build as ob
     ob.build_oracle()
-    g, n = resolve_instance(oracle.count_upto, args.seed)
+    g, n = resolve_instance(oracle.count_upto, args.seed, args.target)
     T = oracle.count_table(g, n)
     count = int(T[0][n])
     K = max(args.steps, 1)

@@ -478,6 +478,7 @@ static int build_memo_to(const int32_t *tail, int k, int32_t top, uint64_t *O, i
     mb.Ct = C;
     mb.cs = cs;
     mb.O = O;
+    mb.rows = *R;
     mb.map = work.as<uint64_t>();
     mb.status = reinterpret_cast<int *>(work.as<char>() + map_bytes);
     mb.bar = reinterpret_cast<unsigned *>(work.as<char>() + map_bytes + 256);

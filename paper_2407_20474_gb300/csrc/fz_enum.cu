@@ -591,6 +591,9 @@ static EnumParams make_params(const EnumLaunch &L) {
 int launch_enumerate(const EnumLaunch &L, uint64_t rank_begin, uint64_t nrows, int32_t *out,
                      uint64_t slice_rows, cudaStream_t s) {
     if (nrows == 0) return FZ_OK;
+    if (!out || !L.C || !L.status || !L.slice_counter || (L.K >= 1 && L.top > 0 && !L.O) ||
+        (L.K >= 1 && L.top > 0 && L.memo_rows > 0 && !L.memo))
+        return set_error(FZ_EINTERNAL, "enumerate: missing device buffer");
     EnumParams P = make_params(L);
     P.out = out;
     P.rank_begin = rank_begin;
@@ -621,6 +624,8 @@ int launch_enumerate(const EnumLaunch &L, uint64_t rank_begin, uint64_t nrows, i
 int launch_unrank(const EnumLaunch &L, const uint64_t *ranks, uint64_t m, int32_t *out,
                   cudaStream_t s) {
     if (m == 0) return FZ_OK;
+    if (!out || !ranks || !L.C || !L.status || (L.K >= 1 && L.top > 0 && !L.O))
+        return set_error(FZ_EINTERNAL, "unrank: missing device buffer");
     EnumParams P = make_params(L);
     P.out = out;
     if (L.d == 1 || (L.K == L.d && L.top > L.n))

@@ -130,6 +130,8 @@ int coop_grid(const void *kernel, int threads) {
 int launch_memo_build(const int32_t *tail, int k, int32_t top, uint64_t rows,
                       const MemoBuffers &mb, cudaStream_t s) {
     if (top <= 0 || rows == 0) return FZ_OK;
+    if (!mb.Ct || !mb.O || !mb.map || !mb.rows || !mb.status || !mb.bar)
+        return set_error(FZ_EINTERNAL, "memo build: missing device buffer");
     MapParams mp{};
     mp.Ct = mb.Ct;
     mp.cs = mb.cs;

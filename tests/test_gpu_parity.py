@@ -149,9 +149,7 @@ def test_small_slices_ring_boundaries(fz, d):
     """Tiny slices and many ring halves: every flush path, every tuple width."""
     rng = np.random.Generator(np.random.PCG64(100 + d))
     g = tuple(sorted(int(x) for x in rng.integers(2, 9, size=d)))
-    n = 4
-    while oracle.count(g, n) < 20000:
-        n += 3
+    n = workloads.find_n(oracle.count_upto, g, 20000)
     ref = oracle.enumerate_desc(g, n)
     for k in (0, min(2, d - 1), min(3, d - 1)):
         for slice_rows in (4, 36, 1000, 0):
@@ -259,7 +257,7 @@ def test_enumerate_host(fz):
 def _memo_on_gpu(fz, tail, top):
     rows = fz.fz_memo_rows(tail, top)
     off = torch.zeros(top + 1, dtype=torch.int64, device="cuda")
-    buf = torch.full((rows + 4) * len(tail), CANARY, dtype=torch.int32, device="cuda")
+    buf = torch.full(((rows + 4) * len(tail),), CANARY, dtype=torch.int32, device="cuda")
     got_rows = fz.fz_build_memo_into(tail, top, off, buf, rows)
     torch.cuda.synchronize()
     assert got_rows == rows
