@@ -106,6 +106,24 @@ int fz_count(const int32_t *g, int d, int32_t n, uint64_t *count, void *stream);
 int fz_count_upto(const int32_t *g, int d, int32_t n_max, uint64_t *counts,
                   void *stream);
 
+/* Allocation-free variant of fz_count_upto, for callers that cannot call
+ * cudaMalloc (while a stream is being captured, in loops that must not wait
+ * on the allocator, or when another allocator owns all device memory).  The
+ * paper has no counterpart; it only concerns how this library gets scratch.
+ * counts_dev (caller device memory, n_max + 1 uint64) receives |Z(r, g)| for
+ * r = 0..n_max, saturated at UINT64_MAX.  `g` is host memory.  All scratch
+ * is one fixed device array inside the library (about 4.4 MB, held by every
+ * GPU that loads the library until the process exits), so n_max is limited
+ * to FZ_NOALLOC_MAX_N; larger n_max gives FZ_EINVAL.  The first call made
+ * with a given device current looks up that array's device address
+ * (cudaGetSymbolAddress); make that first call before any stream capture.
+ * Every call shares the array: calls that overlap on the GPU (other streams
+ * or host threads) race on it.  Asynchronous; calls no allocating routine.
+ * Errors: FZ_EINVAL, FZ_ECUDA. */
+#define FZ_NOALLOC_MAX_N 262143
+int fz_count_upto_noalloc(const int32_t *g, int d, int32_t n_max,
+                          uint64_t *counts_dev, void *stream);
+
 /* The full table C (layout [d+1][n+1], row-major, uint64) into caller device
  * memory `table_dev`.  Asynchronous; saturating at UINT64_MAX.
  * Errors: FZ_EINVAL, FZ_ECUDA. */

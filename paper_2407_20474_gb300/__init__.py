@@ -37,7 +37,7 @@ FZ_EINTERNAL = -9
 # Every symbol include/fz.h declares (checked by the CPU tests).
 EXPORTS = (
     "fz_version", "fz_last_error_string", "fz_status_string", "fz_kernel_launches",
-    "fz_count", "fz_count_upto", "fz_count_table",
+    "fz_count", "fz_count_upto", "fz_count_upto_noalloc", "fz_count_table",
     "fz_memo_rows", "fz_build_memo_into", "fz_build_memo", "fz_memo_info",
     "fz_memo_release",
     "fz_plan_create", "fz_plan_info", "fz_plan_rebuild", "fz_plan_enumerate",
@@ -82,6 +82,7 @@ _SIGS = {
     "fz_count": (ctypes.c_int, [_I32P, ctypes.c_int, ctypes.c_int32, _U64P, _P]),
     "fz_count_upto": (ctypes.c_int, [_I32P, ctypes.c_int, ctypes.c_int32, _U64P, _P]),
     "fz_count_table": (ctypes.c_int, [_I32P, ctypes.c_int, ctypes.c_int32, _P, _P]),
+    "fz_count_upto_noalloc": (ctypes.c_int, [_I32P, ctypes.c_int, ctypes.c_int32, _P, _P]),
     "fz_memo_rows": (ctypes.c_int, [_I32P, ctypes.c_int, ctypes.c_int32, _U64P, _P]),
     "fz_build_memo_into": (ctypes.c_int, [_I32P, ctypes.c_int, ctypes.c_int32, _P, _P,
                                           ctypes.c_uint64, _U64P, _P]),
@@ -194,6 +195,18 @@ def fz_count_upto(g: Sequence[int], n_max: int, stream=None) -> np.ndarray:
     _check(lib().fz_count_upto(ga, d, int(n_max),
                                out.ctypes.data_as(_U64P), _stream(stream)))
     return out
+
+
+FZ_NOALLOC_MAX_N = 262143
+
+
+def fz_count_upto_noalloc(g: Sequence[int], n_max: int, counts, stream=None) -> None:
+    """|Z(r, g)|, r = 0..n_max, into device uint64 ``counts`` without any
+    device allocation (for callers that cannot call cudaMalloc).  Scratch is
+    a fixed array inside the library shared by all calls, so n_max is at most
+    FZ_NOALLOC_MAX_N and overlapping calls race.  Asynchronous."""
+    ga, d = _gens(g)
+    _check(lib().fz_count_upto_noalloc(ga, d, int(n_max), _ptr(counts), _stream(stream)))
 
 
 def fz_count_table(g: Sequence[int], n: int, table, stream=None) -> None:
