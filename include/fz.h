@@ -223,6 +223,128 @@ int fz_plan_sync(fz_plan_t plan, void *stream);
 int fz_plan_destroy(fz_plan_t plan);
 
 /* ------------------------------------------------------------------------
+ * Batches: many instances Z(n_i, g_i) of possibly different d_i in one set
+ * of launches -- batched counting tables, one memo per distinct tail shared
+ * by the instances that have it (each built by the elementwise dynamic pass,
+ * Sections 2.2-2.4, cut to a bounded number of element batches; larger
+ * remainders take the ordinary next-candidate step, Section 3.1), and one
+ * persistent enumeration launch over (instance, slice) work items.
+ * Output: instance i's rows (d_i int32 each, descending lexicographic order)
+ * start at word word_offsets[i] of the output buffer (multiples of 4 words,
+ * so 16-byte aligned when the buffer is); word_offsets[count] is the total.
+ * ---------------------------------------------------------------------- */
+typedef struct fz_instance {
+    const int32_t *g;  /* host generators, d of them */
+    int32_t d;
+    int32_t n;
+} fz_instance_t;
+
+typedef struct fz_batch_s *fz_batch_t;
+typedef struct fz_batch_info {
+    int32_t count;         /* instances */
+    int32_t memos;         /* distinct memos (shared tails counted once) */
+    uint64_t total_rows;   /* sum of |Z(n_i, g_i)| */
+    uint64_t total_words;  /* output words needed (with alignment padding) */
+    uint64_t device_bytes; /* device memory held by the batch */
+    uint64_t work_items;   /* (instance, slice) items of one enumeration */
+} fz_batch_info_t;
+
+/* Validate, count every instance (device), choose each memo depth (opts->k
+ * applies to all instances when not FZ_AUTO), build the memos.  Synchronises.
+ * Errors: FZ_EINVAL, FZ_EOVERFLOW, FZ_ENOMEM, FZ_EINTERNAL, FZ_ECUDA. */
+int fz_batch_create(const fz_instance_t *inst, int count, const fz_opts_t *opt,
+                    fz_batch_t *batch, void *stream);
+int fz_batch_info(fz_batch_t batch, fz_batch_info_t *info);
+/* Host arrays (any may be NULL): rows[count], word_offsets[count + 1],
+ * k[count], top[count]. */
+int fz_batch_layout(fz_batch_t batch, uint64_t *rows, uint64_t *word_offsets,
+                    int32_t *k, int32_t *top);
+/* Recompute every table and memo in place.  Asynchronous (capturable). */
+int fz_batch_rebuild(fz_batch_t batch, void *stream);
+/* All instances' rows into out_dev (capacity in int32 words).  Asynchronous,
+ * one persistent kernel.  Errors: FZ_EINVAL, FZ_ENOSPC, FZ_ECUDA. */
+int fz_batch_enumerate(fz_batch_t batch, int32_t *out_dev,
+                       uint64_t out_capacity_words, void *stream);
+/* Synchronise and report device-side errors (FZ_ETIMEOUT, FZ_EINTERNAL). */
+int fz_batch_sync(fz_batch_t batch, void *stream);
+int fz_batch_destroy(fz_batch_t batch);
+
+/* One-shot: create + enumerate + sync + destroy.  word_offsets (host,
+ * count + 1, may be NULL) and *words_needed receive the layout.  Errors: as
+ * above; FZ_ENOSPC when out_capacity_words is too small (nothing written). */
+int fz_enumerate_batch(const fz_instance_t *inst, int count, const fz_opts_t *opt,
+                       uint64_t *word_offsets, int32_t *out_dev,
+                       uint64_t out_capacity_words, uint64_t *words_needed,
+                       void *stream);
+
+/* ------------------------------------------------------------------------
+ * Serving: a request loop over generator sets kept resident on the device.
+ *
+ * fz_serve_register builds a set's plan once for every n <= n_max (count and
+ * runs tables and memo depend on the generators only) and mirrors its count
+ * row on the host, so fz_serve_submit knows the exact output bytes of a
+ * query at once.  A background thread admits queued requests in arrival
+ * order as soon as a slot (max_in_flight) and the exact bytes are free in the
+ * output budget, and launches each on the next of `streams` CUDA streams:
+ * requests that arrive while others run are admitted as slots and memory
+ * free up, and their work overlaps on the GPU (continuous batching).  A
+ * result stays valid until fz_serve_release.  Times are seconds on the host
+ * steady clock; t_done is stamped when the request's stream reaches it.
+ * The paper serves no requests; this is the deployment layer around the
+ * enumeration of Section 3.1.
+ * ---------------------------------------------------------------------- */
+typedef struct fz_serve_cfg {
+    uint64_t memory_bytes;  /* device bytes for request outputs; 0 = a quarter
+                               of the free memory at creation */
+    int32_t max_in_flight;  /* requests on the device at once (slots) */
+    int32_t streams;        /* CUDA streams the server launches on */
+    int32_t max_queue;      /* queued requests before FZ_EAGAIN */
+    int32_t flags;          /* reserved, 0 */
+} fz_serve_cfg_t;
+
+typedef struct fz_server_s *fz_server_t;
+
+#define FZ_SERVE_DONE 0
+#define FZ_SERVE_QUEUED 1
+#define FZ_SERVE_RUNNING 2
+
+typedef struct fz_result {
+    int32_t status;          /* FZ_SERVE_DONE / QUEUED / RUNNING, or a negative fz_status */
+    int32_t d;
+    uint64_t count;          /* rows */
+    const int32_t *rows_dev; /* count * d int32 (when done), owned by the server */
+    double t_submit, t_admit, t_done;
+} fz_result_t;
+
+typedef struct fz_serve_stats {
+    uint64_t queued, admitted, completed;
+    uint64_t bytes_in_use, bytes_budget;
+    int32_t sets;
+    int32_t last_error;
+} fz_serve_stats_t;
+
+/* Start a server on the current device.  Errors: FZ_EINVAL, FZ_ENOMEM, FZ_ECUDA. */
+int fz_serve_create(const fz_serve_cfg_t *cfg, fz_server_t *srv);
+/* Make generator set g (host, d entries) resident for n <= n_max.
+ * Synchronous.  *set_id receives its index. */
+int fz_serve_register(fz_server_t srv, const int32_t *g, int d, int32_t n_max,
+                      int32_t *set_id);
+/* Queue Z(n, set).  Errors: FZ_ENOTFOUND (set), FZ_EINVAL (n > n_max),
+ * FZ_EAGAIN (queue full), FZ_ENOMEM (larger than the whole budget). */
+int fz_serve_submit(fz_server_t srv, int32_t set_id, int32_t n, uint64_t *ticket);
+/* Current state of a request (non-blocking). */
+int fz_serve_poll(fz_server_t srv, uint64_t ticket, fz_result_t *result);
+/* Block until the request is done (timeout_ms < 0: no limit; FZ_EAGAIN on
+ * timeout). */
+int fz_serve_wait(fz_server_t srv, uint64_t ticket, int32_t timeout_ms,
+                  fz_result_t *result);
+/* Free a finished request's output (FZ_EAGAIN while queued or running). */
+int fz_serve_release(fz_server_t srv, uint64_t ticket);
+int fz_serve_stats(fz_server_t srv, fz_serve_stats_t *stats);
+/* Stop the loop, wait for running requests, free everything. */
+int fz_serve_destroy(fz_server_t srv);
+
+/* ------------------------------------------------------------------------
  * One-shot calls.
  * ---------------------------------------------------------------------- */
 

@@ -43,6 +43,10 @@ EXPORTS = (
     "fz_plan_create", "fz_plan_info", "fz_plan_rebuild", "fz_plan_enumerate",
     "fz_plan_unrank", "fz_plan_sync", "fz_plan_destroy",
     "fz_enumerate", "fz_enumerate_host",
+    "fz_batch_create", "fz_batch_info", "fz_batch_layout", "fz_batch_rebuild",
+    "fz_batch_enumerate", "fz_batch_sync", "fz_batch_destroy", "fz_enumerate_batch",
+    "fz_serve_create", "fz_serve_register", "fz_serve_submit", "fz_serve_poll",
+    "fz_serve_wait", "fz_serve_release", "fz_serve_stats", "fz_serve_destroy",
 )
 
 
@@ -68,6 +72,40 @@ class fz_memo_info_t(ctypes.Structure):
     _fields_ = [("k", ctypes.c_int32), ("top", ctypes.c_int32), ("rows", ctypes.c_uint64),
                 ("offsets_dev", ctypes.c_void_p), ("rows_dev", ctypes.c_void_p)]
 
+
+class fz_instance_t(ctypes.Structure):
+    _fields_ = [("g", ctypes.POINTER(ctypes.c_int32)), ("d", ctypes.c_int32),
+                ("n", ctypes.c_int32)]
+
+
+class fz_batch_info_t(ctypes.Structure):
+    _fields_ = [("count", ctypes.c_int32), ("memos", ctypes.c_int32),
+                ("total_rows", ctypes.c_uint64), ("total_words", ctypes.c_uint64),
+                ("device_bytes", ctypes.c_uint64), ("work_items", ctypes.c_uint64)]
+
+
+class fz_serve_cfg_t(ctypes.Structure):
+    _fields_ = [("memory_bytes", ctypes.c_uint64), ("max_in_flight", ctypes.c_int32),
+                ("streams", ctypes.c_int32), ("max_queue", ctypes.c_int32),
+                ("flags", ctypes.c_int32)]
+
+
+class fz_result_t(ctypes.Structure):
+    _fields_ = [("status", ctypes.c_int32), ("d", ctypes.c_int32), ("count", ctypes.c_uint64),
+                ("rows_dev", ctypes.c_void_p), ("t_submit", ctypes.c_double),
+                ("t_admit", ctypes.c_double), ("t_done", ctypes.c_double)]
+
+
+class fz_serve_stats_t(ctypes.Structure):
+    _fields_ = [("queued", ctypes.c_uint64), ("admitted", ctypes.c_uint64),
+                ("completed", ctypes.c_uint64), ("bytes_in_use", ctypes.c_uint64),
+                ("bytes_budget", ctypes.c_uint64), ("sets", ctypes.c_int32),
+                ("last_error", ctypes.c_int32)]
+
+
+FZ_SERVE_DONE = 0
+FZ_SERVE_QUEUED = 1
+FZ_SERVE_RUNNING = 2
 
 _lib = None
 _P = ctypes.c_void_p
@@ -105,6 +143,26 @@ _SIGS = {
     "fz_enumerate_host": (ctypes.c_int, [_I32P, ctypes.c_int, ctypes.c_int32,
                                          ctypes.POINTER(fz_opts_t), ctypes.c_uint64,
                                          ctypes.c_uint64, _P, ctypes.c_uint64, _U64P, _P]),
+    "fz_batch_create": (ctypes.c_int, [ctypes.POINTER(fz_instance_t), ctypes.c_int,
+                                       ctypes.POINTER(fz_opts_t), ctypes.POINTER(_P), _P]),
+    "fz_batch_info": (ctypes.c_int, [_P, ctypes.POINTER(fz_batch_info_t)]),
+    "fz_batch_layout": (ctypes.c_int, [_P, _U64P, _U64P, _I32P, _I32P]),
+    "fz_batch_rebuild": (ctypes.c_int, [_P, _P]),
+    "fz_batch_enumerate": (ctypes.c_int, [_P, _P, ctypes.c_uint64, _P]),
+    "fz_batch_sync": (ctypes.c_int, [_P, _P]),
+    "fz_batch_destroy": (ctypes.c_int, [_P]),
+    "fz_enumerate_batch": (ctypes.c_int, [ctypes.POINTER(fz_instance_t), ctypes.c_int,
+                                          ctypes.POINTER(fz_opts_t), _U64P, _P,
+                                          ctypes.c_uint64, _U64P, _P]),
+    "fz_serve_create": (ctypes.c_int, [ctypes.POINTER(fz_serve_cfg_t), ctypes.POINTER(_P)]),
+    "fz_serve_register": (ctypes.c_int, [_P, _I32P, ctypes.c_int, ctypes.c_int32, _I32P]),
+    "fz_serve_submit": (ctypes.c_int, [_P, ctypes.c_int32, ctypes.c_int32, _U64P]),
+    "fz_serve_poll": (ctypes.c_int, [_P, ctypes.c_uint64, ctypes.POINTER(fz_result_t)]),
+    "fz_serve_wait": (ctypes.c_int, [_P, ctypes.c_uint64, ctypes.c_int32,
+                                     ctypes.POINTER(fz_result_t)]),
+    "fz_serve_release": (ctypes.c_int, [_P, ctypes.c_uint64]),
+    "fz_serve_stats": (ctypes.c_int, [_P, ctypes.POINTER(fz_serve_stats_t)]),
+    "fz_serve_destroy": (ctypes.c_int, [_P]),
 }
 
 
@@ -364,3 +422,147 @@ def fz_enumerate_host(g: Sequence[int], n: int, out, rank_begin: int = 0,
     _check(lib().fz_enumerate_host(ga, d, int(n), ctypes.byref(o), int(rank_begin), end,
                                    ptr, int(cap), ctypes.byref(w), _stream(stream)))
     return int(w.value)
+
+
+# ----------------------------------------------------------------- batches
+def _instances(instances):
+    """(array of fz_instance_t, keep-alive list) for [(g, n), ...]."""
+    keep = []
+    arr = (fz_instance_t * len(instances))()
+    for i, (g, n) in enumerate(instances):
+        ga, d = _gens(g)
+        keep.append(ga)
+        arr[i].g = ctypes.cast(ga, ctypes.POINTER(ctypes.c_int32))
+        arr[i].d = d
+        arr[i].n = int(n)
+    return arr, keep
+
+
+class Batch:
+    """Many instances [(g, n), ...] enumerated by one persistent launch."""
+
+    def __init__(self, instances, k: int = FZ_AUTO, top: int = FZ_AUTO, stream=None):
+        arr, keep = _instances(instances)
+        h = _P()
+        o = _opts(k, top, 0)
+        _check(lib().fz_batch_create(arr, len(instances), ctypes.byref(o), ctypes.byref(h),
+                                     _stream(stream)))
+        self._h = h
+        self.count = len(instances)
+        info = fz_batch_info_t()
+        _check(lib().fz_batch_info(h, ctypes.byref(info)))
+        self.memos = int(info.memos)
+        self.total_rows = int(info.total_rows)
+        self.total_words = int(info.total_words)
+        self.device_bytes = int(info.device_bytes)
+        self.work_items = int(info.work_items)
+        self.rows = np.zeros(self.count, dtype=np.uint64)
+        self.word_offsets = np.zeros(self.count + 1, dtype=np.uint64)
+        self.k = np.zeros(self.count, dtype=np.int32)
+        self.top = np.zeros(self.count, dtype=np.int32)
+        _check(lib().fz_batch_layout(h, self.rows.ctypes.data_as(_U64P),
+                                     self.word_offsets.ctypes.data_as(_U64P),
+                                     self.k.ctypes.data_as(_I32P), self.top.ctypes.data_as(_I32P)))
+
+    def rebuild(self, stream=None):
+        _check(lib().fz_batch_rebuild(self._h, _stream(stream)))
+
+    def enumerate(self, out, capacity_words: Optional[int] = None, stream=None):
+        if capacity_words is None:
+            capacity_words = out.numel() if hasattr(out, "numel") else 0
+        _check(lib().fz_batch_enumerate(self._h, _ptr(out), int(capacity_words),
+                                        _stream(stream)))
+
+    def sync(self, stream=None):
+        _check(lib().fz_batch_sync(self._h, _stream(stream)))
+
+    def close(self):
+        if getattr(self, "_h", None):
+            lib().fz_batch_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+
+def fz_enumerate_batch(instances, out, k: int = FZ_AUTO, top: int = FZ_AUTO,
+                       capacity_words: Optional[int] = None, stream=None) -> np.ndarray:
+    """One-shot batch; returns the word offsets (count + 1)."""
+    arr, keep = _instances(instances)
+    o = _opts(k, top, 0)
+    offs = np.zeros(len(instances) + 1, dtype=np.uint64)
+    need = ctypes.c_uint64(0)
+    if capacity_words is None:
+        capacity_words = out.numel() if hasattr(out, "numel") else 0
+    _check(lib().fz_enumerate_batch(arr, len(instances), ctypes.byref(o),
+                                    offs.ctypes.data_as(_U64P), _ptr(out), int(capacity_words),
+                                    ctypes.byref(need), _stream(stream)))
+    return offs
+
+
+# ----------------------------------------------------------------- serving
+class Server:
+    """Request loop over resident generator sets (continuous batching)."""
+
+    def __init__(self, memory_bytes: int = 0, max_in_flight: int = 64, streams: int = 8,
+                 max_queue: int = 1 << 20):
+        cfg = fz_serve_cfg_t(int(memory_bytes), int(max_in_flight), int(streams),
+                             int(max_queue), 0)
+        h = _P()
+        _check(lib().fz_serve_create(ctypes.byref(cfg), ctypes.byref(h)))
+        self._h = h
+
+    def register(self, g: Sequence[int], n_max: int) -> int:
+        ga, d = _gens(g)
+        sid = ctypes.c_int32(0)
+        _check(lib().fz_serve_register(self._h, ga, d, int(n_max), ctypes.byref(sid)))
+        return int(sid.value)
+
+    def submit(self, set_id: int, n: int) -> int:
+        t = ctypes.c_uint64(0)
+        _check(lib().fz_serve_submit(self._h, int(set_id), int(n), ctypes.byref(t)))
+        return int(t.value)
+
+    def poll(self, ticket: int) -> fz_result_t:
+        r = fz_result_t()
+        _check(lib().fz_serve_poll(self._h, int(ticket), ctypes.byref(r)))
+        return r
+
+    def wait(self, ticket: int, timeout_ms: int = -1) -> fz_result_t:
+        r = fz_result_t()
+        _check(lib().fz_serve_wait(self._h, int(ticket), int(timeout_ms), ctypes.byref(r)))
+        return r
+
+    def release(self, ticket: int):
+        _check(lib().fz_serve_release(self._h, int(ticket)))
+
+    def stats(self) -> fz_serve_stats_t:
+        st = fz_serve_stats_t()
+        _check(lib().fz_serve_stats(self._h, ctypes.byref(st)))
+        return st
+
+    def close(self):
+        if getattr(self, "_h", None):
+            h, self._h = self._h, None
+            _check(lib().fz_serve_destroy(h))
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()

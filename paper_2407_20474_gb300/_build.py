@@ -16,7 +16,7 @@ BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libfz.so")
 INCLUDE = os.path.join(os.path.dirname(HERE), "include")
 
-SOURCES = ["fz_count.cu", "fz_memo.cu", "fz_enum.cu", "fz_api.cu", "fz_noalloc.cu"]
+SOURCES = ["fz_count.cu", "fz_memo.cu", "fz_enum.cu", "fz_api.cu", "fz_batch.cu", "fz_serve.cu", "fz_noalloc.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ["-std=c++17", "-O3", "-lineinfo", "-Xcompiler", "-fPIC",
               "-Xcompiler", "-Wall", "-I" + INCLUDE]

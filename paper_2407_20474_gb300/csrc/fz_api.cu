@@ -5,6 +5,7 @@
 
 #include <algorithm>
 #include <atomic>
+#include <cstdlib>
 #include <cstring>
 #include <mutex>
 #include <string>
@@ -129,6 +130,11 @@ struct fz_plan_s {
     int64_t tmp_words = 0;
     DevBuf base;   // C, tmp, O, status, bar, counter
     DevBuf memo;   // map + rows
+    DevBuf runs;   // runs table for work-balanced slicing
+    uint64_t *RT = nullptr;
+    int lam_r = 0;
+    uint64_t W = 0;
+    uint64_t total_runs = 0;
     uint64_t *C = nullptr, *tmp = nullptr, *O = nullptr, *map = nullptr;
     int32_t *rows = nullptr;
     int *status = nullptr;
@@ -150,6 +156,17 @@ namespace fz {
 namespace {
 
 size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
+
+// Work of one run of sibling leaves (an advance of the walk), in rows; the
+// environment variable FZ_RUN_COST overrides it (tuning only).
+uint64_t run_cost_rows() {
+    static uint64_t w = [] {
+        const char *e = getenv("FZ_RUN_COST");
+        long long v = e ? atoll(e) : 0;
+        return v > 0 ? (uint64_t)v : (uint64_t)512;
+    }();
+    return w;
+}
 
 // Enqueue the memo of plan p (offsets scan, gather map, fill).
 int plan_enqueue_memo(fz_plan_s *p, cudaStream_t s) {
@@ -287,6 +304,26 @@ int plan_create_impl(const int32_t *g, int d, int32_t n, const fz_opts_t *opt, f
         rc = read_status(p->status, s);
         if (rc != FZ_OK) return rc;
     }
+    // runs table for work-balanced slicing (not needed when the output is a
+    // single block: d == 1 or k == d with a full memo)
+    const bool single_block = d == 1 || (p->K == d && p->top > n);
+    if (!single_block && p->count > 0) {
+        const bool memo = p->K >= 1 && p->K <= d - 1 && p->top > 0;
+        p->lam_r = memo ? d - p->K - 1 : d - 2;
+        p->W = run_cost_rows();
+        rc = p->runs.alloc((size_t)(p->lam_r + 1) * cs * 8);
+        if (rc != FZ_OK) return rc;
+        p->RT = p->runs.as<uint64_t>();
+        rc = launch_runs_table(p->g, p->lam_r, n, p->RT, p->tmp, s);
+        if (rc != FZ_OK) return rc;
+        FZ_CUDA_TRY(cudaMemcpyAsync(&p->total_runs, p->RT + n, 8, cudaMemcpyDeviceToHost, s));
+        FZ_CUDA_TRY(cudaStreamSynchronize(s));
+        uint64_t wr = 0;
+        if (mul_overflows(p->W, p->total_runs, &wr) || p->count + wr < p->count) {
+            p->RT = nullptr;  // costs would not fit in 64 bits: slice by rows
+            p->runs.release();
+        }
+    }
     DeviceProps dp;
     rc = device_props(&dp);
     if (rc != FZ_OK) return rc;
@@ -311,6 +348,13 @@ EnumLaunch launch_of(const fz_plan_s *p) {
     L.K = p->K;
     L.top = p->top;
     L.g = p->g;
+    if (p->RT) {
+        L.RT = p->RT;
+        L.W = p->W;
+        L.lam_r = p->lam_r;
+        L.total_rows = p->count;
+        L.total_cost = p->count + p->W * p->total_runs;
+    }
     return L;
 }
 
@@ -320,6 +364,29 @@ uint64_t rows_in(const fz_plan_s *p, uint64_t b, uint64_t e) {
 }
 
 }  // namespace
+
+int plan_launch_for(fz_plan_t p, int32_t n, EnumLaunch *L) {
+    if (!p || n < 0 || n > p->n) return set_error(FZ_EINVAL, "element outside the plan");
+    *L = launch_of(p);
+    L->n = n;  // tables have stride p->n + 1 and serve every n <= p->n
+    return FZ_OK;
+}
+
+int plan_host_rows(fz_plan_t p, uint64_t *count_row, std::vector<uint64_t> *runs_row,
+                   cudaStream_t s) {
+    const size_t len = (size_t)p->n + 1;
+    FZ_CUDA_TRY(cudaMemcpyAsync(count_row, p->C, len * 8, cudaMemcpyDeviceToHost, s));
+    if (runs_row) {
+        runs_row->clear();
+        if (p->RT) {
+            runs_row->resize(len);
+            FZ_CUDA_TRY(cudaMemcpyAsync(runs_row->data(), p->RT, len * 8, cudaMemcpyDeviceToHost, s));
+        }
+    }
+    FZ_CUDA_TRY(cudaStreamSynchronize(s));
+    return FZ_OK;
+}
+
 }  // namespace fz
 
 extern "C" {
@@ -575,7 +642,7 @@ int fz_plan_info(fz_plan_t p, fz_plan_info_t *info) {
     info->k = p->K;
     info->top = p->top;
     info->memo_rows = p->memo_rows;
-    info->device_bytes = p->base.bytes + p->memo.bytes;
+    info->device_bytes = p->base.bytes + p->memo.bytes + p->runs.bytes;
     info->slice_rows = (int32_t)p->slice_rows;
     info->reserved = 0;
     return FZ_OK;
@@ -586,6 +653,10 @@ int fz_plan_rebuild(fz_plan_t p, void *stream) {
     cudaStream_t s = as_stream(stream);
     int rc = launch_count_table_tmp(p->g, p->d, p->n, p->C, p->tmp, s);
     if (rc != FZ_OK) return rc;
+    if (p->RT) {
+        rc = launch_runs_table(p->g, p->lam_r, p->n, p->RT, p->tmp, s);
+        if (rc != FZ_OK) return rc;
+    }
     return plan_enqueue_memo(p, s);
 }
 

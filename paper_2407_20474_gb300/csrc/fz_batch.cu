@@ -1,0 +1,590 @@
+// fz_batch.cu -- many instances Z(n_i, g_i) in one set of launches.
+//
+// A batch keeps, for every instance, its count table and runs table (for
+// work-balanced slicing) and, per distinct tail, one memo shared by the
+// instances with that tail.  A rebuild is: one initialisation launch and
+// three launches per table level for all instances' tables together (the
+// batched strided scans of fz_count.cu), then one launch that builds every
+// memo (one CTA per memo, the elementwise dynamic pass of Section 2).  The
+// enumeration is one persistent launch over (instance, slice) work items
+// (fz_enum.cu).  Everything after creation is asynchronous, so a rebuild plus
+// an enumeration can be captured in a CUDA graph.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cstring>
+#include <map>
+#include <vector>
+
+#include "fz_internal.cuh"
+
+namespace fz {
+namespace {
+
+struct DevArena {
+    void *p = nullptr;
+    size_t bytes = 0;
+    ~DevArena() {
+        if (p) cudaFree(p);
+    }
+    int alloc(size_t b) {
+        if (b == 0) b = 256;
+        cudaError_t e = cudaMalloc(&p, b);
+        if (e != cudaSuccess) {
+            p = nullptr;
+            return cuda_error(e, "cudaMalloc (batch)");
+        }
+        bytes = b;
+        return FZ_OK;
+    }
+};
+
+size_t a256(size_t x) { return (x + 255) & ~size_t(255); }
+
+// Elementwise batches a batch memo may take (its top is cut to this many
+// batches of min(tail) elements; larger remainders take the ordinary step).
+constexpr int64_t BATCH_MEMO_BATCHES = 64;
+constexpr double BATCH_MEMO_MAX_ROWS = 1 << 20;
+
+struct Inst {
+    int d = 0, n = 0, K = 0, top = 0, lam_r = 0;
+    int32_t g[FZ_MAX_D] = {};
+    size_t off_C = 0, off_RT = 0;  // word offsets into the table arena
+    int memo = -1;                 // memo job index
+    uint64_t count = 0, runs = 0;
+    uint64_t word_off = 0;
+    uint64_t items = 0, slice_cost = 0, slice_rows = 0;
+};
+
+}  // namespace
+}  // namespace fz
+
+using namespace fz;
+
+struct fz_batch_s {
+    int count = 0;
+    std::vector<Inst> inst;
+    uint64_t W = 512;
+    DevArena tables;   // all count and runs tables
+    DevArena scratch;  // block sums of blocked scans
+    DevArena memos;    // memo offsets and rows
+    DevArena meta;     // jobs, tasks, memo jobs, params, item prefix, counters
+    // scan launches: (first task, number of tasks) per launch, in order
+    std::vector<std::pair<int, int>> scan_launches;
+    ScanJob *jobs_dev = nullptr;
+    ScanTask *tasks_dev = nullptr;
+    MemoJob *memo_jobs_dev = nullptr;
+    int nmemo = 0;
+    std::vector<MemoJob> memo_jobs;
+    void *params_dev = nullptr;       // EnumParams images (out = word offset)
+    uint64_t *item0_dev = nullptr;
+    unsigned long long *counter_dev = nullptr;
+    int *status_dev = nullptr;
+    uint64_t nitems = 0;
+    uint64_t total_rows = 0, total_words = 0;
+    std::vector<unsigned char> params_host;
+};
+
+namespace fz {
+namespace {
+
+int build_scan_plan(fz_batch_s *b, uint64_t *table_base, std::vector<ScanJob> &jobs,
+                    std::vector<ScanTask> &tasks, size_t *scratch_words) {
+    const int64_t DIRECT = scan_direct_limit();
+    const int RBk = scan_block_rows();
+    int maxlev = 0;
+    for (const Inst &I : b->inst) maxlev = std::max(maxlev, std::max(I.d, I.lam_r));
+    // initialisation launch: last count row = delta, last runs row = ones
+    {
+        const int first = (int)tasks.size();
+        for (const Inst &I : b->inst) {
+            const int64_t len = (int64_t)I.n + 1;
+            ScanJob jd{};
+            jd.out = table_base + I.off_C + (size_t)I.d * len;
+            jd.len = len;
+            jobs.push_back(jd);
+            for (int64_t a = 0; a < len; a += 8192)
+                tasks.push_back({(int)jobs.size() - 1, TK_DELTA, a, std::min(len, a + 8192)});
+            if (I.lam_r >= 0 && I.off_RT != (size_t)-1) {
+                ScanJob jo{};
+                jo.out = table_base + I.off_RT + (size_t)I.lam_r * len;
+                jo.len = len;
+                jobs.push_back(jo);
+                for (int64_t a = 0; a < len; a += 8192)
+                    tasks.push_back({(int)jobs.size() - 1, TK_ONES, a, std::min(len, a + 8192)});
+            }
+        }
+        b->scan_launches.push_back({first, (int)tasks.size() - first});
+    }
+    size_t max_scratch = 0;
+    for (int t = 0; t < maxlev; ++t) {
+        // jobs of this level: count row d-1-t, runs row lam_r-1-t
+        std::vector<int> step_jobs;
+        for (const Inst &I : b->inst) {
+            const int64_t len = (int64_t)I.n + 1;
+            if (I.d > t) {
+                const int j = I.d - 1 - t;
+                ScanJob J{};
+                J.in = table_base + I.off_C + (size_t)(j + 1) * len;
+                J.out = table_base + I.off_C + (size_t)j * len;
+                J.len = len;
+                J.g = I.g[j];
+                jobs.push_back(J);
+                step_jobs.push_back((int)jobs.size() - 1);
+            }
+            if (I.off_RT != (size_t)-1 && I.lam_r > t) {
+                const int j = I.lam_r - 1 - t;
+                ScanJob J{};
+                J.in = table_base + I.off_RT + (size_t)(j + 1) * len;
+                J.out = table_base + I.off_RT + (size_t)j * len;
+                J.len = len;
+                J.g = I.g[j];
+                jobs.push_back(J);
+                step_jobs.push_back((int)jobs.size() - 1);
+            }
+        }
+        // scratch for blocked jobs of this level (reused by every level)
+        size_t sw = 0;
+        for (int ji : step_jobs) {
+            ScanJob &J = jobs[ji];
+            const int64_t T = (J.len + J.g - 1) / J.g;
+            if (T > DIRECT) {
+                const int64_t nrb = (T + RBk - 1) / RBk;
+                J.slen = nrb * J.g;
+                J.S = reinterpret_cast<uint64_t *>(sw);  // offset, fixed up below
+                J.Sincl = reinterpret_cast<uint64_t *>(sw + (size_t)J.slen);
+                sw += 2 * (size_t)J.slen;
+            }
+        }
+        max_scratch = std::max(max_scratch, sw);
+        int first = (int)tasks.size();
+        for (int ji : step_jobs) {
+            const ScanJob &J = jobs[ji];
+            if (!J.slen) {
+                const int64_t chains = std::min<int64_t>(J.g, J.len);
+                for (int64_t a = 0; a < chains; a += 8)
+                    tasks.push_back({ji, TK_DIRECT, a, std::min(chains, a + 8)});
+            } else {
+                for (int64_t a = 0; a < J.slen; a += 2048)
+                    tasks.push_back({ji, TK_BSUM, a, std::min(J.slen, a + 2048)});
+            }
+        }
+        b->scan_launches.push_back({first, (int)tasks.size() - first});
+        first = (int)tasks.size();
+        for (int ji : step_jobs) {
+            const ScanJob &J = jobs[ji];
+            if (J.slen)
+                for (int64_t a = 0; a < J.g; a += 8)
+                    tasks.push_back({ji, TK_SSCAN, a, std::min<int64_t>(J.g, a + 8)});
+        }
+        b->scan_launches.push_back({first, (int)tasks.size() - first});
+        first = (int)tasks.size();
+        for (int ji : step_jobs) {
+            const ScanJob &J = jobs[ji];
+            if (J.slen)
+                for (int64_t a = 0; a < J.slen; a += 2048)
+                    tasks.push_back({ji, TK_APPLY, a, std::min(J.slen, a + 2048)});
+        }
+        b->scan_launches.push_back({first, (int)tasks.size() - first});
+    }
+    *scratch_words = max_scratch;
+    return FZ_OK;
+}
+
+int batch_enqueue_rebuild(fz_batch_s *b, cudaStream_t s) {
+    for (const auto &L : b->scan_launches) {
+        int rc = launch_scan_tasks(b->jobs_dev, b->tasks_dev + L.first, L.second, s);
+        if (rc != FZ_OK) return rc;
+    }
+    return launch_memo_cta_build(b->memo_jobs_dev, b->nmemo, b->status_dev, s);
+}
+
+__global__ void gather_kernel(const uint64_t *const *ptrs, uint64_t *out, int count) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < count) out[i] = ptrs[i] ? *ptrs[i] : 0ull;
+}
+
+int gather(const std::vector<const uint64_t *> &ptrs, std::vector<uint64_t> &out,
+           cudaStream_t s) {
+    const int count = (int)ptrs.size();
+    out.assign(count, 0);
+    if (!count) return FZ_OK;
+    DevArena tmp;
+    int rc = tmp.alloc(a256((size_t)count * 8) * 2);
+    if (rc != FZ_OK) return rc;
+    const uint64_t **dp = static_cast<const uint64_t **>(tmp.p);
+    uint64_t *dv = reinterpret_cast<uint64_t *>(static_cast<char *>(tmp.p) + a256((size_t)count * 8));
+    FZ_CUDA_TRY(cudaMemcpyAsync(dp, ptrs.data(), (size_t)count * 8, cudaMemcpyHostToDevice, s));
+    gather_kernel<<<(count + 255) / 256, 256, 0, s>>>(dp, dv, count);
+    note_launch();
+    FZ_CUDA_TRY(cudaGetLastError());
+    FZ_CUDA_TRY(cudaMemcpyAsync(out.data(), dv, (size_t)count * 8, cudaMemcpyDeviceToHost, s));
+    FZ_CUDA_TRY(cudaStreamSynchronize(s));
+    return FZ_OK;
+}
+
+// Memo depth of a batch instance: the last min(3, d-1) generators for d >= 3
+// (none for d <= 2), with top cut to BATCH_MEMO_BATCHES elementwise batches
+// and a depth lowered while the continuous estimate top^k / (k! prod t) of
+// its rows is above BATCH_MEMO_MAX_ROWS.
+void choose_batch_memo(Inst &I) {
+    I.K = 0;
+    I.top = 0;
+    if (I.d < 3) return;
+    for (int k = std::min(3, I.d - 1); k >= 2; --k) {
+        int32_t tmin = I.g[I.d - k];
+        double prod = 1.0;
+        for (int i = I.d - k; i < I.d; ++i) {
+            tmin = std::min(tmin, I.g[i]);
+            prod *= I.g[i];
+        }
+        const int64_t top = std::min<int64_t>((int64_t)I.n + 1, BATCH_MEMO_BATCHES * tmin);
+        double est = 1.0;
+        for (int i = 0; i < k; ++i) est *= (double)top / (i + 1);
+        est /= prod;
+        if (est <= BATCH_MEMO_MAX_ROWS) {
+            I.K = k;
+            I.top = (int)top;
+            return;
+        }
+    }
+}
+
+}  // namespace
+}  // namespace fz
+
+extern "C" {
+
+int fz_batch_create(const fz_instance_t *inst, int count, const fz_opts_t *opt,
+                    fz_batch_t *batch, void *stream) {
+    if (!batch) return set_error(FZ_EINVAL, "batch: null pointer");
+    if (count < 0 || (count > 0 && !inst)) return set_error(FZ_EINVAL, "instances");
+    if (opt && opt->flags != 0) return set_error(FZ_EINVAL, "opts.flags must be 0");
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    fz_batch_s *b = new (std::nothrow) fz_batch_s;
+    if (!b) return set_error(FZ_ENOMEM, "host allocation");
+    auto fail = [&](int rc) {
+        cudaStreamSynchronize(s);
+        delete b;
+        return rc;
+    };
+    b->count = count;
+    b->inst.resize(count);
+    size_t words = 0;
+    for (int i = 0; i < count; ++i) {
+        const fz_instance_t &x = inst[i];
+        int rc = validate_gens(x.g, x.d);
+        if (rc != FZ_OK) return fail(rc);
+        if (x.n < 0) return fail(set_error(FZ_EINVAL, "n must be >= 0"));
+        Inst &I = b->inst[i];
+        I.d = x.d;
+        I.n = x.n;
+        for (int j = 0; j < x.d; ++j) I.g[j] = x.g[j];
+        choose_batch_memo(I);
+        if (opt && opt->k != FZ_AUTO) {
+            if (opt->k < 0 || opt->k > x.d - 1)
+                return fail(set_error(FZ_EINVAL, "opts.k must be in 0..d-1 for every instance"));
+            I.K = opt->k;
+            int32_t tmin = I.K ? I.g[I.d - I.K] : 1;
+            for (int j = I.d - I.K; j < I.d; ++j) tmin = std::min(tmin, I.g[j]);
+            I.top = I.K ? (int)std::min<int64_t>((int64_t)I.n + 1, BATCH_MEMO_BATCHES * tmin) : 0;
+        }
+        if (opt && opt->top != FZ_AUTO && I.K > 0) I.top = std::min(I.top, opt->top);
+        if (I.K > 0 && I.top <= 0) I.K = 0;
+        const size_t len = (size_t)I.n + 1;
+        I.off_C = words;
+        words += (size_t)(I.d + 1) * len;
+        I.off_RT = (size_t)-1;
+        if (I.d >= 2) {
+            I.lam_r = I.K > 0 ? I.d - I.K - 1 : I.d - 2;
+            I.off_RT = words;
+            words += (size_t)(I.lam_r + 1) * len;
+        } else {
+            I.lam_r = -1;
+        }
+    }
+    const char *e = getenv("FZ_RUN_COST");
+    if (e && atoll(e) > 0) b->W = (uint64_t)atoll(e);
+    int rc = b->tables.alloc(words * 8);
+    if (rc != FZ_OK) return fail(rc);
+    uint64_t *tb = static_cast<uint64_t *>(b->tables.p);
+
+    std::vector<ScanJob> jobs;
+    std::vector<ScanTask> tasks;
+    size_t scratch_words = 0;
+    rc = build_scan_plan(b, tb, jobs, tasks, &scratch_words);
+    if (rc != FZ_OK) return fail(rc);
+    rc = b->scratch.alloc(scratch_words * 8);
+    if (rc != FZ_OK) return fail(rc);
+    for (ScanJob &J : jobs) {
+        if (J.slen) {
+            J.S = static_cast<uint64_t *>(b->scratch.p) + reinterpret_cast<size_t>(J.S);
+            J.Sincl = static_cast<uint64_t *>(b->scratch.p) + reinterpret_cast<size_t>(J.Sincl);
+        }
+    }
+
+    // memo jobs, one per distinct (tail, k); top = the largest asked for
+    std::map<std::vector<int32_t>, int> memo_of;
+    std::vector<std::vector<int32_t>> memo_tail;
+    std::vector<int> memo_src;  // instance whose table rows feed the memo
+    for (int i = 0; i < count; ++i) {
+        Inst &I = b->inst[i];
+        if (I.K <= 0) continue;
+        std::vector<int32_t> key(I.g + (I.d - I.K), I.g + I.d);
+        auto it = memo_of.find(key);
+        int m;
+        if (it == memo_of.end()) {
+            m = (int)b->memo_jobs.size();
+            memo_of[key] = m;
+            memo_tail.push_back(key);
+            memo_src.push_back(i);
+            MemoJob J{};
+            J.k = I.K;
+            J.top = I.top;
+            b->memo_jobs.push_back(J);
+        } else {
+            m = it->second;
+            if (I.top > b->memo_jobs[m].top) b->memo_jobs[m].top = I.top;
+            if (I.n > b->inst[memo_src[m]].n) memo_src[m] = i;
+        }
+        I.memo = m;
+    }
+    b->nmemo = (int)b->memo_jobs.size();
+    for (int m = 0; m < b->nmemo; ++m) {
+        MemoJob &J = b->memo_jobs[m];
+        const Inst &S = b->inst[memo_src[m]];
+        J.Ct = tb + S.off_C + (size_t)(S.d - J.k) * ((size_t)S.n + 1);
+        J.cs = (int64_t)S.n + 1;
+        int32_t tmin = memo_tail[m][0];
+        for (int c = 0; c < J.k; ++c) {
+            J.t[c] = memo_tail[m][c];
+            tmin = std::min(tmin, J.t[c]);
+        }
+        J.b = tmin;
+        if (J.top > S.n + 1) J.top = S.n + 1;
+    }
+
+    // metadata arena: jobs, tasks, memo jobs, params, item prefix, counters
+    const size_t pbytes = enum_params_bytes();
+    const size_t o_jobs = 0;
+    const size_t o_tasks = a256(o_jobs + jobs.size() * sizeof(ScanJob));
+    const size_t o_mjobs = a256(o_tasks + tasks.size() * sizeof(ScanTask));
+    const size_t o_params = a256(o_mjobs + (size_t)b->nmemo * sizeof(MemoJob));
+    const size_t o_item0 = a256(o_params + (size_t)count * pbytes);
+    const size_t o_misc = a256(o_item0 + ((size_t)count + 1) * 8);
+    const size_t o_mrows = a256(o_misc + 256);
+    rc = b->meta.alloc(a256(o_mrows + (size_t)b->nmemo * 8) + 256);
+    if (rc != FZ_OK) return fail(rc);
+    char *mb = static_cast<char *>(b->meta.p);
+    b->jobs_dev = reinterpret_cast<ScanJob *>(mb + o_jobs);
+    b->tasks_dev = reinterpret_cast<ScanTask *>(mb + o_tasks);
+    b->memo_jobs_dev = reinterpret_cast<MemoJob *>(mb + o_mjobs);
+    b->params_dev = mb + o_params;
+    b->item0_dev = reinterpret_cast<uint64_t *>(mb + o_item0);
+    b->counter_dev = reinterpret_cast<unsigned long long *>(mb + o_misc);
+    b->status_dev = reinterpret_cast<int *>(mb + o_misc + 64);
+    uint64_t *mrows_dev = reinterpret_cast<uint64_t *>(mb + o_mrows);
+    FZ_CUDA_TRY(cudaMemsetAsync(mb + o_misc, 0, 256, s));
+    if (!jobs.empty())
+        FZ_CUDA_TRY(cudaMemcpyAsync(b->jobs_dev, jobs.data(), jobs.size() * sizeof(ScanJob),
+                                    cudaMemcpyHostToDevice, s));
+    if (!tasks.empty())
+        FZ_CUDA_TRY(cudaMemcpyAsync(b->tasks_dev, tasks.data(), tasks.size() * sizeof(ScanTask),
+                                    cudaMemcpyHostToDevice, s));
+    // count and runs tables
+    for (const auto &L : b->scan_launches) {
+        rc = launch_scan_tasks(b->jobs_dev, b->tasks_dev + L.first, L.second, s);
+        if (rc != FZ_OK) return fail(rc);
+    }
+    // memo sizes, then allocation and build
+    std::vector<uint64_t> mrows(b->nmemo, 0);
+    if (b->nmemo) {
+        FZ_CUDA_TRY(cudaMemcpyAsync(b->memo_jobs_dev, b->memo_jobs.data(),
+                                    b->memo_jobs.size() * sizeof(MemoJob),
+                                    cudaMemcpyHostToDevice, s));
+        rc = launch_memo_sizes(b->memo_jobs_dev, b->nmemo, mrows_dev, s);
+        if (rc != FZ_OK) return fail(rc);
+        FZ_CUDA_TRY(cudaMemcpyAsync(mrows.data(), mrows_dev, (size_t)b->nmemo * 8,
+                                    cudaMemcpyDeviceToHost, s));
+        FZ_CUDA_TRY(cudaStreamSynchronize(s));
+        size_t mwords = 0;
+        for (int m = 0; m < b->nmemo; ++m) {
+            if (mrows[m] > MEMO_MAX_ROWS) return fail(set_error(FZ_EINVAL, "batch memo too large"));
+            mwords += a256(((size_t)b->memo_jobs[m].top + 1) * 8) / 8;
+            mwords += a256((size_t)mrows[m] * b->memo_jobs[m].k * 4 + 16) / 8;
+        }
+        rc = b->memos.alloc(mwords * 8);
+        if (rc != FZ_OK) return fail(rc);
+        char *base = static_cast<char *>(b->memos.p);
+        size_t off = 0;
+        for (int m = 0; m < b->nmemo; ++m) {
+            MemoJob &J = b->memo_jobs[m];
+            J.O = reinterpret_cast<uint64_t *>(base + off);
+            off += a256(((size_t)J.top + 1) * 8);
+            J.R = reinterpret_cast<int32_t *>(base + off);
+            off += a256((size_t)mrows[m] * J.k * 4 + 16);
+            J.rows = mrows[m];
+        }
+        FZ_CUDA_TRY(cudaMemcpyAsync(b->memo_jobs_dev, b->memo_jobs.data(),
+                                    b->memo_jobs.size() * sizeof(MemoJob),
+                                    cudaMemcpyHostToDevice, s));
+        rc = launch_memo_cta_build(b->memo_jobs_dev, b->nmemo, b->status_dev, s);
+        if (rc != FZ_OK) return fail(rc);
+    }
+    // counts and run totals
+    std::vector<const uint64_t *> pc(count), pr(count);
+    for (int i = 0; i < count; ++i) {
+        const Inst &I = b->inst[i];
+        pc[i] = tb + I.off_C + I.n;
+        pr[i] = I.off_RT != (size_t)-1 ? tb + I.off_RT + I.n : nullptr;
+    }
+    std::vector<uint64_t> cnt, runs;
+    rc = gather(pc, cnt, s);
+    if (rc == FZ_OK) rc = gather(pr, runs, s);
+    if (rc != FZ_OK) return fail(rc);
+    int hstatus = 0;
+    FZ_CUDA_TRY(cudaMemcpyAsync(&hstatus, b->status_dev, 4, cudaMemcpyDeviceToHost, s));
+    FZ_CUDA_TRY(cudaStreamSynchronize(s));
+    if (hstatus != 0) return fail(set_error(FZ_EINTERNAL, "batch memo build check failed"));
+
+    // layout, work items, per-instance parameter images
+    DeviceProps dp;
+    rc = device_props(&dp);
+    if (rc != FZ_OK) return fail(rc);
+    uint64_t total_cost = 0;
+    uint64_t word = 0;
+    for (int i = 0; i < count; ++i) {
+        Inst &I = b->inst[i];
+        I.count = cnt[i];
+        if (I.count == ~0ull) return fail(set_error(FZ_EOVERFLOW, "|Z(n)| does not fit"));
+        I.runs = runs[i];
+        word = (word + 3) & ~3ull;  // 16-byte aligned start of every instance
+        I.word_off = word;
+        word += I.count * (uint64_t)I.d;
+        b->total_rows += I.count;
+        total_cost += I.count + b->W * I.runs;
+    }
+    b->total_words = word;
+    const uint64_t warps = (uint64_t)dp.sms * 16;
+    const uint64_t target = std::max<uint64_t>(4096, total_cost / (warps * 8 + 1));
+    std::vector<uint64_t> item0(count + 1, 0);
+    b->params_host.resize((size_t)count * pbytes);
+    for (int i = 0; i < count; ++i) {
+        Inst &I = b->inst[i];
+        const uint64_t cost = I.count + b->W * I.runs;
+        I.items = I.count == 0 ? 0 : std::max<uint64_t>(1, (cost + target - 1) / target);
+        I.slice_cost = I.items ? (cost + I.items - 1) / I.items : 64;
+        I.slice_rows = I.items ? std::max<uint64_t>(4, (I.count + I.items - 1) / I.items) : 4;
+        item0[i + 1] = item0[i] + I.items;
+        EnumLaunch L;
+        L.C = tb + I.off_C;
+        L.cs = (int64_t)I.n + 1;
+        L.n = I.n;
+        L.d = I.d;
+        L.K = I.K;
+        L.top = I.top;
+        L.g = I.g;
+        L.status = b->status_dev;
+        L.slice_counter = b->counter_dev;
+        if (I.memo >= 0) {
+            L.O = b->memo_jobs[I.memo].O;
+            L.memo = b->memo_jobs[I.memo].R;
+            L.memo_rows = b->memo_jobs[I.memo].rows;
+        }
+        if (I.off_RT != (size_t)-1) {
+            L.RT = tb + I.off_RT;
+            L.W = b->W;
+            L.lam_r = I.lam_r;
+        }
+        // out holds the word offset; the kernel adds the output base
+        fill_batch_params(L, reinterpret_cast<int32_t *>(I.word_off * 4), I.count, I.slice_rows,
+                          I.slice_cost, b->params_host.data() + (size_t)i * pbytes);
+    }
+    b->nitems = item0[count];
+    if (count) {
+        FZ_CUDA_TRY(cudaMemcpyAsync(b->params_dev, b->params_host.data(), b->params_host.size(),
+                                    cudaMemcpyHostToDevice, s));
+        FZ_CUDA_TRY(cudaMemcpyAsync(b->item0_dev, item0.data(), item0.size() * 8,
+                                    cudaMemcpyHostToDevice, s));
+    }
+    FZ_CUDA_TRY(cudaStreamSynchronize(s));
+    *batch = b;
+    return FZ_OK;
+}
+
+int fz_batch_info(fz_batch_t b, fz_batch_info_t *info) {
+    if (!b || !info) return set_error(FZ_EINVAL, "null pointer");
+    info->count = b->count;
+    info->memos = b->nmemo;
+    info->total_rows = b->total_rows;
+    info->total_words = b->total_words;
+    info->device_bytes = b->tables.bytes + b->scratch.bytes + b->memos.bytes + b->meta.bytes;
+    info->work_items = b->nitems;
+    return FZ_OK;
+}
+
+int fz_batch_layout(fz_batch_t b, uint64_t *rows, uint64_t *word_offsets, int32_t *k,
+                    int32_t *top) {
+    if (!b) return set_error(FZ_EINVAL, "batch: null pointer");
+    for (int i = 0; i < b->count; ++i) {
+        if (rows) rows[i] = b->inst[i].count;
+        if (word_offsets) word_offsets[i] = b->inst[i].word_off;
+        if (k) k[i] = b->inst[i].K;
+        if (top) top[i] = b->inst[i].top;
+    }
+    if (word_offsets) word_offsets[b->count] = b->total_words;
+    return FZ_OK;
+}
+
+int fz_batch_rebuild(fz_batch_t b, void *stream) {
+    if (!b) return set_error(FZ_EINVAL, "batch: null pointer");
+    return batch_enqueue_rebuild(b, static_cast<cudaStream_t>(stream));
+}
+
+int fz_batch_enumerate(fz_batch_t b, int32_t *out_dev, uint64_t out_capacity_words,
+                       void *stream) {
+    if (!b) return set_error(FZ_EINVAL, "batch: null pointer");
+    if (b->total_words == 0) return FZ_OK;
+    if (!out_dev) return set_error(FZ_EINVAL, "out: null pointer");
+    if (((uintptr_t)out_dev & 3u) != 0) return set_error(FZ_EINVAL, "out must be 4-byte aligned");
+    if (out_capacity_words < b->total_words) return set_error(FZ_ENOSPC, "output capacity too small");
+    return launch_enumerate_batch(b->params_dev, b->item0_dev, b->count, b->nitems,
+                                  b->counter_dev, out_dev, static_cast<cudaStream_t>(stream));
+}
+
+int fz_batch_sync(fz_batch_t b, void *stream) {
+    if (!b) return set_error(FZ_EINVAL, "batch: null pointer");
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    int h = 0;
+    FZ_CUDA_TRY(cudaMemcpyAsync(&h, b->status_dev, 4, cudaMemcpyDeviceToHost, s));
+    FZ_CUDA_TRY(cudaStreamSynchronize(s));
+    if (h != 0) {
+        FZ_CUDA_TRY(cudaMemsetAsync(b->status_dev, 0, 4, s));
+        FZ_CUDA_TRY(cudaStreamSynchronize(s));
+        return set_error(h == DEV_TIMEOUT ? FZ_ETIMEOUT : FZ_EINTERNAL,
+                         "device-side check failed in the batch");
+    }
+    return FZ_OK;
+}
+
+int fz_batch_destroy(fz_batch_t b) {
+    if (!b) return set_error(FZ_EINVAL, "batch: null pointer");
+    delete b;
+    return FZ_OK;
+}
+
+int fz_enumerate_batch(const fz_instance_t *inst, int count, const fz_opts_t *opt,
+                       uint64_t *word_offsets, int32_t *out_dev, uint64_t out_capacity_words,
+                       uint64_t *words_needed, void *stream) {
+    fz_batch_t b = nullptr;
+    int rc = fz_batch_create(inst, count, opt, &b, stream);
+    if (rc != FZ_OK) return rc;
+    if (words_needed) *words_needed = b->total_words;
+    if (word_offsets) fz_batch_layout(b, nullptr, word_offsets, nullptr, nullptr);
+    rc = fz_batch_enumerate(b, out_dev, out_capacity_words, stream);
+    if (rc == FZ_OK) rc = fz_batch_sync(b, stream);
+    fz_batch_destroy(b);
+    return rc;
+}
+
+}  // extern "C"

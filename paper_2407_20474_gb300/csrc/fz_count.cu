@@ -170,6 +170,123 @@ int launch_count_table_tmp(const int32_t *g, int d, int32_t n, uint64_t *table, 
     return FZ_OK;
 }
 
+__global__ void row_ones_kernel(uint64_t *__restrict__ row, int64_t len) {
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (; i < len; i += stride) row[i] = 1ull;
+}
+
+// Number of depth-lam nodes (runs of sibling leaves) under a node at depth j
+// with remainder x: RT[lam][x] = 1 and RT[j] = RT[j+1] strided-summed with
+// stride g_j -- the count-table recurrence over the leading generators.
+int launch_runs_table(const int32_t *g, int lam, int32_t n, uint64_t *RT, uint64_t *tmp,
+                      cudaStream_t s) {
+    const int64_t len = (int64_t)n + 1;
+    row_ones_kernel<<<grid_for(len, THREADS), THREADS, 0, s>>>(RT + (int64_t)lam * len, len);
+    note_launch();
+    FZ_CUDA_TRY(cudaGetLastError());
+    for (int j = lam - 1; j >= 0; --j) {
+        int rc = strided_scan(RT + (int64_t)(j + 1) * len, RT + (int64_t)j * len, len, g[j],
+                              tmp, s);
+        if (rc != FZ_OK) return rc;
+    }
+    return FZ_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Batched strided scans: many independent rows (of many instances' count and
+// runs tables) in one launch.  Each CTA executes one task: a range of chains
+// scanned directly (one warp per chain), a range of block sums, a range of
+// chains of block sums, a range of block applications, or a range of a row
+// initialisation (delta or ones).
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ void chain_scan_warp(const uint64_t *__restrict__ in,
+                                                uint64_t *__restrict__ out, int64_t len,
+                                                int64_t g, int64_t rho, int lane) {
+    const int64_t T = (len - rho + g - 1) / g;
+    uint64_t carry = 0;
+    for (int64_t t0 = 0; t0 < T; t0 += 128) {
+        uint64_t v[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            int64_t t = t0 + u * 32 + lane;
+            v[u] = t < T ? __ldg(in + rho + t * g) : 0ull;
+        }
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            int64_t t = t0 + u * 32 + lane;
+            uint64_t sc = sat_add(warp_incl_scan_sat(v[u], lane), carry);
+            if (t < T) out[rho + t * g] = sc;
+            carry = shfl_u64(sc, 31);
+        }
+    }
+}
+
+__global__ void __launch_bounds__(THREADS) scan_tasks_kernel(const ScanJob *__restrict__ jobs,
+                                                             const ScanTask *__restrict__ tasks) {
+    const ScanTask t = tasks[blockIdx.x];
+    const ScanJob J = jobs[t.job];
+    const int lane = threadIdx.x & 31;
+    const int warp = threadIdx.x >> 5;
+    const int nwarps = blockDim.x >> 5;
+    switch (t.kind) {
+        case TK_DIRECT:
+            for (int64_t rho = t.begin + warp; rho < t.end; rho += nwarps)
+                chain_scan_warp(J.in, J.out, J.len, J.g, rho, lane);
+            break;
+        case TK_SSCAN:
+            for (int64_t rho = t.begin + warp; rho < t.end; rho += nwarps)
+                chain_scan_warp(J.S, J.Sincl, J.slen, J.g, rho, lane);
+            break;
+        case TK_BSUM:
+            for (int64_t i = t.begin + threadIdx.x; i < t.end; i += blockDim.x) {
+                const int64_t b = i / J.g, rho = i - b * J.g;
+                const int64_t r0 = (b * RB) * J.g + rho;
+                uint64_t acc = 0;
+                for (int u = 0; u < RB; ++u) {
+                    const int64_t r = r0 + (int64_t)u * J.g;
+                    if (r < J.len) acc = sat_add(acc, __ldg(J.in + r));
+                }
+                J.S[i] = acc;
+            }
+            break;
+        case TK_APPLY:
+            for (int64_t i = t.begin + threadIdx.x; i < t.end; i += blockDim.x) {
+                const int64_t b = i / J.g, rho = i - b * J.g;
+                uint64_t acc = b > 0 ? J.Sincl[i - J.g] : 0ull;
+                const int64_t r0 = (b * RB) * J.g + rho;
+                for (int u = 0; u < RB; ++u) {
+                    const int64_t r = r0 + (int64_t)u * J.g;
+                    if (r < J.len) {
+                        acc = sat_add(acc, __ldg(J.in + r));
+                        J.out[r] = acc;
+                    }
+                }
+            }
+            break;
+        case TK_DELTA:
+            for (int64_t i = t.begin + threadIdx.x; i < t.end; i += blockDim.x)
+                J.out[i] = (i == 0) ? 1ull : 0ull;
+            break;
+        case TK_ONES:
+            for (int64_t i = t.begin + threadIdx.x; i < t.end; i += blockDim.x) J.out[i] = 1ull;
+            break;
+        default:
+            break;
+    }
+}
+
+int launch_scan_tasks(const ScanJob *jobs, const ScanTask *tasks, int ntasks, cudaStream_t s) {
+    if (ntasks <= 0) return FZ_OK;
+    scan_tasks_kernel<<<ntasks, THREADS, 0, s>>>(jobs, tasks);
+    note_launch();
+    FZ_CUDA_TRY(cudaGetLastError());
+    return FZ_OK;
+}
+
+int64_t scan_direct_limit() { return DIRECT_T; }
+int scan_block_rows() { return RB; }
+
 int launch_count_rolling(const int32_t *g, int d, int32_t n, uint64_t *a, uint64_t *b,
                          uint64_t *tmp, uint64_t **result, cudaStream_t s) {
     const int64_t len = (int64_t)n + 1;

@@ -29,6 +29,8 @@
 // ring of two halves and each full half is written to HBM with one bulk
 // (TMA) store, so the stream is written with 16-byte aligned, fully
 // coalesced transactions while the warp generates the next half.
+#include <cstring>
+
 #include "fz_internal.cuh"
 
 namespace fz {
@@ -49,8 +51,12 @@ struct EnumParams {
     unsigned long long *slice_counter;
     uint64_t rank_begin;   // absolute rank of out row 0
     uint64_t nrows;        // rows to write
-    uint64_t slice_rows;   // S (multiple of 4)
+    uint64_t slice_rows;   // S (multiple of 4), used when RT is null
     uint64_t nslices;
+    const uint64_t *RT;    // runs table rows 0..lam_r (stride cs), or null
+    uint64_t W;            // cost of one run, in rows
+    uint64_t slice_cost;   // cost units per work item when RT is set
+    int lam_r;             // coordinate of the runs counted by RT
     int n, d, K, top;
     int lam_m;             // coordinate whose children are memo leaves (d-K-1), or -1
     int lam_w;             // coordinate whose children are walk leaves (d-2)
@@ -115,9 +121,12 @@ __device__ __forceinline__ void descend(const EnumParams &P, WarpPath *wp, int c
                                         int c_to, int lane) {
     int rem = wp->r[c_from];
     for (int c = c_from; c < c_to; ++c) {
-        int v;
-        uint64_t before;
-        find_child(P, c, rem, 0ull, lane, v, before);
+        int v = rem / P.g[c];
+        // usually the largest child is live (one load); else search
+        if (__ldg(P.C + (long long)(c + 1) * P.cs + (rem - v * P.g[c])) == 0ull) {
+            uint64_t before;
+            find_child(P, c, rem, 0ull, lane, v, before);
+        }
         rem -= v * P.g[c];
         if (lane == 0) {
             wp->a[c] = v;
@@ -188,9 +197,12 @@ __device__ bool advance(const EnumParams &P, WarpPath *wp, int lane, RunState &s
         const uint64_t R = __ldg(row + (rem - aj * P.g[j]));  // rows in children >= aj
         const uint64_t total = __ldg(row + rem);
         if (R >= total) continue;
-        int v;
-        uint64_t before;
-        find_child(P, j, rem, R, lane, v, before);
+        // usually the next smaller value is live (one load); else search
+        int v = aj - 1;
+        if (__ldg(P.C + (long long)(j + 1) * P.cs + (rem - v * P.g[j])) == 0ull) {
+            uint64_t before;
+            find_child(P, j, rem, R, lane, v, before);
+        }
         const int p = rem - v * P.g[j];
         if (lane == 0) {
             wp->a[j] = v;
@@ -215,12 +227,84 @@ __device__ bool advance(const EnumParams &P, WarpPath *wp, int lane, RunState &s
     return false;
 }
 
-template <int D>
+// ---------------------------------------------------------------------------
+// Work-balanced slicing.  The cost of a subtree is its rows plus W for every
+// run of sibling leaves in it; RT[j][x] counts those runs (RT[lam_r] = 1, and
+// row j is row j+1 strided-summed with stride g_j, like the count table), so
+// the cost of the children a_j >= v of a node is C[j][x] + W RT[j][x] with
+// x = rem - v g_j.  Work items are equal cost ranges, located by the same
+// 32-probe search as ranks, then snapped to ranks that are multiples of 4
+// from rank_begin (keeping every bulk store 16-byte aligned).
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ uint64_t cost_at(const EnumParams &P, int j, long long idx) {
+    if (idx < 0) return 0ull;
+    return __ldg(P.C + (long long)j * P.cs + idx) + P.W * __ldg(P.RT + (long long)j * P.cs + idx);
+}
+
+// Rank of the first row whose cumulative cost reaches `target` (clamped to
+// the total row count).
+__device__ uint64_t cost_to_rank(const EnumParams &P, uint64_t target, int lane) {
+    int rem = P.n;
+    uint64_t rank = 0;
+    if (target >= cost_at(P, 0, rem)) return __ldg(P.C + rem);
+    for (int j = 0; j < P.lam_r; ++j) {
+        const long long g = P.g[j];
+        const long long umax = rem / g;
+        const long long base = (long long)rem - (umax + 1) * g;
+        long long lo = 0, hi = umax + 1;
+        uint64_t flo = 0;
+        while (hi - lo > 1) {
+            const long long step = (hi - lo + 31) >> 5;
+            const long long u = lo + (long long)(lane + 1) * step;
+            bool ok = false;
+            uint64_t fu = 0;
+            if (u < hi) {
+                fu = cost_at(P, j, base + u * g);
+                ok = fu <= target;
+            }
+            const int cnt = __popc(__ballot_sync(FULL, ok));
+            const uint64_t fsel = shfl_u64(fu, cnt > 0 ? cnt - 1 : 0);
+            if (cnt > 0) {
+                flo = fsel;
+                lo += (long long)cnt * step;
+            }
+            const long long nh = lo + step;
+            if (nh < hi) hi = nh;
+        }
+        const long long idx = base + lo * g;
+        rank += idx >= 0 ? __ldg(P.C + (long long)j * P.cs + idx) : 0ull;
+        target -= flo;
+        rem = (int)(rem - (umax - lo) * g);
+    }
+    const uint64_t rows = __ldg(P.C + (long long)P.lam_r * P.cs + rem);
+    const uint64_t t = target > P.W ? target - P.W : 0ull;
+    return rank + (t < rows ? t : rows);
+}
+
+// Cumulative cost of everything before rank R.
+__device__ uint64_t rank_to_cost(const EnumParams &P, uint64_t R, int lane) {
+    int rem = P.n;
+    if (R >= __ldg(P.C + rem)) return cost_at(P, 0, rem);
+    uint64_t cost = 0;
+    for (int j = 0; j < P.lam_r; ++j) {
+        int v;
+        uint64_t before;
+        find_child(P, j, rem, R, lane, v, before);
+        cost += before + P.W * (rem - (long long)(v + 1) * P.g[j] >= 0
+                                    ? __ldg(P.RT + (long long)j * P.cs +
+                                            (rem - (long long)(v + 1) * P.g[j]))
+                                    : 0ull);
+        R -= before;
+        rem -= v * P.g[j];
+    }
+    return cost + P.W + R;
+}
+
 __device__ __forceinline__ void flush_rows(const EnumParams &P, const int32_t *src,
-                                           uint64_t out_row, uint32_t nrows, int lane,
+                                           uint64_t out_row, uint32_t nrows, int d, int lane,
                                            uint64_t pol) {
-    int32_t *gdst = P.out + out_row * (uint64_t)D;
-    const uint32_t words = nrows * (uint32_t)D;
+    int32_t *gdst = P.out + out_row * (uint64_t)d;
+    const uint32_t words = nrows * (uint32_t)d;
     if (P.aligned) {
         const uint32_t bytes = words * 4u;
         const uint32_t bulk = bytes & ~15u;
@@ -239,7 +323,311 @@ __device__ __forceinline__ void flush_rows(const EnumParams &P, const int32_t *s
     }
 }
 
-template <int D>
+// 4-byte global -> shared copy that does not hold a register (cp.async).
+__device__ __forceinline__ void cp_async4(int32_t *sdst, const int32_t *gsrc) {
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(smem_addr(sdst)), "l"(gsrc)
+                 : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() {
+    asm volatile("cp.async.commit_group;" ::: "memory");
+}
+template <int N>
+__device__ __forceinline__ void cp_async_wait() {
+    asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
+}
+
+// Rounds a completed ring half waits before its bulk store, so that the
+// cp.async copies of its last rows have landed without stalling the warp.
+constexpr int FLUSH_LAG = 2;
+
+// One work item: rows [row0, row1) of the output (relative to P.out),
+// produced by unranking row0 and walking from there.  D > 0: tuple width known
+// at compile time; D == 0: width P.d (at most FZ_MAX_D).  LAMF >= 0: every run
+// is a memo run at coordinate LAMF (full memo, k = D-1-LAMF) fixed at compile
+// time; LAMF < 0: generic (runtime run level, walk leaves).  Returns false if
+// a device-side consistency check failed (status already recorded).
+template <int D, int LAMF>
+__device__ __forceinline__ bool enum_slice(const EnumParams &P, WarpPath *wp, int32_t *ring,
+                                           uint32_t B, uint64_t row0, uint64_t row1,
+                                           uint64_t pol, int lane) {
+    constexpr int DM = D > 0 ? D : FZ_MAX_D;
+    const int d = D > 0 ? D : P.d;
+    const int g_last = P.g[d - 1];
+    constexpr int KF = LAMF >= 0 ? D - 1 - LAMF : 0;
+    uint32_t rows_left = (uint32_t)(row1 - row0);
+
+    RunState st;
+    bool ok;
+    uint64_t skip = unrank_to_leaf(P, wp, P.rank_begin + row0, lane, st, &ok);
+    if (!ok) {
+        if (lane == 0) atomicExch(P.status, (int)DEV_INTERNAL);
+        return false;
+    }
+
+    // ring: rows go to half `half` at position hpos; `nfull` halves of
+    // this slice are complete; a completed half is flushed FLUSH_LAG
+    // rounds later (pend_rounds counts them).
+    uint32_t hpos = 0, half = 0, nfull = 0, pend_rounds = 0;
+    bool pend = false;
+
+    int pre[DM];
+#pragma unroll
+    for (int c = 0; c < DM; ++c) pre[c] = (c < st.lam) ? wp->a[c] : 0;
+
+    while (rows_left > 0) {
+        const int lam = LAMF >= 0 ? LAMF : st.lam;
+        const int rem = wp->r[lam];
+        const int glam = P.g[lam];
+        const bool memo_run =
+            LAMF >= 0 ? true : ((P.lam_m >= 0) && !st.inwalk && lam == P.lam_m);
+        const long long vl = st.vcur - lane;
+        const bool valid = vl >= 0;
+        int p = 0;
+        uint64_t incl = 0;
+        int type = T_NONE;
+        if (valid) {
+            p = (int)((long long)rem - vl * glam);
+            if (p < 0 || p > P.n) {  // cannot happen for 0 <= vl <= rem / glam
+                atomicExch(P.status, (int)DEV_INTERNAL);
+                p = 0;
+            }
+            incl = __ldg(P.C + (long long)lam * P.cs + p);
+            if (memo_run && (LAMF >= 0 || p < P.top))
+                type = T_MEMO;
+            else if (lam == P.lam_w)
+                type = T_WALK;
+            else
+                type = T_INTERNAL;
+        }
+        uint64_t prev = __shfl_up_sync(FULL, incl, 1);
+        if (lane == 0) prev = st.base;
+        const uint64_t size = valid ? incl - prev : 0ull;
+        const unsigned im = __ballot_sync(FULL, type == T_INTERNAL && size > 0);
+        const int first_int = im ? __ffs(im) - 1 : 32;
+        const int nvalid = st.vcur + 1 < 32 ? (int)(st.vcur + 1) : 32;
+        const int consumed = first_int < nvalid ? first_int : nvalid;
+        const uint64_t last_incl = consumed > 0 ? shfl_u64(incl, consumed - 1) : st.base;
+        const uint64_t batch_rows = last_incl - st.base;
+        uint32_t E32 = CAP32, X32 = 0;
+        if (lane < consumed) {
+            const uint64_t e = incl - st.base;
+            E32 = e < (uint64_t)CAP32 ? (uint32_t)e : CAP32;
+            if (type == T_MEMO)
+                X32 = (uint32_t)__ldg(P.O + p);
+            else if (type == T_WALK)
+                X32 = (uint32_t)(p / g_last);
+        }
+        uint64_t q_end64 = skip + rows_left;
+        if (q_end64 > batch_rows) q_end64 = batch_rows;
+        const uint32_t q_begin = (uint32_t)skip;
+        const uint32_t q_end = (uint32_t)q_end64;
+        // ring bookkeeping after a round of cnt rows (both paths)
+        auto after_round = [&](uint32_t cnt) {
+            cp_async_commit();
+            hpos += cnt;
+            if (pend && ++pend_rounds >= (uint32_t)FLUSH_LAG) {
+                cp_async_wait<FLUSH_LAG>();
+                flush_rows(P, ring + (size_t)(half ^ 1u) * B * d,
+                              row0 + (uint64_t)(nfull - 1) * B, B, d, lane, pol);
+                pend = false;
+            }
+            if (hpos == B) {
+                if (pend) {  // (only if a half holds fewer than FLUSH_LAG rounds)
+                    cp_async_wait<0>();
+                    flush_rows(P, ring + (size_t)(half ^ 1u) * B * d,
+                                  row0 + (uint64_t)(nfull - 1) * B, B, d, lane, pol);
+                }
+                pend = true;
+                pend_rounds = 0;
+                ++nfull;
+                half ^= 1u;
+                hpos = 0;
+            }
+        };
+        auto before_round = [&]() {
+            if (hpos == 0 && nfull >= 2) {
+                // re-entering a half: its bulk store (the most recent bulk
+                // group) must have finished reading it
+                if (lane == 0) bulk_wait_read_all();
+                __syncwarp();
+            }
+        };
+        // Dense batches of memo leaves: rounds follow the leaves, so every
+        // lane of a round copies a row of the same leaf (no per-row search).
+        const bool all_memo = __all_sync(FULL, lane >= consumed || type == T_MEMO);
+        const bool dense =
+            memo_run && all_memo && consumed > 0 && batch_rows >= 16ull * (uint64_t)consumed;
+        if (dense && q_end > q_begin) {
+            const int lfirst = __popc(__ballot_sync(FULL, E32 <= q_begin));
+            for (int j = lfirst; j < consumed; ++j) {
+                const uint32_t ej = __shfl_sync(FULL, E32, j);
+                uint32_t sj = __shfl_sync(FULL, E32, j > 0 ? j - 1 : 0);
+                if (j == 0) sj = 0;
+                const uint32_t lo = sj > q_begin ? sj : q_begin;
+                const uint32_t hi = ej < q_end ? ej : q_end;
+                if (lo < hi) {
+                    const uint32_t xj = __shfl_sync(FULL, X32, j);
+                    const int vj = (int)(st.vcur - j);
+                    if ((uint64_t)xj + (hi - sj) > P.memo_rows) {  // bounds guard
+                        if (lane == 0) atomicExch(P.status, (int)DEV_INTERNAL);
+                        break;
+                    }
+                    const int kk = LAMF >= 0 ? KF : P.K;
+                    const int32_t *mbase = P.memo + (size_t)xj * (size_t)kk;
+                    for (uint32_t q0 = lo; q0 < hi;) {
+                        uint32_t cnt = hi - q0;
+                        if (cnt > 32u) cnt = 32u;
+                        if (cnt > B - hpos) cnt = B - hpos;
+                        before_round();
+                        if ((uint32_t)lane < cnt) {
+                            int32_t *dst = ring + (size_t)(half * B + hpos + lane) * d;
+                            const int32_t *mrow =
+                                mbase + (size_t)(q0 + lane - sj) * (size_t)kk;
+                            if constexpr (LAMF >= 0) {
+#pragma unroll
+                                for (int c = 0; c < LAMF; ++c) dst[c] = pre[c];
+                                dst[LAMF] = vj;
+#pragma unroll
+                                for (int c = 0; c < KF; ++c)
+                                    cp_async4(dst + LAMF + 1 + c, mrow + c);
+                            } else {
+#pragma unroll
+                                for (int c = 0; c < DM; ++c) {
+                                    if (c >= d)
+                                        break;
+                                    if (c < lam)
+                                        dst[c] = pre[c];
+                                    else if (c == lam)
+                                        dst[c] = vj;
+                                    else
+                                        cp_async4(dst + c, mrow + (c - lam - 1));
+                                }
+                            }
+                        }
+                        q0 += cnt;
+                        after_round(cnt);
+                    }
+                }
+                if (ej >= q_end) break;
+            }
+        } else {
+        for (uint32_t q0 = q_begin; q0 < q_end;) {
+            uint32_t cnt = q_end - q0;
+            if (cnt > 32u) cnt = 32u;
+            if (cnt > B - hpos) cnt = B - hpos;  // rounds never cross a half boundary
+            before_round();
+            const bool act = (uint32_t)lane < cnt;
+            const uint32_t q_last = q0 + cnt - 1;
+            const uint32_t q = act ? q0 + lane : q_last;  // idle lanes map a row of the round
+            // owning leaf of row q: l = number of leaves ending at or before q
+            const int lcur = __popc(__ballot_sync(FULL, E32 <= q0));
+            const int nb = __popc(__ballot_sync(FULL, E32 > q0 && E32 <= q_last));
+            int l = lcur;
+            if (nb <= 3) {
+                for (int t = 0; t < nb; ++t) {
+                    const uint32_t e = __shfl_sync(FULL, E32, lcur + t);
+                    if (e <= q) ++l;
+                }
+            } else {
+                l = 0;
+#pragma unroll
+                for (int sft = 16; sft >= 1; sft >>= 1) {
+                    const uint32_t e = __shfl_sync(FULL, E32, l + sft - 1);
+                    if (e <= q) l += sft;
+                }
+            }
+            uint32_t eprev = __shfl_sync(FULL, E32, l > 0 ? l - 1 : 0);
+            if (l == 0) eprev = 0;
+            const uint32_t o = q - eprev;
+            const int pl = __shfl_sync(FULL, p, l);
+            const uint32_t xl = __shfl_sync(FULL, X32, l);
+            const int vrow = (int)(st.vcur - l);
+            bool mleaf = memo_run && (LAMF >= 0 || pl < P.top);
+            if (act && mleaf && (uint64_t)xl + o >= P.memo_rows) {  // bounds guard
+                atomicExch(P.status, (int)DEV_INTERNAL);
+                mleaf = false;
+            }
+            if (act) {
+                int32_t *dst = ring + (size_t)(half * B + hpos + lane) * d;
+                if constexpr (LAMF >= 0) {
+#pragma unroll
+                    for (int c = 0; c < LAMF; ++c) dst[c] = pre[c];
+                    dst[LAMF] = vrow;
+                    const int32_t *mrow = P.memo + (size_t)(xl + o) * (size_t)KF;
+                    if (mleaf) {
+#pragma unroll
+                        for (int c = 0; c < KF; ++c) cp_async4(dst + LAMF + 1 + c, mrow + c);
+                    } else {
+#pragma unroll
+                        for (int c = 0; c < KF; ++c) dst[LAMF + 1 + c] = 0;
+                    }
+                } else {
+                    const int32_t *mrow =
+                        mleaf ? P.memo + (size_t)(xl + o) * (size_t)P.K : nullptr;
+#pragma unroll
+                    for (int c = 0; c < DM; ++c) {
+                        if (c >= d)
+                            break;
+                        if (c < lam)
+                            dst[c] = pre[c];
+                        else if (c == lam)
+                            dst[c] = vrow;
+                        else if (mleaf)
+                            cp_async4(dst + c, mrow + (c - lam - 1));
+                        else
+                            dst[c] = (int)xl;
+                    }
+                }
+            }
+            q0 += cnt;
+            after_round(cnt);
+        }
+        }
+        const uint32_t emitted = q_end > q_begin ? q_end - q_begin : 0u;
+        rows_left -= emitted;
+        if (rows_left == 0) break;
+        skip = 0;
+        if (first_int < nvalid) {
+            // the next child is a memo-level prefix beyond the memo: walk it
+            const int ve = (int)(st.vcur - first_int);
+            const int pe = rem - ve * glam;
+            if (lane == 0) {
+                wp->a[lam] = ve;
+                wp->r[lam + 1] = pe;
+            }
+            __syncwarp();
+            descend(P, wp, lam + 1, P.lam_w, lane);
+            st.lam = P.lam_w;
+            st.inwalk = 1;
+            st.vcur = wp->r[P.lam_w] / P.g[P.lam_w];
+            st.base = 0;
+        } else {
+            st.base = last_incl;
+            st.vcur -= consumed;
+            if (st.vcur < 0 && !advance(P, wp, lane, st)) {
+                if (lane == 0) atomicExch(P.status, (int)DEV_INTERNAL);
+                ok = false;
+                break;
+            }
+        }
+#pragma unroll
+        for (int c = 0; c < DM; ++c) pre[c] = (c < st.lam) ? wp->a[c] : 0;
+    }
+    cp_async_wait<0>();
+    if (pend)
+        flush_rows(P, ring + (size_t)(half ^ 1u) * B * d,
+                      row0 + (uint64_t)(nfull - 1) * B, B, d, lane, pol);
+    if (hpos > 0)
+        flush_rows(P, ring + (size_t)half * B * d, row0 + (uint64_t)nfull * B, hpos, d,
+                      lane, pol);
+    if (lane == 0) bulk_wait_read_all();
+    __syncwarp();
+    return ok;
+}
+
+// Rows are handed out as work items (equal-cost ranges when the runs table
+// is present, else equal-row ranges) from an atomic counter.
+template <int D, int LAMF>
 __global__ void __launch_bounds__(ENUM_THREADS, 2)
     fz_enum_kernel(const __grid_constant__ EnumParams P) {
     extern __shared__ __align__(128) unsigned char smem_raw[];
@@ -247,184 +635,153 @@ __global__ void __launch_bounds__(ENUM_THREADS, 2)
     const int wid = threadIdx.x >> 5;
     const uint32_t B = (uint32_t)P.half_rows;
     int32_t *ring = reinterpret_cast<int32_t *>(smem_raw) + (size_t)wid * 2 * B * D;
-    WarpPath *wp = reinterpret_cast<WarpPath *>(smem_raw + (size_t)ENUM_WARPS * 2 * B * D * 4) + wid;
+    WarpPath *wp =
+        reinterpret_cast<WarpPath *>(smem_raw + (size_t)ENUM_WARPS * 2 * B * D * 4) + wid;
     const uint64_t pol = policy_evict_first();
-    const int g_last = P.g[D - 1];
 
+    // cost range of the requested ranks (work-balanced slicing)
+    uint64_t cost_lo = 0, cost_hi = 0;
+    if (P.RT) {
+        cost_lo = rank_to_cost(P, P.rank_begin, lane);
+        cost_hi = rank_to_cost(P, P.rank_begin + P.nrows, lane);
+    }
     for (;;) {
         unsigned long long s = 0;
         if (lane == 0) s = atomicAdd(P.slice_counter, 1ull);
         s = __shfl_sync(FULL, s, 0);
-        if (s >= P.nslices) break;
-        const uint64_t row0 = s * P.slice_rows;  // relative to out
-        uint64_t left64 = P.nrows - row0;
-        uint32_t rows_left = (uint32_t)(left64 < P.slice_rows ? left64 : P.slice_rows);
-
-        RunState st;
-        bool ok;
-        uint64_t skip = unrank_to_leaf(P, wp, P.rank_begin + row0, lane, st, &ok);
-        if (!ok) {
-            if (lane == 0) atomicExch(P.status, (int)DEV_INTERNAL);
-            break;
+        uint64_t row0, row1;  // relative to out
+        if (P.RT) {
+            const uint64_t c0 = cost_lo + s * P.slice_cost;
+            if (c0 >= cost_hi) break;
+            const uint64_t c1 = c0 + P.slice_cost;
+            row0 = 0;
+            if (s > 0) {
+                const uint64_t r = cost_to_rank(P, c0, lane);
+                row0 = r > P.rank_begin ? ((r - P.rank_begin) & ~3ull) : 0ull;
+                if (row0 > P.nrows) row0 = P.nrows;
+            }
+            row1 = P.nrows;
+            if (c1 < cost_hi) {
+                const uint64_t r = cost_to_rank(P, c1, lane);
+                row1 = r > P.rank_begin ? ((r - P.rank_begin) & ~3ull) : 0ull;
+                if (row1 > P.nrows) row1 = P.nrows;
+            }
+            if (row1 <= row0) continue;
+        } else {
+            if (s >= P.nslices) break;
+            row0 = s * P.slice_rows;
+            row1 = row0 + P.slice_rows < P.nrows ? row0 + P.slice_rows : P.nrows;
         }
-
-        // ring bookkeeping: rows go to half `half` at position hpos; `nfull`
-        // halves of this slice have been flushed already
-        uint32_t hpos = 0, half = 0, nfull = 0;
-
-        int pre[D];
-#pragma unroll
-        for (int c = 0; c < D; ++c) pre[c] = (c < st.lam) ? wp->a[c] : 0;
-
-        while (rows_left > 0) {
-            const int lam = st.lam;
-            const int rem = wp->r[lam];
-            const int glam = P.g[lam];
-            const bool memo_run = (P.lam_m >= 0) && !st.inwalk && lam == P.lam_m;
-            const long long vl = st.vcur - lane;
-            const bool valid = vl >= 0;
-            int p = 0;
-            uint64_t incl = 0;
-            int type = T_NONE;
-            if (valid) {
-                p = (int)((long long)rem - vl * glam);
-                if (p < 0 || p > P.n) {  // cannot happen for 0 <= vl <= rem / glam
-                    atomicExch(P.status, (int)DEV_INTERNAL);
-                    p = 0;
-                }
-                incl = __ldg(P.C + (long long)lam * P.cs + p);
-                if (memo_run && p < P.top)
-                    type = T_MEMO;
-                else if (lam == P.lam_w)
-                    type = T_WALK;
-                else
-                    type = T_INTERNAL;
-            }
-            uint64_t prev = __shfl_up_sync(FULL, incl, 1);
-            if (lane == 0) prev = st.base;
-            const uint64_t size = valid ? incl - prev : 0ull;
-            const unsigned im = __ballot_sync(FULL, type == T_INTERNAL && size > 0);
-            const int first_int = im ? __ffs(im) - 1 : 32;
-            const int nvalid = st.vcur + 1 < 32 ? (int)(st.vcur + 1) : 32;
-            const int consumed = first_int < nvalid ? first_int : nvalid;
-            const uint64_t last_incl = consumed > 0 ? shfl_u64(incl, consumed - 1) : st.base;
-            const uint64_t batch_rows = last_incl - st.base;
-            uint32_t E32 = CAP32, X32 = 0;
-            if (lane < consumed) {
-                const uint64_t e = incl - st.base;
-                E32 = e < (uint64_t)CAP32 ? (uint32_t)e : CAP32;
-                if (type == T_MEMO)
-                    X32 = (uint32_t)__ldg(P.O + p);
-                else if (type == T_WALK)
-                    X32 = (uint32_t)(p / g_last);
-            }
-            // rows [skip, q_end) of this batch
-            uint64_t q_end64 = skip + rows_left;
-            if (q_end64 > batch_rows) q_end64 = batch_rows;
-            const uint32_t q_begin = (uint32_t)skip;
-            const uint32_t q_end = (uint32_t)q_end64;
-            for (uint32_t q0 = q_begin; q0 < q_end;) {
-                uint32_t cnt = q_end - q0;
-                if (cnt > 32u) cnt = 32u;
-                if (cnt > B - hpos) cnt = B - hpos;  // rounds never cross a half boundary
-                if (hpos == 0 && nfull >= 2) {
-                    // this half was last stored two flushes ago; the most recent
-                    // flush (the other half) may still be reading
-                    if (lane == 0) asm volatile("cp.async.bulk.wait_group.read 1;" ::: "memory");
-                    __syncwarp();
-                }
-                const bool act = (uint32_t)lane < cnt;
-                const uint32_t q = act ? q0 + lane : q_end - 1;
-                int l = 0;
-#pragma unroll
-                for (int sft = 16; sft >= 1; sft >>= 1) {
-                    const uint32_t e = __shfl_sync(FULL, E32, l + sft - 1);
-                    if (e <= q) l += sft;
-                }
-                uint32_t eprev = __shfl_sync(FULL, E32, l > 0 ? l - 1 : 0);
-                if (l == 0) eprev = 0;
-                const uint32_t o = q - eprev;
-                const int pl = __shfl_sync(FULL, p, l);
-                const uint32_t xl = __shfl_sync(FULL, X32, l);
-                const int vrow = (int)(st.vcur - l);
-                bool mleaf = memo_run && pl < P.top;
-                if (mleaf && (uint64_t)xl + o >= P.memo_rows) {  // bounds guard
-                    atomicExch(P.status, (int)DEV_INTERNAL);
-                    mleaf = false;
-                }
-                if (act) {
-                    int32_t *dst = ring + (size_t)(half * B + hpos + lane) * D;
-                    const int32_t *mrow = mleaf ? P.memo + (size_t)(xl + o) * (size_t)P.K : nullptr;
-                    int vals[D];
-#pragma unroll
-                    for (int c = 0; c < D; ++c) {
-                        int x;
-                        if (c < lam)
-                            x = pre[c];
-                        else if (c == lam)
-                            x = vrow;
-                        else if (mleaf)
-                            x = __ldg(mrow + (c - lam - 1));
-                        else
-                            x = (int)xl;
-                        vals[c] = x;
-                    }
-                    if constexpr ((D & 1) == 0) {
-#pragma unroll
-                        for (int c = 0; c < D; c += 2)
-                            *reinterpret_cast<int2 *>(dst + c) = make_int2(vals[c], vals[c + 1]);
-                    } else {
-#pragma unroll
-                        for (int c = 0; c < D; ++c) dst[c] = vals[c];
-                    }
-                }
-                hpos += cnt;
-                q0 += cnt;
-                if (hpos == B) {
-                    flush_rows<D>(P, ring + (size_t)half * B * D, row0 + (uint64_t)nfull * B, B,
-                                  lane, pol);
-                    ++nfull;
-                    half ^= 1u;
-                    hpos = 0;
-                }
-            }
-            const uint32_t emitted = q_end > q_begin ? q_end - q_begin : 0u;
-            rows_left -= emitted;
-            if (rows_left == 0) break;
-            skip = 0;
-            if (first_int < nvalid) {
-                // the next child is a memo-level prefix beyond the memo: walk it
-                const int ve = (int)(st.vcur - first_int);
-                const int pe = rem - ve * glam;
-                if (lane == 0) {
-                    wp->a[lam] = ve;
-                    wp->r[lam + 1] = pe;
-                }
-                __syncwarp();
-                descend(P, wp, lam + 1, P.lam_w, lane);
-                st.lam = P.lam_w;
-                st.inwalk = 1;
-                st.vcur = wp->r[P.lam_w] / P.g[P.lam_w];
-                st.base = 0;
-            } else {
-                st.base = last_incl;
-                st.vcur -= consumed;
-                if (st.vcur < 0 && !advance(P, wp, lane, st)) {
-                    if (lane == 0) atomicExch(P.status, (int)DEV_INTERNAL);
-                    break;
-                }
-            }
-#pragma unroll
-            for (int c = 0; c < D; ++c) pre[c] = (c < st.lam) ? wp->a[c] : 0;
-        }
-        if (hpos > 0)
-            flush_rows<D>(P, ring + (size_t)half * B * D, row0 + (uint64_t)nfull * B, hpos,
-                          lane, pol);
-        if (lane == 0) bulk_wait_read_all();
-        __syncwarp();
+        if (!enum_slice<D, LAMF>(P, wp, ring, B, row0, row1, pol, lane)) break;
     }
+    cp_async_wait<0>();
     if (lane == 0) bulk_wait_all();
     __syncwarp();
+}
+
+// ---------------------------------------------------------------------------
+// Many instances in one persistent launch.  Work items (instance, slice) are
+// numbered consecutively, instance i owning items [item0[i], item0[i+1]); a
+// warp takes the next item from an atomic counter, finds its instance by a
+// binary search over item0, copies that instance's parameters into its own
+// shared-memory slot (when it changes) and runs the same slice routine as the
+// single-instance kernel with the tuple width read at run time.
+// ---------------------------------------------------------------------------
+struct BatchEnumParams {
+    const EnumParams *inst;   // per-instance parameters; `out` holds a byte offset
+    int32_t *out_base;        // output base the offsets are added to
+    const uint64_t *item0;    // count + 1 prefix of work items
+    int count;
+    uint64_t nitems;
+    unsigned long long *item_counter;
+};
+
+constexpr size_t BATCH_RING_BYTES = RING_BYTES_PER_WARP;
+
+__global__ void __launch_bounds__(ENUM_THREADS, 2)
+    fz_enum_batch_kernel(const __grid_constant__ BatchEnumParams BP) {
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    const int lane = threadIdx.x & 31;
+    const int wid = threadIdx.x >> 5;
+    int32_t *ring = reinterpret_cast<int32_t *>(smem_raw + (size_t)wid * BATCH_RING_BYTES);
+    EnumParams *ep =
+        reinterpret_cast<EnumParams *>(smem_raw + (size_t)ENUM_WARPS * BATCH_RING_BYTES) + wid;
+    WarpPath *wp = reinterpret_cast<WarpPath *>(smem_raw + (size_t)ENUM_WARPS * BATCH_RING_BYTES +
+                                                ENUM_WARPS * sizeof(EnumParams)) +
+                   wid;
+    const uint64_t pol = policy_evict_first();
+    int cur = -1;
+    for (;;) {
+        unsigned long long item = 0;
+        if (lane == 0) item = atomicAdd(BP.item_counter, 1ull);
+        item = __shfl_sync(FULL, item, 0);
+        if (item >= BP.nitems) break;
+        // largest i with item0[i] <= item
+        int lo = 0, hi = BP.count;  // item0[lo] <= item < item0[hi]
+        while (hi - lo > 1) {
+            const int mid = (lo + hi) >> 1;
+            if (__ldg(BP.item0 + mid) <= item)
+                lo = mid;
+            else
+                hi = mid;
+        }
+        if (lo != cur) {
+            const uint32_t *src = reinterpret_cast<const uint32_t *>(BP.inst + lo);
+            uint32_t *dst = reinterpret_cast<uint32_t *>(ep);
+            for (int w = lane; w < (int)(sizeof(EnumParams) / 4); w += 32) dst[w] = __ldg(src + w);
+            __syncwarp();
+            if (lane == 0) {
+                int32_t *o = reinterpret_cast<int32_t *>(reinterpret_cast<char *>(BP.out_base) +
+                                                         reinterpret_cast<uintptr_t>(ep->out));
+                ep->out = o;
+                ep->aligned = ((uintptr_t)o & 15u) == 0;
+            }
+            __syncwarp();
+            cur = lo;
+        }
+        const EnumParams &P = *ep;
+        const uint64_t s = item - __ldg(BP.item0 + lo);
+        uint64_t row0, row1;
+        if (P.RT) {
+            const uint64_t cost_hi = cost_at(P, 0, P.n);
+            const uint64_t c0 = s * P.slice_cost;
+            if (c0 >= cost_hi) continue;
+            const uint64_t c1 = c0 + P.slice_cost;
+            row0 = 0;
+            if (s > 0) {
+                row0 = cost_to_rank(P, c0, lane) & ~3ull;
+                if (row0 > P.nrows) row0 = P.nrows;
+            }
+            row1 = P.nrows;
+            if (c1 < cost_hi) {
+                row1 = cost_to_rank(P, c1, lane) & ~3ull;
+                if (row1 > P.nrows) row1 = P.nrows;
+            }
+        } else {
+            row0 = s * P.slice_rows;
+            row1 = row0 + P.slice_rows < P.nrows ? row0 + P.slice_rows : P.nrows;
+        }
+        if (row1 <= row0) continue;
+        if (P.d == 1 || (P.K == P.d && P.top > P.n)) {
+            // a single block: d == 1 or the output is Memo[n] itself
+            if (P.d == 1) {
+                if (lane == 0 && row0 == 0) P.out[0] = P.n / P.g[0];
+            } else {
+                const uint64_t src0 = (__ldg(P.O + P.n) + row0) * (uint64_t)P.d;
+                for (uint64_t w = lane; w < (row1 - row0) * (uint64_t)P.d; w += 32)
+                    P.out[row0 * (uint64_t)P.d + w] = __ldg(P.memo + src0 + w);
+            }
+            continue;
+        }
+        if (!enum_slice<0, -1>(P, wp, ring, (uint32_t)P.half_rows, row0, row1, pol, lane)) break;
+    }
+    cp_async_wait<0>();
+    if (lane == 0) bulk_wait_all();
+    __syncwarp();
+}
+
+size_t enum_batch_smem_bytes() {
+    return (size_t)ENUM_WARPS * (BATCH_RING_BYTES + sizeof(EnumParams) + sizeof(WarpPath));
 }
 
 // Tuples of given ranks (one warp per rank).
@@ -504,20 +861,20 @@ static size_t enum_smem_bytes(int d) {
            (size_t)ENUM_WARPS * sizeof(WarpPath);
 }
 
-template <int D>
-static int launch_enum_d(const EnumParams &P, cudaStream_t s, int sms) {
+template <int D, int LAMF>
+static int launch_enum_dl(const EnumParams &P, cudaStream_t s, int sms) {
     const size_t smem = enum_smem_bytes(D);
     static bool attr_set[64] = {};
     int dev = 0;
     cudaGetDevice(&dev);
     if (dev < 64 && !attr_set[dev]) {
-        FZ_CUDA_TRY(cudaFuncSetAttribute(fz_enum_kernel<D>,
+        FZ_CUDA_TRY(cudaFuncSetAttribute(fz_enum_kernel<D, LAMF>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)smem));
         attr_set[dev] = true;
     }
     int per_sm = 0;
-    FZ_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fz_enum_kernel<D>,
+    FZ_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fz_enum_kernel<D, LAMF>,
                                                               ENUM_THREADS, smem));
     if (per_sm < 1) per_sm = 1;
     uint64_t want = (P.nslices + ENUM_WARPS - 1) / ENUM_WARPS;
@@ -525,10 +882,22 @@ static int launch_enum_d(const EnumParams &P, cudaStream_t s, int sms) {
     if (want < grid) grid = want;
     if (grid < 1) grid = 1;
     FZ_CUDA_TRY(cudaMemsetAsync(P.slice_counter, 0, sizeof(unsigned long long), s));
-    fz_enum_kernel<D><<<(unsigned)grid, ENUM_THREADS, smem, s>>>(P);
+    fz_enum_kernel<D, LAMF><<<(unsigned)grid, ENUM_THREADS, smem, s>>>(P);
     note_launch();
     FZ_CUDA_TRY(cudaGetLastError());
     return FZ_OK;
+}
+
+// Full memo of depth 2, 3 or 4: every run is a memo run at a fixed
+// coordinate; use the compile-time specialisation.  Otherwise generic.
+template <int D>
+static int launch_enum_d(const EnumParams &P, cudaStream_t s, int sms) {
+    const bool full = P.lam_m >= 0 && P.top > P.n;
+    const int K = P.K;
+    if (full && K == 2 && D >= 3) return launch_enum_dl<D, (D >= 3 ? D - 3 : 0)>(P, s, sms);
+    if (full && K == 3 && D >= 4) return launch_enum_dl<D, (D >= 4 ? D - 4 : 0)>(P, s, sms);
+    if (full && K == 4 && D >= 5) return launch_enum_dl<D, (D >= 5 ? D - 5 : 0)>(P, s, sms);
+    return launch_enum_dl<D, -1>(P, s, sms);
 }
 
 template <int D>
@@ -550,6 +919,9 @@ static EnumParams make_params(const EnumLaunch &L) {
     P.O = L.O;
     P.memo = L.memo;
     P.memo_rows = L.memo_rows;
+    P.RT = L.RT;
+    P.W = L.W;
+    P.lam_r = L.lam_r;
     P.status = L.status;
     P.slice_counter = L.slice_counter;
     P.n = L.n;
@@ -617,6 +989,14 @@ int launch_enumerate(const EnumLaunch &L, uint64_t rank_begin, uint64_t nrows, i
     slice_rows = (slice_rows + 3) & ~3ull;
     P.slice_rows = slice_rows;
     P.nslices = (nrows + slice_rows - 1) / slice_rows;
+    if (P.RT) {
+        // equal-cost work items; about as many as equal-row items would be
+        const uint64_t cost = L.total_cost ? L.total_cost : 1;
+        const uint64_t rows = L.total_rows ? L.total_rows : 1;
+        const double per_row = (double)cost / (double)rows;
+        uint64_t sc = (uint64_t)((double)slice_rows * per_row);
+        P.slice_cost = sc < 64 ? 64 : sc;
+    }
     P.half_rows = half_rows_for(L.d);
     FZ_DISPATCH_D(L.d, launch_enum_d, P, s, dp.sms);
 }
@@ -631,6 +1011,58 @@ int launch_unrank(const EnumLaunch &L, const uint64_t *ranks, uint64_t m, int32_
     if (L.d == 1 || (L.K == L.d && L.top > L.n))
         return set_error(FZ_EINVAL, "unrank: d == 1 or k == d has a single block; use enumerate");
     FZ_DISPATCH_D(L.d, launch_unrank_d, P, ranks, m, s);
+}
+
+size_t enum_params_bytes() { return sizeof(EnumParams); }
+
+// EnumParams of one batch instance (host-side image, copied to the device).
+void fill_batch_params(const EnumLaunch &L, int32_t *out, uint64_t count, uint64_t slice_rows,
+                       uint64_t slice_cost, void *dst) {
+    EnumParams P = make_params(L);
+    P.out = out;
+    P.rank_begin = 0;
+    P.nrows = count;
+    P.aligned = ((uintptr_t)out & 15u) == 0;
+    P.slice_rows = slice_rows < 4 ? 4 : ((slice_rows + 3) & ~3ull);
+    P.nslices = (count + P.slice_rows - 1) / P.slice_rows;
+    P.half_rows = half_rows_for(L.d);
+    P.slice_cost = slice_cost < 64 ? 64 : slice_cost;
+    memcpy(dst, &P, sizeof(P));
+}
+
+int launch_enumerate_batch(const void *params_dev, const uint64_t *item0_dev, int count,
+                           uint64_t nitems, unsigned long long *item_counter, int32_t *out_base,
+                           cudaStream_t s) {
+    if (nitems == 0) return FZ_OK;
+    DeviceProps dp;
+    int rc = device_props(&dp);
+    if (rc != FZ_OK) return rc;
+    const size_t smem = enum_batch_smem_bytes();
+    static bool attr_set[64] = {};
+    if (dp.device >= 0 && dp.device < 64 && !attr_set[dp.device]) {
+        FZ_CUDA_TRY(cudaFuncSetAttribute(fz_enum_batch_kernel,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        attr_set[dp.device] = true;
+    }
+    int per_sm = 0;
+    FZ_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fz_enum_batch_kernel,
+                                                              ENUM_THREADS, smem));
+    if (per_sm < 1) per_sm = 1;
+    uint64_t grid = (uint64_t)per_sm * dp.sms;
+    const uint64_t want = (nitems + ENUM_WARPS - 1) / ENUM_WARPS;
+    if (want < grid) grid = want;
+    BatchEnumParams BP;
+    BP.inst = static_cast<const EnumParams *>(params_dev);
+    BP.out_base = out_base;
+    BP.item0 = item0_dev;
+    BP.count = count;
+    BP.nitems = nitems;
+    BP.item_counter = item_counter;
+    FZ_CUDA_TRY(cudaMemsetAsync(item_counter, 0, sizeof(unsigned long long), s));
+    fz_enum_batch_kernel<<<(unsigned)grid, ENUM_THREADS, smem, s>>>(BP);
+    note_launch();
+    FZ_CUDA_TRY(cudaGetLastError());
+    return FZ_OK;
 }
 
 uint64_t default_slice_rows(uint64_t nrows, int sms) {

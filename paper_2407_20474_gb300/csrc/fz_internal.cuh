@@ -6,6 +6,7 @@
 #include <stdint.h>
 
 #include <string>
+#include <vector>
 
 #include "../../include/fz.h"
 
@@ -212,6 +213,33 @@ int launch_count_table_tmp(const int32_t *g, int d, int32_t n, uint64_t *table, 
 int launch_count_rolling(const int32_t *g, int d, int32_t n, uint64_t *a, uint64_t *b,
                          uint64_t *tmp, uint64_t **result, cudaStream_t s);
 
+// Batched strided scans (fz_count.cu): one row per job, CTA tasks per launch.
+struct ScanJob {
+    const uint64_t *in;  // row below (scan input)
+    uint64_t *out;       // row to write
+    int64_t len;         // entries in the row
+    int64_t g;           // stride
+    uint64_t *S;         // block sums (blocked jobs), else null
+    uint64_t *Sincl;     // their strided inclusive scan
+    int64_t slen;        // entries of S
+};
+enum ScanTaskKind : int {
+    TK_DIRECT = 0,  // chains [begin, end) of in -> out, one warp each
+    TK_BSUM = 1,    // block sums S[begin..end)
+    TK_SSCAN = 2,   // chains [begin, end) of S -> Sincl
+    TK_APPLY = 3,   // blocks [begin, end): out = carry + running sum
+    TK_DELTA = 4,   // out[begin..end) = [i == 0]
+    TK_ONES = 5     // out[begin..end) = 1
+};
+struct ScanTask {
+    int job;
+    int kind;
+    int64_t begin, end;
+};
+int launch_scan_tasks(const ScanJob *jobs, const ScanTask *tasks, int ntasks, cudaStream_t s);
+int64_t scan_direct_limit();  // chains up to this length are scanned directly
+int scan_block_rows();        // entries per block of a blocked scan
+
 // out[0] = 0, out[r + 1] = in[0] + ... + in[r] for r < len (saturating).
 int64_t exclusive_scan_tmp_words(int64_t len);
 int launch_exclusive_scan_tmp(const uint64_t *in, uint64_t *out, int64_t len, uint64_t *tmp,
@@ -230,6 +258,18 @@ struct MemoBuffers {
 // Gather map + batched copy-and-increment fill.  Asynchronous.
 int launch_memo_build(const int32_t *tail, int k, int32_t top, uint64_t rows,
                       const MemoBuffers &mb, cudaStream_t s);
+// Many small memos, one CTA each (fz_memo.cu).
+struct MemoJob {
+    const uint64_t *Ct;  // tail count table rows 0..k, stride cs (row 0: |Z(r, tail)|)
+    int64_t cs;
+    uint64_t *O;         // top + 1 offsets (written by the build)
+    int32_t *R;          // rows * k int32
+    uint64_t rows;       // expected row count (consistency check)
+    int top, k, b;
+    int t[FZ_MAX_D];
+};
+int launch_memo_sizes(const MemoJob *jobs, int njobs, uint64_t *rows_out, cudaStream_t s);
+int launch_memo_cta_build(const MemoJob *jobs, int njobs, int *status, cudaStream_t s);
 
 // Enumeration (fz_enum.cu).
 struct EnumLaunch {
@@ -242,12 +282,36 @@ struct EnumLaunch {
     unsigned long long *slice_counter = nullptr;
     int n = 0, d = 0, K = 0, top = 0;
     const int32_t *g = nullptr;    // host generators
+    // work-balanced slicing (optional): runs table rows 0..lam_r, the cost of
+    // one run in rows, and the totals over the whole set
+    const uint64_t *RT = nullptr;
+    uint64_t W = 0;
+    int lam_r = 0;
+    uint64_t total_cost = 0, total_rows = 0;
 };
+// Runs table: RT[lam][x] = 1, RT[j][x] = sum_t RT[j+1][x - t g_j] (fz_count.cu).
+int launch_runs_table(const int32_t *g, int lam, int32_t n, uint64_t *RT, uint64_t *tmp,
+                      cudaStream_t s);
 int launch_enumerate(const EnumLaunch &L, uint64_t rank_begin, uint64_t nrows, int32_t *out,
                      uint64_t slice_rows, cudaStream_t s);
 int launch_unrank(const EnumLaunch &L, const uint64_t *ranks, uint64_t m, int32_t *out,
                   cudaStream_t s);
 uint64_t default_slice_rows(uint64_t nrows, int sms);
+// Batched enumeration (fz_enum.cu): per-instance parameter images, then one
+// persistent launch over all work items.
+size_t enum_params_bytes();
+void fill_batch_params(const EnumLaunch &L, int32_t *out, uint64_t count, uint64_t slice_rows,
+                       uint64_t slice_cost, void *dst);
+int launch_enumerate_batch(const void *params_dev, const uint64_t *item0_dev, int count,
+                           uint64_t nitems, unsigned long long *item_counter, int32_t *out_base,
+                           cudaStream_t s);
+
+// Plans as seen by the batch and serve layers (fz_api.cu): the launch
+// description of a plan for an element n <= its n, and host copies of row 0
+// of its count table (n + 1 entries) and runs table (empty if none).
+int plan_launch_for(fz_plan_t plan, int32_t n, EnumLaunch *L);
+int plan_host_rows(fz_plan_t plan, uint64_t *count_row, std::vector<uint64_t> *runs_row,
+                   cudaStream_t s);
 
 // Largest memo the library builds (rows); keeps memo row indices in 32 bits.
 constexpr uint64_t MEMO_MAX_ROWS = 1ull << 30;

@@ -18,6 +18,9 @@
 // parallel copy-and-increment step (the kernel copyAndIncrementIndex of
 // Section 2.4), and batches are separated by a bounded grid barrier inside one
 // cooperative launch.  Empty batches need no barrier.
+#include <cstdlib>
+#include <cstring>
+
 #include "fz_internal.cuh"
 
 namespace fz {
@@ -113,6 +116,95 @@ __global__ void __launch_bounds__(THREADS) memo_fill_kernel(FillParams P) {
     }
 }
 
+// ---------------------------------------------------------------------------
+// Cluster variant: one thread-block cluster runs every batch.  Between
+// batches the CTAs meet at the hardware cluster barrier; the arrive and the
+// wait are split so that the gather-map entries of the next batch (which do
+// not depend on the current one) are loaded while the barrier completes.
+// Source rows written by other CTAs of the cluster are read from L2 (ld.cg).
+// ---------------------------------------------------------------------------
+constexpr int CL_THREADS = 1024;
+constexpr int CL_PF = 4;  // map entries prefetched per thread per batch
+
+__device__ __forceinline__ unsigned cluster_rank() {
+    unsigned r;
+    asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
+    return r;
+}
+
+__device__ __forceinline__ unsigned cluster_size() {
+    unsigned r;
+    asm volatile("mov.u32 %0, %%cluster_nctarank;" : "=r"(r));
+    return r;
+}
+
+__device__ __forceinline__ void cluster_arrive_release() {
+    asm volatile("barrier.cluster.arrive.release.aligned;" ::: "memory");
+}
+
+__device__ __forceinline__ void cluster_wait_acquire() {
+    asm volatile("barrier.cluster.wait.acquire.aligned;" ::: "memory");
+}
+
+__device__ __forceinline__ void fill_row(const FillParams &P, uint64_t R, uint64_t e,
+                                         uint64_t R0) {
+    const int k = P.k;
+    int32_t *dst = P.rows + R * k;
+    if (e == MAP_ZERO) {
+        for (int c = 0; c < k; ++c) dst[c] = 0;
+    } else if ((e >> 4) >= R0) {  // bounds guard: sources precede the batch
+        atomicExch(P.status, (int)DEV_INTERNAL);
+    } else {
+        const int inc = (int)(e & 15u);
+        const int32_t *src = P.rows + (e >> 4) * k;
+        for (int c = 0; c < k; ++c) {
+            int32_t v = ld_cg_s32(src + c);
+            dst[c] = v + (c == inc ? 1 : 0);
+        }
+    }
+}
+
+__global__ void __launch_bounds__(CL_THREADS, 1) memo_fill_cluster_kernel(FillParams P) {
+    const uint64_t tid = (uint64_t)cluster_rank() * blockDim.x + threadIdx.x;
+    const uint64_t nthreads = (uint64_t)cluster_size() * blockDim.x;
+    // batch 0 boundaries and map entries
+    uint64_t R0 = __ldg(P.O), R1 = __ldg(P.O + (P.b < P.top ? P.b : P.top));
+    uint64_t pf[CL_PF];
+#pragma unroll
+    for (int j = 0; j < CL_PF; ++j) {
+        const uint64_t R = R0 + tid + j * nthreads;
+        pf[j] = R < R1 ? __ldg(P.map + R) : 0ull;
+    }
+    for (int q = 0; q < P.nbatch; ++q) {
+        if (R1 != R0) {
+#pragma unroll
+            for (int j = 0; j < CL_PF; ++j) {
+                const uint64_t R = R0 + tid + j * nthreads;
+                if (R < R1) fill_row(P, R, pf[j], R0);
+            }
+            for (uint64_t R = R0 + tid + CL_PF * nthreads; R < R1; R += nthreads)
+                fill_row(P, R, __ldg(P.map + R), R0);
+        }
+        // next batch's boundaries and map entries (independent of this batch)
+        const bool more = q + 1 < P.nbatch;
+        uint64_t N0 = R1, N1 = R1;
+        if (more) {
+            int64_t m1 = (int64_t)(q + 2) * P.b;
+            if (m1 > P.top) m1 = P.top;
+            N1 = __ldg(P.O + m1);
+        }
+        if (R1 != R0 && more) cluster_arrive_release();
+#pragma unroll
+        for (int j = 0; j < CL_PF; ++j) {
+            const uint64_t R = N0 + tid + j * nthreads;
+            pf[j] = R < N1 ? __ldg(P.map + R) : 0ull;
+        }
+        if (R1 != R0 && more) cluster_wait_acquire();
+        R0 = N0;
+        R1 = N1;
+    }
+}
+
 int coop_grid(const void *kernel, int threads) {
     DeviceProps dp;
     if (device_props(&dp) != FZ_OK) return -1;
@@ -125,7 +217,151 @@ int coop_grid(const void *kernel, int threads) {
     return per_sm * dp.sms;
 }
 
+// One cluster of 16 CTAs (8 if 16 cannot be co-scheduled).  Returns
+// FZ_ECUDA without launching if no cluster shape fits.
+int launch_fill_cluster(FillParams fp, cudaStream_t s) {
+    static bool attr_set = false;
+    if (!attr_set) {
+        cudaFuncSetAttribute(memo_fill_cluster_kernel,
+                             cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+        attr_set = true;
+    }
+    for (int csize : {16, 8}) {
+        cudaLaunchConfig_t cfg = {};
+        cfg.gridDim = dim3(csize);
+        cfg.blockDim = dim3(CL_THREADS);
+        cfg.dynamicSmemBytes = 0;
+        cfg.stream = s;
+        cudaLaunchAttribute attr[1];
+        attr[0].id = cudaLaunchAttributeClusterDimension;
+        attr[0].val.clusterDim.x = csize;
+        attr[0].val.clusterDim.y = 1;
+        attr[0].val.clusterDim.z = 1;
+        cfg.attrs = attr;
+        cfg.numAttrs = 1;
+        int nclusters = 0;
+        if (cudaOccupancyMaxActiveClusters(&nclusters, memo_fill_cluster_kernel, &cfg) !=
+                cudaSuccess ||
+            nclusters < 1) {
+            cudaGetLastError();
+            continue;
+        }
+        cudaError_t e = cudaLaunchKernelEx(&cfg, memo_fill_cluster_kernel, fp);
+        if (e != cudaSuccess) return cuda_error(e, "memo fill (cluster) launch");
+        note_launch();
+        return FZ_OK;
+    }
+    return set_error(FZ_ECUDA, "memo fill: no cluster shape fits");
+}
+
+// ---------------------------------------------------------------------------
+// Many small memos at once (batched instances): one CTA per memo runs the
+// whole dynamic pass for it -- the offsets by a block-wide scan of the tail's
+// row counts, then the elementwise batches of b = min(tail) elements, each a
+// set of copy-and-increment steps incr_i(Z_{>=i}(m - t_i)) with warps over
+// elements and lanes over rows, separated by __syncthreads (all the data of
+// one memo stays inside one CTA, so CTA-scope ordering suffices).
+// ---------------------------------------------------------------------------
+constexpr int MB_THREADS = 256;
+
+__device__ uint64_t block_exclusive_scan(uint64_t v, uint64_t *smem_warp_sums,
+                                         uint64_t *total) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int nwarps = blockDim.x >> 5;
+    uint64_t incl = warp_incl_scan(v, lane);
+    if (lane == 31) smem_warp_sums[warp] = incl;
+    __syncthreads();
+    if (warp == 0) {
+        uint64_t x = lane < nwarps ? smem_warp_sums[lane] : 0ull;
+        uint64_t xi = warp_incl_scan(x, lane);
+        if (lane < nwarps) smem_warp_sums[lane] = xi - x;  // exclusive
+        if (lane == nwarps - 1) smem_warp_sums[32] = xi;
+    }
+    __syncthreads();
+    const uint64_t r = smem_warp_sums[warp] + incl - v;
+    *total = smem_warp_sums[32];
+    __syncthreads();
+    return r;
+}
+
+__global__ void __launch_bounds__(MB_THREADS) memo_sizes_kernel(const MemoJob *__restrict__ jobs,
+                                                                uint64_t *__restrict__ rows_out) {
+    __shared__ uint64_t sums[33];
+    const MemoJob J = jobs[blockIdx.x];
+    uint64_t acc = 0;
+    for (int r = threadIdx.x; r < J.top; r += blockDim.x) acc += __ldg(J.Ct + r);
+    uint64_t total;
+    block_exclusive_scan(acc, sums, &total);
+    if (threadIdx.x == 0) rows_out[blockIdx.x] = total;
+}
+
+__global__ void __launch_bounds__(MB_THREADS) memo_cta_build_kernel(const MemoJob *__restrict__ jobs,
+                                                                    int *status) {
+    __shared__ uint64_t sums[33];
+    const MemoJob J = jobs[blockIdx.x];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int nwarps = blockDim.x >> 5;
+    const int k = J.k;
+    // offsets: O[0] = 0, O[m+1] = O[m] + |Z(m, tail)| (chunked block scan)
+    uint64_t carry = 0;
+    for (int base = 0; base < J.top; base += blockDim.x) {
+        const int m = base + threadIdx.x;
+        const uint64_t v = m < J.top ? __ldg(J.Ct + m) : 0ull;
+        uint64_t tot;
+        const uint64_t ex = block_exclusive_scan(v, sums, &tot);
+        if (m < J.top) J.O[m] = carry + ex;
+        carry += tot;
+    }
+    if (threadIdx.x == 0) J.O[J.top] = carry;
+    __syncthreads();
+    if (carry != J.rows) {
+        if (threadIdx.x == 0) atomicExch(status, (int)DEV_INTERNAL);
+        return;
+    }
+    // elementwise batches of b elements
+    for (int m0 = 0; m0 < J.top; m0 += J.b) {
+        const int m1 = m0 + J.b < J.top ? m0 + J.b : J.top;
+        for (int m = m0 + warp; m < m1; m += nwarps) {
+            uint64_t dst = J.O[m];
+            if (m == 0) {
+                if (lane < k) J.R[lane] = 0;
+                continue;
+            }
+            for (int i = 0; i < k; ++i) {
+                const int src_m = m - J.t[i];
+                if (src_m < 0) continue;
+                const uint64_t len = __ldg(J.Ct + (int64_t)i * J.cs + src_m);
+                if (len == 0) continue;
+                const uint64_t src = J.O[src_m + 1] - len;  // suffix Z_{>=i}(src_m)
+                for (uint64_t r = lane; r < len; r += 32) {
+                    const int32_t *a = J.R + (src + r) * k;
+                    int32_t *b = J.R + (dst + r) * k;
+                    for (int c = 0; c < k; ++c) b[c] = a[c] + (c == i ? 1 : 0);
+                }
+                dst += len;
+            }
+        }
+        __syncthreads();
+    }
+}
+
 }  // namespace
+
+int launch_memo_sizes(const MemoJob *jobs, int njobs, uint64_t *rows_out, cudaStream_t s) {
+    if (njobs <= 0) return FZ_OK;
+    memo_sizes_kernel<<<njobs, MB_THREADS, 0, s>>>(jobs, rows_out);
+    note_launch();
+    FZ_CUDA_TRY(cudaGetLastError());
+    return FZ_OK;
+}
+
+int launch_memo_cta_build(const MemoJob *jobs, int njobs, int *status, cudaStream_t s) {
+    if (njobs <= 0) return FZ_OK;
+    memo_cta_build_kernel<<<njobs, MB_THREADS, 0, s>>>(jobs, status);
+    note_launch();
+    FZ_CUDA_TRY(cudaGetLastError());
+    return FZ_OK;
+}
 
 int launch_memo_build(const int32_t *tail, int k, int32_t top, uint64_t rows,
                       const MemoBuffers &mb, cudaStream_t s) {
@@ -164,6 +400,23 @@ int launch_memo_build(const int32_t *tail, int k, int32_t top, uint64_t rows,
     fp.k = k;
     fp.b = tmin;
     fp.nbatch = (int)(((int64_t)top + tmin - 1) / tmin);
+    // Batches small enough for one cluster run there (hardware barrier);
+    // larger ones use the whole GPU with the bounded grid barrier.
+    // variant: one cluster (hardware barrier, sources through L2) for batches
+    // of modest size, else the whole GPU with the bounded grid barrier;
+    // FZ_MEMO_FILL=cluster|grid forces one (tuning only)
+    static const int forced = [] {
+        const char *e = getenv("FZ_MEMO_FILL");
+        if (!e) return 0;
+        if (!strcmp(e, "cluster")) return 2;
+        if (!strcmp(e, "grid")) return 3;
+        return 0;
+    }();
+    const uint64_t avg_batch_rows = rows / (uint64_t)fp.nbatch;
+    if ((forced == 0 && avg_batch_rows <= (uint64_t)64 * 1024) || forced == 2) {
+        int rc = launch_fill_cluster(fp, s);
+        if (rc == FZ_OK) return rc;
+    }
     int grid = coop_grid((const void *)memo_fill_kernel, THREADS);
     if (grid <= 0) return set_error(FZ_ECUDA, "memo build: no cooperative occupancy");
     FZ_CUDA_TRY(cudaMemsetAsync(mb.bar, 0, sizeof(unsigned), s));

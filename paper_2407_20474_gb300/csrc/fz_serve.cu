@@ -1,0 +1,419 @@
+// fz_serve.cu -- a request loop that keeps generator sets resident on the
+// device and serves Z(n, g) queries with continuous batching.
+//
+// Registering a set builds its plan once (count table, runs table and memo
+// for every n up to n_max; the tables depend on the generators only) and
+// mirrors row 0 of its count and runs tables on the host, so the exact size
+// of any later query is known at submission without touching the device.
+// A background thread admits queued requests in arrival order whenever a
+// slot and enough output memory (exact bytes, from a first-fit arena carved
+// out of one device allocation) are free, and launches each admitted request
+// on the next of several streams: requests admitted while others run
+// overlap on the GPU.  Completion is recorded by a host callback on the
+// request's stream (cudaLaunchHostFunc), which frees the slot and stamps the
+// completion time; the output stays valid until the client releases it.
+#include <cuda_runtime.h>
+
+#include <atomic>
+#include <chrono>
+#include <condition_variable>
+#include <deque>
+#include <map>
+#include <mutex>
+#include <thread>
+#include <unordered_map>
+#include <vector>
+
+#include "fz_internal.cuh"
+
+struct fz_server_s;
+
+namespace fz {
+namespace {
+
+double now_s() {
+    using namespace std::chrono;
+    return duration<double>(steady_clock::now().time_since_epoch()).count();
+}
+
+// First-fit allocator over [0, size) with 256-byte granules and coalescing.
+class Arena {
+   public:
+    void init(uint64_t size) {
+        free_.clear();
+        size_ = size & ~255ull;
+        if (size_) free_[0] = size_;
+        used_ = 0;
+    }
+    bool alloc(uint64_t bytes, uint64_t *off) {
+        bytes = (bytes + 255) & ~255ull;
+        if (bytes == 0) bytes = 256;
+        for (auto it = free_.begin(); it != free_.end(); ++it) {
+            if (it->second >= bytes) {
+                *off = it->first;
+                const uint64_t rest = it->second - bytes;
+                const uint64_t at = it->first + bytes;
+                free_.erase(it);
+                if (rest) free_[at] = rest;
+                used_ += bytes;
+                return true;
+            }
+        }
+        return false;
+    }
+    void release(uint64_t off, uint64_t bytes) {
+        bytes = (bytes + 255) & ~255ull;
+        if (bytes == 0) bytes = 256;
+        used_ -= bytes;
+        auto it = free_.emplace(off, bytes).first;
+        auto next = std::next(it);
+        if (next != free_.end() && it->first + it->second == next->first) {
+            it->second += next->second;
+            free_.erase(next);
+        }
+        if (it != free_.begin()) {
+            auto prev = std::prev(it);
+            if (prev->first + prev->second == it->first) {
+                prev->second += it->second;
+                free_.erase(it);
+            }
+        }
+    }
+    uint64_t used() const { return used_; }
+    uint64_t size() const { return size_; }
+
+   private:
+    std::map<uint64_t, uint64_t> free_;
+    uint64_t size_ = 0, used_ = 0;
+};
+
+struct SetRec {
+    fz_plan_t plan = nullptr;
+    int d = 0;
+    int32_t n_max = 0;
+    std::vector<uint64_t> count_row;  // |Z(r)|, r = 0..n_max
+    std::vector<uint64_t> runs_row;   // runs under the root, r = 0..n_max (if any)
+};
+
+struct Req;
+
+struct CallbackCtx {
+    fz_server_s *srv;
+    Req *req;
+};
+
+struct Req {
+    uint64_t ticket = 0;
+    int set = 0;
+    int32_t n = 0;
+    uint64_t count = 0, bytes = 0, off = 0;
+    int slot = -1;
+    int status = FZ_SERVE_QUEUED;
+    bool has_mem = false;
+    double t_submit = 0, t_admit = 0, t_done = 0;
+    CallbackCtx cb;
+};
+
+}  // namespace
+}  // namespace fz
+
+using namespace fz;
+
+struct fz_server_s {
+    std::mutex mu;
+    std::condition_variable cv;       // wakes the server thread
+    std::condition_variable done_cv;  // wakes waiters
+    std::thread th;
+    bool stop = false;
+    int device = 0;
+    fz_serve_cfg_t cfg{};
+    std::vector<cudaStream_t> streams;
+    int next_stream = 0;
+    void *arena_base = nullptr;
+    Arena arena;
+    unsigned long long *counters = nullptr;  // one per slot
+    int *status = nullptr;
+    std::vector<int> free_slots;
+    std::vector<SetRec> sets;
+    std::deque<Req *> queue;
+    std::unordered_map<uint64_t, Req *> reqs;
+    uint64_t next_ticket = 1;
+    uint64_t admitted = 0, completed = 0;
+    int launch_error = FZ_OK;
+};
+
+namespace fz {
+namespace {
+
+void CUDART_CB on_done(void *p) {
+    CallbackCtx *c = static_cast<CallbackCtx *>(p);
+    fz_server_s *s = c->srv;
+    {
+        std::lock_guard<std::mutex> lk(s->mu);
+        c->req->t_done = now_s();
+        c->req->status = FZ_SERVE_DONE;
+        s->free_slots.push_back(c->req->slot);
+        c->req->slot = -1;
+        s->completed++;
+    }
+    s->cv.notify_one();
+    s->done_cv.notify_all();
+}
+
+// Enqueue one admitted request (called by the server thread, lock not held).
+int launch_request(fz_server_s *s, Req *r, cudaStream_t st) {
+    const SetRec &S = s->sets[r->set];
+    fz_plan_info_t info;
+    int rc = fz_plan_info(S.plan, &info);
+    if (rc != FZ_OK) return rc;
+    int32_t *out = reinterpret_cast<int32_t *>(static_cast<char *>(s->arena_base) + r->off);
+    if (r->count > 0) {
+        EnumLaunch L;
+        rc = plan_launch_for(S.plan, r->n, &L);
+        if (rc != FZ_OK) return rc;
+        L.slice_counter = s->counters + r->slot;
+        L.status = s->status;
+        if (L.RT) {
+            L.total_rows = r->count;
+            L.total_cost = r->count + L.W * S.runs_row[r->n];
+        }
+        DeviceProps dp;
+        rc = device_props(&dp);
+        if (rc != FZ_OK) return rc;
+        rc = launch_enumerate(L, 0, r->count, out, default_slice_rows(r->count, dp.sms), st);
+        if (rc != FZ_OK) return rc;
+    }
+    r->cb.srv = s;
+    r->cb.req = r;
+    FZ_CUDA_TRY(cudaLaunchHostFunc(st, on_done, &r->cb));
+    return FZ_OK;
+}
+
+void server_loop(fz_server_s *s) {
+    cudaSetDevice(s->device);
+    std::unique_lock<std::mutex> lk(s->mu);
+    while (!s->stop) {
+        // admit in arrival order while a slot and the exact output bytes are free
+        std::vector<std::pair<Req *, cudaStream_t>> go;
+        while (!s->queue.empty() && !s->free_slots.empty()) {
+            Req *r = s->queue.front();
+            uint64_t off = 0;
+            if (!s->arena.alloc(r->bytes, &off)) break;
+            s->queue.pop_front();
+            r->off = off;
+            r->has_mem = true;
+            r->slot = s->free_slots.back();
+            s->free_slots.pop_back();
+            r->status = FZ_SERVE_RUNNING;
+            r->t_admit = now_s();
+            s->admitted++;
+            go.push_back({r, s->streams[s->next_stream]});
+            s->next_stream = (s->next_stream + 1) % (int)s->streams.size();
+        }
+        if (!go.empty()) {
+            lk.unlock();
+            for (auto &x : go) {
+                int rc = launch_request(s, x.first, x.second);
+                if (rc != FZ_OK) {
+                    std::lock_guard<std::mutex> g2(s->mu);
+                    x.first->status = rc;
+                    x.first->t_done = now_s();
+                    s->free_slots.push_back(x.first->slot);
+                    x.first->slot = -1;
+                    s->launch_error = rc;
+                    s->done_cv.notify_all();
+                }
+            }
+            lk.lock();
+            continue;
+        }
+        s->cv.wait_for(lk, std::chrono::microseconds(200));
+    }
+}
+
+}  // namespace
+}  // namespace fz
+
+extern "C" {
+
+int fz_serve_create(const fz_serve_cfg_t *cfg, fz_server_t *srv) {
+    if (!cfg || !srv) return set_error(FZ_EINVAL, "null pointer");
+    if (cfg->flags != 0 || cfg->max_in_flight < 1 || cfg->streams < 1 || cfg->max_queue < 1)
+        return set_error(FZ_EINVAL, "serve config");
+    fz_server_s *s = new (std::nothrow) fz_server_s;
+    if (!s) return set_error(FZ_ENOMEM, "host allocation");
+    s->cfg = *cfg;
+    auto fail = [&](int rc) {
+        for (cudaStream_t st : s->streams) cudaStreamDestroy(st);
+        if (s->arena_base) cudaFree(s->arena_base);
+        if (s->counters) cudaFree(s->counters);
+        delete s;
+        return rc;
+    };
+    cudaError_t e = cudaGetDevice(&s->device);
+    if (e != cudaSuccess) return fail(cuda_error(e, "cudaGetDevice"));
+    uint64_t mem = cfg->memory_bytes;
+    if (mem == 0) {
+        size_t fr = 0, tot = 0;
+        cudaMemGetInfo(&fr, &tot);
+        mem = fr / 4;
+    }
+    e = cudaMalloc(&s->arena_base, mem);
+    if (e != cudaSuccess) return fail(cuda_error(e, "cudaMalloc (serve arena)"));
+    s->arena.init(mem);
+    e = cudaMalloc((void **)&s->counters, 256 + (size_t)cfg->max_in_flight * 8);
+    if (e != cudaSuccess) return fail(cuda_error(e, "cudaMalloc (serve counters)"));
+    s->status = reinterpret_cast<int *>(s->counters + cfg->max_in_flight);
+    cudaMemset(s->counters, 0, 256 + (size_t)cfg->max_in_flight * 8);
+    for (int i = 0; i < cfg->streams; ++i) {
+        cudaStream_t st;
+        e = cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking);
+        if (e != cudaSuccess) return fail(cuda_error(e, "cudaStreamCreate"));
+        s->streams.push_back(st);
+    }
+    for (int i = cfg->max_in_flight - 1; i >= 0; --i) s->free_slots.push_back(i);
+    s->th = std::thread(server_loop, s);
+    *srv = s;
+    return FZ_OK;
+}
+
+int fz_serve_register(fz_server_t s, const int32_t *g, int d, int32_t n_max, int32_t *set_id) {
+    if (!s || !set_id) return set_error(FZ_EINVAL, "null pointer");
+    SetRec rec;
+    rec.d = d;
+    rec.n_max = n_max;
+    fz_opts_t opt{FZ_AUTO, FZ_AUTO, 0, 0};
+    int rc = fz_plan_create(g, d, n_max, &opt, &rec.plan, s->streams[0]);
+    if (rc != FZ_OK) return rc;
+    rec.count_row.resize((size_t)n_max + 1);
+    rc = plan_host_rows(rec.plan, rec.count_row.data(), &rec.runs_row, s->streams[0]);
+    if (rc != FZ_OK) {
+        fz_plan_destroy(rec.plan);
+        return rc;
+    }
+    std::lock_guard<std::mutex> lk(s->mu);
+    s->sets.push_back(std::move(rec));
+    *set_id = (int32_t)s->sets.size() - 1;
+    return FZ_OK;
+}
+
+int fz_serve_submit(fz_server_t s, int32_t set_id, int32_t n, uint64_t *ticket) {
+    if (!s || !ticket) return set_error(FZ_EINVAL, "null pointer");
+    Req *r = nullptr;
+    {
+        std::lock_guard<std::mutex> lk(s->mu);
+        if (set_id < 0 || set_id >= (int32_t)s->sets.size())
+            return set_error(FZ_ENOTFOUND, "unknown generator set");
+        const SetRec &S = s->sets[set_id];
+        if (n < 0 || n > S.n_max) return set_error(FZ_EINVAL, "n outside [0, n_max] of the set");
+        if ((int)s->queue.size() >= s->cfg.max_queue) return set_error(FZ_EAGAIN, "queue full");
+        const uint64_t count = S.count_row[n];
+        uint64_t bytes = 0;
+        if (count == ~0ull || count > (~0ull / 4) / (uint64_t)S.d)
+            return set_error(FZ_EOVERFLOW, "output size");
+        bytes = count * (uint64_t)S.d * 4;
+        if (bytes > s->arena.size()) return set_error(FZ_ENOMEM, "larger than the output budget");
+        r = new (std::nothrow) Req;
+        if (!r) return set_error(FZ_ENOMEM, "host allocation");
+        r->ticket = s->next_ticket++;
+        r->set = set_id;
+        r->n = n;
+        r->count = count;
+        r->bytes = bytes;
+        r->t_submit = now_s();
+        s->reqs[r->ticket] = r;
+        s->queue.push_back(r);
+        *ticket = r->ticket;
+    }
+    s->cv.notify_one();
+    return FZ_OK;
+}
+
+static void fill_result(fz_server_t s, const Req *r, fz_result_t *out) {
+    out->status = r->status;
+    out->d = s->sets[r->set].d;
+    out->count = r->count;
+    out->rows_dev = r->status == FZ_SERVE_DONE
+                        ? reinterpret_cast<const int32_t *>(static_cast<char *>(s->arena_base) + r->off)
+                        : nullptr;
+    out->t_submit = r->t_submit;
+    out->t_admit = r->t_admit;
+    out->t_done = r->t_done;
+}
+
+int fz_serve_poll(fz_server_t s, uint64_t ticket, fz_result_t *res) {
+    if (!s || !res) return set_error(FZ_EINVAL, "null pointer");
+    std::lock_guard<std::mutex> lk(s->mu);
+    auto it = s->reqs.find(ticket);
+    if (it == s->reqs.end()) return set_error(FZ_ENOTFOUND, "unknown ticket");
+    fill_result(s, it->second, res);
+    return FZ_OK;
+}
+
+int fz_serve_wait(fz_server_t s, uint64_t ticket, int32_t timeout_ms, fz_result_t *res) {
+    if (!s || !res) return set_error(FZ_EINVAL, "null pointer");
+    std::unique_lock<std::mutex> lk(s->mu);
+    auto it = s->reqs.find(ticket);
+    if (it == s->reqs.end()) return set_error(FZ_ENOTFOUND, "unknown ticket");
+    Req *r = it->second;
+    auto pred = [&] { return r->status <= 0; };
+    if (timeout_ms < 0)
+        s->done_cv.wait(lk, pred);
+    else if (!s->done_cv.wait_for(lk, std::chrono::milliseconds(timeout_ms), pred))
+        return set_error(FZ_EAGAIN, "not done yet");
+    fill_result(s, r, res);
+    return FZ_OK;
+}
+
+int fz_serve_release(fz_server_t s, uint64_t ticket) {
+    if (!s) return set_error(FZ_EINVAL, "null pointer");
+    {
+        std::lock_guard<std::mutex> lk(s->mu);
+        auto it = s->reqs.find(ticket);
+        if (it == s->reqs.end()) return set_error(FZ_ENOTFOUND, "unknown ticket");
+        Req *r = it->second;
+        if (r->status > 0) return set_error(FZ_EAGAIN, "request still queued or running");
+        if (r->has_mem) s->arena.release(r->off, r->bytes);
+        s->reqs.erase(it);
+        delete r;
+    }
+    s->cv.notify_one();
+    return FZ_OK;
+}
+
+int fz_serve_stats(fz_server_t s, fz_serve_stats_t *st) {
+    if (!s || !st) return set_error(FZ_EINVAL, "null pointer");
+    std::lock_guard<std::mutex> lk(s->mu);
+    st->queued = s->queue.size();
+    st->admitted = s->admitted;
+    st->completed = s->completed;
+    st->bytes_in_use = s->arena.used();
+    st->bytes_budget = s->arena.size();
+    st->sets = (int32_t)s->sets.size();
+    st->last_error = s->launch_error;
+    return FZ_OK;
+}
+
+int fz_serve_destroy(fz_server_t s) {
+    if (!s) return set_error(FZ_EINVAL, "null pointer");
+    {
+        std::lock_guard<std::mutex> lk(s->mu);
+        s->stop = true;
+    }
+    s->cv.notify_all();
+    if (s->th.joinable()) s->th.join();
+    for (cudaStream_t st : s->streams) {
+        cudaStreamSynchronize(st);
+        cudaStreamDestroy(st);
+    }
+    int h = 0;
+    cudaMemcpy(&h, s->status, 4, cudaMemcpyDeviceToHost);
+    for (auto &kv : s->reqs) delete kv.second;
+    for (SetRec &r : s->sets) fz_plan_destroy(r.plan);
+    cudaFree(s->arena_base);
+    cudaFree(s->counters);
+    delete s;
+    return h ? set_error(FZ_EINTERNAL, "device-side check failed while serving") : FZ_OK;
+}
+
+}  // extern "C"

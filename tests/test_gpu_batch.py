@@ -1,0 +1,128 @@
+"""Batched enumeration: many instances in one persistent launch, compared
+with the oracle and with single-instance plans (identical bytes)."""
+import numpy as np
+import pytest
+
+import oracle
+from gpu_checks import check_sorted_solutions
+from paper_2407_20474_gb300 import workloads
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+CANARY = -7
+
+
+@pytest.fixture(scope="module")
+def fz():
+    import __graft_entry__
+    __graft_entry__.build()
+    import paper_2407_20474_gb300 as m
+    assert torch.cuda.is_available(), "GPU tests need CUDA"
+    torch.cuda.set_device(0)
+    return m
+
+
+def run_batch(fz, instances, **kw):
+    with fz.Batch(instances, **kw) as b:
+        out = torch.full((int(b.total_words) + 16,), CANARY, dtype=torch.int32, device="cuda")
+        b.enumerate(out)
+        b.sync()
+        host = out.cpu().numpy()
+        assert (host[int(b.total_words):] == CANARY).all()
+        segs = []
+        for i, (g, n) in enumerate(instances):
+            a, r = int(b.word_offsets[i]), int(b.rows[i])
+            segs.append(host[a:a + r * len(g)].reshape(r, len(g)))
+        return b, segs
+
+
+def small_instances(seed, count, max_rows=60_000):
+    rng = np.random.Generator(np.random.PCG64(seed))
+    out = [((3, 5, 7), 0), ((2, 4), 7), ((7,), 49), ((7,), 50), ((4, 4, 6), 40),
+           ((1, 1, 1, 1), 12), ((5, 8, 11, 14), 500)]
+    while len(out) < count:
+        g, n = workloads.random_small_instance(rng, max_d=8, max_g=60, max_n=3000)
+        if oracle.count(g, n) <= max_rows:
+            out.append((g, n))
+    return out
+
+
+def test_batch_matches_oracle(fz):
+    inst = small_instances(31, 160)
+    b, segs = run_batch(fz, inst)
+    for (g, n), got in zip(inst, segs):
+        assert np.array_equal(got, oracle.enumerate_desc(g, n)), (g, n)
+
+
+def test_batch_every_memo_depth(fz):
+    inst = [x for x in small_instances(32, 60) if len(x[0]) >= 4]
+    for k in (0, 1, 2, 3):
+        b, segs = run_batch(fz, inst, k=k)
+        for (g, n), got in zip(inst, segs):
+            assert np.array_equal(got, oracle.enumerate_desc(g, n)), (g, n, k)
+
+
+def test_batch_shared_tails_and_rebuild(fz):
+    rng = np.random.Generator(np.random.PCG64(33))
+    pool = [workloads.draw_generators(rng, int(rng.integers(3, 8)), 5, 60) for _ in range(6)]
+    inst = []
+    for _ in range(120):
+        g = pool[int(rng.integers(0, len(pool)))]
+        inst.append((g, int(rng.integers(0, 900))))
+    with fz.Batch(inst) as b:
+        assert b.memos <= len(pool)
+        out = torch.full((int(b.total_words) + 16,), CANARY, dtype=torch.int32, device="cuda")
+        first = None
+        for _ in range(3):
+            out.fill_(CANARY)
+            b.rebuild()
+            b.enumerate(out)
+            b.sync()
+            host = out.cpu().numpy()
+            if first is None:
+                first = host.copy()
+            assert np.array_equal(host, first)
+        for i, (g, n) in enumerate(inst):
+            a, r = int(b.word_offsets[i]), int(b.rows[i])
+            got = first[a:a + r * len(g)].reshape(r, len(g))
+            assert np.array_equal(got, oracle.enumerate_desc(g, n)), (g, n)
+
+
+def test_batch_equals_single_instance_plans(fz):
+    inst = []
+    for x in workloads.config4_instances(2, 48):
+        n = workloads.find_n(fz.fz_count_upto, x.g, min(x.target, 200_000), 64)
+        inst.append((x.g, n))
+    b, segs = run_batch(fz, inst)
+    for (g, n), got in zip(inst, segs):
+        c = fz.fz_count(g, n)
+        one = torch.full((c * len(g) + 8,), CANARY, dtype=torch.int32, device="cuda")
+        fz.fz_enumerate(g, n, one)
+        torch.cuda.synchronize()
+        ref = one[:c * len(g)].cpu().numpy().reshape(c, len(g))
+        assert np.array_equal(got, ref), (g, n)
+        assert c == oracle.count(g, n)
+
+
+def test_batch_config4_full(fz):
+    """4096 instances (d 3..8, generators in [2,300], |Z| log-uniform in
+    [1e2, 1e6]): every segment sorted and valid with the oracle's count on a
+    sample of instances, exact rows on the small ones."""
+    insts = workloads.config4_instances(2, 4096)
+    rng = np.random.Generator(np.random.PCG64(34))
+    inst = [(x.g, workloads.find_n(fz.fz_count_upto, x.g, x.target, 64)) for x in insts]
+    with fz.Batch(inst) as b:
+        out = torch.full((int(b.total_words) + 16,), CANARY, dtype=torch.int32, device="cuda")
+        b.enumerate(out)
+        b.sync()
+        assert bool((out[int(b.total_words):] == CANARY).all())
+        sample = set(int(x) for x in rng.integers(0, len(inst), size=200))
+        for i, (g, n) in enumerate(inst):
+            a, r = int(b.word_offsets[i]), int(b.rows[i])
+            rows = out[a:a + r * len(g)].view(r, len(g))
+            check_sorted_solutions(rows, g, n)
+            if i in sample:
+                assert r == oracle.count(g, n), (g, n)
+                if r <= 20_000:
+                    assert np.array_equal(rows.cpu().numpy(), oracle.enumerate_desc(g, n))

@@ -38,8 +38,12 @@ def run_enum(fz, g, n, rank_begin=0, rank_end=None, pad=16, offset_words=0, **kw
     buf = torch.full(((rows + pad) * d + offset_words,), CANARY, dtype=torch.int32,
                      device="cuda")
     view = buf[offset_words:]
-    written = fz.fz_enumerate(g, n, view, rank_begin=rank_begin,
-                              rank_end=rank_end, capacity_rows=rows + pad, **kw)
+    try:
+        written = fz.fz_enumerate(g, n, view, rank_begin=rank_begin,
+                                  rank_end=rank_end, capacity_rows=rows + pad, **kw)
+    except fz.FzError as e:
+        raise AssertionError("g=%s n=%d ranks=[%d,%s) %s: %s"
+                             % (g, n, rank_begin, rank_end, kw, e)) from e
     torch.cuda.synchronize()
     assert written == rows
     host = buf.cpu().numpy()

@@ -1,0 +1,121 @@
+"""Serving: requests over resident generator sets with continuous batching.
+Every result produced in the mix is byte-identical to the same query run
+alone (exact integer output: tolerance 0)."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2407_20474_gb300 import workloads
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def fz():
+    import __graft_entry__
+    __graft_entry__.build()
+    import paper_2407_20474_gb300 as m
+    assert torch.cuda.is_available(), "GPU tests need CUDA"
+    torch.cuda.set_device(0)
+    return m
+
+
+def rows_of(fz, res):
+    words = int(res.count) * int(res.d)
+    if words == 0:
+        return np.zeros((0, int(res.d)), dtype=np.int32)
+    t = torch.empty(words, dtype=torch.int32, device="cuda")
+    import ctypes
+    torch.cuda.synchronize()
+    src = int(res.rows_dev)
+    # copy the server-owned rows into a tensor (device to device)
+    cudart = torch.cuda.cudart()
+    cudart.cudaMemcpy(t.data_ptr(), src, words * 4, 3)  # cudaMemcpyDeviceToDevice
+    torch.cuda.synchronize()
+    return t.cpu().numpy().reshape(int(res.count), int(res.d))
+
+
+def alone(fz, g, n):
+    c = fz.fz_count(g, n)
+    out = torch.empty(max(c, 1) * len(g), dtype=torch.int32, device="cuda")
+    fz.fz_enumerate(g, n, out)
+    torch.cuda.synchronize()
+    return out[:c * len(g)].cpu().numpy().reshape(c, len(g))
+
+
+def test_mix_equals_alone(fz):
+    rng = np.random.Generator(np.random.PCG64(41))
+    sets = [workloads.draw_generators(rng, int(rng.integers(4, 8)), 5, 60) for _ in range(5)]
+    n_max = 700
+    with fz.Server(max_in_flight=16, streams=4) as srv:
+        ids = [srv.register(g, n_max) for g in sets]
+        reqs = []
+        for _ in range(150):
+            s = int(rng.integers(0, len(sets)))
+            n = int(rng.integers(0, n_max + 1))
+            reqs.append((s, n, srv.submit(ids[s], n)))
+        for s, n, t in reqs:
+            res = srv.wait(t, 60000)
+            assert res.status == fz.FZ_SERVE_DONE
+            assert res.t_submit <= res.t_admit <= res.t_done
+            got = rows_of(fz, res)
+            g = sets[s]
+            assert int(res.count) == oracle.count(g, n)
+            assert np.array_equal(got, alone(fz, g, n)), (g, n)
+            if res.count <= 20000:
+                assert np.array_equal(got, oracle.enumerate_desc(g, n))
+            srv.release(t)
+        st = srv.stats()
+        assert st.completed == len(reqs) and st.bytes_in_use == 0
+
+
+def test_admission_by_exact_bytes_and_queue_limit(fz):
+    g = (7, 9, 11, 13, 17)
+    n = 300
+    c = fz.fz_count(g, n)
+    size = c * len(g) * 4
+    budget = ((size + 255) // 256) * 256          # room for exactly one result
+    with fz.Server(memory_bytes=budget, max_in_flight=8, streams=2, max_queue=2) as srv:
+        sid = srv.register(g, 400)
+        t1 = srv.submit(sid, n)
+        r1 = srv.wait(t1, 60000)
+        assert r1.status == fz.FZ_SERVE_DONE
+        t2 = srv.submit(sid, n)                    # waits for memory: t1 not released
+        t3 = srv.submit(sid, n)
+        with pytest.raises(fz.FzError) as e:
+            srv.submit(sid, n)                     # queue holds two: full
+        assert e.value.status == fz.FZ_EAGAIN
+        assert srv.poll(t2).status == fz.FZ_SERVE_QUEUED
+        assert srv.stats().bytes_in_use <= budget
+        ref = rows_of(fz, r1)
+        srv.release(t1)                            # frees the bytes: t2 then t3 run
+        for t in (t2, t3):
+            r = srv.wait(t, 60000)
+            assert r.status == fz.FZ_SERVE_DONE
+            assert np.array_equal(rows_of(fz, r), ref)
+            srv.release(t)
+        with pytest.raises(fz.FzError) as e:
+            srv.submit(sid, 400)                   # larger than the whole budget
+        assert e.value.status == fz.FZ_ENOMEM
+        with pytest.raises(fz.FzError) as e:
+            srv.submit(sid, 401)                   # beyond the set's n_max
+        assert e.value.status == fz.FZ_EINVAL
+        with pytest.raises(fz.FzError) as e:
+            srv.poll(123456789)
+        assert e.value.status == fz.FZ_ENOTFOUND
+
+
+def test_config5_sets_large_requests(fz):
+    stream = workloads.config5_stream(3, n_sets=4, rate=2000.0, duration_s=0.05)
+    with fz.Server(max_in_flight=32, streams=8) as srv:
+        for g in stream.sets:
+            counts = fz.fz_count_upto(g, 4096)
+            n = int(np.argmax(counts >= 200_000)) if (counts >= 200_000).any() else 4096
+            sid = srv.register(g, n)
+            ts = [srv.submit(sid, m) for m in (n, n // 2, n - 1, 0)]
+            for m, t in zip((n, n // 2, n - 1, 0), ts):
+                r = srv.wait(t, 60000)
+                assert r.status == fz.FZ_SERVE_DONE
+                assert np.array_equal(rows_of(fz, r), alone(fz, g, m)), (g, m)
+                srv.release(t)
