@@ -51,6 +51,8 @@ def parse():
     ap.add_argument("--e2e-steps", type=int, default=2)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-graph", action="store_true",
+                    help="launch every step's kernels directly instead of replaying a graph")
     ap.add_argument("--k", type=int, default=-1, help="memo depth (default: autotune)")
     ap.add_argument("--slice-rows", type=int, default=0)
     ap.add_argument("--cpu-seconds", type=float, default=15.0,
@@ -58,6 +60,14 @@ def parse():
     ap.add_argument("--target", type=int, default=0,
                     help="|Z(n)| target of the workload (default 5e8; smaller values give "
                          "the small profiling case)")
+    ap.add_argument("--workload", choices=["single", "batch", "serve", "memo", "table1"],
+                    default="single",
+                    help="single: one large element (default line); batch: 4096 instances "
+                         "in one launch vs per-instance launches; serve: Poisson request "
+                         "stream over 64 resident sets; memo: dynamic build of all "
+                         "Z(0..1500); table1: the paper's Table 1 instances")
+    ap.add_argument("--serve-seconds", type=float, default=10.0)
+    ap.add_argument("--batch-count", type=int, default=4096)
     return ap.parse_args()
 
 
@@ -244,6 +254,30 @@ def run_ours(args):
     plan.sync()
     torch.cuda.synchronize()
 
+    # the step (count tables, memo build, enumeration: about 16 dependent
+    # launches) captured once as a CUDA graph and replayed
+    graph = None
+    if not args.no_graph:
+        try:
+            side = torch.cuda.Stream()
+            side.wait_stream(stream)
+            cg = torch.cuda.CUDAGraph()
+            with torch.cuda.stream(side):
+                plan.rebuild(stream=side)
+                plan.enumerate(out, stream=side)
+                side.synchronize()
+                before = fz.fz_kernel_launches()
+                with torch.cuda.graph(cg, stream=side):
+                    plan.rebuild(stream=side)
+                    plan.enumerate(out, stream=side)
+                kernels_per_step = fz.fz_kernel_launches() - before
+            torch.cuda.synchronize()
+            plan.sync()
+            graph = cg
+        except Exception as e:
+            graph = None
+            graph_error = str(e)[:200]
+
     K = max(args.steps, 1)
     evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
            for _ in range(K)]
@@ -257,18 +291,31 @@ def run_ours(args):
     if sampler:
         sampler.mark_start()
     start.record(stream)
-    for i in range(K):
-        step(evs[i])
+    if graph is not None:
+        for i in range(K):
+            graph.replay()
+    else:
+        for i in range(K):
+            step(evs[i])
     end.record(stream)
     torch.cuda.synchronize()
     if sampler:
         sampler.mark_end()
     barrier(pg, torch)
     launches = fz.fz_kernel_launches() - launches0
+    if graph is not None:
+        launches = kernels_per_step * K  # graph replays launch the captured kernels
     plan.sync()
     ms = start.elapsed_time(end)
     ms = max_over_ranks(pg, ms, torch)
-    enum_ms = statistics.mean(a.elapsed_time(b) for a, b in evs)
+    if graph is not None:
+        # enumeration-kernel time measured on separate (non-graph) steps
+        for i in range(min(K, 20)):
+            step(evs[i])
+        torch.cuda.synchronize()
+        enum_ms = statistics.mean(a.elapsed_time(b) for a, b in evs[:min(K, 20)])
+    else:
+        enum_ms = statistics.mean(a.elapsed_time(b) for a, b in evs)
     clocks = sampler.stop() if sampler else None
 
     value = world * K * count / (ms / 1e3)
@@ -317,6 +364,7 @@ def run_ours(args):
                        "k": plan.k, "top": plan.top, "memo_rows": plan.memo_rows,
                        "slice_rows": plan.slice_rows, "bytes_per_step": bytes_per_launch,
                        "parallelism": "replicas (one instance per GPU)",
+                       "cuda_graph": graph is not None,
                        "l2": "output %.1f GB per step >> 129 MB L2; count table and memo "
                              "rebuilt every step" % (bytes_per_launch / 1e9)},
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
@@ -375,10 +423,250 @@ def run_reference(args):
         pg.destroy_process_group()
 
 
+# ---------------------------------------------------------- other workloads
+def _gpu_env():
+    import torch
+    import __graft_entry__
+    __graft_entry__.build()
+    import paper_2407_20474_gb300 as fz
+    torch.cuda.set_device(0)
+    return torch, fz
+
+
+def _event_time(torch, fn, steps, warmup):
+    for _ in range(warmup):
+        fn()
+    torch.cuda.synchronize()
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record()
+    for _ in range(steps):
+        fn()
+    b.record()
+    torch.cuda.synchronize()
+    return a.elapsed_time(b) / steps
+
+
+def run_batch_workload(args):
+    """4096 instances (d 3..8, generators in [2,300], |Z| log-uniform in
+    [1e2,1e6]) in one persistent launch (the step -- batched counting tables,
+    memos and enumeration -- replayed as a captured CUDA graph), against the
+    same instances launched one plan at a time."""
+    torch, fz = _gpu_env()
+    from paper_2407_20474_gb300 import workloads
+    insts = workloads.config4_instances(2, args.batch_count)
+    inst = [(x.g, workloads.find_n(fz.fz_count_upto, x.g, x.target, 64)) for x in insts]
+    b = fz.Batch(inst)
+    out = torch.empty(int(b.total_words) + 16, dtype=torch.int32, device="cuda")
+    side = torch.cuda.Stream()
+    graph_ok = True
+    try:
+        cg = torch.cuda.CUDAGraph()
+        side.wait_stream(torch.cuda.current_stream())
+        with torch.cuda.stream(side):
+            b.rebuild(stream=side)
+            b.enumerate(out, stream=side)
+            side.synchronize()
+            with torch.cuda.graph(cg, stream=side):
+                b.rebuild(stream=side)
+                b.enumerate(out, stream=side)
+        torch.cuda.synchronize()
+        step = cg.replay
+    except Exception as e:  # capture unsupported: plain launches
+        graph_ok = False
+        graph_err = str(e)[:200]
+
+        def step():
+            b.rebuild()
+            b.enumerate(out)
+    ms = _event_time(torch, step, max(args.steps, 1), max(args.warmup, 1))
+    b.sync()
+    value = b.total_rows / (ms / 1e3)
+    # per-instance launches of the same instances
+    plans = [fz.Plan(gg, n) for gg, n in inst]
+    offs = [int(x) for x in b.word_offsets]
+
+    def per_instance():
+        for i, p in enumerate(plans):
+            if p.count:
+                p.rebuild()
+                p.enumerate(out[offs[i]:], capacity_rows=p.count)
+    steps_pi = max(1, min(args.steps, 5))
+    ms_pi = _event_time(torch, per_instance, steps_pi, 1)
+    for p in plans:
+        p.close()
+    rec = {"metric": "Factorizations/s, batched (4096 instances, one persistent launch)",
+           "value": value, "unit": UNIT, "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
+           "ms_per_step": ms, "higher_is_better": True, "dtype": "int32", "data": "synthetic",
+           "config": {"workload": "batched: %d instances, d uniform 3..8, generators uniform "
+                                  "[2,300] (distinct, gcd 1), |Z| log-uniform [1e2,1e6], "
+                                  "seed 2" % len(inst),
+                      "total_rows": b.total_rows, "memos": b.memos,
+                      "work_items": b.work_items, "cuda_graph": graph_ok,
+                      "per_instance_ms_per_step": ms_pi,
+                      "per_instance_value": b.total_rows / (ms_pi / 1e3),
+                      "speedup_vs_per_instance": ms_pi / ms}}
+    if not graph_ok:
+        rec["config"]["graph_error"] = graph_err
+    print(json.dumps(rec))
+
+
+def run_serve_workload(args):
+    """Open-loop Poisson stream (2000 req/s) of queries over 64 resident
+    generator sets (d 4..7, generators in [5,500]), |Z| log-uniform in
+    [1e3,1e7]; continuous batching against one-request-at-a-time serving."""
+    import threading
+    import numpy as np
+    torch, fz = _gpu_env()
+    from paper_2407_20474_gb300 import workloads
+    st = workloads.config5_stream(3, duration_s=args.serve_seconds)
+    # per set: counts up to the element of the largest target, then each
+    # request's n = the smallest element reaching its target
+    set_counts, n_of = [], np.zeros(len(st.targets), dtype=np.int64)
+    n_max = []
+    for g in st.sets:
+        nm = workloads.find_n(fz.fz_count_upto, g, int(st.targets.max()), 1024)
+        c = fz.fz_count_upto(g, nm).astype(np.float64)
+        set_counts.append(c)
+        n_max.append(nm)
+    for i, (s_i, t) in enumerate(zip(st.set_index, st.targets)):
+        c = set_counts[s_i]
+        n_of[i] = int(np.argmax(c >= t))
+
+    def replay(max_in_flight, streams):
+        srv = fz.Server(max_in_flight=max_in_flight, streams=streams)
+        ids = [srv.register(g, nm) for g, nm in zip(st.sets, n_max)]
+        tickets = [None] * len(n_of)
+        lat = np.zeros(len(n_of))
+        rows = np.zeros(len(n_of))
+        done_t = np.zeros(len(n_of))
+        sub_t = np.zeros(len(n_of))
+        ready = threading.Semaphore(0)
+
+        def drain():
+            for i in range(len(n_of)):
+                ready.acquire()
+                r = srv.wait(tickets[i], -1)
+                lat[i] = r.t_done - r.t_submit
+                rows[i] = r.count
+                done_t[i] = r.t_done
+                sub_t[i] = r.t_submit
+                srv.release(tickets[i])
+
+        th = threading.Thread(target=drain)
+        th.start()
+        t0 = time.perf_counter()
+        for i, (s_i, at) in enumerate(zip(st.set_index, st.arrivals_s)):
+            delay = t0 + at - time.perf_counter()
+            if delay > 0:
+                time.sleep(delay)
+            tickets[i] = srv.submit(ids[s_i], int(n_of[i]))
+            ready.release()
+        th.join()
+        srv.close()
+        span = done_t.max() - sub_t.min()
+        return {"p50_ms": 1e3 * float(np.percentile(lat, 50)),
+                "p99_ms": 1e3 * float(np.percentile(lat, 99)),
+                "mean_ms": 1e3 * float(lat.mean()),
+                "throughput": float(rows.sum() / span), "requests": int(len(n_of)),
+                "rows": float(rows.sum())}
+
+    cont = replay(64, 8)
+    serial = replay(1, 1)
+    rec = {"metric": "Served factorizations/s with p50/p99 latency (Poisson 2000 req/s)",
+           "value": cont["throughput"], "unit": UNIT, "n_gpus": 1, "higher_is_better": True,
+           "dtype": "int32", "data": "synthetic",
+           "p50_ms": cont["p50_ms"], "p99_ms": cont["p99_ms"],
+           "config": {"workload": "served: Poisson %.0f req/s for %.1f s over 64 resident sets "
+                                  "(d 4..7, generators [5,500], gcd 1), |Z| log-uniform "
+                                  "[1e3,1e7], seed 3" % (st.rate, st.duration_s),
+                      "continuous": cont, "serial_one_at_a_time": serial}}
+    print(json.dumps(rec))
+
+
+def run_memo_workload(args):
+    """Dynamic FactorizationsUpToElement build of all Z(0..1500) for d = 5
+    generators in [3,40] (seed 1): the full CSR, elementwise in batches of
+    min(g) elements."""
+    torch, fz = _gpu_env()
+    from paper_2407_20474_gb300 import workloads
+    g = workloads.config3_generators(1)
+    N = workloads.CONFIG3_N
+    rows = fz.fz_memo_rows(g, N + 1)
+    off = torch.zeros(N + 2, dtype=torch.int64, device="cuda")
+    buf = torch.empty(rows * len(g) + 16, dtype=torch.int32, device="cuda")
+    ts = []
+    for i in range(max(args.warmup, 1) + max(min(args.steps, 20), 1)):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        fz.fz_build_memo_into(g, N + 1, off, buf, rows)
+        torch.cuda.synchronize()
+        if i >= max(args.warmup, 1):
+            ts.append(time.perf_counter() - t0)
+    t = statistics.median(ts)
+    rec = {"metric": "Memo rows/s, dynamic build of all Z(0..N) (FactorizationsUpToElement)",
+           "value": rows / t, "unit": "rows/s", "n_gpus": 1, "higher_is_better": True,
+           "ms_per_step": 1e3 * t, "dtype": "int32", "data": "synthetic",
+           "config": {"workload": "d=5 generators %s (seed 1), N=%d" % (list(g), N),
+                      "rows": rows, "bytes_written": rows * len(g) * 4,
+                      "write_GBps": rows * len(g) * 4 / t / 1e9,
+                      "note": "host-timed call including its count table, offsets, "
+                              "gather map and batches"}}
+    print(json.dumps(rec))
+
+
+def run_table1_workload(args):
+    """The paper's Table 1 instances Z(n, first d of (13,37,38,40..45)) with
+    the paper's memo depth, timed end to end on the device (count table +
+    memo + enumeration, output resident), beside the paper's runtimes."""
+    torch, fz = _gpu_env()
+    from paper_2407_20474_gb300 import workloads
+    rows_out = []
+    table = [(3, 1, 100000, 2733), (3, 1, 200000, 7904), (3, 1, 300000, 16241),
+             (4, 2, 5000, 400), (4, 2, 10000, 420), (4, 2, 15000, 679),
+             (5, 2, 1000, 485), (5, 2, 3000, 1047), (5, 2, 5000, 2101), (5, 2, 10000, 7600),
+             (5, 3, 1000, 502), (5, 3, 3000, 702), (5, 3, 5000, 953),
+             (6, 3, 1000, 601), (6, 3, 3000, 1751), (6, 3, 5000, 6298),
+             (6, 4, 1000, 1155), (6, 4, 2000, 4079), (6, 4, 3000, 10640),
+             (7, 4, 1000, 1153), (7, 4, 1500, 2299), (7, 4, 2000, 5416),
+             (8, 4, 1000, 1659), (8, 4, 1500, 5736), (8, 4, 2000, 25165),
+             (9, 4, 500, 1326), (9, 4, 1000, 8202), (9, 4, 1500, 52694),
+             (9, 5, 500, 1129), (9, 5, 1000, 6018), (9, 5, 1500, 47513)]
+    for d, k, n, paper_ms in table:
+        g = workloads.TABLE1_GENERATORS[:d]
+        with fz.Plan(g, n, k=k) as p:
+            out = torch.empty(max(p.count, 1) * d, dtype=torch.int32, device="cuda")
+
+            def step():
+                p.rebuild()
+                p.enumerate(out)
+            ms = _event_time(torch, step, 5, 2)
+            p.sync()
+            rows_out.append({"d": d, "memo_dim": k, "n": n, "count": p.count, "ms": ms,
+                             "fact_per_s": p.count / (ms / 1e3),
+                             "paper_ms": paper_ms, "paper_fact_per_s": p.count / (paper_ms / 1e3)})
+    total = sum(r["count"] for r in rows_out)
+    ms = sum(r["ms"] for r in rows_out)
+    rec = {"metric": "Factorizations/s on the paper's Table 1 instances (paper's memo depth)",
+           "value": total / (ms / 1e3), "unit": UNIT, "n_gpus": 1, "higher_is_better": True,
+           "dtype": "int32", "data": "synthetic",
+           "config": {"workload": "Table 1: Z(n, first d of (13,37,38,40..45))", "rows": rows_out,
+                      "note": "paper: RTX 3080 + Ryzen 3900X, host-buffered output; here "
+                              "output resident in HBM"}}
+    print(json.dumps(rec))
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         run_reference(args)
+    elif args.workload == "batch":
+        run_batch_workload(args)
+    elif args.workload == "serve":
+        run_serve_workload(args)
+    elif args.workload == "memo":
+        run_memo_workload(args)
+    elif args.workload == "table1":
+        run_table1_workload(args)
     else:
         run_ours(args)
 

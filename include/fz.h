@@ -226,12 +226,12 @@ int fz_plan_destroy(fz_plan_t plan);
  * Batches: many instances Z(n_i, g_i) of possibly different d_i in one set
  * of launches -- batched counting tables, one memo per distinct tail shared
  * by the instances that have it (each built by the elementwise dynamic pass,
- * Sections 2.2-2.4, cut to a bounded number of element batches; larger
+ * Sections 2.2-2.4, cut to at most 512 element batches; larger
  * remainders take the ordinary next-candidate step, Section 3.1), and one
  * persistent enumeration launch over (instance, slice) work items.
  * Output: instance i's rows (d_i int32 each, descending lexicographic order)
- * start at word word_offsets[i] of the output buffer (multiples of 4 words,
- * so 16-byte aligned when the buffer is); word_offsets[count] is the total.
+ * start at word word_offsets[i] of the output buffer (multiples of 32 words,
+ * so 128-byte aligned when the buffer is); word_offsets[count] is the total.
  * ---------------------------------------------------------------------- */
 typedef struct fz_instance {
     const int32_t *g;  /* host generators, d of them */
@@ -338,6 +338,11 @@ int fz_serve_poll(fz_server_t srv, uint64_t ticket, fz_result_t *result);
  * timeout). */
 int fz_serve_wait(fz_server_t srv, uint64_t ticket, int32_t timeout_ms,
                   fz_result_t *result);
+/* Copy a finished request's rows into dst (host or device memory, at least
+ * count * d int32 words).  Synchronises `stream`.  Errors: FZ_ENOTFOUND,
+ * FZ_EAGAIN (not done), FZ_ENOSPC (capacity_words too small), FZ_ECUDA. */
+int fz_serve_copy(fz_server_t srv, uint64_t ticket, int32_t *dst, uint64_t capacity_words,
+                  void *stream);
 /* Free a finished request's output (FZ_EAGAIN while queued or running). */
 int fz_serve_release(fz_server_t srv, uint64_t ticket);
 int fz_serve_stats(fz_server_t srv, fz_serve_stats_t *stats);
@@ -354,9 +359,10 @@ int fz_enumerate(const int32_t *g, int d, int32_t n, const fz_opts_t *opt,
                  uint64_t rank_begin, uint64_t rank_end, int32_t *out_dev,
                  uint64_t out_capacity_rows, uint64_t *written, void *stream);
 
-/* As fz_enumerate, but out_host is host memory (pinned memory is fastest).
- * The rows are produced on the device in chunks and copied back while the
- * next chunk is produced.  Synchronises. */
+/* As fz_enumerate, but out_host is host memory.  Page-locked (pinned,
+ * mapped) memory is written by the enumeration kernel itself over the host
+ * link; pageable memory gets the rows in device chunks that are copied back
+ * while the next chunks are produced.  Synchronises. */
 int fz_enumerate_host(const int32_t *g, int d, int32_t n, const fz_opts_t *opt,
                       uint64_t rank_begin, uint64_t rank_end, int32_t *out_host,
                       uint64_t out_capacity_rows, uint64_t *written,

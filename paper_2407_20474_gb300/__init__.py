@@ -46,7 +46,7 @@ EXPORTS = (
     "fz_batch_create", "fz_batch_info", "fz_batch_layout", "fz_batch_rebuild",
     "fz_batch_enumerate", "fz_batch_sync", "fz_batch_destroy", "fz_enumerate_batch",
     "fz_serve_create", "fz_serve_register", "fz_serve_submit", "fz_serve_poll",
-    "fz_serve_wait", "fz_serve_release", "fz_serve_stats", "fz_serve_destroy",
+    "fz_serve_wait", "fz_serve_copy", "fz_serve_release", "fz_serve_stats", "fz_serve_destroy",
 )
 
 
@@ -160,6 +160,7 @@ _SIGS = {
     "fz_serve_poll": (ctypes.c_int, [_P, ctypes.c_uint64, ctypes.POINTER(fz_result_t)]),
     "fz_serve_wait": (ctypes.c_int, [_P, ctypes.c_uint64, ctypes.c_int32,
                                      ctypes.POINTER(fz_result_t)]),
+    "fz_serve_copy": (ctypes.c_int, [_P, ctypes.c_uint64, _P, ctypes.c_uint64, _P]),
     "fz_serve_release": (ctypes.c_int, [_P, ctypes.c_uint64]),
     "fz_serve_stats": (ctypes.c_int, [_P, ctypes.POINTER(fz_serve_stats_t)]),
     "fz_serve_destroy": (ctypes.c_int, [_P]),
@@ -541,6 +542,13 @@ class Server:
         r = fz_result_t()
         _check(lib().fz_serve_wait(self._h, int(ticket), int(timeout_ms), ctypes.byref(r)))
         return r
+
+    def copy(self, ticket: int, dst, capacity_words: Optional[int] = None, stream=None):
+        """Copy a finished result into ``dst`` (torch tensor, host or device)."""
+        if capacity_words is None:
+            capacity_words = dst.numel() if hasattr(dst, "numel") else 0
+        _check(lib().fz_serve_copy(self._h, int(ticket), _ptr(dst), int(capacity_words),
+                                   _stream(stream)))
 
     def release(self, ticket: int):
         _check(lib().fz_serve_release(self._h, int(ticket)))

@@ -157,13 +157,13 @@ namespace {
 
 size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
 
-// Work of one run of sibling leaves (an advance of the walk), in rows; the
+// Work of one leaf candidate of the walk, in rows; the
 // environment variable FZ_RUN_COST overrides it (tuning only).
 uint64_t run_cost_rows() {
     static uint64_t w = [] {
         const char *e = getenv("FZ_RUN_COST");
         long long v = e ? atoll(e) : 0;
-        return v > 0 ? (uint64_t)v : (uint64_t)512;
+        return v > 0 ? (uint64_t)v : (uint64_t)16;
     }();
     return w;
 }
@@ -309,7 +309,9 @@ int plan_create_impl(const int32_t *g, int d, int32_t n, const fz_opts_t *opt, f
     const bool single_block = d == 1 || (p->K == d && p->top > n);
     if (!single_block && p->count > 0) {
         const bool memo = p->K >= 1 && p->K <= d - 1 && p->top > 0;
-        p->lam_r = memo ? d - p->K - 1 : d - 2;
+        // one past the leaf coordinate; with a partial memo most leaves may be
+        // walk leaves, so count candidates at the walk level then
+        p->lam_r = (memo && p->top > n ? d - p->K - 1 : d - 2) + 1;
         p->W = run_cost_rows();
         rc = p->runs.alloc((size_t)(p->lam_r + 1) * cs * 8);
         if (rc != FZ_OK) return rc;
@@ -723,51 +725,68 @@ int fz_enumerate_host(const int32_t *g, int d, int32_t n, const fz_opts_t *opt,
         return rc;
     }
     cudaStream_t s = as_stream(stream);
-    // two device chunks: enumerate chunk i while chunk i-1 is copied back
-    const uint64_t chunk = std::min<uint64_t>(rows, std::max<uint64_t>(1ull << 20,
-                                                  (256ull << 20) / (4ull * d)));
-    DevBuf bufs;
-    rc = bufs.alloc(2 * align256(chunk * (size_t)d * 4));
-    cudaStream_t copy = nullptr;
-    cudaEvent_t made[2] = {nullptr, nullptr}, copied[2] = {nullptr, nullptr};
-    if (rc == FZ_OK && cudaStreamCreateWithFlags(&copy, cudaStreamNonBlocking) != cudaSuccess)
-        rc = set_error(FZ_ECUDA, "stream create");
-    for (int i = 0; i < 2 && rc == FZ_OK; ++i) {
-        if (cudaEventCreateWithFlags(&made[i], cudaEventDisableTiming) != cudaSuccess ||
-            cudaEventCreateWithFlags(&copied[i], cudaEventDisableTiming) != cudaSuccess)
-            rc = set_error(FZ_ECUDA, "event create");
+    // Pinned (page-locked, mapped) host memory is written by the kernel
+    // itself over the host link: no staging buffer, no copy.
+    cudaPointerAttributes attr;
+    if (cudaPointerGetAttributes(&attr, out_host) == cudaSuccess &&
+        attr.type == cudaMemoryTypeHost && attr.devicePointer) {
+        EnumLaunch L = launch_of(p);
+        L.plain_stores = true;
+        rc = launch_enumerate(L, rank_begin, rows, static_cast<int32_t *>(attr.devicePointer),
+                              p->slice_rows, s);
+        if (rc == FZ_OK) rc = fz_plan_sync(p, stream);
+        fz_plan_destroy(p);
+        return rc;
     }
-    const size_t half = align256(chunk * (size_t)d * 4);
+    cudaGetLastError();  // pageable memory: the query above may have set an error
+    // Pageable host memory: device chunks, enumerate chunk i while the
+    // previous ones are copied back on NCOPY copy streams.
+    constexpr int NBUF = 3;
+    const uint64_t chunk = std::min<uint64_t>(rows, std::max<uint64_t>(1ull << 20,
+                                                  (512ull << 20) / (4ull * d)));
+    const size_t cbytes = align256(chunk * (size_t)d * 4);
+    DevBuf bufs;
+    rc = bufs.alloc(NBUF * cbytes);
+    cudaStream_t copy[NBUF] = {};
+    cudaEvent_t made[NBUF] = {}, copied[NBUF] = {};
+    for (int i = 0; i < NBUF && rc == FZ_OK; ++i) {
+        if (cudaStreamCreateWithFlags(&copy[i], cudaStreamNonBlocking) != cudaSuccess ||
+            cudaEventCreateWithFlags(&made[i], cudaEventDisableTiming) != cudaSuccess ||
+            cudaEventCreateWithFlags(&copied[i], cudaEventDisableTiming) != cudaSuccess)
+            rc = set_error(FZ_ECUDA, "stream/event create");
+    }
     uint64_t done = 0;
     int i = 0;
     while (rc == FZ_OK && done < rows) {
+        const int k = i % NBUF;
         const uint64_t now = std::min(chunk, rows - done);
-        int32_t *dbuf = reinterpret_cast<int32_t *>(bufs.as<char>() + (size_t)(i & 1) * half);
-        if (i >= 2 && cudaStreamWaitEvent(s, copied[i & 1], 0) != cudaSuccess) {
+        int32_t *dbuf = reinterpret_cast<int32_t *>(bufs.as<char>() + (size_t)k * cbytes);
+        if (i >= NBUF && cudaStreamWaitEvent(s, copied[k], 0) != cudaSuccess) {
             rc = set_error(FZ_ECUDA, "stream wait");
             break;
         }
         uint64_t w = 0;
         rc = fz_plan_enumerate(p, rank_begin + done, rank_begin + done + now, dbuf, now, &w, s);
         if (rc != FZ_OK) break;
-        if (cudaEventRecord(made[i & 1], s) != cudaSuccess ||
-            cudaStreamWaitEvent(copy, made[i & 1], 0) != cudaSuccess ||
+        if (cudaEventRecord(made[k], s) != cudaSuccess ||
+            cudaStreamWaitEvent(copy[k], made[k], 0) != cudaSuccess ||
             cudaMemcpyAsync(out_host + done * (uint64_t)d, dbuf, now * (size_t)d * 4,
-                            cudaMemcpyDeviceToHost, copy) != cudaSuccess ||
-            cudaEventRecord(copied[i & 1], copy) != cudaSuccess) {
+                            cudaMemcpyDeviceToHost, copy[k]) != cudaSuccess ||
+            cudaEventRecord(copied[k], copy[k]) != cudaSuccess) {
             rc = set_error(FZ_ECUDA, "chunk copy");
             break;
         }
         done += now;
         ++i;
     }
-    if (copy) cudaStreamSynchronize(copy);
+    for (int j = 0; j < NBUF; ++j)
+        if (copy[j]) cudaStreamSynchronize(copy[j]);
     if (rc == FZ_OK) rc = fz_plan_sync(p, stream);
-    for (int j = 0; j < 2; ++j) {
+    for (int j = 0; j < NBUF; ++j) {
         if (made[j]) cudaEventDestroy(made[j]);
         if (copied[j]) cudaEventDestroy(copied[j]);
+        if (copy[j]) cudaStreamDestroy(copy[j]);
     }
-    if (copy) cudaStreamDestroy(copy);
     fz_plan_destroy(p);
     return rc;
 }

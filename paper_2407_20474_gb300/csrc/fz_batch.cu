@@ -43,7 +43,7 @@ size_t a256(size_t x) { return (x + 255) & ~size_t(255); }
 
 // Elementwise batches a batch memo may take (its top is cut to this many
 // batches of min(tail) elements; larger remainders take the ordinary step).
-constexpr int64_t BATCH_MEMO_BATCHES = 64;
+constexpr int64_t BATCH_MEMO_BATCHES = 512;
 constexpr double BATCH_MEMO_MAX_ROWS = 1 << 20;
 
 struct Inst {
@@ -64,7 +64,7 @@ using namespace fz;
 struct fz_batch_s {
     int count = 0;
     std::vector<Inst> inst;
-    uint64_t W = 512;
+    uint64_t W = 16;
     DevArena tables;   // all count and runs tables
     DevArena scratch;  // block sums of blocked scans
     DevArena memos;    // memo offsets and rows
@@ -291,12 +291,14 @@ int fz_batch_create(const fz_instance_t *inst, int count, const fz_opts_t *opt,
         }
         if (opt && opt->top != FZ_AUTO && I.K > 0) I.top = std::min(I.top, opt->top);
         if (I.K > 0 && I.top <= 0) I.K = 0;
+        if (I.K == 0) I.top = 0;
         const size_t len = (size_t)I.n + 1;
         I.off_C = words;
         words += (size_t)(I.d + 1) * len;
         I.off_RT = (size_t)-1;
         if (I.d >= 2) {
-            I.lam_r = I.K > 0 ? I.d - I.K - 1 : I.d - 2;
+            // one past the leaf coordinate (the walk level when the memo is partial)
+            I.lam_r = (I.K > 0 && I.top > I.n ? I.d - I.K - 1 : I.d - 2) + 1;
             I.off_RT = words;
             words += (size_t)(I.lam_r + 1) * len;
         } else {
@@ -458,7 +460,7 @@ int fz_batch_create(const fz_instance_t *inst, int count, const fz_opts_t *opt,
         I.count = cnt[i];
         if (I.count == ~0ull) return fail(set_error(FZ_EOVERFLOW, "|Z(n)| does not fit"));
         I.runs = runs[i];
-        word = (word + 3) & ~3ull;  // 16-byte aligned start of every instance
+        word = (word + 31) & ~31ull;  // every instance starts on a 128-byte line
         I.word_off = word;
         word += I.count * (uint64_t)I.d;
         b->total_rows += I.count;

@@ -37,8 +37,26 @@ namespace fz {
 
 constexpr int ENUM_WARPS = 8;
 constexpr int ENUM_THREADS = ENUM_WARPS * 32;
-constexpr int RING_BYTES_PER_WARP = 12 * 1024;  // two halves
+constexpr int RING_BYTES_PER_WARP = 6 * 1024;  // two halves; 4 CTAs of 8 warps per SM
 constexpr uint32_t CAP32 = 0xffffffffu;
+
+// Division and remainder of a 32-bit value by a fixed divisor via one
+// precomputed 64-bit multiplier (Lemire, Kaser and Kurz, "Faster remainder by
+// direct computation", 2019): M = floor((2^64 - 1) / g) + 1, a / g =
+// hi64(M * a), a % g = hi64(lo64(M * a) * g), exact for all a, g < 2^32, g > 1.
+struct FastDiv {
+    uint64_t M;
+    uint32_t g;
+};
+__host__ __device__ inline FastDiv make_fastdiv(uint32_t g) {
+    FastDiv f;
+    f.g = g;
+    f.M = g > 1 ? ~0ull / g + 1 : 0ull;
+    return f;
+}
+__device__ __forceinline__ uint32_t fd_div(uint32_t a, FastDiv f) {
+    return f.g > 1 ? (uint32_t)__umul64hi(f.M, a) : a;
+}
 
 struct EnumParams {
     const uint64_t *C;     // count table rows 0..d, stride cs
@@ -53,16 +71,17 @@ struct EnumParams {
     uint64_t nrows;        // rows to write
     uint64_t slice_rows;   // S (multiple of 4), used when RT is null
     uint64_t nslices;
-    const uint64_t *RT;    // runs table rows 0..lam_r (stride cs), or null
-    uint64_t W;            // cost of one run, in rows
+    const uint64_t *RT;    // candidates table rows 0..lam_r (stride cs), or null
+    uint64_t W;            // cost of one leaf candidate, in rows
     uint64_t slice_cost;   // cost units per work item when RT is set
-    int lam_r;             // coordinate of the runs counted by RT
+    int lam_r;             // one past the leaf coordinate (RT[lam_r] = 1)
     int n, d, K, top;
     int lam_m;             // coordinate whose children are memo leaves (d-K-1), or -1
     int lam_w;             // coordinate whose children are walk leaves (d-2)
     int half_rows;         // B: rows per ring half (multiple of 32)
     int aligned;           // out is 16-byte aligned
     int g[FZ_MAX_D];
+    FastDiv glast;         // division by g_{d-1} (walk leaves)
 };
 
 struct WarpPath {
@@ -229,12 +248,14 @@ __device__ bool advance(const EnumParams &P, WarpPath *wp, int lane, RunState &s
 
 // ---------------------------------------------------------------------------
 // Work-balanced slicing.  The cost of a subtree is its rows plus W for every
-// run of sibling leaves in it; RT[j][x] counts those runs (RT[lam_r] = 1, and
-// row j is row j+1 strided-summed with stride g_j, like the count table), so
-// the cost of the children a_j >= v of a node is C[j][x] + W RT[j][x] with
-// x = rem - v g_j.  Work items are equal cost ranges, located by the same
-// 32-probe search as ranks, then snapped to ranks that are multiples of 4
-// from rank_begin (keeping every bulk store 16-byte aligned).
+// leaf candidate in it (a prefix the walk evaluates, live or not); RT[j][x]
+// counts those candidates (RT[lam_r] = 1 with lam_r one past the leaf
+// coordinate, and row j is row j+1 strided-summed with stride g_j, like the
+// count table), so the cost of the children a_j >= v of a node is
+// C[j][x] + W RT[j][x] with x = rem - v g_j.  Work items are equal cost ranges, located by the same
+// 32-probe search as ranks, then snapped to ranks that are multiples of 32
+// from rank_begin: 32 rows are 128 d bytes, so every bulk store of a slice
+// starts on a 128-byte line when the output is 128-byte aligned.
 // ---------------------------------------------------------------------------
 __device__ __forceinline__ uint64_t cost_at(const EnumParams &P, int j, long long idx) {
     if (idx < 0) return 0ull;
@@ -352,7 +373,6 @@ __device__ __forceinline__ bool enum_slice(const EnumParams &P, WarpPath *wp, in
                                            uint64_t pol, int lane) {
     constexpr int DM = D > 0 ? D : FZ_MAX_D;
     const int d = D > 0 ? D : P.d;
-    const int g_last = P.g[d - 1];
     constexpr int KF = LAMF >= 0 ? D - 1 - LAMF : 0;
     uint32_t rows_left = (uint32_t)(row1 - row0);
 
@@ -385,19 +405,33 @@ __device__ __forceinline__ bool enum_slice(const EnumParams &P, WarpPath *wp, in
         int p = 0;
         uint64_t incl = 0;
         int type = T_NONE;
+        // a run of walk leaves: candidate v is valid iff g_{d-1} divides the
+        // remainder (the ordinary step's test); row ends by counting, no table
+        const bool walk_run = LAMF < 0 && !memo_run && lam == P.lam_w;
+        uint32_t wq = 0;
+        bool wvalid = false;
         if (valid) {
             p = (int)((long long)rem - vl * glam);
             if (p < 0 || p > P.n) {  // cannot happen for 0 <= vl <= rem / glam
                 atomicExch(P.status, (int)DEV_INTERNAL);
                 p = 0;
             }
-            incl = __ldg(P.C + (long long)lam * P.cs + p);
+            if (walk_run) {
+                wq = fd_div((uint32_t)p, P.glast);
+                wvalid = (uint32_t)p - wq * P.glast.g == 0u;
+            } else {
+                incl = __ldg(P.C + (long long)lam * P.cs + p);
+            }
             if (memo_run && (LAMF >= 0 || p < P.top))
                 type = T_MEMO;
             else if (lam == P.lam_w)
                 type = T_WALK;
             else
                 type = T_INTERNAL;
+        }
+        if (walk_run) {
+            const unsigned vm = __ballot_sync(FULL, wvalid);
+            incl = st.base + (uint64_t)__popc(vm & (0xffffffffu >> (31 - lane)));
         }
         uint64_t prev = __shfl_up_sync(FULL, incl, 1);
         if (lane == 0) prev = st.base;
@@ -415,7 +449,7 @@ __device__ __forceinline__ bool enum_slice(const EnumParams &P, WarpPath *wp, in
             if (type == T_MEMO)
                 X32 = (uint32_t)__ldg(P.O + p);
             else if (type == T_WALK)
-                X32 = (uint32_t)(p / g_last);
+                X32 = walk_run ? wq : fd_div((uint32_t)p, P.glast);
         }
         uint64_t q_end64 = skip + rows_left;
         if (q_end64 > batch_rows) q_end64 = batch_rows;
@@ -628,7 +662,7 @@ __device__ __forceinline__ bool enum_slice(const EnumParams &P, WarpPath *wp, in
 // Rows are handed out as work items (equal-cost ranges when the runs table
 // is present, else equal-row ranges) from an atomic counter.
 template <int D, int LAMF>
-__global__ void __launch_bounds__(ENUM_THREADS, 2)
+__global__ void __launch_bounds__(ENUM_THREADS, 4)
     fz_enum_kernel(const __grid_constant__ EnumParams P) {
     extern __shared__ __align__(128) unsigned char smem_raw[];
     const int lane = threadIdx.x & 31;
@@ -657,13 +691,13 @@ __global__ void __launch_bounds__(ENUM_THREADS, 2)
             row0 = 0;
             if (s > 0) {
                 const uint64_t r = cost_to_rank(P, c0, lane);
-                row0 = r > P.rank_begin ? ((r - P.rank_begin) & ~3ull) : 0ull;
+                row0 = r > P.rank_begin ? ((r - P.rank_begin) & ~31ull) : 0ull;
                 if (row0 > P.nrows) row0 = P.nrows;
             }
             row1 = P.nrows;
             if (c1 < cost_hi) {
                 const uint64_t r = cost_to_rank(P, c1, lane);
-                row1 = r > P.rank_begin ? ((r - P.rank_begin) & ~3ull) : 0ull;
+                row1 = r > P.rank_begin ? ((r - P.rank_begin) & ~31ull) : 0ull;
                 if (row1 > P.nrows) row1 = P.nrows;
             }
             if (row1 <= row0) continue;
@@ -698,7 +732,7 @@ struct BatchEnumParams {
 
 constexpr size_t BATCH_RING_BYTES = RING_BYTES_PER_WARP;
 
-__global__ void __launch_bounds__(ENUM_THREADS, 2)
+__global__ void __launch_bounds__(ENUM_THREADS, 4)
     fz_enum_batch_kernel(const __grid_constant__ BatchEnumParams BP) {
     extern __shared__ __align__(128) unsigned char smem_raw[];
     const int lane = threadIdx.x & 31;
@@ -749,12 +783,12 @@ __global__ void __launch_bounds__(ENUM_THREADS, 2)
             const uint64_t c1 = c0 + P.slice_cost;
             row0 = 0;
             if (s > 0) {
-                row0 = cost_to_rank(P, c0, lane) & ~3ull;
+                row0 = cost_to_rank(P, c0, lane) & ~31ull;
                 if (row0 > P.nrows) row0 = P.nrows;
             }
             row1 = P.nrows;
             if (c1 < cost_hi) {
-                row1 = cost_to_rank(P, c1, lane) & ~3ull;
+                row1 = cost_to_rank(P, c1, lane) & ~31ull;
                 if (row1 > P.nrows) row1 = P.nrows;
             }
         } else {
@@ -822,7 +856,7 @@ __global__ void __launch_bounds__(ENUM_THREADS)
             else if (mleaf)
                 x = __ldg(P.memo + (size_t)(__ldg(P.O + p) + off) * P.K + (lane - lam - 1));
             else
-                x = p / P.g[D - 1];
+                x = (int)fd_div((uint32_t)p, P.glast);
             P.out[i * D + lane] = x;
         }
         __syncwarp();
@@ -929,6 +963,7 @@ static EnumParams make_params(const EnumLaunch &L) {
     P.K = L.K;
     P.top = L.top;
     for (int i = 0; i < L.d; ++i) P.g[i] = L.g[i];
+    P.glast = make_fastdiv((uint32_t)L.g[L.d - 1]);
     const bool memo = L.K >= 1 && L.K <= L.d - 1 && L.top > 0;
     P.lam_m = memo ? L.d - L.K - 1 : -1;
     P.lam_w = L.d - 2;
@@ -970,7 +1005,7 @@ int launch_enumerate(const EnumLaunch &L, uint64_t rank_begin, uint64_t nrows, i
     P.out = out;
     P.rank_begin = rank_begin;
     P.nrows = nrows;
-    P.aligned = ((uintptr_t)out & 15u) == 0;
+    P.aligned = ((uintptr_t)out & 15u) == 0 && !L.plain_stores;
     if (L.d == 1 || (L.K == L.d && L.top > L.n)) {
         const int mode = (L.d == 1 && !(L.K == 1 && L.top > L.n)) ? 2 : 1;
         uint64_t words = nrows * (uint64_t)L.d;
@@ -1071,7 +1106,7 @@ uint64_t default_slice_rows(uint64_t nrows, int sms) {
     uint64_t s = nrows / (warps * 8 + 1);
     if (s < 1024) s = 1024;
     if (s > 65536) s = 65536;
-    return (s + 3) & ~3ull;
+    return (s + 31) & ~31ull;
 }
 
 }  // namespace fz

@@ -288,6 +288,9 @@ struct EnumLaunch {
     uint64_t W = 0;
     int lam_r = 0;
     uint64_t total_cost = 0, total_rows = 0;
+    // the output is host memory reached over the host link: flush rows with
+    // plain coalesced stores instead of bulk (TMA) stores
+    bool plain_stores = false;
 };
 // Runs table: RT[lam][x] = 1, RT[j][x] = sum_t RT[j+1][x - t g_j] (fz_count.cu).
 int launch_runs_table(const int32_t *g, int lam, int32_t n, uint64_t *RT, uint64_t *tmp,

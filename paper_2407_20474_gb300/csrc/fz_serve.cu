@@ -365,6 +365,29 @@ int fz_serve_wait(fz_server_t s, uint64_t ticket, int32_t timeout_ms, fz_result_
     return FZ_OK;
 }
 
+int fz_serve_copy(fz_server_t s, uint64_t ticket, int32_t *dst, uint64_t capacity_words,
+                  void *stream) {
+    if (!s) return set_error(FZ_EINVAL, "null pointer");
+    const void *src = nullptr;
+    uint64_t words = 0;
+    {
+        std::lock_guard<std::mutex> lk(s->mu);
+        auto it = s->reqs.find(ticket);
+        if (it == s->reqs.end()) return set_error(FZ_ENOTFOUND, "unknown ticket");
+        const Req *r = it->second;
+        if (r->status != FZ_SERVE_DONE) return set_error(FZ_EAGAIN, "request not done");
+        words = r->count * (uint64_t)s->sets[r->set].d;
+        src = static_cast<char *>(s->arena_base) + r->off;
+    }
+    if (words == 0) return FZ_OK;
+    if (!dst) return set_error(FZ_EINVAL, "dst: null pointer");
+    if (capacity_words < words) return set_error(FZ_ENOSPC, "capacity too small");
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    FZ_CUDA_TRY(cudaMemcpyAsync(dst, src, words * 4, cudaMemcpyDefault, st));
+    FZ_CUDA_TRY(cudaStreamSynchronize(st));
+    return FZ_OK;
+}
+
 int fz_serve_release(fz_server_t s, uint64_t ticket) {
     if (!s) return set_error(FZ_EINVAL, "null pointer");
     {

@@ -255,6 +255,21 @@ def test_enumerate_host(fz):
     assert (out[ref.size:] == CANARY).all()
 
 
+def test_enumerate_host_pinned_direct(fz):
+    """Page-locked host output is written by the kernel itself."""
+    g, n = (5, 8, 11, 14), 900
+    ref = oracle.enumerate_desc(g, n)
+    out = torch.full((ref.size + 8,), CANARY, dtype=torch.int32).pin_memory()
+    w = fz.fz_enumerate_host(g, n, out)
+    torch.cuda.synchronize()
+    host = out.numpy()
+    assert w == ref.shape[0]
+    assert np.array_equal(host[:ref.size].reshape(ref.shape), ref)
+    assert (host[ref.size:] == CANARY).all()
+    w2 = fz.fz_enumerate_host(g, n, out[4:], rank_begin=7, rank_end=1000)
+    assert np.array_equal(out.numpy()[4:4 + w2 * 4].reshape(w2, 4), ref[7:1000])
+
+
 # --------------------------------------------------------------------------
 # memo build (the dynamic FactorizationsUpToElement pass)
 # --------------------------------------------------------------------------

@@ -21,19 +21,11 @@ def fz():
     return m
 
 
-def rows_of(fz, res):
+def rows_of(srv, ticket, res):
     words = int(res.count) * int(res.d)
-    if words == 0:
-        return np.zeros((0, int(res.d)), dtype=np.int32)
-    t = torch.empty(words, dtype=torch.int32, device="cuda")
-    import ctypes
-    torch.cuda.synchronize()
-    src = int(res.rows_dev)
-    # copy the server-owned rows into a tensor (device to device)
-    cudart = torch.cuda.cudart()
-    cudart.cudaMemcpy(t.data_ptr(), src, words * 4, 3)  # cudaMemcpyDeviceToDevice
-    torch.cuda.synchronize()
-    return t.cpu().numpy().reshape(int(res.count), int(res.d))
+    out = torch.empty(max(words, 1), dtype=torch.int32)
+    srv.copy(ticket, out)
+    return out[:words].numpy().reshape(int(res.count), int(res.d))
 
 
 def alone(fz, g, n):
@@ -59,7 +51,7 @@ def test_mix_equals_alone(fz):
             res = srv.wait(t, 60000)
             assert res.status == fz.FZ_SERVE_DONE
             assert res.t_submit <= res.t_admit <= res.t_done
-            got = rows_of(fz, res)
+            got = rows_of(srv, t, res)
             g = sets[s]
             assert int(res.count) == oracle.count(g, n)
             assert np.array_equal(got, alone(fz, g, n)), (g, n)
@@ -88,12 +80,12 @@ def test_admission_by_exact_bytes_and_queue_limit(fz):
         assert e.value.status == fz.FZ_EAGAIN
         assert srv.poll(t2).status == fz.FZ_SERVE_QUEUED
         assert srv.stats().bytes_in_use <= budget
-        ref = rows_of(fz, r1)
+        ref = rows_of(srv, t1, r1)
         srv.release(t1)                            # frees the bytes: t2 then t3 run
         for t in (t2, t3):
             r = srv.wait(t, 60000)
             assert r.status == fz.FZ_SERVE_DONE
-            assert np.array_equal(rows_of(fz, r), ref)
+            assert np.array_equal(rows_of(srv, t, r), ref)
             srv.release(t)
         with pytest.raises(fz.FzError) as e:
             srv.submit(sid, 400)                   # larger than the whole budget
@@ -117,5 +109,5 @@ def test_config5_sets_large_requests(fz):
             for m, t in zip((n, n // 2, n - 1, 0), ts):
                 r = srv.wait(t, 60000)
                 assert r.status == fz.FZ_SERVE_DONE
-                assert np.array_equal(rows_of(fz, r), alone(fz, g, m)), (g, m)
+                assert np.array_equal(rows_of(srv, t, r), alone(fz, g, m)), (g, m)
                 srv.release(t)
