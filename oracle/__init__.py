@@ -73,6 +73,10 @@ def _load():
             ctypes.POINTER(ctypes.c_int32), ctypes.c_int, ctypes.c_int64,
             ctypes.POINTER(ctypes.c_int64), ctypes.c_int, ctypes.c_int,
             ctypes.POINTER(ctypes.c_uint64), ctypes.POINTER(ctypes.c_uint64)]
+        lib.fzo_lex_lists.restype = ctypes.c_int64
+        lib.fzo_lex_lists.argtypes = [
+            ctypes.POINTER(ctypes.c_int32), ctypes.c_int, ctypes.c_int64,
+            ctypes.POINTER(ctypes.c_uint64), ctypes.POINTER(ctypes.c_int32), ctypes.c_uint64]
         _lib = lib
     return _lib
 
@@ -383,6 +387,24 @@ def memo_csr(tail: Sequence[int], top: int) -> Tuple[np.ndarray, np.ndarray]:
     rows = (np.concatenate(parts, axis=0) if parts
             else np.zeros((0, k), dtype=np.int32))
     return offsets, rows
+
+
+def lex_lists_c(tail: Sequence[int], top: int) -> Tuple[np.ndarray, np.ndarray]:
+    """The memo CSR of :func:`memo_csr` by the single-threaded dynamic list
+    algorithm of Section 2.1, in C (the CPU memo population the paper times
+    beside its GPU one).  Returns (offsets uint64[top+1], rows int32[total, k])."""
+    tt = _gens(tail)
+    k = tt.size
+    top = max(int(top), 0)
+    cap = int(sum(int(x) for x in count_upto(tt, top - 1))) if top > 0 else 0
+    offsets = np.zeros(top + 1, dtype=np.uint64)
+    rows = np.zeros((max(cap, 1), k), dtype=np.int32)
+    got = _load().fzo_lex_lists(tt.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)), k, top,
+                                offsets.ctypes.data_as(ctypes.POINTER(ctypes.c_uint64)),
+                                rows.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)), cap)
+    if got < 0:
+        raise ValueError("oracle rejected its arguments (%d)" % got)
+    return offsets, rows[:got]
 
 
 # ---------------------------------------------------------------------------

@@ -206,3 +206,51 @@ int fzo_sample(const int32_t *g, int d, int64_t n, const int64_t *a1_values,
     if (checksum) *checksum = p.checksum;
     return started == 0 ? 1 : started;
 }
+
+/*
+ * The memo lists Z(m, tail), m = 0..top-1, by the single-threaded dynamic
+ * list algorithm of Section 2.1 (LexicographicFactorizationListsUpToElement):
+ * F[0] = [0]; F[m] is the concatenation over i of incr_i(a) for the rows a
+ * of F[m - t_i] whose coordinates left of i are all zero.  Each row is
+ * tested one by one (no saved cardinalities).  offsets receives top + 1
+ * entries; rows holds at most `capacity` rows of k int32.  Returns the row
+ * count, -1 for bad arguments, -2 if the rows do not fit.
+ */
+int64_t fzo_lex_lists(const int32_t *tail, int k, int64_t top, uint64_t *offsets,
+                      int32_t *rows, uint64_t capacity)
+{
+    if (k < 1 || k > FZO_MAX_D || top < 0 || !tail || !offsets) return -1;
+    for (int i = 0; i < k; ++i)
+        if (tail[i] < 1) return -1;
+    uint64_t total = 0;
+    offsets[0] = 0;
+    for (int64_t m = 0; m < top; ++m) {
+        if (m == 0) {
+            if (capacity < 1 || !rows) return -2;
+            for (int c = 0; c < k; ++c) rows[c] = 0;
+            total = 1;
+            offsets[1] = 1;
+            continue;
+        }
+        for (int i = 0; i < k; ++i) {
+            const int64_t src = m - tail[i];
+            if (src < 0) continue;
+            for (uint64_t r = offsets[src]; r < offsets[src + 1]; ++r) {
+                const int32_t *a = rows + r * (uint64_t)k;
+                int zero_left = 1;
+                for (int j = 0; j < i; ++j)
+                    if (a[j] != 0) {
+                        zero_left = 0;
+                        break;
+                    }
+                if (!zero_left) continue;
+                if (total >= capacity) return -2;
+                int32_t *b = rows + total * (uint64_t)k;
+                for (int c = 0; c < k; ++c) b[c] = a[c] + (c == i ? 1 : 0);
+                ++total;
+            }
+        }
+        offsets[m + 1] = total;
+    }
+    return (int64_t)total;
+}

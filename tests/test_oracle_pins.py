@@ -247,6 +247,16 @@ def test_list_algorithms_match_definition():
             assert seg == ref, (g, m)
 
 
+def test_c_lex_lists_match_definition():
+    """The C single-threaded dynamic list build equals the definition."""
+    for tail, top in (((4, 9, 10), 80), ((2, 2, 5), 41), ((7,), 50), ((1, 3, 4, 9), 46),
+                      ((13, 37, 38), 300), ((6, 4), 61), ((3, 5, 7), 0), ((3, 5, 7), 1)):
+        off, rows = oracle.lex_lists_c(tail, top)
+        ref_off, ref_rows = oracle.memo_csr(tail, top)
+        assert np.array_equal(off, ref_off), tail
+        assert np.array_equal(rows, ref_rows), tail
+
+
 def test_memo_csr_matches_brute_force():
     tail = (4, 9, 10)
     off, rows = oracle.memo_csr(tail, 50)
