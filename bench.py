@@ -53,6 +53,9 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-graph", action="store_true",
                     help="launch every step's kernels directly instead of replaying a graph")
+    ap.add_argument("--no-pipeline", action="store_true",
+                    help="time steps one after another instead of overlapping each step's "
+                         "count/memo build with the previous step's enumeration")
     ap.add_argument("--k", type=int, default=-1, help="memo depth (default: autotune)")
     ap.add_argument("--slice-rows", type=int, default=0)
     ap.add_argument("--cpu-seconds", type=float, default=15.0,
@@ -307,8 +310,78 @@ def run_ours(args):
         launches = kernels_per_step * K  # graph replays launch the captured kernels
     plan.sync()
     ms = start.elapsed_time(end)
+    ms_serial = ms
+    pipelined = False
+    enum_cap = None
+    if not args.no_pipeline:
+        # Pipelined steps: two plans of the same element alternate; step i+1's
+        # count tables and memo build (latency-bound, 16 SMs) run on one
+        # stream while step i's enumeration (bandwidth-bound) runs on another.
+        # The enumeration is capped at 3 or 2 blocks per SM (larger rings) so
+        # the build fits beside it; the faster cap is chosen in the warm-up.
+        # Every step still does its whole path.
+        plan2 = fz.Plan(g, n, k=plan.k, slice_rows=args.slice_rows)
+        plans = [plan, plan2]
+        s_b, s_e = torch.cuda.Stream(), torch.cuda.Stream()
+        built = [torch.cuda.Event(), torch.cuda.Event()]
+        done = [torch.cuda.Event(), torch.cuda.Event()]
+
+        def pipelined_steps(count_steps, kernel_evs=None):
+            st0 = torch.cuda.Event(enable_timing=True)
+            st1 = torch.cuda.Event(enable_timing=True)
+            st0.record(s_e)
+            s_b.wait_event(st0)
+            for i in range(count_steps):
+                j = i & 1
+                if i >= 2:
+                    s_b.wait_event(done[j])
+                plans[j].rebuild(stream=s_b)
+                built[j].record(s_b)
+                s_e.wait_event(built[j])
+                if kernel_evs:  # enumeration launch time, on its own stream
+                    kernel_evs[i][0].record(s_e)
+                plans[j].enumerate(out, stream=s_e)
+                if kernel_evs:
+                    kernel_evs[i][1].record(s_e)
+                done[j].record(s_e)
+            st1.record(s_e)
+            torch.cuda.synchronize()
+            return st0.elapsed_time(st1)
+
+        cap_ms = {}
+        for cap in (3, 2):
+            for p_ in plans:
+                p_.set_enum_ctas_per_sm(cap)
+            pipelined_steps(2)
+            cap_ms[cap] = pipelined_steps(max(args.warmup, 3))
+        enum_cap = min(cap_ms, key=cap_ms.get)
+        for p_ in plans:
+            p_.set_enum_ctas_per_sm(enum_cap)
+        pipelined_steps(2)
+        for p_ in plans:
+            p_.sync()
+        l0 = fz.fz_kernel_launches()
+        barrier(pg, torch)
+        if sampler:
+            sampler.mark_start()
+        pipe_evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+                    for _ in range(K)]
+        ms_pipe = pipelined_steps(K, pipe_evs)
+        if sampler:
+            sampler.mark_end()
+        barrier(pg, torch)
+        launches = fz.fz_kernel_launches() - l0
+        for p_ in plans:
+            p_.sync()
+        plan2.close()
+        plan.set_enum_ctas_per_sm(0)
+        ms = ms_pipe
+        pipelined = True
     ms = max_over_ranks(pg, ms, torch)
-    if graph is not None:
+    if pipelined:
+        # the enumeration launches of the timed (pipelined) steps
+        enum_ms = statistics.mean(a.elapsed_time(b) for a, b in pipe_evs)
+    elif graph is not None:
         # enumeration-kernel time measured on separate (non-graph) steps
         for i in range(min(K, 20)):
             step(evs[i])
@@ -320,6 +393,16 @@ def run_ours(args):
 
     value = world * K * count / (ms / 1e3)
     bytes_per_launch = count * d * 4
+    # a plain device write of the same buffer (memset kernel): the practical
+    # write-only ceiling on this GPU, reported beside the copy peak
+    wz0, wz1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    out.zero_()
+    wz0.record()
+    for _ in range(3):
+        out.zero_()
+    wz1.record()
+    torch.cuda.synchronize()
+    write_peak = 3 * out.numel() * 4 / (wz0.elapsed_time(wz1) / 1e3) / 1e9
     achieved = bytes_per_launch / (enum_ms / 1e3) / 1e9
     peaks = {}
     pp = os.path.join(ROOT, "MEASURED_PEAKS.json")
@@ -365,12 +448,17 @@ def run_ours(args):
                        "slice_rows": plan.slice_rows, "bytes_per_step": bytes_per_launch,
                        "parallelism": "replicas (one instance per GPU)",
                        "cuda_graph": graph is not None,
+                       "pipelined": pipelined,
+                       "pipeline_enum_ctas_per_sm": enum_cap if pipelined else None,
+                       "ms_per_step_serial": ms_serial / K,
                        "l2": "output %.1f GB per step >> 129 MB L2; count table and memo "
                              "rebuilt every step" % (bytes_per_launch / 1e9)},
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                          "frac": achieved / peak, "traffic": kernel_traffic(d),
                          "kernel": "fz_enum_kernel<%d>" % d,
                          "kernel_ms": enum_ms, "peak_source": peak_src,
+                         "write_peak_gbs": write_peak,
+                         "frac_of_write_peak": achieved / write_peak,
                          "algorithmic_bytes_per_launch": bytes_per_launch},
             "cpu_baseline": base,
             "e2e": e2e,
@@ -631,6 +719,40 @@ def run_table1_workload(args):
              (8, 4, 1000, 1659), (8, 4, 1500, 5736), (8, 4, 2000, 25165),
              (9, 4, 500, 1326), (9, 4, 1000, 8202), (9, 4, 1500, 52694),
              (9, 5, 500, 1129), (9, 5, 1000, 6018), (9, 5, 1500, 47513)]
+    # memo population per (d, memo_dim) group, up to the group's largest
+    # element: the device build in each launch schedule (wall clock of the
+    # synchronising call, median of 3) beside the paper's CPU and GPU columns
+    # and the single-threaded CPU build of the oracle (cpu_baseline leg)
+    import oracle
+    paper_memo = {(3, 1): (313, 9764), (4, 2): (2920, 27188), (5, 2): (1674, 30028),
+                  (5, 3): (7952, 26683), (6, 3): (7586, 27999), (6, 4): (43686, 24625),
+                  (7, 4): (44906, 24383), (8, 4): (47843, 25655), (9, 4): (49239, 29815),
+                  (9, 5): (21401, 18208)}
+    memo_rows = []
+    for (d, k), (paper_cpu_us, paper_gpu_us) in paper_memo.items():
+        top = max(n for dd, kk, n, _ in table if (dd, kk) == (d, k)) + 1
+        tail = workloads.TABLE1_GENERATORS[:d][d - k:]
+        rows = fz.fz_memo_rows(tail, top)
+        off = torch.zeros(top + 1, dtype=torch.int64, device="cuda")
+        buf = torch.empty(max(rows, 1) * k, dtype=torch.int32, device="cuda")
+        rec = {"d": d, "memo_dim": k, "top": top, "rows": rows,
+               "paper_cpu_memo_us": paper_cpu_us, "paper_gpu_memo_us": paper_gpu_us}
+        for name, sched in (("batched", fz.FZ_MEMO_BATCHED), ("per_batch", fz.FZ_MEMO_PER_BATCH),
+                            ("per_copy", fz.FZ_MEMO_PER_COPY)):
+            ts = []
+            for _ in range(4):
+                t0 = time.perf_counter()
+                fz.fz_build_memo_schedule(tail, top, sched, off, buf, rows)
+                ts.append(time.perf_counter() - t0)
+            rec["gpu_memo_us_" + name] = 1e6 * statistics.median(ts[1:])
+        ts = []
+        for _ in range(3):
+            t0 = time.perf_counter()
+            oracle.lex_lists_c(tail, top)
+            ts.append(time.perf_counter() - t0)
+        rec["cpu_memo_us_oracle_1thread"] = 1e6 * statistics.median(ts)
+        memo_rows.append(rec)
+        del off, buf
     for d, k, n, paper_ms in table:
         g = workloads.TABLE1_GENERATORS[:d]
         with fz.Plan(g, n, k=k) as p:
@@ -650,6 +772,7 @@ def run_table1_workload(args):
            "value": total / (ms / 1e3), "unit": UNIT, "n_gpus": 1, "higher_is_better": True,
            "dtype": "int32", "data": "synthetic",
            "config": {"workload": "Table 1: Z(n, first d of (13,37,38,40..45))", "rows": rows_out,
+                      "memo_population": memo_rows,
                       "note": "paper: RTX 3080 + Ryzen 3900X, host-buffered output; here "
                               "output resident in HBM"}}
     print(json.dumps(rec))

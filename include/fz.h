@@ -154,6 +154,32 @@ int fz_build_memo_into(const int32_t *tail, int k, int32_t top,
                        uint64_t rows_capacity, uint64_t *rows_needed,
                        void *stream);
 
+/* Launch schedules of the memo build (Section 2.2 names the two kinds of
+ * parallelism of the dynamic pass; Section 2.4 gives the factorizationwise
+ * algorithm).  All give the same memo.
+ *   FZ_MEMO_BATCHED    elementwise batches of min(tail) elements, each batch
+ *                      factorizationwise parallel, all in ONE launch (batches
+ *                      separated by a cluster or bounded grid barrier); the
+ *                      schedule every other call uses.
+ *   FZ_MEMO_PER_BATCH  the same batches, one kernel launch per batch ("both"
+ *                      parallelism, ordered by the stream).
+ *   FZ_MEMO_PER_COPY   the factorizationwise parallel algorithm of Section
+ *                      2.4: one copyAndIncrementIndex launch per element m and
+ *                      generator i with a non-empty block, sized from the
+ *                      saved cardinalities (host copies of the count table
+ *                      and offsets).  top * k launches at most: for
+ *                      comparison, not for large tops. */
+#define FZ_MEMO_BATCHED 0
+#define FZ_MEMO_PER_BATCH 1
+#define FZ_MEMO_PER_COPY 2
+
+/* fz_build_memo_into with an explicit schedule.  Errors: those of
+ * fz_build_memo_into; FZ_EINVAL for an unknown schedule. */
+int fz_build_memo_schedule(const int32_t *tail, int k, int32_t top, int schedule,
+                           uint64_t *offsets_dev, int32_t *rows_dev,
+                           uint64_t rows_capacity, uint64_t *rows_needed,
+                           void *stream);
+
 typedef struct fz_memo_s *fz_memo_t;
 typedef struct fz_memo_info {
     int32_t k, top;
@@ -197,6 +223,23 @@ typedef struct fz_plan_info {
 int fz_plan_create(const int32_t *g, int d, int32_t n, const fz_opts_t *opt,
                    fz_plan_t *plan, void *stream);
 int fz_plan_info(fz_plan_t plan, fz_plan_info_t *info);
+
+/* Cap the enumeration kernel of this plan at `ctas` blocks per SM (0 = as
+ * many as fit; the kernel fits 4).  Leaving room lets other kernels run
+ * beside it, e.g. another plan's rebuild overlapping this enumeration.
+ * Errors: FZ_EINVAL. */
+int fz_plan_set_enum_ctas_per_sm(fz_plan_t plan, int32_t ctas);
+
+/* Empirical tuning of the implementation options for Z(n, g): each memo
+ * depth k = 0..min(d-1, 4) whose memo fits (and three work-item sizes for
+ * each) is built and timed on the device -- its rebuild plus the
+ * enumeration of four rank windows spread over the set, extrapolated to the
+ * whole set.  The fastest is written to *best (and its estimated ms per
+ * step to *best_ms, may be NULL) and remembered for this (g, n) and device:
+ * later plans created with k = FZ_AUTO use it.  Synchronises.
+ * Errors: as fz_plan_create. */
+int fz_autotune(const int32_t *g, int d, int32_t n, fz_opts_t *best, double *best_ms,
+                void *stream);
 
 /* Recompute the count table and rebuild the memo in the plan's buffers.
  * Asynchronous (no host synchronisation), so it can be captured in a CUDA

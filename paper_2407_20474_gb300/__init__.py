@@ -38,9 +38,12 @@ FZ_EINTERNAL = -9
 EXPORTS = (
     "fz_version", "fz_last_error_string", "fz_status_string", "fz_kernel_launches",
     "fz_count", "fz_count_upto", "fz_count_upto_noalloc", "fz_count_table",
-    "fz_memo_rows", "fz_build_memo_into", "fz_build_memo", "fz_memo_info",
+    "fz_memo_rows", "fz_build_memo_into", "fz_build_memo_schedule", "fz_build_memo",
+    "fz_memo_info",
     "fz_memo_release",
-    "fz_plan_create", "fz_plan_info", "fz_plan_rebuild", "fz_plan_enumerate",
+    "fz_autotune", "fz_plan_create", "fz_plan_info", "fz_plan_set_enum_ctas_per_sm",
+    "fz_plan_rebuild",
+    "fz_plan_enumerate",
     "fz_plan_unrank", "fz_plan_sync", "fz_plan_destroy",
     "fz_enumerate", "fz_enumerate_host",
     "fz_batch_create", "fz_batch_info", "fz_batch_layout", "fz_batch_rebuild",
@@ -124,6 +127,8 @@ _SIGS = {
     "fz_memo_rows": (ctypes.c_int, [_I32P, ctypes.c_int, ctypes.c_int32, _U64P, _P]),
     "fz_build_memo_into": (ctypes.c_int, [_I32P, ctypes.c_int, ctypes.c_int32, _P, _P,
                                           ctypes.c_uint64, _U64P, _P]),
+    "fz_build_memo_schedule": (ctypes.c_int, [_I32P, ctypes.c_int, ctypes.c_int32, ctypes.c_int,
+                                              _P, _P, ctypes.c_uint64, _U64P, _P]),
     "fz_build_memo": (ctypes.c_int, [_I32P, ctypes.c_int, ctypes.c_int32,
                                      ctypes.POINTER(_P), _P]),
     "fz_memo_info": (ctypes.c_int, [_P, ctypes.POINTER(fz_memo_info_t)]),
@@ -131,7 +136,10 @@ _SIGS = {
     "fz_plan_create": (ctypes.c_int, [_I32P, ctypes.c_int, ctypes.c_int32,
                                       ctypes.POINTER(fz_opts_t), ctypes.POINTER(_P), _P]),
     "fz_plan_info": (ctypes.c_int, [_P, ctypes.POINTER(fz_plan_info_t)]),
+    "fz_autotune": (ctypes.c_int, [_I32P, ctypes.c_int, ctypes.c_int32,
+                                   ctypes.POINTER(fz_opts_t), ctypes.POINTER(ctypes.c_double), _P]),
     "fz_plan_rebuild": (ctypes.c_int, [_P, _P]),
+    "fz_plan_set_enum_ctas_per_sm": (ctypes.c_int, [_P, ctypes.c_int32]),
     "fz_plan_enumerate": (ctypes.c_int, [_P, ctypes.c_uint64, ctypes.c_uint64, _P,
                                          ctypes.c_uint64, _U64P, _P]),
     "fz_plan_unrank": (ctypes.c_int, [_P, _P, ctypes.c_uint64, _P, _P]),
@@ -293,6 +301,20 @@ def fz_build_memo_into(tail: Sequence[int], top: int, offsets, rows, rows_capaci
     return int(need.value)
 
 
+FZ_MEMO_BATCHED, FZ_MEMO_PER_BATCH, FZ_MEMO_PER_COPY = 0, 1, 2
+
+
+def fz_build_memo_schedule(tail: Sequence[int], top: int, schedule: int, offsets, rows,
+                           rows_capacity: int, stream=None) -> int:
+    """fz_build_memo_into with an explicit launch schedule (FZ_MEMO_*)."""
+    ga, k = _gens(tail)
+    need = ctypes.c_uint64(0)
+    _check(lib().fz_build_memo_schedule(ga, k, int(top), int(schedule), _ptr(offsets),
+                                        _ptr(rows), int(rows_capacity), ctypes.byref(need),
+                                        _stream(stream)))
+    return int(need.value)
+
+
 class Memo:
     """Library-owned memo (fz_build_memo / fz_memo_release)."""
 
@@ -323,6 +345,17 @@ def fz_build_memo(tail: Sequence[int], top: int, stream=None) -> Memo:
 
 
 # ------------------------------------------------------------------- plans
+def fz_autotune(g: Sequence[int], n: int, stream=None):
+    """Measured best (k, slice_rows) for Z(n, g); remembered for later
+    FZ_AUTO plans of the same (g, n).  Returns (k, slice_rows, est_ms)."""
+    ga, d = _gens(g)
+    o = fz_opts_t(0, 0, 0, 0)
+    ms = ctypes.c_double(0.0)
+    _check(lib().fz_autotune(ga, d, int(n), ctypes.byref(o), ctypes.byref(ms),
+                             _stream(stream)))
+    return int(o.k), int(o.slice_rows), float(ms.value)
+
+
 class Plan:
     """One instance Z(n, g) with its count table and memo resident on the device."""
 
@@ -346,6 +379,10 @@ class Plan:
 
     def rebuild(self, stream=None):
         _check(lib().fz_plan_rebuild(self._h, _stream(stream)))
+
+    def set_enum_ctas_per_sm(self, ctas: int):
+        """Cap the enumeration kernel's blocks per SM (0 = no cap)."""
+        _check(lib().fz_plan_set_enum_ctas_per_sm(self._h, int(ctas)))
 
     def enumerate(self, out, rank_begin: int = 0, rank_end: Optional[int] = None,
                   capacity_rows: Optional[int] = None, stream=None) -> int:

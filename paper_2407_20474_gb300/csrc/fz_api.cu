@@ -7,6 +7,7 @@
 #include <atomic>
 #include <cstdlib>
 #include <cstring>
+#include <map>
 #include <mutex>
 #include <string>
 #include <vector>
@@ -135,6 +136,7 @@ struct fz_plan_s {
     int lam_r = 0;
     uint64_t W = 0;
     uint64_t total_runs = 0;
+    int ctas_per_sm = 0;
     uint64_t *C = nullptr, *tmp = nullptr, *O = nullptr, *map = nullptr;
     int32_t *rows = nullptr;
     int *status = nullptr;
@@ -184,6 +186,8 @@ int plan_enqueue_memo(fz_plan_s *p, cudaStream_t s) {
     mb.rows = p->rows;
     mb.status = p->status;
     mb.bar = p->bar;
+    // an enumeration capped below full occupancy leaves room for a small build
+    mb.small_ctas = p->ctas_per_sm > 0 && p->ctas_per_sm <= 3;
     return launch_memo_build(p->g + (p->d - p->K), p->K, p->top, p->memo_rows, mb, s);
 }
 
@@ -234,6 +238,27 @@ int choose_k(fz_plan_s *p, cudaStream_t s, int *k_out) {
     return FZ_OK;
 }
 
+// Measured options by (device, g, n), filled by fz_autotune.
+std::mutex g_tune_mu;
+std::map<std::vector<int32_t>, fz_opts_t> g_tune;
+
+std::vector<int32_t> tune_key(const int32_t *g, int d, int32_t n) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    std::vector<int32_t> key(g, g + d);
+    key.push_back(n);
+    key.push_back(dev);
+    return key;
+}
+
+bool autotune_lookup(const int32_t *g, int d, int32_t n, fz_opts_t *out) {
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    auto it = g_tune.find(tune_key(g, d, n));
+    if (it == g_tune.end()) return false;
+    *out = it->second;
+    return true;
+}
+
 int plan_create_impl(const int32_t *g, int d, int32_t n, const fz_opts_t *opt, fz_plan_s *p,
                      cudaStream_t s) {
     int rc = validate_gens(g, d);
@@ -278,11 +303,19 @@ int plan_create_impl(const int32_t *g, int d, int32_t n, const fz_opts_t *opt, f
     FZ_CUDA_TRY(cudaStreamSynchronize(s));
     if (p->count == ~0ull) return set_error(FZ_EOVERFLOW, "|Z(n)| does not fit in 64 bits");
 
-    // memo depth and top
+    // memo depth and top: the caller's, else a measured choice cached by
+    // fz_autotune for this (g, n), else the size heuristic
     int k = opt ? opt->k : FZ_AUTO;
+    int32_t tuned_slice = 0;
     if (k == FZ_AUTO) {
-        rc = choose_k(p, s, &k);
-        if (rc != FZ_OK) return rc;
+        fz_opts_t cached;
+        if (autotune_lookup(g, d, n, &cached)) {
+            k = cached.k;
+            tuned_slice = cached.slice_rows;
+        } else {
+            rc = choose_k(p, s, &k);
+            if (rc != FZ_OK) return rc;
+        }
     }
     int64_t top = (opt && opt->top != FZ_AUTO) ? opt->top : (int64_t)n + 1;
     if (top > (int64_t)n + 1) top = (int64_t)n + 1;
@@ -331,6 +364,8 @@ int plan_create_impl(const int32_t *g, int d, int32_t n, const fz_opts_t *opt, f
     if (rc != FZ_OK) return rc;
     if (opt && opt->slice_rows > 0)
         p->slice_rows = ((uint64_t)opt->slice_rows + 3) & ~3ull;
+    else if (tuned_slice > 0)
+        p->slice_rows = (uint64_t)tuned_slice;
     else
         p->slice_rows = default_slice_rows(p->count, dp.sms);
     return FZ_OK;
@@ -350,6 +385,7 @@ EnumLaunch launch_of(const fz_plan_s *p) {
     L.K = p->K;
     L.top = p->top;
     L.g = p->g;
+    L.ctas_per_sm = p->ctas_per_sm;
     if (p->RT) {
         L.RT = p->RT;
         L.W = p->W;
@@ -516,7 +552,7 @@ int fz_memo_rows(const int32_t *tail, int k, int32_t top, uint64_t *rows, void *
 
 static int build_memo_to(const int32_t *tail, int k, int32_t top, uint64_t *O, int32_t **R,
                          uint64_t rows_capacity, uint64_t *rows_needed, DevBuf *own_rows,
-                         cudaStream_t s) {
+                         cudaStream_t s, int schedule = FZ_MEMO_BATCHED) {
     DevBuf table, work;
     uint64_t *C = nullptr;
     int64_t tmpw = 0;
@@ -552,7 +588,7 @@ static int build_memo_to(const int32_t *tail, int k, int32_t top, uint64_t *O, i
     mb.status = reinterpret_cast<int *>(work.as<char>() + map_bytes);
     mb.bar = reinterpret_cast<unsigned *>(work.as<char>() + map_bytes + 256);
     FZ_CUDA_TRY(cudaMemsetAsync(work.as<char>() + map_bytes, 0, 512, s));
-    rc = launch_memo_build(tail, k, top, rows, mb, s);
+    rc = launch_memo_build(tail, k, top, rows, mb, s, schedule);
     if (rc != FZ_OK) return rc;
     return read_status(mb.status, s);
 }
@@ -560,6 +596,16 @@ static int build_memo_to(const int32_t *tail, int k, int32_t top, uint64_t *O, i
 int fz_build_memo_into(const int32_t *tail, int k, int32_t top, uint64_t *offsets_dev,
                        int32_t *rows_dev, uint64_t rows_capacity, uint64_t *rows_needed,
                        void *stream) {
+    return fz_build_memo_schedule(tail, k, top, FZ_MEMO_BATCHED, offsets_dev, rows_dev,
+                                  rows_capacity, rows_needed, stream);
+}
+
+int fz_build_memo_schedule(const int32_t *tail, int k, int32_t top, int schedule,
+                           uint64_t *offsets_dev, int32_t *rows_dev, uint64_t rows_capacity,
+                           uint64_t *rows_needed, void *stream) {
+    if (schedule != FZ_MEMO_BATCHED && schedule != FZ_MEMO_PER_BATCH &&
+        schedule != FZ_MEMO_PER_COPY)
+        return set_error(FZ_EINVAL, "unknown memo schedule");
     if (!offsets_dev || (!rows_dev && rows_capacity > 0))
         return set_error(FZ_EINVAL, "memo buffers: null pointer");
     if (top == 0) {
@@ -572,7 +618,7 @@ int fz_build_memo_into(const int32_t *tail, int k, int32_t top, uint64_t *offset
     }
     int32_t *R = rows_dev;
     return build_memo_to(tail, k, top, offsets_dev, &R, rows_capacity, rows_needed, nullptr,
-                         as_stream(stream));
+                         as_stream(stream), schedule);
 }
 
 int fz_build_memo(const int32_t *tail, int k, int32_t top, fz_memo_t *memo, void *stream) {
@@ -620,6 +666,113 @@ int fz_memo_release(fz_memo_t memo) {
     return FZ_OK;
 }
 
+// ----------------------------------------------------------------- tuning
+// Time one plan: its rebuild (count tables + memo), then the enumeration of
+// `windows` rank windows of `wrows` rows spread evenly over the set, in ms.
+static int time_plan(fz_plan_t p, int32_t *buf, uint64_t wrows, int windows, cudaStream_t s,
+                     double *build_ms, double *enum_ms_per_row) {
+    cudaEvent_t e0, e1, e2;
+    FZ_CUDA_TRY(cudaEventCreate(&e0));
+    FZ_CUDA_TRY(cudaEventCreate(&e1));
+    FZ_CUDA_TRY(cudaEventCreate(&e2));
+    int rc = FZ_OK;
+    double bsum = 0, esum = 0;
+    uint64_t rows_done = 0;
+    for (int rep = 0; rep < 3 && rc == FZ_OK; ++rep) {  // rep 0 warms up
+        cudaEventRecord(e0, s);
+        rc = fz_plan_rebuild(p, s);
+        cudaEventRecord(e1, s);
+        uint64_t rows = 0;
+        for (int w = 0; w < windows && rc == FZ_OK; ++w) {
+            const uint64_t span = p->count > wrows ? p->count - wrows : 0;
+            const uint64_t b = windows > 1 ? span * (uint64_t)w / (uint64_t)(windows - 1) : 0;
+            uint64_t got = 0;
+            rc = fz_plan_enumerate(p, b & ~31ull, (b & ~31ull) + wrows, buf, wrows, &got, s);
+            rows += got;
+        }
+        cudaEventRecord(e2, s);
+        if (rc == FZ_OK) rc = fz_plan_sync(p, s);
+        float b_ms = 0, e_ms = 0;
+        cudaEventElapsedTime(&b_ms, e0, e1);
+        cudaEventElapsedTime(&e_ms, e1, e2);
+        if (rep > 0) {
+            bsum += b_ms;
+            esum += e_ms;
+            rows_done += rows;
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    cudaEventDestroy(e2);
+    *build_ms = bsum / 2;
+    *enum_ms_per_row = rows_done ? esum / (double)rows_done : 0.0;
+    return rc;
+}
+
+int fz_autotune(const int32_t *g, int d, int32_t n, fz_opts_t *best, double *best_ms,
+                void *stream) {
+    if (!best) return set_error(FZ_EINVAL, "best: null pointer");
+    cudaStream_t s = as_stream(stream);
+    // the heuristic plan gives the count and the depths worth trying
+    fz_plan_t p0 = nullptr;
+    fz_opts_t o0{FZ_AUTO, FZ_AUTO, 0, 0};
+    {
+        std::lock_guard<std::mutex> lk(g_tune_mu);
+        g_tune.erase(tune_key(g, d, n));
+    }
+    int rc = fz_plan_create(g, d, n, &o0, &p0, stream);
+    if (rc != FZ_OK) return rc;
+    const uint64_t count = p0->count;
+    const int k0 = p0->K;
+    fz_plan_destroy(p0);
+    *best = fz_opts_t{k0, FZ_AUTO, 0, 0};
+    if (best_ms) *best_ms = 0;
+    if (count == 0 || d == 1) return FZ_OK;
+    // sample: four windows, at most 2^24 rows and 256 MB in total
+    const int windows = 4;
+    uint64_t wrows = std::min<uint64_t>(count / windows, (1ull << 22));
+    wrows = std::min<uint64_t>(wrows, (256ull << 20) / (4ull * d * windows));
+    wrows = std::max<uint64_t>(32, wrows & ~31ull);
+    DevBuf buf;
+    rc = buf.alloc(wrows * (size_t)d * 4 + 256);
+    if (rc != FZ_OK) return rc;
+    double best_t = 1e300;
+    fz_opts_t best_o = *best;
+    std::vector<int> ks;
+    for (int k = 0; k <= std::min(d - 1, 4); ++k) ks.push_back(k);
+    for (int k : ks) {
+        fz_opts_t o{k, FZ_AUTO, 0, 0};
+        fz_plan_t p = nullptr;
+        if (fz_plan_create(g, d, n, &o, &p, stream) != FZ_OK) continue;  // memo too large
+        if (p->memo_rows * (uint64_t)(4 * k + 8) > std::max<uint64_t>(64ull << 20, count * d)) {
+            fz_plan_destroy(p);
+            continue;
+        }
+        const uint64_t base_slice = p->slice_rows;
+        for (uint64_t sl : {base_slice / 2, base_slice, base_slice * 2}) {
+            if (sl < 1024) continue;
+            p->slice_rows = (sl + 31) & ~31ull;
+            double b_ms = 0, e_row = 0;
+            rc = time_plan(p, buf.as<int32_t>(), wrows, windows, s, &b_ms, &e_row);
+            if (rc != FZ_OK) {
+                fz_plan_destroy(p);
+                return rc;
+            }
+            const double t = b_ms + e_row * (double)count;
+            if (t < best_t) {
+                best_t = t;
+                best_o = fz_opts_t{k, FZ_AUTO, (int32_t)p->slice_rows, 0};
+            }
+        }
+        fz_plan_destroy(p);
+    }
+    *best = best_o;
+    if (best_ms) *best_ms = best_t;
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    g_tune[tune_key(g, d, n)] = best_o;
+    return FZ_OK;
+}
+
 // -------------------------------------------------------------------- plans
 int fz_plan_create(const int32_t *g, int d, int32_t n, const fz_opts_t *opt, fz_plan_t *plan,
                    void *stream) {
@@ -647,6 +800,13 @@ int fz_plan_info(fz_plan_t p, fz_plan_info_t *info) {
     info->device_bytes = p->base.bytes + p->memo.bytes + p->runs.bytes;
     info->slice_rows = (int32_t)p->slice_rows;
     info->reserved = 0;
+    return FZ_OK;
+}
+
+int fz_plan_set_enum_ctas_per_sm(fz_plan_t p, int32_t ctas) {
+    if (!p) return set_error(FZ_EINVAL, "plan: null pointer");
+    if (ctas < 0) return set_error(FZ_EINVAL, "ctas must be >= 0");
+    p->ctas_per_sm = ctas;
     return FZ_OK;
 }
 

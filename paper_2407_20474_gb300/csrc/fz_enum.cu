@@ -31,6 +31,8 @@
 // coalesced transactions while the warp generates the next half.
 #include <cstring>
 
+#include <cstdlib>
+
 #include "fz_internal.cuh"
 
 namespace fz {
@@ -80,6 +82,7 @@ struct EnumParams {
     int lam_w;             // coordinate whose children are walk leaves (d-2)
     int half_rows;         // B: rows per ring half (multiple of 32)
     int aligned;           // out is 16-byte aligned
+    int ctas_per_sm;       // occupancy cap of the launch (0 = none)
     int g[FZ_MAX_D];
     FastDiv glast;         // division by g_{d-1} (walk leaves)
 };
@@ -338,8 +341,18 @@ __device__ __forceinline__ void flush_rows(const EnumParams &P, const int32_t *s
         const uint32_t rem_words = (bytes - bulk) >> 2;
         if ((uint32_t)lane < rem_words) gdst[(bulk >> 2) + lane] = src[(bulk >> 2) + lane];
     } else {
+        // plain stores (unaligned output, or host memory over the host link):
+        // 16-byte vectors when both sides allow it
         __syncwarp();
-        for (uint32_t w = lane; w < words; w += 32) gdst[w] = src[w];
+        uint32_t w0 = 0;
+        if ((((uintptr_t)gdst | (uintptr_t)src) & 15u) == 0) {
+            const uint32_t nv = words >> 2;
+            const int4 *s4 = reinterpret_cast<const int4 *>(src);
+            int4 *g4 = reinterpret_cast<int4 *>(gdst);
+            for (uint32_t v = lane; v < nv; v += 32) g4[v] = s4[v];
+            w0 = nv << 2;
+        }
+        for (uint32_t w = w0 + lane; w < words; w += 32) gdst[w] = src[w];
         __syncwarp();
     }
 }
@@ -884,32 +897,47 @@ __global__ void fz_direct_kernel(const EnumParams P, int mode) {
 // ---------------------------------------------------------------------------
 // host launchers
 // ---------------------------------------------------------------------------
-static int half_rows_for(int d) {
-    int b = RING_BYTES_PER_WARP / (8 * d);
+static int half_rows_for(int d, int ring_bytes = RING_BYTES_PER_WARP) {
+    int b = ring_bytes / (8 * d);
     b = (b / 32) * 32;
     return b < 32 ? 32 : b;
 }
 
-static size_t enum_smem_bytes(int d) {
-    return (size_t)ENUM_WARPS * 2 * half_rows_for(d) * d * 4 +
-           (size_t)ENUM_WARPS * sizeof(WarpPath);
+// Ring bytes per warp for an occupancy cap: fewer resident warps get larger
+// rings, so the bytes in flight per SM stay about the same.
+// FZ_ENUM_RING_KB overrides (tuning only).
+static int ring_bytes_for(int ctas_per_sm) {
+    static const int forced = [] {
+        const char *e = getenv("FZ_ENUM_RING_KB");
+        const int kb = e ? atoi(e) : 0;
+        return (kb >= 4 && kb <= 24) ? kb * 1024 : 0;
+    }();
+    if (forced) return forced;
+    if (ctas_per_sm <= 0 || ctas_per_sm >= 4) return RING_BYTES_PER_WARP;
+    const int b = (192 * 1024) / (ctas_per_sm * ENUM_WARPS);
+    return b > 16 * 1024 ? 16 * 1024 : (b / 1024) * 1024;
 }
+
+constexpr int ENUM_MAX_SMEM = 200 * 1024;
 
 template <int D, int LAMF>
 static int launch_enum_dl(const EnumParams &P, cudaStream_t s, int sms) {
-    const size_t smem = enum_smem_bytes(D);
+    const size_t smem = (size_t)ENUM_WARPS * 2 * P.half_rows * D * 4 +
+                        (size_t)ENUM_WARPS * sizeof(WarpPath);
+    if (smem > (size_t)ENUM_MAX_SMEM) return set_error(FZ_EINTERNAL, "enumerate: ring too large");
     static bool attr_set[64] = {};
     int dev = 0;
     cudaGetDevice(&dev);
     if (dev < 64 && !attr_set[dev]) {
         FZ_CUDA_TRY(cudaFuncSetAttribute(fz_enum_kernel<D, LAMF>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)smem));
+                                         ENUM_MAX_SMEM));
         attr_set[dev] = true;
     }
     int per_sm = 0;
     FZ_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fz_enum_kernel<D, LAMF>,
                                                               ENUM_THREADS, smem));
+    if (P.ctas_per_sm > 0 && per_sm > P.ctas_per_sm) per_sm = P.ctas_per_sm;
     if (per_sm < 1) per_sm = 1;
     uint64_t want = (P.nslices + ENUM_WARPS - 1) / ENUM_WARPS;
     uint64_t grid = (uint64_t)per_sm * sms;
@@ -953,6 +981,7 @@ static EnumParams make_params(const EnumLaunch &L) {
     P.O = L.O;
     P.memo = L.memo;
     P.memo_rows = L.memo_rows;
+    P.ctas_per_sm = L.ctas_per_sm;
     P.RT = L.RT;
     P.W = L.W;
     P.lam_r = L.lam_r;
@@ -1032,7 +1061,7 @@ int launch_enumerate(const EnumLaunch &L, uint64_t rank_begin, uint64_t nrows, i
         uint64_t sc = (uint64_t)((double)slice_rows * per_row);
         P.slice_cost = sc < 64 ? 64 : sc;
     }
-    P.half_rows = half_rows_for(L.d);
+    P.half_rows = half_rows_for(L.d, ring_bytes_for(L.ctas_per_sm));
     FZ_DISPATCH_D(L.d, launch_enum_d, P, s, dp.sms);
 }
 

@@ -254,10 +254,12 @@ struct MemoBuffers {
     int32_t *rows = nullptr;       // rows * k
     int *status = nullptr;         // device status word
     unsigned *bar = nullptr;       // 2 words: barrier count, generation
+    bool small_ctas = false;       // fill with small CTAs (beside a capped enumeration)
 };
 // Gather map + batched copy-and-increment fill.  Asynchronous.
+// schedule: FZ_MEMO_BATCHED (one launch), FZ_MEMO_PER_BATCH or FZ_MEMO_PER_COPY.
 int launch_memo_build(const int32_t *tail, int k, int32_t top, uint64_t rows,
-                      const MemoBuffers &mb, cudaStream_t s);
+                      const MemoBuffers &mb, cudaStream_t s, int schedule = FZ_MEMO_BATCHED);
 // Many small memos, one CTA each (fz_memo.cu).
 struct MemoJob {
     const uint64_t *Ct;  // tail count table rows 0..k, stride cs (row 0: |Z(r, tail)|)
@@ -291,6 +293,9 @@ struct EnumLaunch {
     // the output is host memory reached over the host link: flush rows with
     // plain coalesced stores instead of bulk (TMA) stores
     bool plain_stores = false;
+    // at most this many CTAs of the enumeration kernel per SM (0 = as many as
+    // fit), leaving room for other kernels to run beside it
+    int ctas_per_sm = 0;
 };
 // Runs table: RT[lam][x] = 1, RT[j][x] = sum_t RT[j+1][x - t g_j] (fz_count.cu).
 int launch_runs_table(const int32_t *g, int lam, int32_t n, uint64_t *RT, uint64_t *tmp,

@@ -20,6 +20,7 @@
 // cooperative launch.  Empty batches need no barrier.
 #include <cstdlib>
 #include <cstring>
+#include <vector>
 
 #include "fz_internal.cuh"
 
@@ -84,33 +85,103 @@ struct FillParams {
     int nbatch;
 };
 
-// Batches of b elements; one copy-and-increment per memo row; bounded grid
-// barrier between non-empty batches.
-__global__ void __launch_bounds__(THREADS) memo_fill_kernel(FillParams P) {
-    const int64_t tid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    const int64_t nthreads = (int64_t)gridDim.x * blockDim.x;
+// The copies run over memo WORDS: word w is coordinate w % k of row w / k.
+// A thread first loads the source words of all the words it owns in the
+// batch and only then stores them (sources precede the batch, so the loads
+// cannot alias the stores): one L2 round trip per batch, not one per row.
+constexpr int FILL_W = 4;  // words per thread per pass
+
+struct WordPos {
+    uint64_t R;  // row
+    uint32_t c;  // coordinate
+};
+
+__device__ __forceinline__ WordPos word_pos(uint64_t w, int k) {
+    WordPos p;
+    p.R = w / (uint64_t)k;
+    p.c = (uint32_t)(w - p.R * (uint64_t)k);
+    return p;
+}
+
+// advance by `nthreads` words, nthreads = qn * k + rn
+__device__ __forceinline__ void word_step(WordPos &p, uint64_t qn, uint32_t rn, int k) {
+    p.R += qn;
+    p.c += rn;
+    if (p.c >= (uint32_t)k) {
+        p.c -= (uint32_t)k;
+        p.R += 1;
+    }
+}
+
+// Value of one word of a copied row: the source row's word, plus one on the
+// incremented coordinate.  False if the map names a source inside the batch.
+// LOCAL: every row was written by this CTA (ordered by __syncthreads), so
+// the source may come from L1; otherwise it is read from L2 (ld.cg).
+template <bool LOCAL>
+__device__ __forceinline__ bool word_value(const FillParams &P, uint64_t e, uint32_t c,
+                                           uint64_t R0, int32_t &v) {
+    if (e == MAP_ZERO) {
+        v = 0;
+        return true;
+    }
+    const uint64_t sr = e >> 4;
+    if (sr >= R0) return false;  // bounds guard: sources precede the batch
+    const int32_t *src = P.rows + sr * (uint64_t)P.k + c;
+    v = (LOCAL ? *src : ld_cg_s32(src)) + (c == (uint32_t)(e & 15u) ? 1 : 0);
+    return true;
+}
+
+// One pass over words base, base + nthreads, ... (FILL_W of them, < W1),
+// with the map entries already in e[] when `have_map`.
+template <bool HAVE_MAP, bool LOCAL = false>
+__device__ __forceinline__ void fill_pass(const FillParams &P, uint64_t base, uint64_t W1,
+                                          uint64_t R0, uint64_t nthreads, uint64_t qn,
+                                          uint32_t rn, uint64_t (&e)[FILL_W]) {
     const int k = P.k;
+    WordPos pos = word_pos(base, k);
+    uint32_t c[FILL_W];
+#pragma unroll
+    for (int j = 0; j < FILL_W; ++j) {
+        c[j] = pos.c;
+        if (!HAVE_MAP) e[j] = base + j * nthreads < W1 ? __ldg(P.map + pos.R) : MAP_ZERO;
+        word_step(pos, qn, rn, k);
+    }
+    int32_t v[FILL_W];
+    unsigned ok = 0;
+#pragma unroll
+    for (int j = 0; j < FILL_W; ++j)
+        if (base + j * nthreads < W1 && word_value<LOCAL>(P, e[j], c[j], R0, v[j]))
+            ok |= 1u << j;
+#pragma unroll
+    for (int j = 0; j < FILL_W; ++j) {
+        const uint64_t w = base + j * nthreads;
+        if (w < W1) {
+            if (ok >> j & 1u)
+                P.rows[w] = v[j];
+            else
+                atomicExch(P.status, (int)DEV_INTERNAL);
+        }
+    }
+}
+
+// Batches of b elements over the whole grid; bounded grid barrier between
+// non-empty batches.
+__global__ void __launch_bounds__(THREADS) memo_fill_kernel(FillParams P) {
+    const uint64_t tid = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const uint64_t nthreads = (uint64_t)gridDim.x * blockDim.x;
+    const int k = P.k;
+    const uint64_t qn = nthreads / (uint64_t)k;
+    const uint32_t rn = (uint32_t)(nthreads - qn * (uint64_t)k);
     for (int q = 0; q < P.nbatch; ++q) {
         const int64_t m0 = (int64_t)q * P.b;
         int64_t m1 = m0 + P.b;
         if (m1 > P.top) m1 = P.top;
         const uint64_t R0 = __ldg(P.O + m0), R1 = __ldg(P.O + m1);
         if (R1 == R0) continue;
-        for (uint64_t R = R0 + tid; R < R1; R += nthreads) {
-            const uint64_t e = __ldg(P.map + R);
-            int32_t *dst = P.rows + R * k;
-            if (e == MAP_ZERO) {
-                for (int c = 0; c < k; ++c) dst[c] = 0;
-            } else if ((e >> 4) >= R0) {  // bounds guard: sources precede the batch
-                atomicExch(P.status, (int)DEV_INTERNAL);
-            } else {
-                const int inc = (int)(e & 15u);
-                const int32_t *src = P.rows + (e >> 4) * k;
-                for (int c = 0; c < k; ++c) {
-                    int32_t v = ld_cg_s32(src + c);
-                    dst[c] = v + (c == inc ? 1 : 0);
-                }
-            }
+        const uint64_t W1 = R1 * (uint64_t)k;
+        for (uint64_t base = R0 * (uint64_t)k + tid; base < W1; base += FILL_W * nthreads) {
+            uint64_t e[FILL_W];
+            fill_pass<false>(P, base, W1, R0, nthreads, qn, rn, e);
         }
         if (q + 1 < P.nbatch && !grid_barrier(P.bar, P.status)) return;
     }
@@ -119,12 +190,17 @@ __global__ void __launch_bounds__(THREADS) memo_fill_kernel(FillParams P) {
 // ---------------------------------------------------------------------------
 // Cluster variant: one thread-block cluster runs every batch.  Between
 // batches the CTAs meet at the hardware cluster barrier; the arrive and the
-// wait are split so that the gather-map entries of the next batch (which do
-// not depend on the current one) are loaded while the barrier completes.
-// Source rows written by other CTAs of the cluster are read from L2 (ld.cg).
+// wait are split so that the gather-map entries of the next batch's first
+// pass (which do not depend on the current batch) are loaded while the
+// barrier completes.  Source words written by other CTAs of the cluster are
+// read from L2 (ld.cg).  ONE_CTA: a single CTA (no cluster) for memos whose
+// batches are a few rows each -- __syncthreads between batches and sources
+// from L1.  Instances: 16 x 1024 threads; 16 x 256 threads at <= 48
+// registers (fits beside an enumeration capped at 3 CTAs per SM); 1 x 1024.
 // ---------------------------------------------------------------------------
 constexpr int CL_THREADS = 1024;
-constexpr int CL_PF = 4;  // map entries prefetched per thread per batch
+constexpr int CL_SMALL_THREADS = 256;
+constexpr uint64_t ONE_CTA_MAX_WORDS = 2048;  // average words per batch
 
 __device__ __forceinline__ unsigned cluster_rank() {
     unsigned r;
@@ -146,63 +222,99 @@ __device__ __forceinline__ void cluster_wait_acquire() {
     asm volatile("barrier.cluster.wait.acquire.aligned;" ::: "memory");
 }
 
-__device__ __forceinline__ void fill_row(const FillParams &P, uint64_t R, uint64_t e,
-                                         uint64_t R0) {
-    const int k = P.k;
-    int32_t *dst = P.rows + R * k;
-    if (e == MAP_ZERO) {
-        for (int c = 0; c < k; ++c) dst[c] = 0;
-    } else if ((e >> 4) >= R0) {  // bounds guard: sources precede the batch
-        atomicExch(P.status, (int)DEV_INTERNAL);
-    } else {
-        const int inc = (int)(e & 15u);
-        const int32_t *src = P.rows + (e >> 4) * k;
-        for (int c = 0; c < k; ++c) {
-            int32_t v = ld_cg_s32(src + c);
-            dst[c] = v + (c == inc ? 1 : 0);
-        }
+__device__ __forceinline__ void prefetch_map(const FillParams &P, uint64_t base, uint64_t W1,
+                                             uint64_t nthreads, uint64_t qn, uint32_t rn,
+                                             uint64_t (&e)[FILL_W]) {
+    WordPos pos = word_pos(base, P.k);
+#pragma unroll
+    for (int j = 0; j < FILL_W; ++j) {
+        e[j] = base + j * nthreads < W1 ? __ldg(P.map + pos.R) : MAP_ZERO;
+        word_step(pos, qn, rn, P.k);
     }
 }
 
-__global__ void __launch_bounds__(CL_THREADS, 1) memo_fill_cluster_kernel(FillParams P) {
-    const uint64_t tid = (uint64_t)cluster_rank() * blockDim.x + threadIdx.x;
-    const uint64_t nthreads = (uint64_t)cluster_size() * blockDim.x;
+template <int MAXT, int MINB, bool ONE_CTA>
+__global__ void __launch_bounds__(MAXT, MINB) memo_fill_cluster_kernel(FillParams P) {
+    const uint64_t tid = (ONE_CTA ? 0u : (uint64_t)cluster_rank() * blockDim.x) + threadIdx.x;
+    const uint64_t nthreads = (ONE_CTA ? 1u : (uint64_t)cluster_size()) * blockDim.x;
+    const int k = P.k;
+    const uint64_t qn = nthreads / (uint64_t)k;
+    const uint32_t rn = (uint32_t)(nthreads - qn * (uint64_t)k);
     // batch 0 boundaries and map entries
     uint64_t R0 = __ldg(P.O), R1 = __ldg(P.O + (P.b < P.top ? P.b : P.top));
-    uint64_t pf[CL_PF];
-#pragma unroll
-    for (int j = 0; j < CL_PF; ++j) {
-        const uint64_t R = R0 + tid + j * nthreads;
-        pf[j] = R < R1 ? __ldg(P.map + R) : 0ull;
-    }
+    uint64_t e[FILL_W];
+    prefetch_map(P, R0 * k + tid, R1 * k, nthreads, qn, rn, e);
     for (int q = 0; q < P.nbatch; ++q) {
-        if (R1 != R0) {
-#pragma unroll
-            for (int j = 0; j < CL_PF; ++j) {
-                const uint64_t R = R0 + tid + j * nthreads;
-                if (R < R1) fill_row(P, R, pf[j], R0);
-            }
-            for (uint64_t R = R0 + tid + CL_PF * nthreads; R < R1; R += nthreads)
-                fill_row(P, R, __ldg(P.map + R), R0);
+        const uint64_t W0 = R0 * (uint64_t)k, W1 = R1 * (uint64_t)k;
+        if (W1 != W0) {
+            fill_pass<true, ONE_CTA>(P, W0 + tid, W1, R0, nthreads, qn, rn, e);
+            for (uint64_t base = W0 + tid + FILL_W * nthreads; base < W1;
+                 base += FILL_W * nthreads)
+                fill_pass<false, ONE_CTA>(P, base, W1, R0, nthreads, qn, rn, e);
         }
-        // next batch's boundaries and map entries (independent of this batch)
+        // next batch's boundaries and first map entries (independent of this batch)
         const bool more = q + 1 < P.nbatch;
-        uint64_t N0 = R1, N1 = R1;
+        uint64_t N1 = R1;
         if (more) {
             int64_t m1 = (int64_t)(q + 2) * P.b;
             if (m1 > P.top) m1 = P.top;
             N1 = __ldg(P.O + m1);
         }
-        if (R1 != R0 && more) cluster_arrive_release();
-#pragma unroll
-        for (int j = 0; j < CL_PF; ++j) {
-            const uint64_t R = N0 + tid + j * nthreads;
-            pf[j] = R < N1 ? __ldg(P.map + R) : 0ull;
+        if (ONE_CTA) {
+            prefetch_map(P, R1 * k + tid, N1 * k, nthreads, qn, rn, e);
+            if (W1 != W0 && more) __syncthreads();
+        } else {
+            if (W1 != W0 && more) cluster_arrive_release();
+            prefetch_map(P, R1 * k + tid, N1 * k, nthreads, qn, rn, e);
+            if (W1 != W0 && more) cluster_wait_acquire();
         }
-        if (R1 != R0 && more) cluster_wait_acquire();
-        R0 = N0;
+        R0 = R1;
         R1 = N1;
     }
+}
+
+// ---------------------------------------------------------------------------
+// Launch-per-step schedules (Section 2.2 and the factorizationwise parallel
+// algorithm of Section 2.4), kept for comparison with the single-launch
+// build above.
+//
+// Per batch ("both" parallelism): one launch per elementwise batch, covering
+// every copy of the batch; consecutive launches on one stream order the
+// batches.
+__global__ void __launch_bounds__(THREADS) memo_batch_kernel(FillParams P, int q) {
+    const uint64_t tid = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const uint64_t nthreads = (uint64_t)gridDim.x * blockDim.x;
+    const int k = P.k;
+    const uint64_t qn = nthreads / (uint64_t)k;
+    const uint32_t rn = (uint32_t)(nthreads - qn * (uint64_t)k);
+    const int64_t m0 = (int64_t)q * P.b;
+    int64_t m1 = m0 + P.b;
+    if (m1 > P.top) m1 = P.top;
+    const uint64_t R0 = __ldg(P.O + m0), R1 = __ldg(P.O + m1);
+    const uint64_t W1 = R1 * (uint64_t)k;
+    for (uint64_t base = R0 * (uint64_t)k + tid; base < W1; base += FILL_W * nthreads) {
+        uint64_t e[FILL_W];
+        fill_pass<false>(P, base, W1, R0, nthreads, qn, rn, e);
+    }
+}
+
+// Per copy (factorizationwise): one launch per (m, i), the kernel
+// copyAndIncrementIndex -- `len` rows from row `src` to row `dst`, coordinate
+// `inc` plus one, one thread per word.
+__global__ void __launch_bounds__(THREADS) copy_and_increment_kernel(int32_t *rows, int k,
+                                                                     uint64_t dst, uint64_t src,
+                                                                     uint64_t len, int inc) {
+    const uint64_t words = len * (uint64_t)k;
+    const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+    for (uint64_t w = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; w < words; w += stride) {
+        const uint64_t r = w / (uint64_t)k;
+        const int c = (int)(w - r * (uint64_t)k);
+        rows[dst * k + w] = rows[src * k + w] + (c == inc ? 1 : 0);
+    }
+}
+
+__global__ void zero_row_kernel(int32_t *rows, int k) {
+    if (threadIdx.x < (unsigned)k) rows[threadIdx.x] = 0;
 }
 
 int coop_grid(const void *kernel, int threads) {
@@ -219,17 +331,18 @@ int coop_grid(const void *kernel, int threads) {
 
 // One cluster of 16 CTAs (8 if 16 cannot be co-scheduled).  Returns
 // FZ_ECUDA without launching if no cluster shape fits.
-int launch_fill_cluster(FillParams fp, cudaStream_t s) {
+template <int MAXT, int MINB>
+static int launch_fill_cluster_t(FillParams fp, int threads, cudaStream_t s) {
+    auto kern = memo_fill_cluster_kernel<MAXT, MINB, false>;
     static bool attr_set = false;
     if (!attr_set) {
-        cudaFuncSetAttribute(memo_fill_cluster_kernel,
-                             cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+        cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
         attr_set = true;
     }
     for (int csize : {16, 8}) {
         cudaLaunchConfig_t cfg = {};
         cfg.gridDim = dim3(csize);
-        cfg.blockDim = dim3(CL_THREADS);
+        cfg.blockDim = dim3(threads);
         cfg.dynamicSmemBytes = 0;
         cfg.stream = s;
         cudaLaunchAttribute attr[1];
@@ -240,18 +353,37 @@ int launch_fill_cluster(FillParams fp, cudaStream_t s) {
         cfg.attrs = attr;
         cfg.numAttrs = 1;
         int nclusters = 0;
-        if (cudaOccupancyMaxActiveClusters(&nclusters, memo_fill_cluster_kernel, &cfg) !=
-                cudaSuccess ||
+        if (cudaOccupancyMaxActiveClusters(&nclusters, kern, &cfg) != cudaSuccess ||
             nclusters < 1) {
             cudaGetLastError();
             continue;
         }
-        cudaError_t e = cudaLaunchKernelEx(&cfg, memo_fill_cluster_kernel, fp);
+        cudaError_t e = cudaLaunchKernelEx(&cfg, kern, fp);
         if (e != cudaSuccess) return cuda_error(e, "memo fill (cluster) launch");
         note_launch();
         return FZ_OK;
     }
     return set_error(FZ_ECUDA, "memo fill: no cluster shape fits");
+}
+
+int launch_fill_cluster(FillParams fp, bool small_ctas, cudaStream_t s) {
+    // FZ_MEMO_CL_THREADS=256|512|1024 sets the CTA size of the large
+    // variant (tuning only)
+    static const int threads = [] {
+        const char *e = getenv("FZ_MEMO_CL_THREADS");
+        const int t = e ? atoi(e) : CL_THREADS;
+        return (t == 256 || t == 512 || t == 1024) ? t : CL_THREADS;
+    }();
+    if (small_ctas)
+        return launch_fill_cluster_t<CL_SMALL_THREADS, 5>(fp, CL_SMALL_THREADS, s);
+    return launch_fill_cluster_t<CL_THREADS, 1>(fp, threads, s);
+}
+
+int launch_fill_one_cta(FillParams fp, cudaStream_t s) {
+    memo_fill_cluster_kernel<CL_THREADS, 1, true><<<1, CL_THREADS, 0, s>>>(fp);
+    note_launch();
+    FZ_CUDA_TRY(cudaGetLastError());
+    return FZ_OK;
 }
 
 // ---------------------------------------------------------------------------
@@ -363,9 +495,50 @@ int launch_memo_cta_build(const MemoJob *jobs, int njobs, int *status, cudaStrea
     return FZ_OK;
 }
 
+// Factorizationwise schedule: the host walks m and i in the algorithm's
+// order with the saved cardinalities (copied to the host once) and launches
+// one copy per non-empty block.
+static int launch_memo_per_copy(const int32_t *tail, int k, int32_t top, uint64_t rows,
+                                const MemoBuffers &mb, cudaStream_t s) {
+    std::vector<uint64_t> O((size_t)top + 1), Ct((size_t)k * (size_t)mb.cs);
+    FZ_CUDA_TRY(cudaMemcpyAsync(O.data(), mb.O, O.size() * 8, cudaMemcpyDeviceToHost, s));
+    FZ_CUDA_TRY(cudaMemcpyAsync(Ct.data(), mb.Ct, Ct.size() * 8, cudaMemcpyDeviceToHost, s));
+    FZ_CUDA_TRY(cudaStreamSynchronize(s));
+    if (O[top] != rows) return set_error(FZ_EINTERNAL, "memo build: offsets disagree");
+    DeviceProps dp;
+    int rc = device_props(&dp);
+    if (rc != FZ_OK) return rc;
+    zero_row_kernel<<<1, 32, 0, s>>>(mb.rows, k);  // Z(0) = [0]
+    note_launch();
+    for (int64_t m = 1; m < top; ++m) {
+        uint64_t dst = O[m];
+        for (int i = 0; i < k; ++i) {
+            const int64_t sm = m - (int64_t)tail[i];
+            if (sm < 0) continue;
+            const uint64_t len = Ct[(size_t)i * mb.cs + sm];
+            if (len == 0) continue;
+            const uint64_t src = O[sm + 1] - len;  // Z_{>=i}(m - t_i): the last len rows
+            if (dst + len > O[m + 1]) return set_error(FZ_EINTERNAL, "memo build: block overflow");
+            uint64_t blocks = (len * (uint64_t)k + THREADS - 1) / THREADS;
+            if (blocks > (uint64_t)dp.sms * 8) blocks = (uint64_t)dp.sms * 8;
+            copy_and_increment_kernel<<<(unsigned)blocks, THREADS, 0, s>>>(mb.rows, k, dst, src,
+                                                                          len, i);
+            note_launch();
+            dst += len;
+        }
+        if (dst != O[m + 1]) return set_error(FZ_EINTERNAL, "memo build: blocks do not tile");
+    }
+    FZ_CUDA_TRY(cudaGetLastError());
+    return FZ_OK;
+}
+
 int launch_memo_build(const int32_t *tail, int k, int32_t top, uint64_t rows,
-                      const MemoBuffers &mb, cudaStream_t s) {
+                      const MemoBuffers &mb, cudaStream_t s, int schedule) {
     if (top <= 0 || rows == 0) return FZ_OK;
+    if (schedule == FZ_MEMO_PER_COPY) {
+        if (!mb.Ct || !mb.O || !mb.rows) return set_error(FZ_EINTERNAL, "memo build: missing device buffer");
+        return launch_memo_per_copy(tail, k, top, rows, mb, s);
+    }
     if (!mb.Ct || !mb.O || !mb.map || !mb.rows || !mb.status || !mb.bar)
         return set_error(FZ_EINTERNAL, "memo build: missing device buffer");
     MapParams mp{};
@@ -404,17 +577,32 @@ int launch_memo_build(const int32_t *tail, int k, int32_t top, uint64_t rows,
     // larger ones use the whole GPU with the bounded grid barrier.
     // variant: one cluster (hardware barrier, sources through L2) for batches
     // of modest size, else the whole GPU with the bounded grid barrier;
-    // FZ_MEMO_FILL=cluster|grid forces one (tuning only)
+    // FZ_MEMO_FILL=cta|cluster|grid forces one (tuning only)
     static const int forced = [] {
         const char *e = getenv("FZ_MEMO_FILL");
         if (!e) return 0;
+        if (!strcmp(e, "cta")) return 1;
         if (!strcmp(e, "cluster")) return 2;
         if (!strcmp(e, "grid")) return 3;
         return 0;
     }();
+    if (schedule == FZ_MEMO_PER_BATCH) {
+        DeviceProps dp;
+        int rc = device_props(&dp);
+        if (rc != FZ_OK) return rc;
+        for (int q = 0; q < fp.nbatch; ++q) {
+            memo_batch_kernel<<<dp.sms * 4, THREADS, 0, s>>>(fp, q);
+            note_launch();
+        }
+        FZ_CUDA_TRY(cudaGetLastError());
+        return FZ_OK;
+    }
     const uint64_t avg_batch_rows = rows / (uint64_t)fp.nbatch;
+    // a few rows per batch: one CTA (its barrier and L1 beat a cluster's)
+    if ((forced == 0 && avg_batch_rows * (uint64_t)k <= ONE_CTA_MAX_WORDS) || forced == 1)
+        return launch_fill_one_cta(fp, s);
     if ((forced == 0 && avg_batch_rows <= (uint64_t)64 * 1024) || forced == 2) {
-        int rc = launch_fill_cluster(fp, s);
+        int rc = launch_fill_cluster(fp, mb.small_ctas, s);
         if (rc == FZ_OK) return rc;
     }
     int grid = coop_grid((const void *)memo_fill_kernel, THREADS);

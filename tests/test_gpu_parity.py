@@ -148,6 +148,18 @@ def test_autotuned_random_instances(fz):
         assert np.array_equal(run_enum(fz, g, n), oracle.enumerate_desc(g, n)), (g, n)
 
 
+def test_measured_autotune(fz):
+    """Options measured on the device are remembered and give the same output."""
+    for g, n in (((7, 11, 13, 17, 19), 900), ((5, 8, 11, 14), 700), ((3, 4), 50), ((3,), 30)):
+        k, slice_rows, est_ms = fz.fz_autotune(g, n)
+        assert 0 <= k <= len(g) and est_ms >= 0
+        with fz.Plan(g, n) as plan:
+            assert plan.k == k
+            if slice_rows > 0:
+                assert plan.slice_rows == slice_rows
+        assert np.array_equal(run_enum(fz, g, n), oracle.enumerate_desc(g, n)), (g, n)
+
+
 @pytest.mark.parametrize("d", [2, 3, 5, 6, 7, 9, 12, 16])
 def test_small_slices_ring_boundaries(fz, d):
     """Tiny slices and many ring halves: every flush path, every tuple width."""
@@ -302,6 +314,28 @@ def test_memo_matches_factorizationwise_algorithm(fz):
     ref_off, ref_rows = oracle.fwpar_lists(g, N)
     assert np.array_equal(off, ref_off)
     assert np.array_equal(rows, ref_rows)
+
+
+@pytest.mark.parametrize("schedule", [1, 2])
+def test_memo_launch_schedules(fz, schedule):
+    """One launch per batch and one launch per (m, i) copy give the same memo."""
+    for tail, top in (((11, 14), 501), ((4, 9, 10), 300), ((2, 2, 3), 50), ((5,), 40),
+                      ((13, 37, 38, 40), 400)):
+        ref_off, ref_rows = oracle.lex_lists_c(tail, top)
+        rows = int(ref_off[-1])
+        k = len(tail)
+        off = torch.zeros(top + 1, dtype=torch.int64, device="cuda")
+        buf = torch.full(((rows + 4) * k,), CANARY, dtype=torch.int32, device="cuda")
+        got = fz.fz_build_memo_schedule(tail, top, schedule, off, buf, rows)
+        torch.cuda.synchronize()
+        assert got == rows
+        host = buf.cpu().numpy()
+        assert (host[rows * k:] == CANARY).all()
+        assert np.array_equal(off.cpu().numpy().view(np.uint64), ref_off), (tail, schedule)
+        assert np.array_equal(host[:rows * k].reshape(rows, k), ref_rows), (tail, schedule)
+    with pytest.raises(fz.FzError) as e:
+        fz.fz_build_memo_schedule((3, 4), 10, 7, off, buf, rows)
+    assert e.value.status == fz.FZ_EINVAL
 
 
 def test_memo_library_owned_handle(fz):
