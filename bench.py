@@ -312,31 +312,36 @@ def run_ours(args):
     ms = start.elapsed_time(end)
     ms_serial = ms
     pipelined = False
-    enum_cap = None
+    enum_cap = depth = None
+    trial_ms = {}
     if not args.no_pipeline:
-        # Pipelined steps: two plans of the same element alternate; step i+1's
-        # count tables and memo build (latency-bound, 16 SMs) run on one
-        # stream while step i's enumeration (bandwidth-bound) runs on another.
-        # The enumeration is capped at 3 or 2 blocks per SM (larger rings) so
-        # the build fits beside it; the faster cap is chosen in the warm-up.
-        # Every step still does its whole path.
-        plan2 = fz.Plan(g, n, k=plan.k, slice_rows=args.slice_rows)
-        plans = [plan, plan2]
-        s_b, s_e = torch.cuda.Stream(), torch.cuda.Stream()
-        built = [torch.cuda.Event(), torch.cuda.Event()]
-        done = [torch.cuda.Event(), torch.cuda.Event()]
+        # Pipelined steps: `depth` plans of the same element take turns; the
+        # count tables and memo builds of the next steps (latency-bound, 16
+        # SMs each, one stream per plan) run while the current step's
+        # enumeration (bandwidth-bound) runs on its own stream.  The
+        # enumeration is capped at 3 or 2 blocks per SM (larger rings) so the
+        # builds fit beside it.  The cap and the depth (2 or 3) are chosen in
+        # the warm-up.  Every step still does its whole path.
+        plans = [plan] + [fz.Plan(g, n, k=plan.k, slice_rows=args.slice_rows)
+                          for _ in range(2)]
+        s_bs = [torch.cuda.Stream() for _ in plans]
+        s_e = torch.cuda.Stream()
+        built = [torch.cuda.Event() for _ in plans]
+        done = [torch.cuda.Event() for _ in plans]
+        depth = 2
 
         def pipelined_steps(count_steps, kernel_evs=None):
             st0 = torch.cuda.Event(enable_timing=True)
             st1 = torch.cuda.Event(enable_timing=True)
             st0.record(s_e)
-            s_b.wait_event(st0)
+            for sb in s_bs:
+                sb.wait_event(st0)
             for i in range(count_steps):
-                j = i & 1
-                if i >= 2:
-                    s_b.wait_event(done[j])
-                plans[j].rebuild(stream=s_b)
-                built[j].record(s_b)
+                j = i % depth
+                if i >= depth:
+                    s_bs[j].wait_event(done[j])
+                plans[j].rebuild(stream=s_bs[j])
+                built[j].record(s_bs[j])
                 s_e.wait_event(built[j])
                 if kernel_evs:  # enumeration launch time, on its own stream
                     kernel_evs[i][0].record(s_e)
@@ -348,16 +353,18 @@ def run_ours(args):
             torch.cuda.synchronize()
             return st0.elapsed_time(st1)
 
-        cap_ms = {}
-        for cap in (3, 2):
-            for p_ in plans:
-                p_.set_enum_ctas_per_sm(cap)
-            pipelined_steps(2)
-            cap_ms[cap] = pipelined_steps(max(args.warmup, 3))
-        enum_cap = min(cap_ms, key=cap_ms.get)
+        for dep in (2, 3):
+            for cap in (3, 2):
+                depth = dep
+                for p_ in plans:
+                    p_.set_enum_ctas_per_sm(cap)
+                pipelined_steps(dep + 1)
+                c = max(args.warmup, 3) + dep
+                trial_ms[(dep, cap)] = pipelined_steps(c) / c
+        depth, enum_cap = min(trial_ms, key=trial_ms.get)
         for p_ in plans:
             p_.set_enum_ctas_per_sm(enum_cap)
-        pipelined_steps(2)
+        pipelined_steps(depth + 1)
         for p_ in plans:
             p_.sync()
         l0 = fz.fz_kernel_launches()
@@ -373,7 +380,8 @@ def run_ours(args):
         launches = fz.fz_kernel_launches() - l0
         for p_ in plans:
             p_.sync()
-        plan2.close()
+        for p_ in plans[1:]:
+            p_.close()
         plan.set_enum_ctas_per_sm(0)
         ms = ms_pipe
         pipelined = True
@@ -393,16 +401,18 @@ def run_ours(args):
 
     value = world * K * count / (ms / 1e3)
     bytes_per_launch = count * d * 4
-    # a plain device write of the same buffer (memset kernel): the practical
-    # write-only ceiling on this GPU, reported beside the copy peak
+    # a plain device write of the same bytes (a fill of 8-byte words, the
+    # vectorised path): the practical write-only ceiling on this GPU,
+    # reported beside the copy peak
+    wbuf = out[:(out.numel() // 2) * 2].view(torch.int64)
     wz0, wz1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    out.zero_()
+    wbuf.fill_(-1)
     wz0.record()
     for _ in range(3):
-        out.zero_()
+        wbuf.fill_(-1)
     wz1.record()
     torch.cuda.synchronize()
-    write_peak = 3 * out.numel() * 4 / (wz0.elapsed_time(wz1) / 1e3) / 1e9
+    write_peak = 3 * wbuf.numel() * 8 / (wz0.elapsed_time(wz1) / 1e3) / 1e9
     achieved = bytes_per_launch / (enum_ms / 1e3) / 1e9
     peaks = {}
     pp = os.path.join(ROOT, "MEASURED_PEAKS.json")
@@ -450,6 +460,10 @@ def run_ours(args):
                        "cuda_graph": graph is not None,
                        "pipelined": pipelined,
                        "pipeline_enum_ctas_per_sm": enum_cap if pipelined else None,
+                       "pipeline_depth": depth if pipelined else None,
+                       "pipeline_trials_ms_per_step": (
+                           {"depth%d_cap%d" % k_: round(v_, 4) for k_, v_ in trial_ms.items()}
+                           if pipelined else None),
                        "ms_per_step_serial": ms_serial / K,
                        "l2": "output %.1f GB per step >> 129 MB L2; count table and memo "
                              "rebuilt every step" % (bytes_per_launch / 1e9)},

@@ -132,6 +132,9 @@ struct fz_plan_s {
     DevBuf base;   // C, tmp, O, status, bar, counter
     DevBuf memo;   // map + rows
     DevBuf runs;   // runs table for work-balanced slicing
+    DevBuf runm;   // memo in run order + class starts (full memo, k <= 3)
+    int4 *run_memo = nullptr;
+    uint64_t *cls_beg = nullptr;
     uint64_t *RT = nullptr;
     int lam_r = 0;
     uint64_t W = 0;
@@ -170,7 +173,16 @@ uint64_t run_cost_rows() {
     return w;
 }
 
-// Enqueue the memo of plan p (offsets scan, gather map, fill).
+// FZ_RUN_MEMO=0 keeps full memos in element order only (tuning only).
+bool run_memo_enabled() {
+    static const bool on = [] {
+        const char *e = getenv("FZ_RUN_MEMO");
+        return !(e && e[0] == '0');
+    }();
+    return on;
+}
+
+// Enqueue the memo of plan p (offsets scan, gather map, fill, run order).
 int plan_enqueue_memo(fz_plan_s *p, cudaStream_t s) {
     if (p->K < 1 || p->top < 1) return FZ_OK;
     const int64_t cs = (int64_t)p->n + 1;
@@ -188,7 +200,11 @@ int plan_enqueue_memo(fz_plan_s *p, cudaStream_t s) {
     mb.bar = p->bar;
     // an enumeration capped below full occupancy leaves room for a small build
     mb.small_ctas = p->ctas_per_sm > 0 && p->ctas_per_sm <= 3;
-    return launch_memo_build(p->g + (p->d - p->K), p->K, p->top, p->memo_rows, mb, s);
+    rc = launch_memo_build(p->g + (p->d - p->K), p->K, p->top, p->memo_rows, mb, s);
+    if (rc != FZ_OK || !p->run_memo) return rc;
+    const int lam = p->d - p->K - 1;
+    return launch_run_memo(p->C, cs, lam, p->n, p->g[lam], p->O, p->rows, p->K, p->memo_rows,
+                           p->cls_beg, p->run_memo, p->status, s);
 }
 
 int read_status(int *status_dev, cudaStream_t s) {
@@ -332,6 +348,20 @@ int plan_create_impl(const int32_t *g, int d, int32_t n, const fz_opts_t *opt, f
         if (rc != FZ_OK) return rc;
         p->map = p->memo.as<uint64_t>();
         p->rows = reinterpret_cast<int32_t *>(p->memo.as<char>() + off_rows);
+        // full memo of depth <= 3: also keep it in run order (16 bytes per
+        // row), which lets the enumeration copy whole subtrees of the last
+        // walked coordinate as one contiguous range
+        if (p->top > n && k <= 3 && k <= d - 1 && run_memo_enabled()) {
+            const int32_t glam = p->g[d - k - 1];
+            const int64_t G = glam < (int64_t)n + 1 ? glam : (int64_t)n + 1;
+            const size_t rm_bytes = align256(p->memo_rows * 16);
+            if (p->runm.alloc(rm_bytes + (size_t)(G + 1) * 8) == FZ_OK) {
+                p->run_memo = p->runm.as<int4>();
+                p->cls_beg = reinterpret_cast<uint64_t *>(p->runm.as<char>() + rm_bytes);
+            } else {
+                cudaGetLastError();  // optional: without it the leaf-by-leaf copy runs
+            }
+        }
         rc = plan_enqueue_memo(p, s);
         if (rc != FZ_OK) return rc;
         rc = read_status(p->status, s);
@@ -340,7 +370,7 @@ int plan_create_impl(const int32_t *g, int d, int32_t n, const fz_opts_t *opt, f
     // runs table for work-balanced slicing (not needed when the output is a
     // single block: d == 1 or k == d with a full memo)
     const bool single_block = d == 1 || (p->K == d && p->top > n);
-    if (!single_block && p->count > 0) {
+    if (!single_block && p->count > 0 && !p->run_memo) {
         const bool memo = p->K >= 1 && p->K <= d - 1 && p->top > 0;
         // one past the leaf coordinate; with a partial memo most leaves may be
         // walk leaves, so count candidates at the walk level then
@@ -386,6 +416,8 @@ EnumLaunch launch_of(const fz_plan_s *p) {
     L.top = p->top;
     L.g = p->g;
     L.ctas_per_sm = p->ctas_per_sm;
+    L.run_memo = p->run_memo;
+    L.cls_beg = p->cls_beg;
     if (p->RT) {
         L.RT = p->RT;
         L.W = p->W;

@@ -78,8 +78,10 @@ block_sum_kernel(const uint64_t *__restrict__ in, uint64_t *__restrict__ S, int6
     }
 }
 
-// out[r] = carry(block) + running sum inside the block.
-__global__ void __launch_bounds__(THREADS)
+// out[r] = carry(block) + running sum inside the block.  At most 64
+// registers (4 blocks per SM), so that it fits beside an enumeration capped
+// at 3 blocks per SM.
+__global__ void __launch_bounds__(THREADS, 4)
 block_apply_kernel(const uint64_t *__restrict__ in, uint64_t *__restrict__ out,
                    const uint64_t *__restrict__ Sincl, int64_t len, int64_t g, int64_t slen) {
     int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -88,7 +90,7 @@ block_apply_kernel(const uint64_t *__restrict__ in, uint64_t *__restrict__ out,
         const int64_t b = i / g, rho = i - b * g;
         uint64_t acc = b > 0 ? Sincl[i - g] : 0ull;
         const int64_t r0 = (b * RB) * g + rho;
-#pragma unroll 8
+#pragma unroll 4
         for (int t = 0; t < RB; ++t) {
             int64_t r = r0 + (int64_t)t * g;
             if (r < len) {

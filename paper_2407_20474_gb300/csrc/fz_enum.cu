@@ -83,6 +83,9 @@ struct EnumParams {
     int half_rows;         // B: rows per ring half (multiple of 32)
     int aligned;           // out is 16-byte aligned
     int ctas_per_sm;       // occupancy cap of the launch (0 = none)
+    int dense_min;         // memo batches with >= dense_min rows per leaf go leaf by leaf
+    const int4 *run_memo;  // full memo in run order (k <= 3), or null
+    const uint64_t *cls_beg;
     int g[FZ_MAX_D];
     FastDiv glast;         // division by g_{d-1} (walk leaves)
 };
@@ -358,12 +361,14 @@ __device__ __forceinline__ void flush_rows(const EnumParams &P, const int32_t *s
 }
 
 // 4-byte global -> shared copy that does not hold a register (cp.async).
+// No memory clobber: the source (memo) is read-only, the destination word is
+// touched by nothing else until cp.async.wait_group (which has the clobber),
+// and volatile keeps issue order with the commit and the wait.
 __device__ __forceinline__ void cp_async4(int32_t *sdst, const int32_t *gsrc) {
-    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(smem_addr(sdst)), "l"(gsrc)
-                 : "memory");
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(smem_addr(sdst)), "l"(gsrc));
 }
 __device__ __forceinline__ void cp_async_commit() {
-    asm volatile("cp.async.commit_group;" ::: "memory");
+    asm volatile("cp.async.commit_group;");
 }
 template <int N>
 __device__ __forceinline__ void cp_async_wait() {
@@ -502,8 +507,8 @@ __device__ __forceinline__ bool enum_slice(const EnumParams &P, WarpPath *wp, in
         // Dense batches of memo leaves: rounds follow the leaves, so every
         // lane of a round copies a row of the same leaf (no per-row search).
         const bool all_memo = __all_sync(FULL, lane >= consumed || type == T_MEMO);
-        const bool dense =
-            memo_run && all_memo && consumed > 0 && batch_rows >= 16ull * (uint64_t)consumed;
+        const bool dense = memo_run && all_memo && consumed > 0 &&
+                           batch_rows >= (uint64_t)P.dense_min * (uint64_t)consumed;
         if (dense && q_end > q_begin) {
             const int lfirst = __popc(__ballot_sync(FULL, E32 <= q_begin));
             for (int j = lfirst; j < consumed; ++j) {
@@ -727,6 +732,164 @@ __global__ void __launch_bounds__(ENUM_THREADS, 4)
 }
 
 // ---------------------------------------------------------------------------
+// Full memo of depth K <= 3 in run order.  The walk covers the leading LAMF
+// coordinates only: for a prefix (a_0..a_{LAMF-1}) with remainder r, the
+// rows of its whole subtree -- every a_LAMF from r div g down to 0, each with
+// Memo[r - a_LAMF g] -- are the contiguous run-memo range
+// [cls_beg[r mod g], + C[LAMF][r]) with a_LAMF = r div g - (first word).  A
+// round is then one 16-byte load and one row store per lane.
+// ---------------------------------------------------------------------------
+template <int D, int LAMF, int K>
+__device__ __forceinline__ void run_store_row(int32_t *dst, const int (&a)[LAMF > 0 ? LAMF : 1],
+                                              int vmax, int4 m) {
+    int32_t w[D];
+#pragma unroll
+    for (int c = 0; c < LAMF; ++c) w[c] = a[c];
+    w[LAMF] = vmax - m.x;
+    if constexpr (K >= 1) w[LAMF + 1] = m.y;
+    if constexpr (K >= 2) w[LAMF + 2] = m.z;
+    if constexpr (K >= 3) w[LAMF + 3] = m.w;
+    if constexpr (D % 2 == 0) {  // row starts are 8-byte aligned: 8-byte stores
+#pragma unroll
+        for (int c = 0; c < D; c += 2)
+            *reinterpret_cast<int2 *>(dst + c) = make_int2(w[c], w[c + 1]);
+    } else {
+#pragma unroll
+        for (int c = 0; c < D; ++c) dst[c] = w[c];
+    }
+}
+
+template <int D, int LAMF, int K>
+__device__ __forceinline__ bool runs_slice(const EnumParams &P, int32_t *ring, uint32_t B,
+                                           uint64_t row0, uint64_t row1, uint64_t pol,
+                                           int lane) {
+    // unrank the first row: the prefix, its remainder and the offset in its run
+    int a[LAMF > 0 ? LAMF : 1];
+    int r[LAMF + 1];
+    uint64_t R = P.rank_begin + row0;
+    r[0] = P.n;
+    a[0] = 0;
+#pragma unroll
+    for (int j = 0; j < LAMF; ++j) {
+        int v;
+        uint64_t before;
+        find_child(P, j, r[j], R, lane, v, before);
+        a[j] = v;
+        R -= before;
+        r[j + 1] = r[j] - v * P.g[j];
+    }
+    uint64_t off = R;
+    uint64_t left = row1 - row0;
+    uint32_t hpos = 0, half = 0, nfull = 0;
+    const int glam = P.g[LAMF];
+    bool ok = true;
+    for (;;) {
+        const int rem = r[LAMF];
+        const uint64_t run_rows = __ldg(P.C + (long long)LAMF * P.cs + rem);
+        if (off < run_rows) {
+            const int vmax = rem / glam;
+            const int cls = rem - vmax * glam;
+            uint64_t src = __ldg(P.cls_beg + cls) + off;
+            uint64_t take = run_rows - off;
+            if (take > left) take = left;
+            if (src + take > P.memo_rows) {  // bounds guard: the run lies in the memo
+                if (lane == 0) atomicExch(P.status, (int)DEV_INTERNAL);
+                ok = false;
+                break;
+            }
+            left -= take;
+            // rounds of up to 32 rows (never across a ring half); the next
+            // round's memo rows are loaded before this round's rows are stored
+            uint32_t cnt = take < 32 ? (uint32_t)take : 32u;
+            if (cnt > B - hpos) cnt = B - hpos;
+            int4 cur = make_int4(0, 0, 0, 0);
+            if ((uint32_t)lane < cnt) cur = __ldg(P.run_memo + src + lane);
+            while (take > 0) {
+                const uint64_t take2 = take - cnt;
+                const uint32_t hpos2 = hpos + cnt == B ? 0u : hpos + cnt;
+                uint32_t cnt2 = take2 < 32 ? (uint32_t)take2 : 32u;
+                if (cnt2 > B - hpos2) cnt2 = B - hpos2;
+                int4 nxt = make_int4(0, 0, 0, 0);
+                if ((uint32_t)lane < cnt2) nxt = __ldg(P.run_memo + src + cnt + lane);
+                if (hpos == 0 && nfull >= 2) {
+                    // re-entering a half: the bulk store issued from it two
+                    // flushes ago must have finished reading it
+                    if (lane == 0) bulk_wait_read<1>();
+                    __syncwarp();
+                }
+                if ((uint32_t)lane < cnt)
+                    run_store_row<D, LAMF, K>(ring + (size_t)(half * B + hpos + lane) * D, a,
+                                              vmax, cur);
+                hpos += cnt;
+                if (hpos == B) {
+                    flush_rows(P, ring + (size_t)half * B * D, row0 + (uint64_t)nfull * B, B, D,
+                               lane, pol);
+                    ++nfull;
+                    half ^= 1u;
+                    hpos = 0;
+                }
+                src += cnt;
+                take = take2;
+                cnt = cnt2;
+                cur = nxt;
+            }
+            if (left == 0) break;
+        }
+        off = 0;
+        // the next prefix in descending order: decrement the deepest positive
+        // coordinate, reset the ones after it to their maxima
+        int jj = -1;
+#pragma unroll
+        for (int j = 0; j < LAMF; ++j)
+            if (a[j] > 0) jj = j;
+        if (jj < 0) {  // past the last prefix with rows still owed
+            if (lane == 0) atomicExch(P.status, (int)DEV_INTERNAL);
+            ok = false;
+            break;
+        }
+#pragma unroll
+        for (int j = 0; j < LAMF; ++j) {
+            if (j == jj) {
+                a[j] -= 1;
+                r[j + 1] = r[j] - a[j] * P.g[j];
+            } else if (j > jj) {
+                a[j] = r[j] / P.g[j];
+                r[j + 1] = r[j] - a[j] * P.g[j];
+            }
+        }
+    }
+    if (hpos > 0)
+        flush_rows(P, ring + (size_t)half * B * D, row0 + (uint64_t)nfull * B, hpos, D, lane,
+                   pol);
+    if (lane == 0) bulk_wait_read_all();
+    __syncwarp();
+    return ok;
+}
+
+// Equal-row work items (every row costs the same here) from an atomic counter.
+template <int D, int LAMF, int K>
+__global__ void __launch_bounds__(ENUM_THREADS, 4)
+    fz_enum_runs_kernel(const __grid_constant__ EnumParams P) {
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    const int lane = threadIdx.x & 31;
+    const int wid = threadIdx.x >> 5;
+    const uint32_t B = (uint32_t)P.half_rows;
+    int32_t *ring = reinterpret_cast<int32_t *>(smem_raw) + (size_t)wid * 2 * B * D;
+    const uint64_t pol = policy_evict_first();
+    for (;;) {
+        unsigned long long s = 0;
+        if (lane == 0) s = atomicAdd(P.slice_counter, 1ull);
+        s = __shfl_sync(FULL, s, 0);
+        if (s >= P.nslices) break;
+        const uint64_t row0 = s * P.slice_rows;
+        const uint64_t row1 = row0 + P.slice_rows < P.nrows ? row0 + P.slice_rows : P.nrows;
+        if (!runs_slice<D, LAMF, K>(P, ring, B, row0, row1, pol, lane)) break;
+    }
+    if (lane == 0) bulk_wait_all();
+    __syncwarp();
+}
+
+// ---------------------------------------------------------------------------
 // Many instances in one persistent launch.  Work items (instance, slice) are
 // numbered consecutively, instance i owning items [item0[i], item0[i+1]); a
 // warp takes the next item from an atomic counter, finds its instance by a
@@ -920,23 +1083,21 @@ static int ring_bytes_for(int ctas_per_sm) {
 
 constexpr int ENUM_MAX_SMEM = 200 * 1024;
 
-template <int D, int LAMF>
-static int launch_enum_dl(const EnumParams &P, cudaStream_t s, int sms) {
+template <typename Kern>
+static int launch_enum_kernel(Kern kern, const EnumParams &P, int D, cudaStream_t s, int sms,
+                              bool (&attr_set)[64]) {
     const size_t smem = (size_t)ENUM_WARPS * 2 * P.half_rows * D * 4 +
                         (size_t)ENUM_WARPS * sizeof(WarpPath);
     if (smem > (size_t)ENUM_MAX_SMEM) return set_error(FZ_EINTERNAL, "enumerate: ring too large");
-    static bool attr_set[64] = {};
     int dev = 0;
     cudaGetDevice(&dev);
     if (dev < 64 && !attr_set[dev]) {
-        FZ_CUDA_TRY(cudaFuncSetAttribute(fz_enum_kernel<D, LAMF>,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize,
+        FZ_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          ENUM_MAX_SMEM));
         attr_set[dev] = true;
     }
     int per_sm = 0;
-    FZ_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fz_enum_kernel<D, LAMF>,
-                                                              ENUM_THREADS, smem));
+    FZ_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, ENUM_THREADS, smem));
     if (P.ctas_per_sm > 0 && per_sm > P.ctas_per_sm) per_sm = P.ctas_per_sm;
     if (per_sm < 1) per_sm = 1;
     uint64_t want = (P.nslices + ENUM_WARPS - 1) / ENUM_WARPS;
@@ -944,10 +1105,22 @@ static int launch_enum_dl(const EnumParams &P, cudaStream_t s, int sms) {
     if (want < grid) grid = want;
     if (grid < 1) grid = 1;
     FZ_CUDA_TRY(cudaMemsetAsync(P.slice_counter, 0, sizeof(unsigned long long), s));
-    fz_enum_kernel<D, LAMF><<<(unsigned)grid, ENUM_THREADS, smem, s>>>(P);
+    kern<<<(unsigned)grid, ENUM_THREADS, smem, s>>>(P);
     note_launch();
     FZ_CUDA_TRY(cudaGetLastError());
     return FZ_OK;
+}
+
+template <int D, int LAMF>
+static int launch_enum_dl(const EnumParams &P, cudaStream_t s, int sms) {
+    static bool attr_set[64] = {};
+    return launch_enum_kernel(fz_enum_kernel<D, LAMF>, P, D, s, sms, attr_set);
+}
+
+template <int D, int LAMF, int K>
+static int launch_enum_runs(const EnumParams &P, cudaStream_t s, int sms) {
+    static bool attr_set[64] = {};
+    return launch_enum_kernel(fz_enum_runs_kernel<D, LAMF, K>, P, D, s, sms, attr_set);
 }
 
 // Full memo of depth 2, 3 or 4: every run is a memo run at a fixed
@@ -956,6 +1129,11 @@ template <int D>
 static int launch_enum_d(const EnumParams &P, cudaStream_t s, int sms) {
     const bool full = P.lam_m >= 0 && P.top > P.n;
     const int K = P.K;
+    if (full && P.run_memo && P.cls_beg) {
+        if (K == 1 && D >= 2) return launch_enum_runs<D, (D >= 2 ? D - 2 : 0), 1>(P, s, sms);
+        if (K == 2 && D >= 3) return launch_enum_runs<D, (D >= 3 ? D - 3 : 0), 2>(P, s, sms);
+        if (K == 3 && D >= 4) return launch_enum_runs<D, (D >= 4 ? D - 4 : 0), 3>(P, s, sms);
+    }
     if (full && K == 2 && D >= 3) return launch_enum_dl<D, (D >= 3 ? D - 3 : 0)>(P, s, sms);
     if (full && K == 3 && D >= 4) return launch_enum_dl<D, (D >= 4 ? D - 4 : 0)>(P, s, sms);
     if (full && K == 4 && D >= 5) return launch_enum_dl<D, (D >= 5 ? D - 5 : 0)>(P, s, sms);
@@ -982,6 +1160,13 @@ static EnumParams make_params(const EnumLaunch &L) {
     P.memo = L.memo;
     P.memo_rows = L.memo_rows;
     P.ctas_per_sm = L.ctas_per_sm;
+    // FZ_ENUM_DENSE_MIN overrides the leaf-by-leaf threshold (tuning only)
+    static const int dense_min = [] {
+        const char *e = getenv("FZ_ENUM_DENSE_MIN");
+        const int v = e ? atoi(e) : 16;
+        return v >= 0 ? v : 16;
+    }();
+    P.dense_min = dense_min;
     P.RT = L.RT;
     P.W = L.W;
     P.lam_r = L.lam_r;
@@ -1000,6 +1185,11 @@ static EnumParams make_params(const EnumLaunch &L) {
         P.K = 0;
         P.top = 0;
     }
+    // the run-order memo serves full memos of depth 1..3
+    const bool runs = memo && L.top > L.n && L.K <= 3 && L.run_memo && L.cls_beg;
+    P.run_memo = runs ? L.run_memo : nullptr;
+    P.cls_beg = runs ? L.cls_beg : nullptr;
+    if (runs) P.RT = nullptr;  // every row costs the same: equal-row work items
     return P;
 }
 

@@ -138,6 +138,13 @@ __device__ __forceinline__ void bulk_wait_read_all() {
     asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory");
 }
 
+// Wait until at most N of this thread's committed bulk groups are still
+// reading their shared-memory source.
+template <int N>
+__device__ __forceinline__ void bulk_wait_read() {
+    asm volatile("cp.async.bulk.wait_group.read %0;" ::"n"(N) : "memory");
+}
+
 // Wait until every committed bulk group of this thread has completed.
 __device__ __forceinline__ void bulk_wait_all() {
     asm volatile("cp.async.bulk.wait_group 0;" ::: "memory");
@@ -271,6 +278,17 @@ struct MemoJob {
     int t[FZ_MAX_D];
 };
 int launch_memo_sizes(const MemoJob *jobs, int njobs, uint64_t *rows_out, cudaStream_t s);
+
+// The memo of a full plan (tail = g_{lam+1}..g_{d-1}, every element 0..n) in
+// run order: the rows of the elements p = c, c + g_lam, c + 2 g_lam, ... of
+// each residue class c mod g_lam, classes in increasing order, each row as
+// int4 (p div g_lam, its k <= 3 memo words, zero padding).  For a prefix
+// with remainder r at level lam, the rows of its whole subtree over a_lam are
+// then the contiguous range [cls_beg[r mod g_lam], + C[lam][r]), and a_lam =
+// r div g_lam - (first word).  cls_beg: G = min(g_lam, n + 1) class starts.
+int launch_run_memo(const uint64_t *C, int64_t cs, int lam, int32_t n, int32_t g_lam,
+                    const uint64_t *O, const int32_t *rows, int k, uint64_t memo_rows,
+                    uint64_t *cls_beg, int4 *run_memo, int *status, cudaStream_t s);
 int launch_memo_cta_build(const MemoJob *jobs, int njobs, int *status, cudaStream_t s);
 
 // Enumeration (fz_enum.cu).
@@ -296,6 +314,9 @@ struct EnumLaunch {
     // at most this many CTAs of the enumeration kernel per SM (0 = as many as
     // fit), leaving room for other kernels to run beside it
     int ctas_per_sm = 0;
+    // full memo of depth K <= 3 in run order (see launch_run_memo), or null
+    const int4 *run_memo = nullptr;
+    const uint64_t *cls_beg = nullptr;
 };
 // Runs table: RT[lam][x] = 1, RT[j][x] = sum_t RT[j+1][x - t g_j] (fz_count.cu).
 int launch_runs_table(const int32_t *g, int lam, int32_t n, uint64_t *RT, uint64_t *tmp,

@@ -477,7 +477,92 @@ __global__ void __launch_bounds__(MB_THREADS) memo_cta_build_kernel(const MemoJo
     }
 }
 
+// ---------------------------------------------------------------------------
+// The memo in run order (declared in fz_internal.cuh).  The element p of
+// class c = p mod g_lam, q = p div g_lam, starts at
+//   cls_beg[c] + sum_{p' = c mod g, p' < p} |Z(p', tail)|
+//             = cls_beg[c] + C[lam][p] - C[lam+1][p]
+// because the rows of a class up to p are exactly Z(p, (g_lam, tail)).
+// ---------------------------------------------------------------------------
+constexpr int RUN_CB_THREADS = 1024;
+
+__global__ void __launch_bounds__(RUN_CB_THREADS) run_class_begin_kernel(
+    const uint64_t *__restrict__ Clam, const uint64_t *__restrict__ O, int32_t n, int32_t g,
+    int32_t G, uint64_t *__restrict__ cls_beg, int *status) {
+    __shared__ uint64_t sums[33];
+    uint64_t carry = 0;
+    for (int base = 0; base < G; base += blockDim.x) {
+        const int c = base + (int)threadIdx.x;
+        uint64_t v = 0;
+        if (c < G) {
+            const int64_t last = c + (int64_t)((n - c) / g) * g;  // last element of class c
+            v = __ldg(Clam + last);
+        }
+        uint64_t total;
+        const uint64_t ex = block_exclusive_scan(v, sums, &total);
+        if (c < G) cls_beg[c] = carry + ex;
+        carry += total;
+    }
+    if (threadIdx.x == 0) {
+        cls_beg[G] = carry;
+        if (carry != __ldg(O + (int64_t)n + 1)) atomicExch(status, (int)DEV_INTERNAL);
+    }
+}
+
+// One warp per element: its rows, with q = p div g_lam in front, to their
+// place in run order.
+__global__ void __launch_bounds__(THREADS) run_memo_kernel(
+    const uint64_t *__restrict__ Clam, const uint64_t *__restrict__ Cnext,
+    const uint64_t *__restrict__ O, const int32_t *__restrict__ rows, int k, int32_t n,
+    int32_t g, const uint64_t *__restrict__ cls_beg, int4 *__restrict__ out, uint64_t out_rows,
+    int *status) {
+    const int lane = threadIdx.x & 31;
+    const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t p = warp; p <= n; p += nwarps) {
+        const int64_t q = p / g, c = p - q * g;
+        const uint64_t o0 = __ldg(O + p), len = __ldg(O + p + 1) - o0;
+        const uint64_t tail_rows = __ldg(Cnext + p);
+        const uint64_t dst = __ldg(cls_beg + c) + __ldg(Clam + p) - tail_rows;
+        if (len != tail_rows || dst + len > out_rows) {  // the tables must agree
+            if (lane == 0) atomicExch(status, (int)DEV_INTERNAL);
+            continue;
+        }
+        const int32_t *src = rows + o0 * (uint64_t)k;
+        for (uint64_t r = lane; r < len; r += 32) {
+            const int32_t *s = src + r * (uint64_t)k;
+            int4 v;
+            v.x = (int)q;
+            v.y = k > 0 ? s[0] : 0;
+            v.z = k > 1 ? s[1] : 0;
+            v.w = k > 2 ? s[2] : 0;
+            out[dst + r] = v;
+        }
+    }
+}
+
 }  // namespace
+
+int launch_run_memo(const uint64_t *C, int64_t cs, int lam, int32_t n, int32_t g_lam,
+                    const uint64_t *O, const int32_t *rows, int k, uint64_t memo_rows,
+                    uint64_t *cls_beg, int4 *run_memo, int *status, cudaStream_t s) {
+    if (k < 1 || k > 3 || g_lam < 1 || n < 0)
+        return set_error(FZ_EINTERNAL, "run memo: unsupported shape");
+    if (!C || !O || !rows || !cls_beg || !run_memo || !status)
+        return set_error(FZ_EINTERNAL, "run memo: missing device buffer");
+    const uint64_t *Clam = C + (int64_t)lam * cs;
+    const uint64_t *Cnext = C + (int64_t)(lam + 1) * cs;
+    const int32_t G = g_lam < n + 1 ? g_lam : n + 1;
+    run_class_begin_kernel<<<1, RUN_CB_THREADS, 0, s>>>(Clam, O, n, g_lam, G, cls_beg, status);
+    note_launch();
+    int64_t blocks = ((int64_t)n + 1) * 32 / THREADS + 1;
+    if (blocks > 4096) blocks = 4096;
+    run_memo_kernel<<<(int)blocks, THREADS, 0, s>>>(Clam, Cnext, O, rows, k, n, g_lam, cls_beg,
+                                                    run_memo, memo_rows, status);
+    note_launch();
+    FZ_CUDA_TRY(cudaGetLastError());
+    return FZ_OK;
+}
 
 int launch_memo_sizes(const MemoJob *jobs, int njobs, uint64_t *rows_out, cudaStream_t s) {
     if (njobs <= 0) return FZ_OK;
