@@ -229,6 +229,14 @@ def kernel_traffic(d):
     return rec.get("bytes_per_full_launch")
 
 
+def enum_kernel_name(plan):
+    """Name of the enumeration kernel the plan launches."""
+    d, k = plan.d, plan.k
+    if plan.run_order:
+        return "fz_enum_runs_kernel<%d, %d, %d>" % (d, d - k - 1, k)
+    return "fz_enum_kernel<%d>" % d
+
+
 def run_ours(args):
     import torch
     import __graft_entry__
@@ -319,9 +327,10 @@ def run_ours(args):
         # count tables and memo builds of the next steps (latency-bound, 16
         # SMs each, one stream per plan) run while the current step's
         # enumeration (bandwidth-bound) runs on its own stream.  The
-        # enumeration is capped at 3 or 2 blocks per SM (larger rings) so the
-        # builds fit beside it.  The cap and the depth (2 or 3) are chosen in
-        # the warm-up.  Every step still does its whole path.
+        # enumeration is capped at 4, 3 or 2 blocks per SM (larger rings at
+        # lower caps) so the builds fit beside it.  The cap and the depth (2
+        # or 3) are chosen in the warm-up.  Every step still does its whole
+        # path.
         plans = [plan] + [fz.Plan(g, n, k=plan.k, slice_rows=args.slice_rows)
                           for _ in range(2)]
         s_bs = [torch.cuda.Stream() for _ in plans]
@@ -354,7 +363,7 @@ def run_ours(args):
             return st0.elapsed_time(st1)
 
         for dep in (2, 3):
-            for cap in (3, 2):
+            for cap in (4, 3, 2):
                 depth = dep
                 for p_ in plans:
                     p_.set_enum_ctas_per_sm(cap)
@@ -469,7 +478,7 @@ def run_ours(args):
                              "rebuilt every step" % (bytes_per_launch / 1e9)},
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                          "frac": achieved / peak, "traffic": kernel_traffic(d),
-                         "kernel": "fz_enum_kernel<%d>" % d,
+                         "kernel": enum_kernel_name(plan),
                          "kernel_ms": enum_ms, "peak_source": peak_src,
                          "write_peak_gbs": write_peak,
                          "frac_of_write_peak": achieved / write_peak,

@@ -214,7 +214,8 @@ typedef struct fz_plan_info {
     uint64_t memo_rows;     /* rows in the memo (0 if k == 0) */
     uint64_t device_bytes;  /* device memory held by the plan */
     int32_t slice_rows;     /* resolved rows per warp work item */
-    int32_t reserved;
+    int32_t run_order;      /* 1 when the memo is also kept in run order and
+                               the subtree-run kernel enumerates, else 0 */
 } fz_plan_info_t;
 
 /* Count (device), choose k and top (opts or autotune), allocate, build the

@@ -68,7 +68,7 @@ class fz_plan_info_t(ctypes.Structure):
     _fields_ = [("count", ctypes.c_uint64), ("d", ctypes.c_int32), ("n", ctypes.c_int32),
                 ("k", ctypes.c_int32), ("top", ctypes.c_int32),
                 ("memo_rows", ctypes.c_uint64), ("device_bytes", ctypes.c_uint64),
-                ("slice_rows", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+                ("slice_rows", ctypes.c_int32), ("run_order", ctypes.c_int32)]
 
 
 class fz_memo_info_t(ctypes.Structure):
@@ -376,6 +376,7 @@ class Plan:
         self.memo_rows = int(info.memo_rows)
         self.device_bytes = int(info.device_bytes)
         self.slice_rows = int(info.slice_rows)
+        self.run_order = bool(info.run_order)
 
     def rebuild(self, stream=None):
         _check(lib().fz_plan_rebuild(self._h, _stream(stream)))

@@ -164,13 +164,17 @@ size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
 
 // Work of one leaf candidate of the walk, in rows; the
 // environment variable FZ_RUN_COST overrides it (tuning only).
-uint64_t run_cost_rows() {
-    static uint64_t w = [] {
+// Cost of one walked candidate in rows (work balancing).  A leaf candidate
+// of the leaf-by-leaf walk costs about 16 rows; a prefix of the run-order
+// walk costs a chain of three dependent table and memo loads, about 64 rows
+// of copying.  FZ_RUN_COST overrides both (tuning only).
+uint64_t run_cost_rows(bool run_order) {
+    static const long long forced = [] {
         const char *e = getenv("FZ_RUN_COST");
-        long long v = e ? atoll(e) : 0;
-        return v > 0 ? (uint64_t)v : (uint64_t)16;
+        return e ? atoll(e) : 0ll;
     }();
-    return w;
+    if (forced > 0) return (uint64_t)forced;
+    return run_order ? 64u : 16u;
 }
 
 // FZ_RUN_MEMO=0 keeps full memos in element order only (tuning only).
@@ -370,12 +374,19 @@ int plan_create_impl(const int32_t *g, int d, int32_t n, const fz_opts_t *opt, f
     // runs table for work-balanced slicing (not needed when the output is a
     // single block: d == 1 or k == d with a full memo)
     const bool single_block = d == 1 || (p->K == d && p->top > n);
-    if (!single_block && p->count > 0 && !p->run_memo) {
+    if (!single_block && p->count > 0) {
         const bool memo = p->K >= 1 && p->K <= d - 1 && p->top > 0;
-        // one past the leaf coordinate; with a partial memo most leaves may be
-        // walk leaves, so count candidates at the walk level then
-        p->lam_r = (memo && p->top > n ? d - p->K - 1 : d - 2) + 1;
-        p->W = run_cost_rows();
+        if (p->run_memo) {
+            // run-order memo: the walk visits every prefix of the leading
+            // d - K - 1 coordinates (empty or not) and copies its run
+            p->lam_r = d - p->K - 1;
+            p->W = run_cost_rows(true);
+        } else {
+            // one past the leaf coordinate; with a partial memo most leaves
+            // may be walk leaves, so count candidates at the walk level then
+            p->lam_r = (memo && p->top > n ? d - p->K - 1 : d - 2) + 1;
+            p->W = run_cost_rows(false);
+        }
         rc = p->runs.alloc((size_t)(p->lam_r + 1) * cs * 8);
         if (rc != FZ_OK) return rc;
         p->RT = p->runs.as<uint64_t>();
@@ -831,7 +842,7 @@ int fz_plan_info(fz_plan_t p, fz_plan_info_t *info) {
     info->memo_rows = p->memo_rows;
     info->device_bytes = p->base.bytes + p->memo.bytes + p->runs.bytes;
     info->slice_rows = (int32_t)p->slice_rows;
-    info->reserved = 0;
+    info->run_order = p->run_memo ? 1 : 0;
     return FZ_OK;
 }
 

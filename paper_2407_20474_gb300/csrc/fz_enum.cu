@@ -327,6 +327,51 @@ __device__ uint64_t rank_to_cost(const EnumParams &P, uint64_t R, int lane) {
     return cost + P.W + R;
 }
 
+// Rows [row0, row1) (relative to out) of work item s.  With a candidates
+// table the items are cost ranges of [cost_lo, cost_hi) snapped to multiples
+// of 32 rows: the first four fifths of the cost in items of slice_cost, the
+// rest in items of an eighth of that, so the warps that take the last items
+// finish close together.  Otherwise equal-row ranges.  Returns 0 when s is
+// past the last item, 1 when the item is empty, 2 otherwise.
+__device__ __forceinline__ int item_rows(const EnumParams &P, uint64_t s, uint64_t cost_lo,
+                                         uint64_t cost_hi, int lane, uint64_t &row0,
+                                         uint64_t &row1) {
+    if (P.RT) {
+        const uint64_t sc = P.slice_cost;
+        const uint64_t n1 = (cost_hi - cost_lo) / sc * 4 / 5;  // large items
+        const uint64_t sc_t = sc / 8 > 64 ? sc / 8 : 64;
+        uint64_t c0, c1;
+        if (s < n1) {
+            c0 = cost_lo + s * sc;
+            c1 = c0 + sc;
+        } else {
+            const uint64_t t = s - n1;
+            const uint64_t base = cost_lo + n1 * sc;
+            if (t >= (cost_hi - base + sc_t - 1) / sc_t) return 0;
+            c0 = base + t * sc_t;
+            c1 = c0 + sc_t;
+        }
+        if (c0 >= cost_hi) return 0;
+        row0 = 0;
+        if (s > 0) {
+            const uint64_t r = cost_to_rank(P, c0, lane);
+            row0 = r > P.rank_begin ? ((r - P.rank_begin) & ~31ull) : 0ull;
+            if (row0 > P.nrows) row0 = P.nrows;
+        }
+        row1 = P.nrows;
+        if (c1 < cost_hi) {
+            const uint64_t r = cost_to_rank(P, c1, lane);
+            row1 = r > P.rank_begin ? ((r - P.rank_begin) & ~31ull) : 0ull;
+            if (row1 > P.nrows) row1 = P.nrows;
+        }
+        return row1 > row0 ? 2 : 1;
+    }
+    if (s >= P.nslices) return 0;
+    row0 = s * P.slice_rows;
+    row1 = row0 + P.slice_rows < P.nrows ? row0 + P.slice_rows : P.nrows;
+    return 2;
+}
+
 __device__ __forceinline__ void flush_rows(const EnumParams &P, const int32_t *src,
                                            uint64_t out_row, uint32_t nrows, int d, int lane,
                                            uint64_t pol) {
@@ -701,29 +746,10 @@ __global__ void __launch_bounds__(ENUM_THREADS, 4)
         unsigned long long s = 0;
         if (lane == 0) s = atomicAdd(P.slice_counter, 1ull);
         s = __shfl_sync(FULL, s, 0);
-        uint64_t row0, row1;  // relative to out
-        if (P.RT) {
-            const uint64_t c0 = cost_lo + s * P.slice_cost;
-            if (c0 >= cost_hi) break;
-            const uint64_t c1 = c0 + P.slice_cost;
-            row0 = 0;
-            if (s > 0) {
-                const uint64_t r = cost_to_rank(P, c0, lane);
-                row0 = r > P.rank_begin ? ((r - P.rank_begin) & ~31ull) : 0ull;
-                if (row0 > P.nrows) row0 = P.nrows;
-            }
-            row1 = P.nrows;
-            if (c1 < cost_hi) {
-                const uint64_t r = cost_to_rank(P, c1, lane);
-                row1 = r > P.rank_begin ? ((r - P.rank_begin) & ~31ull) : 0ull;
-                if (row1 > P.nrows) row1 = P.nrows;
-            }
-            if (row1 <= row0) continue;
-        } else {
-            if (s >= P.nslices) break;
-            row0 = s * P.slice_rows;
-            row1 = row0 + P.slice_rows < P.nrows ? row0 + P.slice_rows : P.nrows;
-        }
+        uint64_t row0 = 0, row1 = 0;  // relative to out
+        const int it = item_rows(P, s, cost_lo, cost_hi, lane, row0, row1);
+        if (it == 0) break;
+        if (it == 1) continue;
         if (!enum_slice<D, LAMF>(P, wp, ring, B, row0, row1, pol, lane)) break;
     }
     cp_async_wait<0>();
@@ -798,29 +824,35 @@ __device__ __forceinline__ bool runs_slice(const EnumParams &P, int32_t *ring, u
                 break;
             }
             left -= take;
-            // rounds of up to 32 rows (never across a ring half); the next
-            // round's memo rows are loaded before this round's rows are stored
-            uint32_t cnt = take < 32 ? (uint32_t)take : 32u;
-            if (cnt > B - hpos) cnt = B - hpos;
-            int4 cur = make_int4(0, 0, 0, 0);
-            if ((uint32_t)lane < cnt) cur = __ldg(P.run_memo + src + lane);
+            // rounds of up to 32 rows (never across a ring half); the memo
+            // rows of the next two rounds are loaded before this round's rows
+            // are stored, so each load has two rounds to arrive from L2
+            uint32_t c0 = take < 32 ? (uint32_t)take : 32u;
+            if (c0 > B - hpos) c0 = B - hpos;
+            uint32_t hp1 = hpos + c0 == B ? 0u : hpos + c0;
+            uint64_t t1 = take - c0;
+            uint32_t c1 = t1 < 32 ? (uint32_t)t1 : 32u;
+            if (c1 > B - hp1) c1 = B - hp1;
+            int4 m0 = make_int4(0, 0, 0, 0), m1 = make_int4(0, 0, 0, 0);
+            if ((uint32_t)lane < c0) m0 = __ldg(P.run_memo + src + lane);
+            if ((uint32_t)lane < c1) m1 = __ldg(P.run_memo + src + c0 + lane);
             while (take > 0) {
-                const uint64_t take2 = take - cnt;
-                const uint32_t hpos2 = hpos + cnt == B ? 0u : hpos + cnt;
-                uint32_t cnt2 = take2 < 32 ? (uint32_t)take2 : 32u;
-                if (cnt2 > B - hpos2) cnt2 = B - hpos2;
-                int4 nxt = make_int4(0, 0, 0, 0);
-                if ((uint32_t)lane < cnt2) nxt = __ldg(P.run_memo + src + cnt + lane);
+                const uint32_t hp2 = hp1 + c1 == B ? 0u : hp1 + c1;
+                const uint64_t t2 = t1 - c1;
+                uint32_t c2 = t2 < 32 ? (uint32_t)t2 : 32u;
+                if (c2 > B - hp2) c2 = B - hp2;
+                int4 m2 = make_int4(0, 0, 0, 0);
+                if ((uint32_t)lane < c2) m2 = __ldg(P.run_memo + src + c0 + c1 + lane);
                 if (hpos == 0 && nfull >= 2) {
                     // re-entering a half: the bulk store issued from it two
                     // flushes ago must have finished reading it
                     if (lane == 0) bulk_wait_read<1>();
                     __syncwarp();
                 }
-                if ((uint32_t)lane < cnt)
+                if ((uint32_t)lane < c0)
                     run_store_row<D, LAMF, K>(ring + (size_t)(half * B + hpos + lane) * D, a,
-                                              vmax, cur);
-                hpos += cnt;
+                                              vmax, m0);
+                hpos += c0;
                 if (hpos == B) {
                     flush_rows(P, ring + (size_t)half * B * D, row0 + (uint64_t)nfull * B, B, D,
                                lane, pol);
@@ -828,10 +860,14 @@ __device__ __forceinline__ bool runs_slice(const EnumParams &P, int32_t *ring, u
                     half ^= 1u;
                     hpos = 0;
                 }
-                src += cnt;
-                take = take2;
-                cnt = cnt2;
-                cur = nxt;
+                src += c0;
+                take = t1;
+                c0 = c1;
+                m0 = m1;
+                t1 = t2;
+                c1 = c2;
+                m1 = m2;
+                hp1 = hp2;
             }
             if (left == 0) break;
         }
@@ -866,7 +902,10 @@ __device__ __forceinline__ bool runs_slice(const EnumParams &P, int32_t *ring, u
     return ok;
 }
 
-// Equal-row work items (every row costs the same here) from an atomic counter.
+// Work items from an atomic counter: equal-cost ranges when the plan has a
+// candidates table counted at level LAMF (each walked prefix costs W rows, so
+// the items at the start of the order, where prefixes hold few rows each, are
+// short), else equal-row ranges.
 template <int D, int LAMF, int K>
 __global__ void __launch_bounds__(ENUM_THREADS, 4)
     fz_enum_runs_kernel(const __grid_constant__ EnumParams P) {
@@ -876,13 +915,19 @@ __global__ void __launch_bounds__(ENUM_THREADS, 4)
     const uint32_t B = (uint32_t)P.half_rows;
     int32_t *ring = reinterpret_cast<int32_t *>(smem_raw) + (size_t)wid * 2 * B * D;
     const uint64_t pol = policy_evict_first();
+    uint64_t cost_lo = 0, cost_hi = 0;
+    if (P.RT) {
+        cost_lo = rank_to_cost(P, P.rank_begin, lane);
+        cost_hi = rank_to_cost(P, P.rank_begin + P.nrows, lane);
+    }
     for (;;) {
         unsigned long long s = 0;
         if (lane == 0) s = atomicAdd(P.slice_counter, 1ull);
         s = __shfl_sync(FULL, s, 0);
-        if (s >= P.nslices) break;
-        const uint64_t row0 = s * P.slice_rows;
-        const uint64_t row1 = row0 + P.slice_rows < P.nrows ? row0 + P.slice_rows : P.nrows;
+        uint64_t row0 = 0, row1 = 0;
+        const int it = item_rows(P, s, cost_lo, cost_hi, lane, row0, row1);
+        if (it == 0) break;
+        if (it == 1) continue;
         if (!runs_slice<D, LAMF, K>(P, ring, B, row0, row1, pol, lane)) break;
     }
     if (lane == 0) bulk_wait_all();
@@ -1189,7 +1234,9 @@ static EnumParams make_params(const EnumLaunch &L) {
     const bool runs = memo && L.top > L.n && L.K <= 3 && L.run_memo && L.cls_beg;
     P.run_memo = runs ? L.run_memo : nullptr;
     P.cls_beg = runs ? L.cls_beg : nullptr;
-    if (runs) P.RT = nullptr;  // every row costs the same: equal-row work items
+    // the run walk's candidates are the prefixes of its LAMF = d - K - 1
+    // leading coordinates; a table counted at another level cannot balance it
+    if (runs && P.lam_r != L.d - L.K - 1) P.RT = nullptr;
     return P;
 }
 
