@@ -815,59 +815,64 @@ __device__ __forceinline__ bool runs_slice(const EnumParams &P, int32_t *ring, u
         if (off < run_rows) {
             const int vmax = rem / glam;
             const int cls = rem - vmax * glam;
-            uint64_t src = __ldg(P.cls_beg + cls) + off;
-            uint64_t take = run_rows - off;
-            if (take > left) take = left;
-            if (src + take > P.memo_rows) {  // bounds guard: the run lies in the memo
+            const uint64_t src64 = __ldg(P.cls_beg + cls) + off;
+            uint64_t take64 = run_rows - off;
+            if (take64 > left) take64 = left;
+            if (src64 + take64 > P.memo_rows) {  // bounds guard: the run lies in the memo
                 if (lane == 0) atomicExch(P.status, (int)DEV_INTERNAL);
                 ok = false;
                 break;
             }
-            left -= take;
-            // rounds of up to 32 rows (never across a ring half); the memo
-            // rows of the next two rounds are loaded before this round's rows
-            // are stored, so each load has two rounds to arrive from L2
-            uint32_t c0 = take < 32 ? (uint32_t)take : 32u;
+            left -= take64;
+            // the run lies in the memo (< 2^30 rows): 32-bit row indices
+            uint32_t src = (uint32_t)src64, take = (uint32_t)take64;
+            // Rounds of up to 64 rows (never across a ring half); lane l
+            // stores rows l and l + 32 of a round.  The memo rows of the next
+            // round are loaded before this round's rows are stored.  The loop
+            // is unrolled twice so the two register sets swap roles without
+            // moves.
+            uint32_t c0 = take < 64u ? take : 64u;
             if (c0 > B - hpos) c0 = B - hpos;
-            uint32_t hp1 = hpos + c0 == B ? 0u : hpos + c0;
-            uint64_t t1 = take - c0;
-            uint32_t c1 = t1 < 32 ? (uint32_t)t1 : 32u;
-            if (c1 > B - hp1) c1 = B - hp1;
-            int4 m0 = make_int4(0, 0, 0, 0), m1 = make_int4(0, 0, 0, 0);
-            if ((uint32_t)lane < c0) m0 = __ldg(P.run_memo + src + lane);
-            if ((uint32_t)lane < c1) m1 = __ldg(P.run_memo + src + c0 + lane);
-            while (take > 0) {
-                const uint32_t hp2 = hp1 + c1 == B ? 0u : hp1 + c1;
-                const uint64_t t2 = t1 - c1;
-                uint32_t c2 = t2 < 32 ? (uint32_t)t2 : 32u;
-                if (c2 > B - hp2) c2 = B - hp2;
-                int4 m2 = make_int4(0, 0, 0, 0);
-                if ((uint32_t)lane < c2) m2 = __ldg(P.run_memo + src + c0 + c1 + lane);
+            int4 x0 = make_int4(0, 0, 0, 0), x1 = x0, y0 = x0, y1 = x0;
+            {
+                const int4 *ms = P.run_memo + src;
+                if ((uint32_t)lane < c0) x0 = __ldg(ms + lane);
+                if ((uint32_t)lane + 32u < c0) x1 = __ldg(ms + 32 + lane);
+            }
+            auto round = [&](const int4 &cur0, const int4 &cur1, int4 &nxt0, int4 &nxt1) {
+                const uint32_t hp1 = hpos + c0 == B ? 0u : hpos + c0;
+                const uint32_t t1 = take - c0;
+                uint32_t c1 = t1 < 64u ? t1 : 64u;
+                if (c1 > B - hp1) c1 = B - hp1;
+                const int4 *ns = P.run_memo + (src + c0);
+                if ((uint32_t)lane < c1) nxt0 = __ldg(ns + lane);
+                if ((uint32_t)lane + 32u < c1) nxt1 = __ldg(ns + 32 + lane);
                 if (hpos == 0 && nfull >= 2) {
                     // re-entering a half: the bulk store issued from it two
                     // flushes ago must have finished reading it
                     if (lane == 0) bulk_wait_read<1>();
                     __syncwarp();
                 }
-                if ((uint32_t)lane < c0)
-                    run_store_row<D, LAMF, K>(ring + (size_t)(half * B + hpos + lane) * D, a,
-                                              vmax, m0);
-                hpos += c0;
-                if (hpos == B) {
+                int32_t *dst = ring + (size_t)(half * B + hpos + lane) * D;
+                if ((uint32_t)lane < c0) run_store_row<D, LAMF, K>(dst, a, vmax, cur0);
+                if ((uint32_t)lane + 32u < c0)
+                    run_store_row<D, LAMF, K>(dst + 32 * D, a, vmax, cur1);
+                if (hp1 == 0) {
                     flush_rows(P, ring + (size_t)half * B * D, row0 + (uint64_t)nfull * B, B, D,
                                lane, pol);
                     ++nfull;
                     half ^= 1u;
-                    hpos = 0;
                 }
+                hpos = hp1;
                 src += c0;
                 take = t1;
                 c0 = c1;
-                m0 = m1;
-                t1 = t2;
-                c1 = c2;
-                m1 = m2;
-                hp1 = hp2;
+            };
+            for (;;) {
+                round(x0, x1, y0, y1);
+                if (take == 0) break;
+                round(y0, y1, x0, x1);
+                if (take == 0) break;
             }
             if (left == 0) break;
         }
