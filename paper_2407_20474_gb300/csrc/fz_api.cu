@@ -137,6 +137,7 @@ struct fz_plan_s {
     uint64_t *cls_beg = nullptr;
     uint64_t *RT = nullptr;
     int lam_r = 0;
+    int clamp_row = -1;
     uint64_t W = 0;
     uint64_t total_runs = 0;
     int ctas_per_sm = 0;
@@ -162,20 +163,43 @@ namespace {
 
 size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
 
-// Work of one leaf candidate of the walk, in rows; the
-// environment variable FZ_RUN_COST overrides it (tuning only).
-// Cost of one walked candidate in rows (work balancing).  A leaf candidate
-// of the leaf-by-leaf walk costs about 16 rows; a prefix of the run-order
-// walk costs a chain of three dependent table and memo loads, about 64 rows
-// of copying.  FZ_RUN_COST overrides both (tuning only).
-uint64_t run_cost_rows(bool run_order) {
+}  // namespace
+
+// FZ_RUN_COST overrides W (tuning only).
+void balance_level(int d, int K, int top, int n, bool run_order, int *lam_r, uint64_t *W,
+                   int *clamp_row) {
     static const long long forced = [] {
         const char *e = getenv("FZ_RUN_COST");
         return e ? atoll(e) : 0ll;
     }();
-    if (forced > 0) return (uint64_t)forced;
-    return run_order ? 64u : 16u;
+    const bool memo = K >= 1 && K <= d - 1 && top > 0;
+    *clamp_row = -1;
+    if (run_order) {
+        // the run-order walk visits every prefix of the leading d - K - 1
+        // coordinates (empty or not) and copies its run
+        *lam_r = d - K - 1;
+        *W = 64;
+    } else if (memo && top > n) {
+        // full memo: the leaves are the memo leaves, evaluated 32 at a time
+        *lam_r = d - K;
+        *W = 16;
+    } else if (K == 1 || !walk_progression_enabled()) {
+        // walk leaves evaluated candidate by candidate: count the candidates
+        *lam_r = d - 1;
+        *W = 16;
+    } else {
+        // walk runs: prefixes of length d - 2, each an advance to the next
+        // prefix plus a progression; a memo leaf (a prefix of length d - K
+        // with remainder below top) is one unit whatever lies under it
+        *lam_r = d - 2;
+        *W = 64;
+        if (memo && K > 2) *clamp_row = d - K;
+    }
+    if (*lam_r < 0) *lam_r = 0;
+    if (forced > 0) *W = (uint64_t)forced;
 }
+
+namespace {
 
 // FZ_RUN_MEMO=0 keeps full memos in element order only (tuning only).
 bool run_memo_enabled() {
@@ -375,22 +399,12 @@ int plan_create_impl(const int32_t *g, int d, int32_t n, const fz_opts_t *opt, f
     // single block: d == 1 or k == d with a full memo)
     const bool single_block = d == 1 || (p->K == d && p->top > n);
     if (!single_block && p->count > 0) {
-        const bool memo = p->K >= 1 && p->K <= d - 1 && p->top > 0;
-        if (p->run_memo) {
-            // run-order memo: the walk visits every prefix of the leading
-            // d - K - 1 coordinates (empty or not) and copies its run
-            p->lam_r = d - p->K - 1;
-            p->W = run_cost_rows(true);
-        } else {
-            // one past the leaf coordinate; with a partial memo most leaves
-            // may be walk leaves, so count candidates at the walk level then
-            p->lam_r = (memo && p->top > n ? d - p->K - 1 : d - 2) + 1;
-            p->W = run_cost_rows(false);
-        }
+        balance_level(d, p->K, p->top, n, p->run_memo != nullptr, &p->lam_r, &p->W,
+                      &p->clamp_row);
         rc = p->runs.alloc((size_t)(p->lam_r + 1) * cs * 8);
         if (rc != FZ_OK) return rc;
         p->RT = p->runs.as<uint64_t>();
-        rc = launch_runs_table(p->g, p->lam_r, n, p->RT, p->tmp, s);
+        rc = launch_runs_table(p->g, p->lam_r, n, p->RT, p->tmp, p->clamp_row, p->top, s);
         if (rc != FZ_OK) return rc;
         FZ_CUDA_TRY(cudaMemcpyAsync(&p->total_runs, p->RT + n, 8, cudaMemcpyDeviceToHost, s));
         FZ_CUDA_TRY(cudaStreamSynchronize(s));
@@ -859,7 +873,7 @@ int fz_plan_rebuild(fz_plan_t p, void *stream) {
     int rc = launch_count_table_tmp(p->g, p->d, p->n, p->C, p->tmp, s);
     if (rc != FZ_OK) return rc;
     if (p->RT) {
-        rc = launch_runs_table(p->g, p->lam_r, p->n, p->RT, p->tmp, s);
+        rc = launch_runs_table(p->g, p->lam_r, p->n, p->RT, p->tmp, p->clamp_row, p->top, s);
         if (rc != FZ_OK) return rc;
     }
     return plan_enqueue_memo(p, s);

@@ -47,11 +47,12 @@ constexpr int64_t BATCH_MEMO_BATCHES = 512;
 constexpr double BATCH_MEMO_MAX_ROWS = 1 << 20;
 
 struct Inst {
-    int d = 0, n = 0, K = 0, top = 0, lam_r = 0;
+    int d = 0, n = 0, K = 0, top = 0, lam_r = 0, clamp_row = -1;
     int32_t g[FZ_MAX_D] = {};
     size_t off_C = 0, off_RT = 0;  // word offsets into the table arena
     int memo = -1;                 // memo job index
     uint64_t count = 0, runs = 0;
+    uint64_t W = 16;  // cost of one prefix counted by the runs table, in rows
     uint64_t word_off = 0;
     uint64_t items = 0, slice_cost = 0, slice_rows = 0;
 };
@@ -64,7 +65,6 @@ using namespace fz;
 struct fz_batch_s {
     int count = 0;
     std::vector<Inst> inst;
-    uint64_t W = 16;
     DevArena tables;   // all count and runs tables
     DevArena scratch;  // block sums of blocked scans
     DevArena memos;    // memo offsets and rows
@@ -105,6 +105,18 @@ int build_scan_plan(fz_batch_s *b, uint64_t *table_base, std::vector<ScanJob> &j
             jobs.push_back(jd);
             for (int64_t a = 0; a < len; a += 8192)
                 tasks.push_back({(int)jobs.size() - 1, TK_DELTA, a, std::min(len, a + 8192)});
+            if (I.d >= 2) {
+                // rows d-2 and d-1 in closed form (no scans)
+                ScanJob jp{};
+                jp.out = table_base + I.off_C + (size_t)(I.d - 2) * len;
+                jp.len = len;
+                jp.g = I.g[I.d - 2];
+                jp.h = I.g[I.d - 1];
+                pair_params(jp.g, jp.h, &jp.e, &jp.h1, &jp.g1, &jp.inv);
+                jobs.push_back(jp);
+                for (int64_t a = 0; a < len; a += 8192)
+                    tasks.push_back({(int)jobs.size() - 1, TK_PAIR, a, std::min(len, a + 8192)});
+            }
             if (I.lam_r >= 0 && I.off_RT != (size_t)-1) {
                 ScanJob jo{};
                 jo.out = table_base + I.off_RT + (size_t)I.lam_r * len;
@@ -112,17 +124,30 @@ int build_scan_plan(fz_batch_s *b, uint64_t *table_base, std::vector<ScanJob> &j
                 jobs.push_back(jo);
                 for (int64_t a = 0; a < len; a += 8192)
                     tasks.push_back({(int)jobs.size() - 1, TK_ONES, a, std::min(len, a + 8192)});
+                if (I.lam_r >= 1) {
+                    // the row above the ones row: x / g + 1
+                    ScanJob jl{};
+                    const int j = I.lam_r - 1;
+                    jl.out = table_base + I.off_RT + (size_t)j * len;
+                    jl.len = len;
+                    jl.g = I.g[j];
+                    if (j == I.clamp_row) jl.ones_below = I.top;
+                    jobs.push_back(jl);
+                    for (int64_t a = 0; a < len; a += 8192)
+                        tasks.push_back(
+                            {(int)jobs.size() - 1, TK_LINEAR, a, std::min(len, a + 8192)});
+                }
             }
         }
         b->scan_launches.push_back({first, (int)tasks.size() - first});
     }
     size_t max_scratch = 0;
     for (int t = 0; t < maxlev; ++t) {
-        // jobs of this level: count row d-1-t, runs row lam_r-1-t
+        // jobs of this level: count row d-1-t (from d-3 on), runs row lam_r-2-t
         std::vector<int> step_jobs;
         for (const Inst &I : b->inst) {
             const int64_t len = (int64_t)I.n + 1;
-            if (I.d > t) {
+            if (I.d > t && (I.d < 2 || I.d - 1 - t < I.d - 2)) {  // rows d-2, d-1: closed form
                 const int j = I.d - 1 - t;
                 ScanJob J{};
                 J.in = table_base + I.off_C + (size_t)(j + 1) * len;
@@ -132,13 +157,16 @@ int build_scan_plan(fz_batch_s *b, uint64_t *table_base, std::vector<ScanJob> &j
                 jobs.push_back(J);
                 step_jobs.push_back((int)jobs.size() - 1);
             }
-            if (I.off_RT != (size_t)-1 && I.lam_r > t) {
-                const int j = I.lam_r - 1 - t;
+            if (I.off_RT != (size_t)-1 && I.lam_r > t + 1) {
+                // rows lam_r - 2, lam_r - 3, ..., 0 (lam_r and lam_r - 1 are
+                // written in closed form by the initialisation launch)
+                const int j = I.lam_r - 2 - t;
                 ScanJob J{};
                 J.in = table_base + I.off_RT + (size_t)(j + 1) * len;
                 J.out = table_base + I.off_RT + (size_t)j * len;
                 J.len = len;
                 J.g = I.g[j];
+                if (j == I.clamp_row) J.ones_below = I.top;
                 jobs.push_back(J);
                 step_jobs.push_back((int)jobs.size() - 1);
             }
@@ -223,30 +251,49 @@ int gather(const std::vector<const uint64_t *> &ptrs, std::vector<uint64_t> &out
     return FZ_OK;
 }
 
-// Memo depth of a batch instance: the last min(3, d-1) generators for d >= 3
-// (none for d <= 2), with top cut to BATCH_MEMO_BATCHES elementwise batches
-// and a depth lowered while the continuous estimate top^k / (k! prod t) of
-// its rows is above BATCH_MEMO_MAX_ROWS.
-void choose_batch_memo(Inst &I) {
+// Memo depth of a batch instance, chosen for the largest element n_set
+// asked of the same generators in the batch (so instances of one generator
+// set share one memo).  A memo's rows are estimated by the volume
+// top^K / (K! prod tail), with top = min(n_set + 1, BATCH_MEMO_BATCHES
+// elementwise batches of min(tail) elements).  Preferred: the deepest full
+// memo (top > n_set) within BATCH_MEMO_MAX_ROWS rows and half the
+// instance's estimated rows (volume n^(d-1) / ((d-1)! prod g)) -- the
+// deeper the memo, the fewer prefixes the walk visits.  Otherwise the deepest
+// partial memo of depth <= 3 within BATCH_MEMO_MAX_ROWS rows for d >= 4, and
+// no memo for d = 3 (walk leaves form a progression, one row each).
+void choose_batch_memo(Inst &I, int n_set) {
     I.K = 0;
     I.top = 0;
     if (I.d < 3) return;
-    for (int k = std::min(3, I.d - 1); k >= 2; --k) {
+    double count = 1.0 / (double)I.g[I.d - 1];
+    for (int i = 0; i < I.d - 1; ++i) count *= (double)n_set / (double)(i + 1) / (double)I.g[i];
+    int part_k = 0;
+    int64_t part_top = 0;
+    for (int k = I.d - 1; k >= 2; --k) {
         int32_t tmin = I.g[I.d - k];
         double prod = 1.0;
         for (int i = I.d - k; i < I.d; ++i) {
             tmin = std::min(tmin, I.g[i]);
             prod *= I.g[i];
         }
-        const int64_t top = std::min<int64_t>((int64_t)I.n + 1, BATCH_MEMO_BATCHES * tmin);
-        double est = 1.0;
-        for (int i = 0; i < k; ++i) est *= (double)top / (i + 1);
-        est /= prod;
-        if (est <= BATCH_MEMO_MAX_ROWS) {
+        const int64_t top = std::min<int64_t>((int64_t)n_set + 1, BATCH_MEMO_BATCHES * tmin);
+        double rows = 1.0;
+        for (int i = 0; i < k; ++i) rows *= (double)top / (i + 1);
+        rows /= prod;
+        if (rows > BATCH_MEMO_MAX_ROWS) continue;
+        if (top > n_set && rows <= 0.5 * count + 4096.0) {
             I.K = k;
-            I.top = (int)top;
+            I.top = (int)std::min<int64_t>((int64_t)I.n + 1, top);
             return;
         }
+        if (!part_k && k <= 3 && I.d >= 4) {
+            part_k = k;
+            part_top = top;
+        }
+    }
+    if (part_k) {
+        I.K = part_k;
+        I.top = (int)std::min<int64_t>((int64_t)I.n + 1, part_top);
     }
 }
 
@@ -271,6 +318,14 @@ int fz_batch_create(const fz_instance_t *inst, int count, const fz_opts_t *opt,
     b->count = count;
     b->inst.resize(count);
     size_t words = 0;
+    // largest element asked of each generator set (memo depth per set)
+    std::map<std::vector<int32_t>, int> n_set;
+    for (int i = 0; i < count; ++i) {
+        if (inst[i].d < 1 || inst[i].d > FZ_MAX_D || !inst[i].g) continue;  // validated below
+        std::vector<int32_t> key(inst[i].g, inst[i].g + inst[i].d);
+        int &m = n_set[key];
+        m = std::max(m, inst[i].n);
+    }
     for (int i = 0; i < count; ++i) {
         const fz_instance_t &x = inst[i];
         int rc = validate_gens(x.g, x.d);
@@ -280,7 +335,7 @@ int fz_batch_create(const fz_instance_t *inst, int count, const fz_opts_t *opt,
         I.d = x.d;
         I.n = x.n;
         for (int j = 0; j < x.d; ++j) I.g[j] = x.g[j];
-        choose_batch_memo(I);
+        choose_batch_memo(I, n_set[std::vector<int32_t>(x.g, x.g + x.d)]);
         if (opt && opt->k != FZ_AUTO) {
             if (opt->k < 0 || opt->k > x.d - 1)
                 return fail(set_error(FZ_EINVAL, "opts.k must be in 0..d-1 for every instance"));
@@ -297,19 +352,19 @@ int fz_batch_create(const fz_instance_t *inst, int count, const fz_opts_t *opt,
         words += (size_t)(I.d + 1) * len;
         I.off_RT = (size_t)-1;
         if (I.d >= 2) {
-            // one past the leaf coordinate (the walk level when the memo is partial)
-            I.lam_r = (I.K > 0 && I.top > I.n ? I.d - I.K - 1 : I.d - 2) + 1;
+            balance_level(I.d, I.K, I.top, I.n, false, &I.lam_r, &I.W, &I.clamp_row);
             I.off_RT = words;
             words += (size_t)(I.lam_r + 1) * len;
         } else {
             I.lam_r = -1;
         }
     }
-    const char *e = getenv("FZ_RUN_COST");
-    if (e && atoll(e) > 0) b->W = (uint64_t)atoll(e);
     int rc = b->tables.alloc(words * 8);
     if (rc != FZ_OK) return fail(rc);
     uint64_t *tb = static_cast<uint64_t *>(b->tables.p);
+    // every table entry is written by each rebuild; poison them first so an
+    // entry the build missed shows up as an error instead of stale zeros
+    FZ_CUDA_TRY(cudaMemsetAsync(tb, 0xff, words * 8, s));
 
     std::vector<ScanJob> jobs;
     std::vector<ScanTask> tasks;
@@ -464,7 +519,7 @@ int fz_batch_create(const fz_instance_t *inst, int count, const fz_opts_t *opt,
         I.word_off = word;
         word += I.count * (uint64_t)I.d;
         b->total_rows += I.count;
-        total_cost += I.count + b->W * I.runs;
+        total_cost += I.count + I.W * I.runs;
     }
     b->total_words = word;
     const uint64_t warps = (uint64_t)dp.sms * 16;
@@ -473,7 +528,7 @@ int fz_batch_create(const fz_instance_t *inst, int count, const fz_opts_t *opt,
     b->params_host.resize((size_t)count * pbytes);
     for (int i = 0; i < count; ++i) {
         Inst &I = b->inst[i];
-        const uint64_t cost = I.count + b->W * I.runs;
+        const uint64_t cost = I.count + I.W * I.runs;
         I.items = I.count == 0 ? 0 : std::max<uint64_t>(1, (cost + target - 1) / target);
         I.slice_cost = I.items ? (cost + I.items - 1) / I.items : 64;
         I.slice_rows = I.items ? std::max<uint64_t>(4, (I.count + I.items - 1) / I.items) : 4;
@@ -495,7 +550,7 @@ int fz_batch_create(const fz_instance_t *inst, int count, const fz_opts_t *opt,
         }
         if (I.off_RT != (size_t)-1) {
             L.RT = tb + I.off_RT;
-            L.W = b->W;
+            L.W = I.W;
             L.lam_r = I.lam_r;
         }
         // out holds the word offset; the kernel adds the output base

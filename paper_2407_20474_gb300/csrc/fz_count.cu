@@ -182,7 +182,7 @@ __global__ void row_ones_kernel(uint64_t *__restrict__ row, int64_t len) {
 // with remainder x: RT[lam][x] = 1 and RT[j] = RT[j+1] strided-summed with
 // stride g_j -- the count-table recurrence over the leading generators.
 int launch_runs_table(const int32_t *g, int lam, int32_t n, uint64_t *RT, uint64_t *tmp,
-                      cudaStream_t s) {
+                      int clamp_row, int64_t clamp_top, cudaStream_t s) {
     const int64_t len = (int64_t)n + 1;
     row_ones_kernel<<<grid_for(len, THREADS), THREADS, 0, s>>>(RT + (int64_t)lam * len, len);
     note_launch();
@@ -191,6 +191,12 @@ int launch_runs_table(const int32_t *g, int lam, int32_t n, uint64_t *RT, uint64
         int rc = strided_scan(RT + (int64_t)(j + 1) * len, RT + (int64_t)j * len, len, g[j],
                               tmp, s);
         if (rc != FZ_OK) return rc;
+        if (j == clamp_row && clamp_top > 0) {
+            const int64_t m = clamp_top < len ? clamp_top : len;
+            row_ones_kernel<<<grid_for(m, THREADS), THREADS, 0, s>>>(RT + (int64_t)j * len, m);
+            note_launch();
+            FZ_CUDA_TRY(cudaGetLastError());
+        }
     }
     return FZ_OK;
 }
@@ -204,7 +210,8 @@ int launch_runs_table(const int32_t *g, int lam, int32_t n, uint64_t *RT, uint64
 // ---------------------------------------------------------------------------
 __device__ __forceinline__ void chain_scan_warp(const uint64_t *__restrict__ in,
                                                 uint64_t *__restrict__ out, int64_t len,
-                                                int64_t g, int64_t rho, int lane) {
+                                                int64_t g, int64_t rho, int lane,
+                                                int64_t ones_below = 0) {
     const int64_t T = (len - rho + g - 1) / g;
     uint64_t carry = 0;
     for (int64_t t0 = 0; t0 < T; t0 += 128) {
@@ -218,7 +225,7 @@ __device__ __forceinline__ void chain_scan_warp(const uint64_t *__restrict__ in,
         for (int u = 0; u < 4; ++u) {
             int64_t t = t0 + u * 32 + lane;
             uint64_t sc = sat_add(warp_incl_scan_sat(v[u], lane), carry);
-            if (t < T) out[rho + t * g] = sc;
+            if (t < T) out[rho + t * g] = rho + t * g < ones_below ? 1ull : sc;
             carry = shfl_u64(sc, 31);
         }
     }
@@ -234,7 +241,7 @@ __global__ void __launch_bounds__(THREADS) scan_tasks_kernel(const ScanJob *__re
     switch (t.kind) {
         case TK_DIRECT:
             for (int64_t rho = t.begin + warp; rho < t.end; rho += nwarps)
-                chain_scan_warp(J.in, J.out, J.len, J.g, rho, lane);
+                chain_scan_warp(J.in, J.out, J.len, J.g, rho, lane, J.ones_below);
             break;
         case TK_SSCAN:
             for (int64_t rho = t.begin + warp; rho < t.end; rho += nwarps)
@@ -261,7 +268,7 @@ __global__ void __launch_bounds__(THREADS) scan_tasks_kernel(const ScanJob *__re
                     const int64_t r = r0 + (int64_t)u * J.g;
                     if (r < J.len) {
                         acc = sat_add(acc, __ldg(J.in + r));
-                        J.out[r] = acc;
+                        J.out[r] = r < J.ones_below ? 1ull : acc;
                     }
                 }
             }
@@ -272,6 +279,25 @@ __global__ void __launch_bounds__(THREADS) scan_tasks_kernel(const ScanJob *__re
             break;
         case TK_ONES:
             for (int64_t i = t.begin + threadIdx.x; i < t.end; i += blockDim.x) J.out[i] = 1ull;
+            break;
+        case TK_PAIR:
+            // |Z(r, (g, h))|: the a with g a = r (mod h) in [0, r / g] are
+            // a = a* (mod h1), a* = (r / e) inv (mod h1), when e divides r
+            for (int64_t r = t.begin + threadIdx.x; r < t.end; r += blockDim.x) {
+                uint64_t c = 0;
+                if (r % J.e == 0) {
+                    const int64_t re = r / J.e;
+                    const int64_t astar = (re % J.h1) * J.inv % J.h1;
+                    const int64_t q = re / J.g1;
+                    c = q >= astar ? (uint64_t)((q - astar) / J.h1 + 1) : 0ull;
+                }
+                J.out[r] = c;
+                J.out[J.len + r] = (r % J.h == 0) ? 1ull : 0ull;
+            }
+            break;
+        case TK_LINEAR:
+            for (int64_t x = t.begin + threadIdx.x; x < t.end; x += blockDim.x)
+                J.out[x] = x < J.ones_below ? 1ull : (uint64_t)(x / J.g + 1);
             break;
         default:
             break;

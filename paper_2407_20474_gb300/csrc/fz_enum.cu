@@ -88,6 +88,12 @@ struct EnumParams {
     const uint64_t *cls_beg;
     int g[FZ_MAX_D];
     FastDiv glast;         // division by g_{d-1} (walk leaves)
+    // Walk leaves as a progression: with e = gcd(g_{d-2}, g_{d-1}), the
+    // candidates a_{d-2} = v of remainder r with g_{d-1} | r - v g_{d-2} are
+    // v = v* (mod h1), h1 = g_{d-1}/e, v* = (r/e) inv (mod h1), inv the inverse
+    // of g1 = g_{d-2}/e mod h1 (0 when h1 = 1); e must divide r.  Along the
+    // progression a_{d-1} grows by g1.  wl_h1 = 0: candidate by candidate.
+    int wl_e, wl_h1, wl_g1, wl_inv;
 };
 
 struct WarpPath {
@@ -263,6 +269,12 @@ __device__ bool advance(const EnumParams &P, WarpPath *wp, int lane, RunState &s
 // from rank_begin: 32 rows are 128 d bytes, so every bulk store of a slice
 // starts on a 128-byte line when the output is 128-byte aligned.
 // ---------------------------------------------------------------------------
+// A memo leaf above the counted level (a partial memo of depth K > 2 whose
+// runs table counts walk runs): the node at depth j is one unit of cost.
+__device__ __forceinline__ bool is_memo_unit(const EnumParams &P, int j, int rem) {
+    return P.lam_m >= 0 && j == P.lam_m + 1 && j < P.lam_r && rem < P.top;
+}
+
 __device__ __forceinline__ uint64_t cost_at(const EnumParams &P, int j, long long idx) {
     if (idx < 0) return 0ull;
     return __ldg(P.C + (long long)j * P.cs + idx) + P.W * __ldg(P.RT + (long long)j * P.cs + idx);
@@ -274,7 +286,12 @@ __device__ uint64_t cost_to_rank(const EnumParams &P, uint64_t target, int lane)
     int rem = P.n;
     uint64_t rank = 0;
     if (target >= cost_at(P, 0, rem)) return __ldg(P.C + rem);
+    int lev = P.lam_r;
     for (int j = 0; j < P.lam_r; ++j) {
+        if (is_memo_unit(P, j, rem)) {
+            lev = j;
+            break;
+        }
         const long long g = P.g[j];
         const long long umax = rem / g;
         const long long base = (long long)rem - (umax + 1) * g;
@@ -303,7 +320,7 @@ __device__ uint64_t cost_to_rank(const EnumParams &P, uint64_t target, int lane)
         target -= flo;
         rem = (int)(rem - (umax - lo) * g);
     }
-    const uint64_t rows = __ldg(P.C + (long long)P.lam_r * P.cs + rem);
+    const uint64_t rows = __ldg(P.C + (long long)lev * P.cs + rem);
     const uint64_t t = target > P.W ? target - P.W : 0ull;
     return rank + (t < rows ? t : rows);
 }
@@ -314,6 +331,7 @@ __device__ uint64_t rank_to_cost(const EnumParams &P, uint64_t R, int lane) {
     if (R >= __ldg(P.C + rem)) return cost_at(P, 0, rem);
     uint64_t cost = 0;
     for (int j = 0; j < P.lam_r; ++j) {
+        if (is_memo_unit(P, j, rem)) break;
         int v;
         uint64_t before;
         find_child(P, j, rem, R, lane, v, before);
@@ -457,12 +475,95 @@ __device__ __forceinline__ bool enum_slice(const EnumParams &P, WarpPath *wp, in
 #pragma unroll
     for (int c = 0; c < DM; ++c) pre[c] = (c < st.lam) ? wp->a[c] : 0;
 
+    // ring bookkeeping after a round of cnt rows (both paths)
+    auto after_round = [&](uint32_t cnt) {
+        cp_async_commit();
+        hpos += cnt;
+        if (pend && ++pend_rounds >= (uint32_t)FLUSH_LAG) {
+            cp_async_wait<FLUSH_LAG>();
+            flush_rows(P, ring + (size_t)(half ^ 1u) * B * d,
+                          row0 + (uint64_t)(nfull - 1) * B, B, d, lane, pol);
+            pend = false;
+        }
+        if (hpos == B) {
+            if (pend) {  // (only if a half holds fewer than FLUSH_LAG rounds)
+                cp_async_wait<0>();
+                flush_rows(P, ring + (size_t)(half ^ 1u) * B * d,
+                              row0 + (uint64_t)(nfull - 1) * B, B, d, lane, pol);
+            }
+            pend = true;
+            pend_rounds = 0;
+            ++nfull;
+            half ^= 1u;
+            hpos = 0;
+        }
+    };
+    auto before_round = [&]() {
+        if (hpos == 0 && nfull >= 2) {
+            // re-entering a half: its bulk store (the most recent bulk
+            // group) must have finished reading it
+            if (lane == 0) bulk_wait_read_all();
+            __syncwarp();
+        }
+    };
     while (rows_left > 0) {
         const int lam = LAMF >= 0 ? LAMF : st.lam;
         const int rem = wp->r[lam];
         const int glam = P.g[lam];
         const bool memo_run =
             LAMF >= 0 ? true : ((P.lam_m >= 0) && !st.inwalk && lam == P.lam_m);
+        if (LAMF < 0 && !memo_run && lam == P.lam_w && P.wl_h1 > 0) {
+            // A run of walk leaves (the ordinary step at the last two
+            // coordinates): only the candidates a_{d-2} = v whose remainder
+            // g_{d-1} divides hold a row, and they form a progression, so
+            // rows are produced directly -- v from the largest valid value
+            // <= st.vcur down by h1, a_{d-1} up by g1 -- with no candidate
+            // that holds no row evaluated.
+            long long vtop = -1;
+            if (rem % P.wl_e == 0) {
+                const long long h1 = P.wl_h1;
+                const long long vstar = (long long)((rem / P.wl_e) % h1) * P.wl_inv % h1;
+                if (st.vcur >= vstar) vtop = st.vcur - (st.vcur - vstar) % h1;
+            }
+            const uint32_t nrun = vtop >= 0 ? (uint32_t)(vtop / P.wl_h1) + 1u : 0u;
+            const int wtop =
+                vtop >= 0 ? (int)(((long long)rem - vtop * glam) / P.g[d - 1]) : 0;
+            uint64_t qe = skip + rows_left;
+            if (qe > nrun) qe = nrun;
+            const uint32_t q_end = (uint32_t)qe;
+            for (uint32_t q0 = (uint32_t)skip; q0 < q_end;) {
+                uint32_t cnt = q_end - q0;
+                if (cnt > 32u) cnt = 32u;
+                if (cnt > B - hpos) cnt = B - hpos;
+                before_round();
+                if ((uint32_t)lane < cnt) {
+                    const int q = (int)(q0 + lane);
+                    int32_t *dst = ring + (size_t)(half * B + hpos + lane) * d;
+#pragma unroll
+                    for (int c = 0; c < DM; ++c) {
+                        if (c >= d - 2) break;
+                        dst[c] = pre[c];
+                    }
+                    dst[d - 2] = (int)(vtop - (long long)q * P.wl_h1);
+                    dst[d - 1] = wtop + q * P.wl_g1;
+                }
+                q0 += cnt;
+                after_round(cnt);
+            }
+            const uint32_t emitted = q_end > (uint32_t)skip ? q_end - (uint32_t)skip : 0u;
+            rows_left -= emitted;
+            if (rows_left == 0) break;
+            skip = 0;
+            st.vcur = -1;
+            if (!advance(P, wp, lane, st)) {
+                if (lane == 0) atomicExch(P.status, (int)DEV_INTERNAL);
+                ok = false;
+                break;
+            }
+#pragma unroll
+            for (int c = 0; c < DM; ++c) pre[c] = (c < st.lam) ? wp->a[c] : 0;
+            continue;
+        }
         const long long vl = st.vcur - lane;
         const bool valid = vl >= 0;
         int p = 0;
@@ -518,37 +619,6 @@ __device__ __forceinline__ bool enum_slice(const EnumParams &P, WarpPath *wp, in
         if (q_end64 > batch_rows) q_end64 = batch_rows;
         const uint32_t q_begin = (uint32_t)skip;
         const uint32_t q_end = (uint32_t)q_end64;
-        // ring bookkeeping after a round of cnt rows (both paths)
-        auto after_round = [&](uint32_t cnt) {
-            cp_async_commit();
-            hpos += cnt;
-            if (pend && ++pend_rounds >= (uint32_t)FLUSH_LAG) {
-                cp_async_wait<FLUSH_LAG>();
-                flush_rows(P, ring + (size_t)(half ^ 1u) * B * d,
-                              row0 + (uint64_t)(nfull - 1) * B, B, d, lane, pol);
-                pend = false;
-            }
-            if (hpos == B) {
-                if (pend) {  // (only if a half holds fewer than FLUSH_LAG rounds)
-                    cp_async_wait<0>();
-                    flush_rows(P, ring + (size_t)(half ^ 1u) * B * d,
-                                  row0 + (uint64_t)(nfull - 1) * B, B, d, lane, pol);
-                }
-                pend = true;
-                pend_rounds = 0;
-                ++nfull;
-                half ^= 1u;
-                hpos = 0;
-            }
-        };
-        auto before_round = [&]() {
-            if (hpos == 0 && nfull >= 2) {
-                // re-entering a half: its bulk store (the most recent bulk
-                // group) must have finished reading it
-                if (lane == 0) bulk_wait_read_all();
-                __syncwarp();
-            }
-        };
         // Dense batches of memo leaves: rounds follow the leaves, so every
         // lane of a round copies a row of the same leaf (no per-row search).
         const bool all_memo = __all_sync(FULL, lane >= consumed || type == T_MEMO);
@@ -1202,6 +1272,38 @@ static int launch_unrank_d(const EnumParams &P, const uint64_t *ranks, uint64_t 
     return FZ_OK;
 }
 
+void pair_params(int64_t g, int64_t h, int64_t *e_out, int64_t *h1_out, int64_t *g1_out,
+                 int64_t *inv_out) {
+    // extended Euclid: x g + y h = e
+    int64_t r0 = g, r1 = h, x0 = 1, x1 = 0;
+    while (r1 != 0) {
+        const int64_t q = r0 / r1;
+        int64_t t = r0 - q * r1;
+        r0 = r1;
+        r1 = t;
+        t = x0 - q * x1;
+        x0 = x1;
+        x1 = t;
+    }
+    const int64_t e = r0, h1 = h / e;
+    int64_t inv = h1 > 1 ? x0 % h1 : 0;  // (g/e) x = 1 (mod h/e)
+    if (inv < 0) inv += h1;
+    *e_out = e;
+    *h1_out = h1;
+    *g1_out = g / e;
+    *inv_out = inv;
+}
+
+// FZ_WALK_PROGRESSION=0 evaluates walk leaves candidate by candidate as the
+// ordinary step does (tuning and testing only).
+bool walk_progression_enabled() {
+    static const bool on = [] {
+        const char *e = getenv("FZ_WALK_PROGRESSION");
+        return !(e && e[0] == '0');
+    }();
+    return on;
+}
+
 static EnumParams make_params(const EnumLaunch &L) {
     EnumParams P{};
     P.C = L.C;
@@ -1228,6 +1330,16 @@ static EnumParams make_params(const EnumLaunch &L) {
     P.top = L.top;
     for (int i = 0; i < L.d; ++i) P.g[i] = L.g[i];
     P.glast = make_fastdiv((uint32_t)L.g[L.d - 1]);
+    P.wl_e = 1;
+    P.wl_h1 = P.wl_g1 = P.wl_inv = 0;
+    if (L.d >= 2 && walk_progression_enabled()) {
+        int64_t e, h1, g1, inv;
+        pair_params(L.g[L.d - 2], L.g[L.d - 1], &e, &h1, &g1, &inv);
+        P.wl_e = (int)e;
+        P.wl_h1 = (int)h1;
+        P.wl_g1 = (int)g1;
+        P.wl_inv = (int)inv;
+    }
     const bool memo = L.K >= 1 && L.K <= L.d - 1 && L.top > 0;
     P.lam_m = memo ? L.d - L.K - 1 : -1;
     P.lam_w = L.d - 2;

@@ -229,6 +229,11 @@ struct ScanJob {
     uint64_t *S;         // block sums (blocked jobs), else null
     uint64_t *Sincl;     // their strided inclusive scan
     int64_t slen;        // entries of S
+    int64_t ones_below;  // entries r < ones_below of out are written as 1
+    // TK_PAIR: out = row d-2 of a count table, out + len = row d-1, for the
+    // last two generators g (= this g) and h, e = gcd(g, h), h1 = h / e,
+    // g1 = g / e, inv = g1^-1 mod h1 (0 when h1 = 1)
+    int64_t h, e, h1, g1, inv;
 };
 enum ScanTaskKind : int {
     TK_DIRECT = 0,  // chains [begin, end) of in -> out, one warp each
@@ -236,8 +241,13 @@ enum ScanTaskKind : int {
     TK_SSCAN = 2,   // chains [begin, end) of S -> Sincl
     TK_APPLY = 3,   // blocks [begin, end): out = carry + running sum
     TK_DELTA = 4,   // out[begin..end) = [i == 0]
-    TK_ONES = 5     // out[begin..end) = 1
+    TK_ONES = 5,    // out[begin..end) = 1
+    TK_PAIR = 6,    // rows d-2 and d-1 of a count table in closed form
+    TK_LINEAR = 7   // out[x] = x / g + 1 (a runs-table row above the ones row)
 };
+// Extended Euclid for the last two generators (g, h): e = gcd, h1 = h / e,
+// g1 = g / e, inv = g1^-1 mod h1 (0 when h1 = 1).
+void pair_params(int64_t g, int64_t h, int64_t *e, int64_t *h1, int64_t *g1, int64_t *inv);
 struct ScanTask {
     int job;
     int kind;
@@ -292,6 +302,20 @@ int launch_run_memo(const uint64_t *C, int64_t cs, int lam, int32_t n, int32_t g
 int launch_memo_cta_build(const MemoJob *jobs, int njobs, int *status, cudaStream_t s);
 
 // Enumeration (fz_enum.cu).
+// Walk leaves are produced as a progression (FZ_WALK_PROGRESSION != 0).
+bool walk_progression_enabled();
+
+// Work balancing: the level lam_r whose prefixes the candidates table counts
+// and the cost W of one such prefix in rows, for an instance of d generators
+// with memo depth K and top (top > n: full memo); run_order: the memo is kept
+// in run order.  Walk runs (the last two coordinates as a progression) and
+// run-order runs cost a chain of dependent loads each (W = 32 and 64); leaf
+// candidates evaluated 32 at a time cost W = 16.
+// *clamp_row >= 0: the table row whose entries below top are set to 1 (a
+// memo leaf is one unit, whatever lies under it), else -1.
+void balance_level(int d, int K, int top, int n, bool run_order, int *lam_r, uint64_t *W,
+                   int *clamp_row);
+
 struct EnumLaunch {
     const uint64_t *C = nullptr;   // count table rows 0..d, stride cs = n + 1
     int64_t cs = 0;
@@ -318,8 +342,11 @@ struct EnumLaunch {
     const int4 *run_memo = nullptr;
     const uint64_t *cls_beg = nullptr;
 };
-// Runs table: RT[lam][x] = 1, RT[j][x] = sum_t RT[j+1][x - t g_j] (fz_count.cu).
+// Runs table: RT[lam][x] = 1, RT[j][x] = sum_t RT[j+1][x - t g_j]
+// (fz_count.cu); if clamp_row >= 0, RT[clamp_row][x] = 1 for x < clamp_top
+// (before the rows above it are summed).
 int launch_runs_table(const int32_t *g, int lam, int32_t n, uint64_t *RT, uint64_t *tmp,
+                      int clamp_row, int64_t clamp_top,
                       cudaStream_t s);
 int launch_enumerate(const EnumLaunch &L, uint64_t rank_begin, uint64_t nrows, int32_t *out,
                      uint64_t slice_rows, cudaStream_t s);

@@ -173,6 +173,33 @@ def test_small_slices_ring_boundaries(fz, d):
             assert np.array_equal(got, ref), (g, n, k, slice_rows)
 
 
+@pytest.mark.parametrize("g", [(6, 10), (4, 9, 6, 15), (5, 8, 12, 18), (3, 7, 7),
+                               (9, 14, 1, 5), (11, 4, 4), (13, 6, 21, 35), (2, 3, 5, 1, 1)])
+def test_walk_leaves_as_progression(fz, g):
+    """Walk leaves produced directly along the progression of valid a_{d-2}
+    values: last two generators coprime, with a common factor, equal, or 1;
+    no memo and partial memos; windows and tiny slices that start work items
+    inside a run of walk leaves."""
+    n = workloads.find_n(oracle.count_upto, g, 3000)
+    ref = oracle.enumerate_desc(g, n)
+    total = ref.shape[0]
+    d = len(g)
+    for k, top in ((0, -1), (2, 7), (min(3, d - 1), 25), (2, -1)):
+        if k > d:
+            continue
+        for slice_rows in (4, 52, 0):
+            got = run_enum(fz, g, n, k=k, top=top, slice_rows=slice_rows)
+            assert np.array_equal(got, ref), (g, n, k, top, slice_rows)
+    rng = np.random.Generator(np.random.PCG64(sum(g)))
+    for _ in range(8):
+        a = int(rng.integers(0, total))
+        b = int(rng.integers(a, total + 1))
+        got = run_enum(fz, g, n, rank_begin=a, rank_end=b, k=0, slice_rows=8)
+        assert np.array_equal(got, ref[a:b]), (g, n, a, b)
+    for n2 in (n + 1, n + 7):  # other residues (some not divisible by the gcd)
+        assert np.array_equal(run_enum(fz, g, n2, k=0), oracle.enumerate_desc(g, n2)), (g, n2)
+
+
 def test_rank_windows_and_unaligned_output(fz):
     g, n = (7, 11, 13, 17, 19), 420
     ref = oracle.enumerate_desc(g, n)
