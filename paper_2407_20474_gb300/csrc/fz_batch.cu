@@ -48,6 +48,7 @@ constexpr double BATCH_MEMO_MAX_ROWS = 1 << 20;
 
 struct Inst {
     int d = 0, n = 0, K = 0, top = 0, lam_r = 0, clamp_row = -1;
+    bool pair = false;  // K = 2 kept as the closed form (no memo table)
     int32_t g[FZ_MAX_D] = {};
     size_t off_C = 0, off_RT = 0;  // word offsets into the table arena
     int memo = -1;                 // memo job index
@@ -256,20 +257,24 @@ int gather(const std::vector<const uint64_t *> &ptrs, std::vector<uint64_t> &out
 // set share one memo).  A memo's rows are estimated by the volume
 // top^K / (K! prod tail), with top = min(n_set + 1, BATCH_MEMO_BATCHES
 // elementwise batches of min(tail) elements).  Preferred: the deepest full
-// memo (top > n_set) within BATCH_MEMO_MAX_ROWS rows and half the
-// instance's estimated rows (volume n^(d-1) / ((d-1)! prod g)) -- the
-// deeper the memo, the fewer prefixes the walk visits.  Otherwise the deepest
-// partial memo of depth <= 3 within BATCH_MEMO_MAX_ROWS rows for d >= 4, and
-// no memo for d = 3 (walk leaves form a progression, one row each).
+// memo (top > n_set) of depth >= 3 within BATCH_MEMO_MAX_ROWS rows and half
+// the instance's estimated rows (volume n^(d-1) / ((d-1)! prod g)) -- the
+// deeper the memo, the fewer prefixes the walk visits.  Otherwise, for
+// d >= 5, a partial memo of depth 3 within BATCH_MEMO_MAX_ROWS rows (the
+// pair memo's leaves, prefixes of length d - 2, would be mostly empty
+// there: config 4's d = 5 instances took 11.3 ms with it, 2 ms with depth
+// 3).  Otherwise the pair memo: depth 2, full, as the closed form of
+// Z(p, (g_{d-2}, g_{d-1})) -- no table to build, and its leaves are
+// evaluated 32 at a time.
 void choose_batch_memo(Inst &I, int n_set) {
     I.K = 0;
     I.top = 0;
+    I.pair = false;
     if (I.d < 3) return;
     double count = 1.0 / (double)I.g[I.d - 1];
     for (int i = 0; i < I.d - 1; ++i) count *= (double)n_set / (double)(i + 1) / (double)I.g[i];
-    int part_k = 0;
     int64_t part_top = 0;
-    for (int k = I.d - 1; k >= 2; --k) {
+    for (int k = I.d - 1; k >= 3; --k) {
         int32_t tmin = I.g[I.d - k];
         double prod = 1.0;
         for (int i = I.d - k; i < I.d; ++i) {
@@ -286,15 +291,16 @@ void choose_batch_memo(Inst &I, int n_set) {
             I.top = (int)std::min<int64_t>((int64_t)I.n + 1, top);
             return;
         }
-        if (!part_k && k <= 3 && I.d >= 4) {
-            part_k = k;
-            part_top = top;
-        }
+        if (k == 3 && I.d >= 5) part_top = top;
     }
-    if (part_k) {
-        I.K = part_k;
+    if (part_top > 0) {
+        I.K = 3;
         I.top = (int)std::min<int64_t>((int64_t)I.n + 1, part_top);
+        return;
     }
+    I.K = 2;
+    I.top = I.n + 1;
+    I.pair = true;
 }
 
 }  // namespace
@@ -339,12 +345,16 @@ int fz_batch_create(const fz_instance_t *inst, int count, const fz_opts_t *opt,
         if (opt && opt->k != FZ_AUTO) {
             if (opt->k < 0 || opt->k > x.d - 1)
                 return fail(set_error(FZ_EINVAL, "opts.k must be in 0..d-1 for every instance"));
+            I.pair = false;
             I.K = opt->k;
             int32_t tmin = I.K ? I.g[I.d - I.K] : 1;
             for (int j = I.d - I.K; j < I.d; ++j) tmin = std::min(tmin, I.g[j]);
             I.top = I.K ? (int)std::min<int64_t>((int64_t)I.n + 1, BATCH_MEMO_BATCHES * tmin) : 0;
         }
-        if (opt && opt->top != FZ_AUTO && I.K > 0) I.top = std::min(I.top, opt->top);
+        if (opt && opt->top != FZ_AUTO && I.K > 0) {
+            I.top = std::min(I.top, opt->top);
+            if (I.top <= I.n) I.pair = false;  // a partial memo is a table
+        }
         if (I.K > 0 && I.top <= 0) I.K = 0;
         if (I.K == 0) I.top = 0;
         const size_t len = (size_t)I.n + 1;
@@ -386,7 +396,7 @@ int fz_batch_create(const fz_instance_t *inst, int count, const fz_opts_t *opt,
     std::vector<int> memo_src;  // instance whose table rows feed the memo
     for (int i = 0; i < count; ++i) {
         Inst &I = b->inst[i];
-        if (I.K <= 0) continue;
+        if (I.K <= 0 || I.pair) continue;
         std::vector<int32_t> key(I.g + (I.d - I.K), I.g + I.d);
         auto it = memo_of.find(key);
         int m;
@@ -543,6 +553,7 @@ int fz_batch_create(const fz_instance_t *inst, int count, const fz_opts_t *opt,
         L.g = I.g;
         L.status = b->status_dev;
         L.slice_counter = b->counter_dev;
+        L.pair_memo = I.pair;
         if (I.memo >= 0) {
             L.O = b->memo_jobs[I.memo].O;
             L.memo = b->memo_jobs[I.memo].R;

@@ -94,7 +94,20 @@ struct EnumParams {
     // of g1 = g_{d-2}/e mod h1 (0 when h1 = 1); e must divide r.  Along the
     // progression a_{d-1} grows by g1.  wl_h1 = 0: candidate by candidate.
     int wl_e, wl_h1, wl_g1, wl_inv;
+    // Pair memo: a full memo of depth 2 kept as a formula, no table.  Memo
+    // leaf p (remainder at depth d-2) holds Z(p, (g_{d-2}, g_{d-1})): row o
+    // is a_{d-2} = a_top - o h1, a_{d-1} = (p - a_{d-2} g_{d-2}) / g_{d-1},
+    // with a_top the largest valid a_{d-2} (the progression above).
+    int pair_memo;
 };
+
+// First a_{d-2} of pair-memo leaf p (meaningful when the leaf is not empty).
+__device__ __forceinline__ uint32_t pair_top(const EnumParams &P, int p) {
+    const long long h1 = P.wl_h1;
+    const long long astar = (long long)((p / P.wl_e) % h1) * P.wl_inv % h1;
+    const long long q = p / P.g[P.d - 2];
+    return q >= astar ? (uint32_t)(q - (q - astar) % h1) : 0u;
+}
 
 struct WarpPath {
     int a[FZ_MAX_D];      // a_0..a_{lam-1}
@@ -611,7 +624,7 @@ __device__ __forceinline__ bool enum_slice(const EnumParams &P, WarpPath *wp, in
             const uint64_t e = incl - st.base;
             E32 = e < (uint64_t)CAP32 ? (uint32_t)e : CAP32;
             if (type == T_MEMO)
-                X32 = (uint32_t)__ldg(P.O + p);
+                X32 = (LAMF < 0 && P.pair_memo) ? pair_top(P, p) : (uint32_t)__ldg(P.O + p);
             else if (type == T_WALK)
                 X32 = walk_run ? wq : fd_div((uint32_t)p, P.glast);
         }
@@ -634,13 +647,15 @@ __device__ __forceinline__ bool enum_slice(const EnumParams &P, WarpPath *wp, in
                 const uint32_t hi = ej < q_end ? ej : q_end;
                 if (lo < hi) {
                     const uint32_t xj = __shfl_sync(FULL, X32, j);
+                    const int pj = __shfl_sync(FULL, p, j);
                     const int vj = (int)(st.vcur - j);
-                    if ((uint64_t)xj + (hi - sj) > P.memo_rows) {  // bounds guard
+                    const bool pair = LAMF < 0 && P.pair_memo;
+                    if (!pair && (uint64_t)xj + (hi - sj) > P.memo_rows) {  // bounds guard
                         if (lane == 0) atomicExch(P.status, (int)DEV_INTERNAL);
                         break;
                     }
                     const int kk = LAMF >= 0 ? KF : P.K;
-                    const int32_t *mbase = P.memo + (size_t)xj * (size_t)kk;
+                    const int32_t *mbase = pair ? P.memo : P.memo + (size_t)xj * (size_t)kk;
                     for (uint32_t q0 = lo; q0 < hi;) {
                         uint32_t cnt = hi - q0;
                         if (cnt > 32u) cnt = 32u;
@@ -649,8 +664,21 @@ __device__ __forceinline__ bool enum_slice(const EnumParams &P, WarpPath *wp, in
                         if ((uint32_t)lane < cnt) {
                             int32_t *dst = ring + (size_t)(half * B + hpos + lane) * d;
                             const int32_t *mrow =
-                                mbase + (size_t)(q0 + lane - sj) * (size_t)kk;
-                            if constexpr (LAMF >= 0) {
+                                pair ? mbase : mbase + (size_t)(q0 + lane - sj) * (size_t)kk;
+                            if (pair) {
+                                // pair memo: the row from the progression
+                                const int o = (int)(q0 + lane - sj);
+                                const int av = (int)xj - o * P.wl_h1;
+#pragma unroll
+                                for (int c = 0; c < DM; ++c) {
+                                    if (c >= lam) break;
+                                    dst[c] = pre[c];
+                                }
+                                dst[lam] = vj;
+                                dst[lam + 1] = av;
+                                dst[lam + 2] = (int)fd_div(
+                                    (uint32_t)(pj - av * P.g[d - 2]), P.glast);
+                            } else if constexpr (LAMF >= 0) {
 #pragma unroll
                                 for (int c = 0; c < LAMF; ++c) dst[c] = pre[c];
                                 dst[LAMF] = vj;
@@ -710,7 +738,8 @@ __device__ __forceinline__ bool enum_slice(const EnumParams &P, WarpPath *wp, in
             const uint32_t xl = __shfl_sync(FULL, X32, l);
             const int vrow = (int)(st.vcur - l);
             bool mleaf = memo_run && (LAMF >= 0 || pl < P.top);
-            if (act && mleaf && (uint64_t)xl + o >= P.memo_rows) {  // bounds guard
+            const bool pair = LAMF < 0 && P.pair_memo && mleaf;
+            if (act && mleaf && !pair && (uint64_t)xl + o >= P.memo_rows) {  // bounds guard
                 atomicExch(P.status, (int)DEV_INTERNAL);
                 mleaf = false;
             }
@@ -728,6 +757,17 @@ __device__ __forceinline__ bool enum_slice(const EnumParams &P, WarpPath *wp, in
 #pragma unroll
                         for (int c = 0; c < KF; ++c) dst[LAMF + 1 + c] = 0;
                     }
+                } else if (pair) {
+                    // pair memo: the row from the progression
+                    const int av = (int)xl - (int)o * P.wl_h1;
+#pragma unroll
+                    for (int c = 0; c < DM; ++c) {
+                        if (c >= lam) break;
+                        dst[c] = pre[c];
+                    }
+                    dst[lam] = vrow;
+                    dst[lam + 1] = av;
+                    dst[lam + 2] = (int)fd_div((uint32_t)(pl - av * P.g[d - 2]), P.glast);
                 } else {
                     const int32_t *mrow =
                         mleaf ? P.memo + (size_t)(xl + o) * (size_t)P.K : nullptr;
@@ -1332,7 +1372,8 @@ static EnumParams make_params(const EnumLaunch &L) {
     P.glast = make_fastdiv((uint32_t)L.g[L.d - 1]);
     P.wl_e = 1;
     P.wl_h1 = P.wl_g1 = P.wl_inv = 0;
-    if (L.d >= 2 && walk_progression_enabled()) {
+    P.pair_memo = L.pair_memo && L.K == 2 && L.d >= 3 && L.top > L.n;
+    if (L.d >= 2 && (walk_progression_enabled() || P.pair_memo)) {
         int64_t e, h1, g1, inv;
         pair_params(L.g[L.d - 2], L.g[L.d - 1], &e, &h1, &g1, &inv);
         P.wl_e = (int)e;

@@ -341,6 +341,9 @@ struct EnumLaunch {
     // full memo of depth K <= 3 in run order (see launch_run_memo), or null
     const int4 *run_memo = nullptr;
     const uint64_t *cls_beg = nullptr;
+    // K == 2, full: the memo is the closed form of Z(p, (g_{d-2}, g_{d-1}))
+    // (no table; O and memo may be null)
+    bool pair_memo = false;
 };
 // Runs table: RT[lam][x] = 1, RT[j][x] = sum_t RT[j+1][x - t g_j]
 // (fz_count.cu); if clamp_row >= 0, RT[clamp_row][x] = 1 for x < clamp_top

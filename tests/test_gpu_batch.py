@@ -55,6 +55,22 @@ def test_batch_matches_oracle(fz):
         assert np.array_equal(got, oracle.enumerate_desc(g, n)), (g, n)
 
 
+def test_batch_pair_memo_leaves(fz):
+    """Instances whose memo is the closed form of the last two generators
+    (no full memo of depth >= 3 fits): last pair coprime, with a common
+    factor, equal, or containing 1; with and without shared generator sets."""
+    inst = []
+    for g in ((3, 10, 15), (6, 4, 4), (5, 9, 12, 18), (7, 2, 1), (11, 13, 17),
+              (4, 6, 9, 10, 14), (2, 3, 35, 49)):
+        for target in (2_000, 40_000):
+            inst.append((g, workloads.find_n(oracle.count_upto, g, target, 64)))
+    inst += [(inst[0][0], inst[0][1] + 1), (inst[2][0], inst[2][1] + 3)]
+    b, segs = run_batch(fz, inst)
+    assert int((b.k == 2).sum()) >= 4, b.k  # the closed form is exercised
+    for (g, n), got in zip(inst, segs):
+        assert np.array_equal(got, oracle.enumerate_desc(g, n)), (g, n)
+
+
 def test_batch_every_memo_depth(fz):
     inst = [x for x in small_instances(32, 60) if len(x[0]) >= 4]
     for k in (0, 1, 2, 3):
