@@ -87,6 +87,15 @@ const char *fz_status_string(int status);
  * counted). */
 uint64_t fz_kernel_launches(void);
 
+/* Measurement utility (the paper has no counterpart): writes out_dev[w] = w
+ * for w < words with 16-byte stores, one pass, so a caller can time the
+ * write-only bandwidth the device reaches for distinct data of the same
+ * size as an enumeration (constant fills are written faster than distinct
+ * data by this GPU's memory system, so they overstate that ceiling).
+ * out_dev: caller-owned device memory, 16-byte aligned.  Asynchronous.
+ * Errors: FZ_EINVAL (null or unaligned pointer), FZ_ECUDA. */
+int fz_write_probe(int32_t *out_dev, uint64_t words, void *stream);
+
 /* ------------------------------------------------------------------------
  * Counting (the saved subset cardinalities of Section 2.3, generalised).
  *

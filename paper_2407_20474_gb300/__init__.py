@@ -37,6 +37,7 @@ FZ_EINTERNAL = -9
 # Every symbol include/fz.h declares (checked by the CPU tests).
 EXPORTS = (
     "fz_version", "fz_last_error_string", "fz_status_string", "fz_kernel_launches",
+    "fz_write_probe",
     "fz_count", "fz_count_upto", "fz_count_upto_noalloc", "fz_count_table",
     "fz_memo_rows", "fz_build_memo_into", "fz_build_memo_schedule", "fz_build_memo",
     "fz_memo_info",
@@ -120,6 +121,7 @@ _SIGS = {
     "fz_last_error_string": (ctypes.c_char_p, []),
     "fz_status_string": (ctypes.c_char_p, [ctypes.c_int]),
     "fz_kernel_launches": (ctypes.c_uint64, []),
+    "fz_write_probe": (ctypes.c_int, [_P, ctypes.c_uint64, _P]),
     "fz_count": (ctypes.c_int, [_I32P, ctypes.c_int, ctypes.c_int32, _U64P, _P]),
     "fz_count_upto": (ctypes.c_int, [_I32P, ctypes.c_int, ctypes.c_int32, _U64P, _P]),
     "fz_count_table": (ctypes.c_int, [_I32P, ctypes.c_int, ctypes.c_int32, _P, _P]),
@@ -245,6 +247,13 @@ def fz_version() -> int:
 def fz_kernel_launches() -> int:
     """Kernels the library has enqueued in this process (tracing counter)."""
     return int(lib().fz_kernel_launches())
+
+
+def fz_write_probe(out, stream=None):
+    """Write out[w] = w over a 16-byte aligned int32 CUDA tensor (measurement
+    utility: the write-only ceiling for distinct data)."""
+    _check(lib().fz_write_probe(ctypes.c_void_p(out.data_ptr()), int(out.numel()),
+                                _stream(stream)))
 
 
 def fz_count(g: Sequence[int], n: int, stream=None) -> int:

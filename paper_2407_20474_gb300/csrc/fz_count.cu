@@ -340,4 +340,36 @@ int launch_exclusive_scan_tmp(const uint64_t *in, uint64_t *out, int64_t len, ui
     return strided_scan(in, out + 1, len, 1, tmp, s);
 }
 
+// ---------------------------------------------------------------------------
+// Write probe (fz_write_probe): distinct words, 16-byte stores, a grid of
+// 8 CTAs of 256 threads per SM striding over the buffer.
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(256) write_probe_kernel(int4 *__restrict__ out, uint64_t n16,
+                                                          int32_t *__restrict__ tail,
+                                                          uint64_t tail_words, uint64_t tail_w0) {
+    const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+    for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n16; i += stride) {
+        const int32_t w = (int32_t)(i * 4);
+        out[i] = make_int4(w, w + 1, w + 2, w + 3);
+    }
+    if (blockIdx.x == 0 && threadIdx.x < tail_words)
+        tail[threadIdx.x] = (int32_t)(tail_w0 + threadIdx.x);
+}
+
+int launch_write_probe(int32_t *out, uint64_t words, cudaStream_t s) {
+    int dev = 0, sms = 1;
+    FZ_CUDA_TRY(cudaGetDevice(&dev));
+    FZ_CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    const uint64_t n16 = words / 4;
+    const uint64_t tail_words = words - n16 * 4;  // < 4
+    uint64_t grid = (uint64_t)sms * 8;
+    const uint64_t want = (n16 + 255) / 256;
+    if (want < grid) grid = want < 1 ? 1 : want;
+    write_probe_kernel<<<(unsigned)grid, 256, 0, s>>>(reinterpret_cast<int4 *>(out), n16,
+                                                      out + n16 * 4, tail_words, n16 * 4);
+    note_launch();
+    FZ_CUDA_TRY(cudaGetLastError());
+    return FZ_OK;
+}
+
 }  // namespace fz

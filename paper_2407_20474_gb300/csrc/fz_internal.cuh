@@ -301,6 +301,9 @@ int launch_run_memo(const uint64_t *C, int64_t cs, int lam, int32_t n, int32_t g
                     uint64_t *cls_beg, int4 *run_memo, int *status, cudaStream_t s);
 int launch_memo_cta_build(const MemoJob *jobs, int njobs, int *status, cudaStream_t s);
 
+// out[w] = w for w < words, 16-byte stores (fz_write_probe; fz_count.cu).
+int launch_write_probe(int32_t *out, uint64_t words, cudaStream_t s);
+
 // Enumeration (fz_enum.cu).
 // Walk leaves are produced as a progression (FZ_WALK_PROGRESSION != 0).
 bool walk_progression_enabled();
