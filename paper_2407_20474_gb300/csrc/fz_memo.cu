@@ -165,25 +165,57 @@ __device__ __forceinline__ void fill_pass(const FillParams &P, uint64_t base, ui
 }
 
 // Batches of b elements over the whole grid; bounded grid barrier between
-// non-empty batches.
-__global__ void __launch_bounds__(THREADS) memo_fill_kernel(FillParams P) {
+// non-empty batches.  One CTA of GRID_THREADS per SM, so a barrier has one
+// arrival per SM, and a batch of up to FILL_W * GRID_THREADS * SMs words
+// (about 620k words on 152 SMs) is one pass.  The gather-map entries of the
+// next batch's first pass do not depend on this batch: they are loaded
+// before the barrier.
+constexpr int GRID_THREADS = 1024;
+
+__global__ void __launch_bounds__(GRID_THREADS) memo_fill_kernel(FillParams P) {
     const uint64_t tid = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
     const uint64_t nthreads = (uint64_t)gridDim.x * blockDim.x;
     const int k = P.k;
     const uint64_t qn = nthreads / (uint64_t)k;
     const uint32_t rn = (uint32_t)(nthreads - qn * (uint64_t)k);
+    uint64_t e[FILL_W];
+    bool have = false;  // e[] holds the map entries of this batch's first pass
     for (int q = 0; q < P.nbatch; ++q) {
         const int64_t m0 = (int64_t)q * P.b;
         int64_t m1 = m0 + P.b;
         if (m1 > P.top) m1 = P.top;
         const uint64_t R0 = __ldg(P.O + m0), R1 = __ldg(P.O + m1);
-        if (R1 == R0) continue;
-        const uint64_t W1 = R1 * (uint64_t)k;
-        for (uint64_t base = R0 * (uint64_t)k + tid; base < W1; base += FILL_W * nthreads) {
-            uint64_t e[FILL_W];
-            fill_pass<false>(P, base, W1, R0, nthreads, qn, rn, e);
+        if (R1 == R0) {
+            have = false;
+            continue;
         }
-        if (q + 1 < P.nbatch && !grid_barrier(P.bar, P.status)) return;
+        const uint64_t W1 = R1 * (uint64_t)k;
+        uint64_t base = R0 * (uint64_t)k + tid;
+        if (have && base < W1) {
+            fill_pass<true>(P, base, W1, R0, nthreads, qn, rn, e);
+            base += FILL_W * nthreads;
+        }
+        for (; base < W1; base += FILL_W * nthreads) fill_pass<false>(P, base, W1, R0, nthreads, qn, rn, e);
+        have = false;
+        if (q + 1 < P.nbatch) {
+            // prefetch the next batch's first-pass map entries
+            const int64_t n0 = m1;
+            int64_t n1 = n0 + P.b;
+            if (n1 > P.top) n1 = P.top;
+            const uint64_t NR0 = __ldg(P.O + n0), NR1 = __ldg(P.O + n1);
+            const uint64_t NW1 = NR1 * (uint64_t)k;
+            const uint64_t nbase = NR0 * (uint64_t)k + tid;
+            if (NR1 > NR0 && nbase < NW1) {
+                WordPos pos = word_pos(nbase, k);
+#pragma unroll
+                for (int j = 0; j < FILL_W; ++j) {
+                    e[j] = nbase + j * nthreads < NW1 ? __ldg(P.map + pos.R) : MAP_ZERO;
+                    word_step(pos, qn, rn, k);
+                }
+                have = true;
+            }
+            if (!grid_barrier(P.bar, P.status)) return;
+        }
     }
 }
 
@@ -325,7 +357,7 @@ int coop_grid(const void *kernel, int threads) {
         cudaSuccess)
         return -1;
     if (per_sm < 1) return -1;
-    if (per_sm > 2) per_sm = 2;
+    if (per_sm > 1) per_sm = 1;  // one CTA per SM: one barrier arrival per SM
     return per_sm * dp.sms;
 }
 
@@ -690,12 +722,12 @@ int launch_memo_build(const int32_t *tail, int k, int32_t top, uint64_t rows,
         int rc = launch_fill_cluster(fp, mb.small_ctas, s);
         if (rc == FZ_OK) return rc;
     }
-    int grid = coop_grid((const void *)memo_fill_kernel, THREADS);
+    int grid = coop_grid((const void *)memo_fill_kernel, GRID_THREADS);
     if (grid <= 0) return set_error(FZ_ECUDA, "memo build: no cooperative occupancy");
     FZ_CUDA_TRY(cudaMemsetAsync(mb.bar, 0, sizeof(unsigned), s));
     void *args[] = {&fp};
     FZ_CUDA_TRY(cudaLaunchCooperativeKernel((const void *)memo_fill_kernel, dim3(grid),
-                                            dim3(THREADS), args, 0, s));
+                                            dim3(GRID_THREADS), args, 0, s));
                                             note_launch();
     return FZ_OK;
 }
