@@ -459,8 +459,15 @@ __global__ void __launch_bounds__(MB_THREADS) memo_sizes_kernel(const MemoJob *_
     if (threadIdx.x == 0) rows_out[blockIdx.x] = total;
 }
 
-__global__ void __launch_bounds__(MB_THREADS) memo_cta_build_kernel(const MemoJob *__restrict__ jobs,
-                                                                    int *status) {
+// One CTA of MB_BUILD_THREADS per memo.  Inside an elementwise batch each
+// warp copies whole (element, generator) blocks as flat word copies; a lane
+// loads MB_ILP words before it stores them, so a block of W words costs
+// about W / (32 MB_ILP) L2 round trips.
+constexpr int MB_BUILD_THREADS = 1024;
+constexpr int MB_ILP = 8;
+
+__global__ void __launch_bounds__(MB_BUILD_THREADS) memo_cta_build_kernel(
+    const MemoJob *__restrict__ jobs, int *status) {
     __shared__ uint64_t sums[33];
     const MemoJob J = jobs[blockIdx.x];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -497,10 +504,27 @@ __global__ void __launch_bounds__(MB_THREADS) memo_cta_build_kernel(const MemoJo
                 const uint64_t len = __ldg(J.Ct + (int64_t)i * J.cs + src_m);
                 if (len == 0) continue;
                 const uint64_t src = J.O[src_m + 1] - len;  // suffix Z_{>=i}(src_m)
-                for (uint64_t r = lane; r < len; r += 32) {
-                    const int32_t *a = J.R + (src + r) * k;
-                    int32_t *b = J.R + (dst + r) * k;
-                    for (int c = 0; c < k; ++c) b[c] = a[c] + (c == i ? 1 : 0);
+                // the block is a flat copy of len * k words with one added to
+                // every word of coordinate i: word w of the block is
+                // coordinate w mod k of row w div k
+                const uint64_t W = len * (uint64_t)k;
+                const int32_t *a = J.R + src * (uint64_t)k;
+                int32_t *b = J.R + dst * (uint64_t)k;
+                const uint32_t step = (uint32_t)(32 % k);
+                uint32_t c0 = (uint32_t)(lane % k);  // coordinate of word lane
+                for (uint64_t w0 = lane; w0 < W; w0 += 32 * MB_ILP) {
+                    int32_t v[MB_ILP];
+#pragma unroll
+                    for (int u = 0; u < MB_ILP; ++u)
+                        if (w0 + 32 * u < W) v[u] = a[w0 + 32 * u];
+                    uint32_t c = c0;
+#pragma unroll
+                    for (int u = 0; u < MB_ILP; ++u) {
+                        if (w0 + 32 * u < W) b[w0 + 32 * u] = v[u] + (c == (uint32_t)i ? 1 : 0);
+                        c += step;
+                        if (c >= (uint32_t)k) c -= (uint32_t)k;
+                    }
+                    c0 = c;
                 }
                 dst += len;
             }
@@ -606,7 +630,7 @@ int launch_memo_sizes(const MemoJob *jobs, int njobs, uint64_t *rows_out, cudaSt
 
 int launch_memo_cta_build(const MemoJob *jobs, int njobs, int *status, cudaStream_t s) {
     if (njobs <= 0) return FZ_OK;
-    memo_cta_build_kernel<<<njobs, MB_THREADS, 0, s>>>(jobs, status);
+    memo_cta_build_kernel<<<njobs, MB_BUILD_THREADS, 0, s>>>(jobs, status);
     note_launch();
     FZ_CUDA_TRY(cudaGetLastError());
     return FZ_OK;
