@@ -198,6 +198,41 @@ __device__ __forceinline__ bool grid_barrier(GridBarrier b, int *status) {
 }
 
 // ---------------------------------------------------------------------------
+// Bounded monotonic grid barrier for cooperative launches: *count (zeroed
+// before the launch) counts arrivals; the i-th barrier (i = 0, 1, ...)
+// completes when it reaches (i + 1) * gridDim.  One atomic and one poll per
+// barrier.  A block whose wait runs past the limit records DEV_TIMEOUT and
+// returns false (the others then time out too, each on its own).
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ bool grid_barrier_mono(unsigned *count, unsigned index, int *status) {
+    __shared__ int ok_flag_m;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        int ok = 1;
+        const unsigned target = (index + 1u) * (gridDim.x * gridDim.y * gridDim.z);
+        // release-add: the block's writes (ordered before this thread by the
+        // __syncthreads above) are visible to whoever acquires the count
+        asm volatile("red.release.gpu.global.add.u32 [%0], 1;" ::"l"(count) : "memory");
+        uint64_t t0 = 0;
+        uint32_t polls = 0;
+        while (ld_acquire_u32(count) < target) {
+            if (polls == 0) t0 = globaltimer_ns();
+            if (++polls >= BARRIER_MAX_POLLS ||
+                ((polls & 255u) == 0 && globaltimer_ns() - t0 > BARRIER_TIMEOUT_NS)) {
+                atomicExch(status, (int)DEV_TIMEOUT);
+                ok = 0;
+                break;
+            }
+            __nanosleep(20);
+        }
+        ok_flag_m = ok;
+    }
+    __syncthreads();
+    return ok_flag_m != 0;
+}
+
+
+// ---------------------------------------------------------------------------
 // Host helpers.
 // ---------------------------------------------------------------------------
 struct DeviceProps {

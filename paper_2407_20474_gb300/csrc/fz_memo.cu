@@ -180,11 +180,13 @@ __global__ void __launch_bounds__(GRID_THREADS) memo_fill_kernel(FillParams P) {
     const uint32_t rn = (uint32_t)(nthreads - qn * (uint64_t)k);
     uint64_t e[FILL_W];
     bool have = false;  // e[] holds the map entries of this batch's first pass
+    unsigned nbar = 0;  // barriers passed
+    uint64_t R0 = __ldg(P.O + 0);
     for (int q = 0; q < P.nbatch; ++q) {
         const int64_t m0 = (int64_t)q * P.b;
         int64_t m1 = m0 + P.b;
         if (m1 > P.top) m1 = P.top;
-        const uint64_t R0 = __ldg(P.O + m0), R1 = __ldg(P.O + m1);
+        const uint64_t R1 = __ldg(P.O + m1);  // R0 carried over from the previous batch
         if (R1 == R0) {
             have = false;
             continue;
@@ -198,14 +200,14 @@ __global__ void __launch_bounds__(GRID_THREADS) memo_fill_kernel(FillParams P) {
         for (; base < W1; base += FILL_W * nthreads) fill_pass<false>(P, base, W1, R0, nthreads, qn, rn, e);
         have = false;
         if (q + 1 < P.nbatch) {
-            // prefetch the next batch's first-pass map entries
-            const int64_t n0 = m1;
-            int64_t n1 = n0 + P.b;
+            // prefetch the next batch's first-pass map entries (the map and
+            // the offsets are read-only here)
+            int64_t n1 = m1 + P.b;
             if (n1 > P.top) n1 = P.top;
-            const uint64_t NR0 = __ldg(P.O + n0), NR1 = __ldg(P.O + n1);
+            const uint64_t NR1 = __ldg(P.O + n1);
             const uint64_t NW1 = NR1 * (uint64_t)k;
-            const uint64_t nbase = NR0 * (uint64_t)k + tid;
-            if (NR1 > NR0 && nbase < NW1) {
+            const uint64_t nbase = R1 * (uint64_t)k + tid;
+            if (NR1 > R1 && nbase < NW1) {
                 WordPos pos = word_pos(nbase, k);
 #pragma unroll
                 for (int j = 0; j < FILL_W; ++j) {
@@ -214,8 +216,9 @@ __global__ void __launch_bounds__(GRID_THREADS) memo_fill_kernel(FillParams P) {
                 }
                 have = true;
             }
-            if (!grid_barrier(P.bar, P.status)) return;
+            if (!grid_barrier_mono(P.bar.count, nbar++, P.status)) return;
         }
+        R0 = R1;
     }
 }
 
