@@ -200,6 +200,19 @@ def test_walk_leaves_as_progression(fz, g):
         assert np.array_equal(run_enum(fz, g, n2, k=0), oracle.enumerate_desc(g, n2)), (g, n2)
 
 
+def test_write_probe(fz):
+    """The measurement utility writes out[w] = w and nothing past the end."""
+    for words in (0, 1, 5, 1023, 1 << 20, (1 << 20) + 3):
+        buf = torch.full((words + 64,), CANARY, dtype=torch.int32, device="cuda")
+        fz.fz_write_probe(buf[:words] if words else buf[:0])
+        torch.cuda.synchronize()
+        host = buf.cpu().numpy()
+        assert np.array_equal(host[:words], np.arange(words, dtype=np.int32)), words
+        assert (host[words:] == CANARY).all(), words
+    with pytest.raises(fz.FzError):
+        fz.fz_write_probe(torch.zeros(9, dtype=torch.int32, device="cuda")[1:])  # unaligned
+
+
 def test_rank_windows_and_unaligned_output(fz):
     g, n = (7, 11, 13, 17, 19), 420
     ref = oracle.enumerate_desc(g, n)
