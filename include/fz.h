@@ -92,7 +92,8 @@ uint64_t fz_kernel_launches(void);
  * write-only bandwidth the device reaches for distinct data of the same
  * size as an enumeration (constant fills are written faster than distinct
  * data by this GPU's memory system, so they overstate that ceiling).
- * out_dev: caller-owned device memory, 16-byte aligned.  Asynchronous.
+ * out_dev: caller-owned device memory, 16-byte aligned (may be null when
+ * words == 0, which does nothing).  Asynchronous.
  * Errors: FZ_EINVAL (null or unaligned pointer), FZ_ECUDA. */
 int fz_write_probe(int32_t *out_dev, uint64_t words, void *stream);
 

@@ -491,9 +491,9 @@ int fz_version(void) { return 100; }
 uint64_t fz_kernel_launches(void) { return fz::g_launches.load(std::memory_order_relaxed); }
 
 int fz_write_probe(int32_t *out_dev, uint64_t words, void *stream) {
+    if (words == 0) return FZ_OK;
     if (!out_dev || ((uintptr_t)out_dev & 15u) != 0)
         return fz::set_error(FZ_EINVAL, "write probe: null or unaligned output");
-    if (words == 0) return FZ_OK;
     int rc = fz::launch_write_probe(out_dev, words, static_cast<cudaStream_t>(stream));
     return rc;
 }

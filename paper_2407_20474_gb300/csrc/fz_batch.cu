@@ -95,36 +95,48 @@ int build_scan_plan(fz_batch_s *b, uint64_t *table_base, std::vector<ScanJob> &j
     const int RBk = scan_block_rows();
     int maxlev = 0;
     for (const Inst &I : b->inst) maxlev = std::max(maxlev, std::max(I.d, I.lam_r));
-    // initialisation launch: last count row = delta, last runs row = ones
+    // Initialisation launch.  Rows nothing reads are not written (the poison
+    // fill of a new arena would turn a wrong omission into an error): the
+    // delta row C[d] (it only fed the scan of C[d-1], now closed form),
+    // C[d-1] unless a memo is built from this table or the candidates table
+    // is counted at level d - 1, and the runs table's ones row RT[lam_r] when
+    // the row above it is closed form.
     {
         const int first = (int)tasks.size();
         for (const Inst &I : b->inst) {
             const int64_t len = (int64_t)I.n + 1;
-            ScanJob jd{};
-            jd.out = table_base + I.off_C + (size_t)I.d * len;
-            jd.len = len;
-            jobs.push_back(jd);
-            for (int64_t a = 0; a < len; a += 8192)
-                tasks.push_back({(int)jobs.size() - 1, TK_DELTA, a, std::min(len, a + 8192)});
-            if (I.d >= 2) {
+            if (I.d < 2) {
+                ScanJob jd{};
+                jd.out = table_base + I.off_C + (size_t)I.d * len;
+                jd.len = len;
+                jobs.push_back(jd);
+                for (int64_t a = 0; a < len; a += 8192)
+                    tasks.push_back({(int)jobs.size() - 1, TK_DELTA, a, std::min(len, a + 8192)});
+            } else {
                 // rows d-2 and d-1 in closed form (no scans)
                 ScanJob jp{};
                 jp.out = table_base + I.off_C + (size_t)(I.d - 2) * len;
                 jp.len = len;
                 jp.g = I.g[I.d - 2];
                 jp.h = I.g[I.d - 1];
+                // row d-1 is read by a memo build from this table, or as the
+                // leaf row of a candidates table counted at level d - 1
+                jp.ones_below = ((I.K > 0 && !I.pair) || I.lam_r >= I.d - 1) ? 1 : 0;
                 pair_params(jp.g, jp.h, &jp.e, &jp.h1, &jp.g1, &jp.inv);
                 jobs.push_back(jp);
                 for (int64_t a = 0; a < len; a += 8192)
                     tasks.push_back({(int)jobs.size() - 1, TK_PAIR, a, std::min(len, a + 8192)});
             }
             if (I.lam_r >= 0 && I.off_RT != (size_t)-1) {
-                ScanJob jo{};
-                jo.out = table_base + I.off_RT + (size_t)I.lam_r * len;
-                jo.len = len;
-                jobs.push_back(jo);
-                for (int64_t a = 0; a < len; a += 8192)
-                    tasks.push_back({(int)jobs.size() - 1, TK_ONES, a, std::min(len, a + 8192)});
+                if (I.lam_r == 0) {
+                    ScanJob jo{};
+                    jo.out = table_base + I.off_RT + (size_t)I.lam_r * len;
+                    jo.len = len;
+                    jobs.push_back(jo);
+                    for (int64_t a = 0; a < len; a += 8192)
+                        tasks.push_back(
+                            {(int)jobs.size() - 1, TK_ONES, a, std::min(len, a + 8192)});
+                }
                 if (I.lam_r >= 1) {
                     // the row above the ones row: x / g + 1
                     ScanJob jl{};

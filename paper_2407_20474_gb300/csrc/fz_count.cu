@@ -292,7 +292,7 @@ __global__ void __launch_bounds__(THREADS) scan_tasks_kernel(const ScanJob *__re
                     c = q >= astar ? (uint64_t)((q - astar) / J.h1 + 1) : 0ull;
                 }
                 J.out[r] = c;
-                J.out[J.len + r] = (r % J.h == 0) ? 1ull : 0ull;
+                if (J.ones_below) J.out[J.len + r] = (r % J.h == 0) ? 1ull : 0ull;
             }
             break;
         case TK_LINEAR:
