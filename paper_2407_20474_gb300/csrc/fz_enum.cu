@@ -74,7 +74,7 @@ struct EnumParams {
     uint64_t slice_rows;   // S (multiple of 4), used when RT is null
     uint64_t nslices;
     const uint64_t *RT;    // candidates table rows 0..lam_r (stride cs), or null
-    uint64_t W;            // cost of one leaf candidate, in rows
+    uint64_t W;            // cost of one unit of walk work (a prefix of length lam_r), in rows
     uint64_t slice_cost;   // cost units per work item when RT is set
     int lam_r;             // one past the leaf coordinate (RT[lam_r] = 1)
     int n, d, K, top;
@@ -273,10 +273,12 @@ __device__ bool advance(const EnumParams &P, WarpPath *wp, int lane, RunState &s
 
 // ---------------------------------------------------------------------------
 // Work-balanced slicing.  The cost of a subtree is its rows plus W for every
-// leaf candidate in it (a prefix the walk evaluates, live or not); RT[j][x]
-// counts those candidates (RT[lam_r] = 1 with lam_r one past the leaf
-// coordinate, and row j is row j+1 strided-summed with stride g_j, like the
-// count table), so the cost of the children a_j >= v of a node is
+// unit of walk work in it -- a leaf candidate, a walk run or a run-order run,
+// i.e. a prefix of length lam_r the walk evaluates, live or not (balance_level
+// picks lam_r and W); RT[j][x] counts those prefixes (RT[lam_r] = 1, and row j
+// is row j+1 strided-summed with stride g_j, like the count table; a memo
+// leaf above level lam_r is clamped to one unit), so the cost of the
+// children a_j >= v of a node is
 // C[j][x] + W RT[j][x] with x = rem - v g_j.  Work items are equal cost ranges, located by the same
 // 32-probe search as ranks, then snapped to ranks that are multiples of 32
 // from rank_begin: 32 rows are 128 d bytes, so every bulk store of a slice

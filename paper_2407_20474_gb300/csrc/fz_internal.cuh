@@ -348,8 +348,8 @@ bool walk_progression_enabled();
 // and the cost W of one such prefix in rows, for an instance of d generators
 // with memo depth K and top (top > n: full memo); run_order: the memo is kept
 // in run order.  Walk runs (the last two coordinates as a progression) and
-// run-order runs cost a chain of dependent loads each (W = 32 and 64); leaf
-// candidates evaluated 32 at a time cost W = 16.
+// run-order runs cost a chain of dependent loads each (W = 64); memo leaves
+// and candidates evaluated 32 at a time cost W = 16.
 // *clamp_row >= 0: the table row whose entries below top are set to 1 (a
 // memo leaf is one unit, whatever lies under it), else -1.
 void balance_level(int d, int K, int top, int n, bool run_order, int *lam_r, uint64_t *W,
