@@ -23,6 +23,7 @@ no data exchange); times are the max over ranks.
 import argparse
 import hashlib
 import json
+import re
 import os
 import statistics
 import subprocess
@@ -223,10 +224,19 @@ def kernel_traffic(d):
         rec = json.load(open(path))
     except ValueError:
         return None
-    src = open(os.path.join(ROOT, "paper_2407_20474_gb300", "csrc", "fz_enum.cu"), "rb").read()
-    if rec.get("source_sha256") != hashlib.sha256(src).hexdigest():
+    src = open(os.path.join(ROOT, "paper_2407_20474_gb300", "csrc", "fz_enum.cu")).read()
+    if rec.get("code_sha256") != code_hash(src):
         return None
     return rec.get("bytes_per_full_launch")
+
+
+def code_hash(src):
+    """sha256 of CUDA source with comments, blank lines and trailing spaces
+    removed: edits to comments do not invalidate a profile of the code."""
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    src = re.sub(r"//[^\n]*", "", src)
+    lines = [l.rstrip() for l in src.splitlines()]
+    return hashlib.sha256("\n".join(l for l in lines if l).encode()).hexdigest()
 
 
 def enum_kernel_name(plan):
