@@ -195,11 +195,17 @@ def lib():
     return _lib
 
 
+_STATUS_NAMES = {FZ_OK: "FZ_OK", FZ_EINVAL: "FZ_EINVAL", FZ_EOVERFLOW: "FZ_EOVERFLOW",
+                 FZ_ENOSPC: "FZ_ENOSPC", FZ_ENOMEM: "FZ_ENOMEM", FZ_EAGAIN: "FZ_EAGAIN",
+                 FZ_ETIMEOUT: "FZ_ETIMEOUT", FZ_ECUDA: "FZ_ECUDA",
+                 FZ_ENOTFOUND: "FZ_ENOTFOUND", FZ_EINTERNAL: "FZ_EINTERNAL"}
+
+
 def status_string(status: int) -> str:
-    try:
-        return lib().fz_status_string(int(status)).decode()
-    except FzError:
-        return "FZ_STATUS_%d" % status
+    """Name of a status code (from the library when it is loaded)."""
+    if _lib is None:  # never load the library just to name an error
+        return _STATUS_NAMES.get(int(status), "FZ_STATUS_%d" % status)
+    return _lib.fz_status_string(int(status)).decode()
 
 
 def _check(rc: int):

@@ -228,7 +228,12 @@ int plan_enqueue_memo(fz_plan_s *p, cudaStream_t s) {
     mb.bar = p->bar;
     // an enumeration capped below full occupancy leaves room for a small build
     mb.small_ctas = p->ctas_per_sm > 0 && p->ctas_per_sm <= 3;
-    rc = launch_memo_build(p->g + (p->d - p->K), p->K, p->top, p->memo_rows, mb, s);
+    // depth 1 and 2: the closed form of the tail sets (same rows as the
+    // dynamic pass, no dependent batches); deeper memos: the dynamic pass
+    if (p->K <= 2)
+        rc = launch_memo_closed(p->g + (p->d - p->K), p->K, p->top, p->O, p->rows, p->status, s);
+    else
+        rc = launch_memo_build(p->g + (p->d - p->K), p->K, p->top, p->memo_rows, mb, s);
     if (rc != FZ_OK || !p->run_memo) return rc;
     const int lam = p->d - p->K - 1;
     return launch_run_memo(p->C, cs, lam, p->n, p->g[lam], p->O, p->rows, p->K, p->memo_rows,

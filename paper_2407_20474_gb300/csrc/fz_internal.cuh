@@ -309,6 +309,10 @@ struct MemoBuffers {
     unsigned *bar = nullptr;       // 2 words: barrier count, generation
     bool small_ctas = false;       // fill with small CTAs (beside a capped enumeration)
 };
+// Memo of depth 1 or 2 written in closed form from its offsets O (one warp
+// per element; no gather map, no batches).  Asynchronous.
+int launch_memo_closed(const int32_t *tail, int k, int32_t top, const uint64_t *O,
+                       int32_t *rows, int *status, cudaStream_t s);
 // Gather map + batched copy-and-increment fill.  Asynchronous.
 // schedule: FZ_MEMO_BATCHED (one launch), FZ_MEMO_PER_BATCH or FZ_MEMO_PER_COPY.
 int launch_memo_build(const int32_t *tail, int k, int32_t top, uint64_t rows,

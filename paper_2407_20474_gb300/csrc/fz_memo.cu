@@ -223,6 +223,89 @@ __global__ void __launch_bounds__(GRID_THREADS) memo_fill_kernel(FillParams P) {
 }
 
 // ---------------------------------------------------------------------------
+// Memos of depth 1 and 2 in closed form (plans only; the dynamic pass above
+// builds the same rows).  Z(m, (t0)) is the row (m / t0) when t0 divides m;
+// Z(m, (t0, t1)) is the progression a0 = a_top, a_top - h1, ... (descending,
+// so the rows come out in the memo's order) with a1 = (m - a0 t0) / t1, h1 =
+// t1 / gcd, a_top the largest a0 <= m / t0 with t1 | m - a0 t0.  One warp per
+// element; offsets O from the count scan.  A row count that disagrees with
+// the closed form is recorded as DEV_INTERNAL.
+// ---------------------------------------------------------------------------
+struct ClosedParams {
+    const uint64_t *O;
+    int32_t *rows;
+    int *status;
+    int top, k;
+    int64_t t0, t1, e, h1, g1, inv;
+};
+
+__global__ void __launch_bounds__(THREADS) memo_closed_kernel(ClosedParams P) {
+    const int lane = threadIdx.x & 31;
+    const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t m = warp; m < P.top; m += nwarps) {
+        const uint64_t beg = __ldg(P.O + m);
+        const uint64_t cnt = __ldg(P.O + m + 1) - beg;
+        if (P.k == 1) {
+            const uint64_t want = (m % P.t0 == 0) ? 1u : 0u;
+            if (lane == 0) {
+                if (cnt != want)
+                    atomicExch(P.status, (int)DEV_INTERNAL);
+                else if (cnt)
+                    P.rows[beg] = (int32_t)(m / P.t0);
+            }
+            continue;
+        }
+        int64_t atop = -1;
+        uint64_t want = 0;
+        if (m % P.e == 0) {
+            const int64_t astar = ((m / P.e) % P.h1) * P.inv % P.h1;
+            const int64_t q = m / P.t0;
+            if (q >= astar) {
+                atop = q - (q - astar) % P.h1;
+                want = (uint64_t)(atop / P.h1) + 1;
+            }
+        }
+        if (cnt != want) {
+            if (lane == 0) atomicExch(P.status, (int)DEV_INTERNAL);
+            continue;
+        }
+        for (uint64_t j = lane; j < cnt; j += 32) {
+            const int64_t a0 = atop - (int64_t)j * P.h1;
+            P.rows[(beg + j) * 2] = (int32_t)a0;
+            P.rows[(beg + j) * 2 + 1] = (int32_t)((m - a0 * P.t0) / P.t1);
+        }
+    }
+}
+
+}  // namespace
+
+int launch_memo_closed(const int32_t *tail, int k, int32_t top, const uint64_t *O,
+                       int32_t *rows, int *status, cudaStream_t s) {
+    if (top <= 0) return FZ_OK;
+    if (k != 1 && k != 2) return set_error(FZ_EINTERNAL, "closed-form memo: depth 1 or 2 only");
+    ClosedParams P{};
+    P.O = O;
+    P.rows = rows;
+    P.status = status;
+    P.top = top;
+    P.k = k;
+    P.t0 = tail[0];
+    P.t1 = k == 2 ? tail[1] : 1;
+    P.e = 1;
+    P.h1 = 1;
+    if (k == 2) pair_params(P.t0, P.t1, &P.e, &P.h1, &P.g1, &P.inv);
+    int64_t blocks = ((int64_t)top * 32 + THREADS - 1) / THREADS;
+    if (blocks > 4096) blocks = 4096;
+    memo_closed_kernel<<<(int)blocks, THREADS, 0, s>>>(P);
+    note_launch();
+    FZ_CUDA_TRY(cudaGetLastError());
+    return FZ_OK;
+}
+
+namespace {
+
+// ---------------------------------------------------------------------------
 // Cluster variant: one thread-block cluster runs every batch.  Between
 // batches the CTAs meet at the hardware cluster barrier; the arrive and the
 // wait are split so that the gather-map entries of the next batch's first

@@ -59,3 +59,27 @@ def test_argument_errors_need_no_gpu(libfz):
     with pytest.raises(fz.FzError) as e:
         fz.fz_memo_rows((4, 0), 10)
     assert e.value.status == fz.FZ_EINVAL
+
+
+def test_missing_or_broken_library_fails_loudly(tmp_path):
+    """No CPU fallback: a missing or unloadable libfz.so raises FzError."""
+    import subprocess
+    import sys
+    broken = tmp_path / "libfz_broken.so"
+    broken.write_text("not a shared object")
+    code = (
+        "import sys; sys.path.insert(0, %r)\n"
+        "import paper_2407_20474_gb300 as fz\n"
+        "for path in (%r, %r):\n"
+        "    fz.LIB_PATH = path; fz._lib = None\n"
+        "    try:\n"
+        "        fz.fz_count((3, 5), 10)\n"
+        "    except fz.FzError as e:\n"
+        "        assert e.status == fz.FZ_ECUDA, e\n"
+        "        print('raised', e)\n"
+        "    else:\n"
+        "        raise SystemExit('no error for ' + path)\n"
+        % (ROOT, str(tmp_path / "missing.so"), str(broken)))
+    r = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, timeout=120)
+    assert r.returncode == 0, r.stdout + r.stderr
+    assert r.stdout.count("raised") == 2
