@@ -462,12 +462,14 @@ constexpr int FLUSH_LAG = 2;
 // at compile time; D == 0: width P.d (at most FZ_MAX_D).  LAMF >= 0: every run
 // is a memo run at coordinate LAMF (full memo, k = D-1-LAMF) fixed at compile
 // time; LAMF < 0: generic (runtime run level, walk leaves).  Returns false if
-// a device-side consistency check failed (status already recorded).
-template <int D, int LAMF>
+// a device-side consistency check failed (status already recorded).  DMAX:
+// with D == 0, the largest width the call serves (shorter row loops and
+// prefix arrays for narrow tuples).
+template <int D, int LAMF, int DMAX = FZ_MAX_D>
 __device__ __forceinline__ bool enum_slice(const EnumParams &P, WarpPath *wp, int32_t *ring,
                                            uint32_t B, uint64_t row0, uint64_t row1,
                                            uint64_t pol, int lane) {
-    constexpr int DM = D > 0 ? D : FZ_MAX_D;
+    constexpr int DM = D > 0 ? D : DMAX;
     const int d = D > 0 ? D : P.d;
     constexpr int KF = LAMF >= 0 ? D - 1 - LAMF : 0;
     uint32_t rows_left = (uint32_t)(row1 - row0);
@@ -1145,7 +1147,13 @@ __global__ void __launch_bounds__(ENUM_THREADS, 4)
             }
             continue;
         }
-        if (!enum_slice<0, -1>(P, wp, ring, (uint32_t)P.half_rows, row0, row1, pol, lane)) break;
+        // one walk for every width up to 8 (row loops unrolled to 8), the
+        // 16-wide one beyond: two code paths at most, so warps of different
+        // instances share the instruction cache
+        const bool ok =
+            P.d <= 8 ? enum_slice<0, -1, 8>(P, wp, ring, (uint32_t)P.half_rows, row0, row1, pol, lane)
+                     : enum_slice<0, -1>(P, wp, ring, (uint32_t)P.half_rows, row0, row1, pol, lane);
+        if (!ok) break;
     }
     cp_async_wait<0>();
     if (lane == 0) bulk_wait_all();
