@@ -99,14 +99,25 @@ struct EnumParams {
     // is a_{d-2} = a_top - o h1, a_{d-1} = (p - a_{d-2} g_{d-2}) / g_{d-1},
     // with a_top the largest valid a_{d-2} (the progression above).
     int pair_memo;
+    FastDiv fd_e, fd_h1, fd_g2;  // division by e, h1 and g_{d-2}
 };
 
-// First a_{d-2} of pair-memo leaf p (meaningful when the leaf is not empty).
+__device__ __forceinline__ uint32_t fd_mod(uint32_t a, FastDiv f) {
+    return a - fd_div(a, f) * f.g;
+}
+
+// First a_{d-2} of pair-memo leaf p (meaningful when the leaf is not empty):
+// 32-bit divisions by precomputed multipliers; the product (p/e mod h1) inv
+// fits 32 bits when h1 < 2^16, else it takes a 64-bit remainder.
 __device__ __forceinline__ uint32_t pair_top(const EnumParams &P, int p) {
-    const long long h1 = P.wl_h1;
-    const long long astar = (long long)((p / P.wl_e) % h1) * P.wl_inv % h1;
-    const long long q = p / P.g[P.d - 2];
-    return q >= astar ? (uint32_t)(q - (q - astar) % h1) : 0u;
+    const uint32_t up = (uint32_t)p;
+    const uint32_t h1 = (uint32_t)P.wl_h1;
+    const uint32_t xr = fd_mod(fd_div(up, P.fd_e), P.fd_h1);
+    const uint32_t astar = h1 < 65536u
+                               ? fd_mod(xr * (uint32_t)P.wl_inv, P.fd_h1)
+                               : (uint32_t)((uint64_t)xr * (uint32_t)P.wl_inv % h1);
+    const uint32_t q = fd_div(up, P.fd_g2);
+    return q >= astar ? q - fd_mod(q - astar, P.fd_h1) : 0u;
 }
 
 struct WarpPath {
@@ -1382,6 +1393,7 @@ static EnumParams make_params(const EnumLaunch &L) {
     P.glast = make_fastdiv((uint32_t)L.g[L.d - 1]);
     P.wl_e = 1;
     P.wl_h1 = P.wl_g1 = P.wl_inv = 0;
+    P.fd_e = P.fd_h1 = P.fd_g2 = make_fastdiv(1u);
     P.pair_memo = L.pair_memo && L.K == 2 && L.d >= 3 && L.top > L.n;
     if (L.d >= 2 && (walk_progression_enabled() || P.pair_memo)) {
         int64_t e, h1, g1, inv;
@@ -1390,6 +1402,9 @@ static EnumParams make_params(const EnumLaunch &L) {
         P.wl_h1 = (int)h1;
         P.wl_g1 = (int)g1;
         P.wl_inv = (int)inv;
+        P.fd_e = make_fastdiv((uint32_t)e);
+        P.fd_h1 = make_fastdiv((uint32_t)h1);
+        P.fd_g2 = make_fastdiv((uint32_t)L.g[L.d - 2]);
     }
     const bool memo = L.K >= 1 && L.K <= L.d - 1 && L.top > 0;
     P.lam_m = memo ? L.d - L.K - 1 : -1;
