@@ -89,6 +89,17 @@ struct fz_batch_s {
 namespace fz {
 namespace {
 
+// Row 0 of an instance's count and runs tables is only ever read along the
+// chain n, n - g_1, n - 2 g_1, ... (unranking, the walk at the first
+// coordinate, the costs and the totals): its jobs cover that chain alone,
+// as a strided view of n div g_1 + 1 entries.  For d = 3 with the pair memo
+// the same holds for row 1, which only feeds row 0's chain.
+void chain_view(ScanJob &J, const Inst &I) {
+    J.off = I.n % I.g[0];
+    J.es = I.g[0];
+    J.len = I.n / I.g[0] + 1;
+}
+
 int build_scan_plan(fz_batch_s *b, uint64_t *table_base, std::vector<ScanJob> &jobs,
                     std::vector<ScanTask> &tasks, size_t *scratch_words) {
     const int64_t DIRECT = scan_direct_limit();
@@ -123,9 +134,11 @@ int build_scan_plan(fz_batch_s *b, uint64_t *table_base, std::vector<ScanJob> &j
                 // leaf row of a candidates table counted at level d - 1
                 jp.ones_below = ((I.K > 0 && !I.pair) || I.lam_r >= I.d - 1) ? 1 : 0;
                 pair_params(jp.g, jp.h, &jp.e, &jp.h1, &jp.g1, &jp.inv);
+                if (!jp.ones_below && (I.d == 2 || (I.d == 3 && I.pair))) chain_view(jp, I);
                 jobs.push_back(jp);
-                for (int64_t a = 0; a < len; a += 8192)
-                    tasks.push_back({(int)jobs.size() - 1, TK_PAIR, a, std::min(len, a + 8192)});
+                for (int64_t a = 0; a < jp.len; a += 8192)
+                    tasks.push_back(
+                        {(int)jobs.size() - 1, TK_PAIR, a, std::min(jp.len, a + 8192)});
             }
             if (I.lam_r >= 0 && I.off_RT != (size_t)-1) {
                 if (I.lam_r == 0) {
@@ -145,10 +158,11 @@ int build_scan_plan(fz_batch_s *b, uint64_t *table_base, std::vector<ScanJob> &j
                     jl.len = len;
                     jl.g = I.g[j];
                     if (j == I.clamp_row) jl.ones_below = I.top;
+                    if (j == 0) chain_view(jl, I);
                     jobs.push_back(jl);
-                    for (int64_t a = 0; a < len; a += 8192)
+                    for (int64_t a = 0; a < jl.len; a += 8192)
                         tasks.push_back(
-                            {(int)jobs.size() - 1, TK_LINEAR, a, std::min(len, a + 8192)});
+                            {(int)jobs.size() - 1, TK_LINEAR, a, std::min(jl.len, a + 8192)});
                 }
             }
         }
@@ -167,6 +181,10 @@ int build_scan_plan(fz_batch_s *b, uint64_t *table_base, std::vector<ScanJob> &j
                 J.out = table_base + I.off_C + (size_t)j * len;
                 J.len = len;
                 J.g = I.g[j];
+                if (j == 0) {
+                    chain_view(J, I);
+                    J.g = 1;  // consecutive entries of the chain
+                }
                 jobs.push_back(J);
                 step_jobs.push_back((int)jobs.size() - 1);
             }
@@ -180,6 +198,10 @@ int build_scan_plan(fz_batch_s *b, uint64_t *table_base, std::vector<ScanJob> &j
                 J.len = len;
                 J.g = I.g[j];
                 if (j == I.clamp_row) J.ones_below = I.top;
+                if (j == 0) {
+                    chain_view(J, I);
+                    J.g = 1;
+                }
                 jobs.push_back(J);
                 step_jobs.push_back((int)jobs.size() - 1);
             }

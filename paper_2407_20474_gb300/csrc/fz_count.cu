@@ -208,10 +208,14 @@ int launch_runs_table(const int32_t *g, int lam, int32_t n, uint64_t *RT, uint64
 // chains of block sums, a range of block applications, or a range of a row
 // initialisation (delta or ones).
 // ---------------------------------------------------------------------------
+// Logical entry r of a job's rows is entry off + r * es of the table row
+// (es = 1, off = 0: the whole row; es = g_1, off = n mod g_1: the one chain
+// of row 0 that is ever read).
 __device__ __forceinline__ void chain_scan_warp(const uint64_t *__restrict__ in,
                                                 uint64_t *__restrict__ out, int64_t len,
                                                 int64_t g, int64_t rho, int lane,
-                                                int64_t ones_below = 0) {
+                                                int64_t ones_below = 0, int64_t off = 0,
+                                                int64_t es = 1) {
     const int64_t T = (len - rho + g - 1) / g;
     uint64_t carry = 0;
     for (int64_t t0 = 0; t0 < T; t0 += 128) {
@@ -219,13 +223,14 @@ __device__ __forceinline__ void chain_scan_warp(const uint64_t *__restrict__ in,
 #pragma unroll
         for (int u = 0; u < 4; ++u) {
             int64_t t = t0 + u * 32 + lane;
-            v[u] = t < T ? __ldg(in + rho + t * g) : 0ull;
+            v[u] = t < T ? __ldg(in + off + (rho + t * g) * es) : 0ull;
         }
 #pragma unroll
         for (int u = 0; u < 4; ++u) {
             int64_t t = t0 + u * 32 + lane;
             uint64_t sc = sat_add(warp_incl_scan_sat(v[u], lane), carry);
-            if (t < T) out[rho + t * g] = rho + t * g < ones_below ? 1ull : sc;
+            const int64_t x = off + (rho + t * g) * es;
+            if (t < T) out[x] = x < ones_below ? 1ull : sc;
             carry = shfl_u64(sc, 31);
         }
     }
@@ -238,10 +243,11 @@ __global__ void __launch_bounds__(THREADS) scan_tasks_kernel(const ScanJob *__re
     const int lane = threadIdx.x & 31;
     const int warp = threadIdx.x >> 5;
     const int nwarps = blockDim.x >> 5;
+    const int64_t es = J.es ? J.es : 1, off = J.off;
     switch (t.kind) {
         case TK_DIRECT:
             for (int64_t rho = t.begin + warp; rho < t.end; rho += nwarps)
-                chain_scan_warp(J.in, J.out, J.len, J.g, rho, lane, J.ones_below);
+                chain_scan_warp(J.in, J.out, J.len, J.g, rho, lane, J.ones_below, off, es);
             break;
         case TK_SSCAN:
             for (int64_t rho = t.begin + warp; rho < t.end; rho += nwarps)
@@ -254,7 +260,7 @@ __global__ void __launch_bounds__(THREADS) scan_tasks_kernel(const ScanJob *__re
                 uint64_t acc = 0;
                 for (int u = 0; u < RB; ++u) {
                     const int64_t r = r0 + (int64_t)u * J.g;
-                    if (r < J.len) acc = sat_add(acc, __ldg(J.in + r));
+                    if (r < J.len) acc = sat_add(acc, __ldg(J.in + off + r * es));
                 }
                 J.S[i] = acc;
             }
@@ -267,23 +273,27 @@ __global__ void __launch_bounds__(THREADS) scan_tasks_kernel(const ScanJob *__re
                 for (int u = 0; u < RB; ++u) {
                     const int64_t r = r0 + (int64_t)u * J.g;
                     if (r < J.len) {
-                        acc = sat_add(acc, __ldg(J.in + r));
-                        J.out[r] = r < J.ones_below ? 1ull : acc;
+                        const int64_t x = off + r * es;
+                        acc = sat_add(acc, __ldg(J.in + x));
+                        J.out[x] = x < J.ones_below ? 1ull : acc;
                     }
                 }
             }
             break;
         case TK_DELTA:
             for (int64_t i = t.begin + threadIdx.x; i < t.end; i += blockDim.x)
-                J.out[i] = (i == 0) ? 1ull : 0ull;
+                J.out[off + i * es] = (off + i * es == 0) ? 1ull : 0ull;
             break;
         case TK_ONES:
-            for (int64_t i = t.begin + threadIdx.x; i < t.end; i += blockDim.x) J.out[i] = 1ull;
+            for (int64_t i = t.begin + threadIdx.x; i < t.end; i += blockDim.x)
+                J.out[off + i * es] = 1ull;
             break;
         case TK_PAIR:
             // |Z(r, (g, h))|: the a with g a = r (mod h) in [0, r / g] are
             // a = a* (mod h1), a* = (r / e) inv (mod h1), when e divides r
-            for (int64_t r = t.begin + threadIdx.x; r < t.end; r += blockDim.x) {
+            // (row d-1 is written only for whole rows: es == 1)
+            for (int64_t i = t.begin + threadIdx.x; i < t.end; i += blockDim.x) {
+                const int64_t r = off + i * es;
                 uint64_t c = 0;
                 if (r % J.e == 0) {
                     const int64_t re = r / J.e;
@@ -292,12 +302,14 @@ __global__ void __launch_bounds__(THREADS) scan_tasks_kernel(const ScanJob *__re
                     c = q >= astar ? (uint64_t)((q - astar) / J.h1 + 1) : 0ull;
                 }
                 J.out[r] = c;
-                if (J.ones_below) J.out[J.len + r] = (r % J.h == 0) ? 1ull : 0ull;
+                if (J.ones_below && es == 1) J.out[J.len + r] = (r % J.h == 0) ? 1ull : 0ull;
             }
             break;
         case TK_LINEAR:
-            for (int64_t x = t.begin + threadIdx.x; x < t.end; x += blockDim.x)
+            for (int64_t i = t.begin + threadIdx.x; i < t.end; i += blockDim.x) {
+                const int64_t x = off + i * es;
                 J.out[x] = x < J.ones_below ? 1ull : (uint64_t)(x / J.g + 1);
+            }
             break;
         default:
             break;

@@ -265,11 +265,14 @@ struct ScanJob {
     uint64_t *Sincl;     // their strided inclusive scan
     int64_t slen;        // entries of S
     int64_t ones_below;  // entries r < ones_below of out are written as 1
+    // strided view: logical entry r of in/out is entry off + r * es (es = 0
+    // means 1); the one chain of a row that is ever read
     // TK_PAIR: out = row d-2 of a count table, out + len = row d-1 (written
     // only when ones_below != 0), for the last two generators g (= this g)
     // and h, e = gcd(g, h), h1 = h / e, g1 = g / e, inv = g1^-1 mod h1 (0 when
     // h1 = 1)
     int64_t h, e, h1, g1, inv;
+    int64_t off, es;
 };
 enum ScanTaskKind : int {
     TK_DIRECT = 0,  // chains [begin, end) of in -> out, one warp each
