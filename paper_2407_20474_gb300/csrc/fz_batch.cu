@@ -526,9 +526,20 @@ int fz_batch_create(const fz_instance_t *inst, int count, const fz_opts_t *opt,
             off += a256((size_t)mrows[m] * J.k * 4 + 16);
             J.rows = mrows[m];
         }
-        FZ_CUDA_TRY(cudaMemcpyAsync(b->memo_jobs_dev, b->memo_jobs.data(),
-                                    b->memo_jobs.size() * sizeof(MemoJob),
-                                    cudaMemcpyHostToDevice, s));
+        // the build launches one CTA per memo in job order and far more memos
+        // than fit on the GPU at once: longest first (rows copied plus a
+        // barrier's worth per elementwise batch), so the long ones start in
+        // the first wave and the short ones fill in behind them
+        std::vector<MemoJob> by_work(b->memo_jobs);
+        auto work = [](const MemoJob &J) {
+            const double nbatch = ((double)J.top + J.b - 1) / (double)J.b;
+            return (double)J.rows * J.k + 4096.0 * nbatch;
+        };
+        std::stable_sort(by_work.begin(), by_work.end(),
+                         [&](const MemoJob &x, const MemoJob &y) { return work(x) > work(y); });
+        FZ_CUDA_TRY(cudaMemcpyAsync(b->memo_jobs_dev, by_work.data(),
+                                    by_work.size() * sizeof(MemoJob), cudaMemcpyHostToDevice, s));
+        FZ_CUDA_TRY(cudaStreamSynchronize(s));  // by_work is a host temporary
         rc = launch_memo_cta_build(b->memo_jobs_dev, b->nmemo, b->status_dev, s);
         if (rc != FZ_OK) return fail(rc);
     }
