@@ -150,52 +150,9 @@ __device__ __forceinline__ void bulk_wait_all() {
     asm volatile("cp.async.bulk.wait_group 0;" ::: "memory");
 }
 
-// ---------------------------------------------------------------------------
-// Bounded grid barrier for cooperative launches.  Every block calls it the
-// same number of times.  The wait polls a generation word with an iteration
-// and wall-clock limit; when the limit is hit the block records DEV_TIMEOUT
-// in *status and the barrier returns false (the caller then returns).
-// ---------------------------------------------------------------------------
-struct GridBarrier {
-    unsigned *count;  // arrivals in the current generation (left at 0)
-    unsigned *gen;    // generation number
-};
-
+// Limits of every bounded device-side wait.
 constexpr uint64_t BARRIER_TIMEOUT_NS = 2000000000ull;  // 2 s
 constexpr uint32_t BARRIER_MAX_POLLS = 1u << 26;
-
-__device__ __forceinline__ bool grid_barrier(GridBarrier b, int *status) {
-    __shared__ int ok_flag;
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        int ok = 1;
-        unsigned my_gen = ld_acquire_u32(b.gen);
-        __threadfence();
-        unsigned arrived = atomicAdd(b.count, 1u) + 1u;
-        if (arrived == gridDim.x * gridDim.y * gridDim.z) {
-            atomicExch(b.count, 0u);
-            __threadfence();
-            st_release_u32(b.gen, my_gen + 1u);
-        } else {
-            uint64_t t0 = globaltimer_ns();
-            uint32_t polls = 0;
-            while (ld_acquire_u32(b.gen) == my_gen) {
-                if (++polls >= BARRIER_MAX_POLLS ||
-                    ((polls & 255u) == 0 && globaltimer_ns() - t0 > BARRIER_TIMEOUT_NS)) {
-                    atomicExch(status, (int)DEV_TIMEOUT);
-                    ok = 0;
-                    break;
-                }
-                __nanosleep(32);
-            }
-        }
-        // a timeout anywhere stops every block at its next barrier
-        if (ok && *((volatile int *)status) == (int)DEV_TIMEOUT) ok = 0;
-        ok_flag = ok;
-    }
-    __syncthreads();
-    return ok_flag != 0;
-}
 
 // ---------------------------------------------------------------------------
 // Bounded monotonic grid barrier for cooperative launches: *count (zeroed
@@ -309,7 +266,7 @@ struct MemoBuffers {
     uint64_t *map = nullptr;       // rows entries (gather map)
     int32_t *rows = nullptr;       // rows * k
     int *status = nullptr;         // device status word
-    unsigned *bar = nullptr;       // 2 words: barrier count, generation
+    unsigned *bar = nullptr;       // grid-barrier arrival count (zeroed before each fill)
     bool small_ctas = false;       // fill with small CTAs (beside a capped enumeration)
 };
 // Memo of depth 1 or 2 written in closed form from its offsets O (one warp

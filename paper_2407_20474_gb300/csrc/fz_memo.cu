@@ -78,7 +78,7 @@ struct FillParams {
     const uint64_t *map;
     int32_t *rows;
     int *status;
-    GridBarrier bar;
+    unsigned *bar;  // arrival count of the monotonic grid barrier (zero at launch)
     int top;
     int k;
     int b;        // elements per batch
@@ -216,7 +216,7 @@ __global__ void __launch_bounds__(GRID_THREADS) memo_fill_kernel(FillParams P) {
                 }
                 have = true;
             }
-            if (!grid_barrier_mono(P.bar.count, nbar++, P.status)) return;
+            if (!grid_barrier_mono(P.bar, nbar++, P.status)) return;
         }
         R0 = R1;
     }
@@ -794,8 +794,7 @@ int launch_memo_build(const int32_t *tail, int k, int32_t top, uint64_t rows,
     fp.map = mb.map;
     fp.rows = mb.rows;
     fp.status = mb.status;
-    fp.bar.count = mb.bar;
-    fp.bar.gen = mb.bar + 1;
+    fp.bar = mb.bar;
     fp.top = top;
     fp.k = k;
     fp.b = tmin;
