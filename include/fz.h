@@ -97,6 +97,16 @@ uint64_t fz_kernel_launches(void);
  * Errors: FZ_EINVAL (null or unaligned pointer), FZ_ECUDA. */
 int fz_write_probe(int32_t *out_dev, uint64_t words, void *stream);
 
+/* Self-test of the bounded device-side waits (the paper has no counterpart):
+ * two blocks wait at the library's grid barrier for arrivals that never
+ * come; after limit_ms (1..2000) each gives up, records the timeout status
+ * and returns, as every wait in the library does instead of hanging.
+ * *status_seen (host) receives the status the host then reports: FZ_ETIMEOUT
+ * when the mechanism works.  The context stays usable.  Synchronises.
+ * Errors: FZ_EINVAL (null pointer, limit out of range), FZ_ENOMEM,
+ * FZ_ECUDA. */
+int fz_selftest_bounded_wait(uint32_t limit_ms, int *status_seen, void *stream);
+
 /* ------------------------------------------------------------------------
  * Counting (the saved subset cardinalities of Section 2.3, generalised).
  *

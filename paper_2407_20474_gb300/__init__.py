@@ -37,7 +37,7 @@ FZ_EINTERNAL = -9
 # Every symbol include/fz.h declares (checked by the CPU tests).
 EXPORTS = (
     "fz_version", "fz_last_error_string", "fz_status_string", "fz_kernel_launches",
-    "fz_write_probe",
+    "fz_write_probe", "fz_selftest_bounded_wait",
     "fz_count", "fz_count_upto", "fz_count_upto_noalloc", "fz_count_table",
     "fz_memo_rows", "fz_build_memo_into", "fz_build_memo_schedule", "fz_build_memo",
     "fz_memo_info",
@@ -122,6 +122,7 @@ _SIGS = {
     "fz_status_string": (ctypes.c_char_p, [ctypes.c_int]),
     "fz_kernel_launches": (ctypes.c_uint64, []),
     "fz_write_probe": (ctypes.c_int, [_P, ctypes.c_uint64, _P]),
+    "fz_selftest_bounded_wait": (ctypes.c_int, [ctypes.c_uint32, ctypes.POINTER(ctypes.c_int), _P]),
     "fz_count": (ctypes.c_int, [_I32P, ctypes.c_int, ctypes.c_int32, _U64P, _P]),
     "fz_count_upto": (ctypes.c_int, [_I32P, ctypes.c_int, ctypes.c_int32, _U64P, _P]),
     "fz_count_table": (ctypes.c_int, [_I32P, ctypes.c_int, ctypes.c_int32, _P, _P]),
@@ -253,6 +254,14 @@ def fz_version() -> int:
 def fz_kernel_launches() -> int:
     """Kernels the library has enqueued in this process (tracing counter)."""
     return int(lib().fz_kernel_launches())
+
+
+def fz_selftest_bounded_wait(limit_ms: int = 20, stream=None) -> int:
+    """Run the bounded-wait self-test; returns the status the device reported
+    (FZ_ETIMEOUT when waits give up as designed)."""
+    st = ctypes.c_int(0)
+    _check(lib().fz_selftest_bounded_wait(int(limit_ms), ctypes.byref(st), _stream(stream)))
+    return int(st.value)
 
 
 def fz_write_probe(out, stream=None):

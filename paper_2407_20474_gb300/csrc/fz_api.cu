@@ -489,11 +489,53 @@ int plan_host_rows(fz_plan_t p, uint64_t *count_row, std::vector<uint64_t> *runs
 
 }  // namespace fz
 
+namespace fz {
+namespace {
+// Two blocks wait at the monotonic grid barrier for the arrivals of a grid
+// ten times larger: the wait can only end by its time limit.
+__global__ void bounded_wait_selftest_kernel(unsigned *count, int *status, uint64_t limit_ns) {
+    grid_barrier_mono(count, 9u, status, limit_ns);
+}
+}  // namespace
+}  // namespace fz
+
 extern "C" {
 
 int fz_version(void) { return 100; }
 
 uint64_t fz_kernel_launches(void) { return fz::g_launches.load(std::memory_order_relaxed); }
+
+
+int fz_selftest_bounded_wait(uint32_t limit_ms, int *status_seen, void *stream) {
+    if (!status_seen) return fz::set_error(FZ_EINVAL, "status_seen: null pointer");
+    if (limit_ms < 1 || limit_ms > 2000) return fz::set_error(FZ_EINVAL, "limit_ms must be 1..2000");
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    void *buf = nullptr;
+    if (cudaMalloc(&buf, 256) != cudaSuccess) {
+        cudaGetLastError();
+        return fz::set_error(FZ_ENOMEM, "self-test buffer");
+    }
+    unsigned *count = static_cast<unsigned *>(buf);
+    int *status = reinterpret_cast<int *>(static_cast<char *>(buf) + 128);
+    int rc = FZ_OK;
+    if (cudaMemsetAsync(buf, 0, 256, s) != cudaSuccess) rc = fz::set_error(FZ_ECUDA, "memset");
+    if (rc == FZ_OK) {
+        fz::bounded_wait_selftest_kernel<<<2, 32, 0, s>>>(count, status,
+                                                          (uint64_t)limit_ms * 1000000ull);
+        fz::note_launch();
+        if (cudaGetLastError() != cudaSuccess) rc = fz::set_error(FZ_ECUDA, "self-test launch");
+    }
+    int h = 0;
+    if (rc == FZ_OK && (cudaMemcpyAsync(&h, status, sizeof(int), cudaMemcpyDeviceToHost, s) !=
+                            cudaSuccess ||
+                        cudaStreamSynchronize(s) != cudaSuccess))
+        rc = fz::set_error(FZ_ECUDA, "self-test status");
+    cudaFree(buf);
+    if (rc != FZ_OK) return rc;
+    *status_seen = fz::status_to_fz(h);
+    fz::set_error(FZ_OK, "");
+    return FZ_OK;
+}
 
 int fz_write_probe(int32_t *out_dev, uint64_t words, void *stream) {
     if (words == 0) return FZ_OK;

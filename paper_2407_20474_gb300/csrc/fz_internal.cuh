@@ -161,7 +161,8 @@ constexpr uint32_t BARRIER_MAX_POLLS = 1u << 26;
 // barrier.  A block whose wait runs past the limit records DEV_TIMEOUT and
 // returns false (the others then time out too, each on its own).
 // ---------------------------------------------------------------------------
-__device__ __forceinline__ bool grid_barrier_mono(unsigned *count, unsigned index, int *status) {
+__device__ __forceinline__ bool grid_barrier_mono(unsigned *count, unsigned index, int *status,
+                                                  uint64_t timeout_ns = BARRIER_TIMEOUT_NS) {
     __shared__ int ok_flag_m;
     __syncthreads();
     if (threadIdx.x == 0) {
@@ -175,7 +176,7 @@ __device__ __forceinline__ bool grid_barrier_mono(unsigned *count, unsigned inde
         while (ld_acquire_u32(count) < target) {
             if (polls == 0) t0 = globaltimer_ns();
             if (++polls >= BARRIER_MAX_POLLS ||
-                ((polls & 255u) == 0 && globaltimer_ns() - t0 > BARRIER_TIMEOUT_NS)) {
+                ((polls & 255u) == 0 && globaltimer_ns() - t0 > timeout_ns)) {
                 atomicExch(status, (int)DEV_TIMEOUT);
                 ok = 0;
                 break;

@@ -200,6 +200,23 @@ def test_walk_leaves_as_progression(fz, g):
         assert np.array_equal(run_enum(fz, g, n2, k=0), oracle.enumerate_desc(g, n2)), (g, n2)
 
 
+def test_bounded_device_wait_times_out(fz):
+    """A device wait that can never complete gives up after its limit and the
+    host reads FZ_ETIMEOUT; the context stays usable (no fault, no hang)."""
+    import time
+    for limit_ms in (5, 50):
+        t0 = time.perf_counter()
+        st = fz.fz_selftest_bounded_wait(limit_ms)
+        dt = time.perf_counter() - t0
+        assert st == fz.FZ_ETIMEOUT, fz.status_string(st)
+        assert dt >= limit_ms / 1e3, dt
+        assert dt < 10.0, dt
+    with pytest.raises(fz.FzError):
+        fz.fz_selftest_bounded_wait(0)
+    g, n = (5, 8, 11, 14), 500
+    assert np.array_equal(run_enum(fz, g, n, k=2), oracle.enumerate_desc(g, n))
+
+
 def test_write_probe(fz):
     """The measurement utility writes out[w] = w and nothing past the end."""
     for words in (0, 1, 5, 1023, 1 << 20, (1 << 20) + 3):
