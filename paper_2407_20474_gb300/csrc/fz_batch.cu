@@ -291,9 +291,9 @@ int gather(const std::vector<const uint64_t *> &ptrs, std::vector<uint64_t> &out
 // set share one memo).  A memo's rows are estimated by the volume
 // top^K / (K! prod tail), with top = min(n_set + 1, BATCH_MEMO_BATCHES
 // elementwise batches of min(tail) elements).  Preferred: the deepest full
-// memo (top > n_set) of depth >= 3 within BATCH_MEMO_MAX_ROWS rows and half
-// the instance's estimated rows (volume n^(d-1) / ((d-1)! prod g)) -- the
-// deeper the memo, the fewer prefixes the walk visits.  Otherwise, for
+// memo (top > n_set) of depth >= 3 within BATCH_MEMO_MAX_ROWS rows and
+// cap_rows times the instance's estimated rows (volume n^(d-1) / ((d-1)!
+// prod g)) -- the deeper the memo, the fewer prefixes the walk visits.  Otherwise, for
 // d >= 5, a partial memo of depth 3 within BATCH_MEMO_MAX_ROWS rows (the
 // pair memo's leaves, prefixes of length d - 2, would be mostly empty
 // there: config 4's d = 5 instances took 11.3 ms with it, 2 ms with depth
@@ -308,6 +308,11 @@ void choose_batch_memo(Inst &I, int n_set) {
     double count = 1.0 / (double)I.g[I.d - 1];
     for (int i = 0; i < I.d - 1; ++i) count *= (double)n_set / (double)(i + 1) / (double)I.g[i];
     int64_t part_top = 0;
+    // memo rows allowed per estimated instance row: the batch walk pays per
+    // memo leaf, so deeper memos (fewer, larger leaves) repay their build at
+    // d >= 6 up to ~4x the instance's rows (config 4: d = 6..8 enumeration
+    // 11.9 -> 4.1 ms for 1.6 ms more build); at d <= 5 they did not
+    const double cap_rows = I.d >= 6 ? 4.0 : 1.0;
     for (int k = I.d - 1; k >= 3; --k) {
         int32_t tmin = I.g[I.d - k];
         double prod = 1.0;
@@ -320,7 +325,7 @@ void choose_batch_memo(Inst &I, int n_set) {
         for (int i = 0; i < k; ++i) rows *= (double)top / (i + 1);
         rows /= prod;
         if (rows > BATCH_MEMO_MAX_ROWS) continue;
-        if (top > n_set && rows <= 0.5 * count + 4096.0) {
+        if (top > n_set && rows <= cap_rows * count + 4096.0) {
             I.K = k;
             I.top = (int)std::min<int64_t>((int64_t)I.n + 1, top);
             return;
