@@ -180,7 +180,9 @@ int fz_build_memo_into(const int32_t *tail, int k, int32_t top,
  *   FZ_MEMO_BATCHED    elementwise batches of min(tail) elements, each batch
  *                      factorizationwise parallel, all in ONE launch (batches
  *                      separated by a cluster or bounded grid barrier); the
- *                      schedule every other call uses.
+ *                      schedule every other call uses, except that plans
+ *                      fill memos of depth 1 and 2 from their closed forms
+ *                      (the same rows, with no dependent batches).
  *   FZ_MEMO_PER_BATCH  the same batches, one kernel launch per batch ("both"
  *                      parallelism, ordered by the stream).
  *   FZ_MEMO_PER_COPY   the factorizationwise parallel algorithm of Section
@@ -223,7 +225,11 @@ int fz_memo_release(fz_memo_t memo);
  * coordinates a_1..a_{d-k} are walked in descending order; each prefix with
  * p = n - phi(prefix) < top emits Memo[p] with the prefix prepended, and the
  * state is left at (prefix, 0, ..., 0); prefixes with p >= top continue with
- * the ordinary step of Algorithm 3.1.  Work is split by exact rank ranges
+ * the ordinary step of Algorithm 3.1 (at the last two coordinates its
+ * candidates that hold a row form one residue class and are generated
+ * directly).  With a full memo of depth <= 3 the memo is also kept in run
+ * order and a prefix's whole subtree over the last walked coordinate is
+ * copied as one contiguous run.  Work is split by exact rank ranges
  * from the count table (each warp unranks the start of its range), which
  * plays the role of the paper's splitWork.
  * ---------------------------------------------------------------------- */
@@ -291,8 +297,11 @@ int fz_plan_destroy(fz_plan_t plan);
  * of launches -- batched counting tables, one memo per distinct tail shared
  * by the instances that have it (each built by the elementwise dynamic pass,
  * Sections 2.2-2.4, cut to at most 512 element batches; larger
- * remainders take the ordinary next-candidate step, Section 3.1), and one
- * persistent enumeration launch over (instance, slice) work items.
+ * remainders take the ordinary next-candidate step, Section 3.1; a memo of
+ * depth 2 over the last two generators is kept as its closed form, with no
+ * table), and one persistent enumeration launch over (instance, slice) work
+ * items.  The memo depth of each generator set is chosen by the library
+ * unless opts.k is given.
  * Output: instance i's rows (d_i int32 each, descending lexicographic order)
  * start at word word_offsets[i] of the output buffer (multiples of 32 words,
  * so 128-byte aligned when the buffer is); word_offsets[count] is the total.
