@@ -439,7 +439,25 @@ def test_config2_full_size(fz):
         # the oracle's own walk over the first ranks
         head = oracle.enumerate_desc(g, n, 0, 50000)
         assert np.array_equal(rows[:50000].cpu().numpy(), head)
-        del out
+        # the launch configuration bench.py times: the enumeration capped at
+        # 3 or 2 CTAs per SM (larger rings) while another plan of the same
+        # element rebuilds on a second stream; the bytes must not change
+        out2 = torch.empty_like(out)
+        side = torch.cuda.Stream()
+        main = torch.cuda.current_stream()
+        with fz.Plan(g, n, k=plan.k) as other:
+            for cap in (3, 2):
+                out2.fill_(CANARY)
+                plan.set_enum_ctas_per_sm(cap)
+                side.wait_stream(main)
+                other.rebuild(stream=side)
+                assert plan.enumerate(out2) == total
+                torch.cuda.synchronize()
+                plan.sync()
+                other.sync()
+                assert torch.equal(out2, out), cap
+            plan.set_enum_ctas_per_sm(0)
+        del out, out2
 
 
 def test_config3_full_memo_build(fz):
