@@ -636,6 +636,7 @@ def run_batch_workload(args):
                                   "seed 2%s" % (len(inst), (", only d = %d" % args.batch_d)
                                                 if args.batch_d else ""),
                       "total_rows": b.total_rows, "memos": b.memos,
+                      "run_order_instances": b.run_order, "run_order_memos": b.run_memos,
                       "work_items": b.work_items, "cuda_graph": graph_ok,
                       "per_instance_ms_per_step": ms_pi,
                       "per_instance_value": b.total_rows / (ms_pi / 1e3),

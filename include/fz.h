@@ -320,6 +320,8 @@ typedef struct fz_batch_info {
     uint64_t total_words;  /* output words needed (with alignment padding) */
     uint64_t device_bytes; /* device memory held by the batch */
     uint64_t work_items;   /* (instance, slice) items of one enumeration */
+    int32_t run_order;     /* instances whose full memo is copied in run order */
+    int32_t run_memos;     /* distinct run-order memos */
 } fz_batch_info_t;
 
 /* Validate, count every instance (device), choose each memo depth (opts->k

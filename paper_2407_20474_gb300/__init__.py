@@ -85,7 +85,8 @@ class fz_instance_t(ctypes.Structure):
 class fz_batch_info_t(ctypes.Structure):
     _fields_ = [("count", ctypes.c_int32), ("memos", ctypes.c_int32),
                 ("total_rows", ctypes.c_uint64), ("total_words", ctypes.c_uint64),
-                ("device_bytes", ctypes.c_uint64), ("work_items", ctypes.c_uint64)]
+                ("device_bytes", ctypes.c_uint64), ("work_items", ctypes.c_uint64),
+                ("run_order", ctypes.c_int32), ("run_memos", ctypes.c_int32)]
 
 
 class fz_serve_cfg_t(ctypes.Structure):
@@ -519,6 +520,8 @@ class Batch:
         self.total_words = int(info.total_words)
         self.device_bytes = int(info.device_bytes)
         self.work_items = int(info.work_items)
+        self.run_order = int(info.run_order)
+        self.run_memos = int(info.run_memos)
         self.rows = np.zeros(self.count, dtype=np.uint64)
         self.word_offsets = np.zeros(self.count + 1, dtype=np.uint64)
         self.k = np.zeros(self.count, dtype=np.int32)

@@ -199,9 +199,8 @@ void balance_level(int d, int K, int top, int n, bool run_order, int *lam_r, uin
     if (forced > 0) *W = (uint64_t)forced;
 }
 
-namespace {
-
-// FZ_RUN_MEMO=0 keeps full memos in element order only (tuning only).
+// FZ_RUN_MEMO=0 keeps full memos in element order only, in plans and
+// batches (tuning only).
 bool run_memo_enabled() {
     static const bool on = [] {
         const char *e = getenv("FZ_RUN_MEMO");
@@ -209,6 +208,8 @@ bool run_memo_enabled() {
     }();
     return on;
 }
+
+namespace {
 
 // Enqueue the memo of plan p (offsets scan, gather map, fill, run order).
 int plan_enqueue_memo(fz_plan_s *p, cudaStream_t s) {

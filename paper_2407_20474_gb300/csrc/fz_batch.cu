@@ -49,6 +49,11 @@ constexpr double BATCH_MEMO_MAX_ROWS = 1 << 20;
 struct Inst {
     int d = 0, n = 0, K = 0, top = 0, lam_r = 0, clamp_row = -1;
     bool pair = false;  // K = 2 kept as the closed form (no memo table)
+    bool run = false;   // full memo copied in run order (RunJob run_job)
+    int run_job = -1;
+    const int4 *run_memo = nullptr;
+    const uint64_t *cls_beg = nullptr;
+    uint64_t run_rows = 0;
     int32_t g[FZ_MAX_D] = {};
     size_t off_C = 0, off_RT = 0;  // word offsets into the table arena
     int memo = -1;                 // memo job index
@@ -70,6 +75,7 @@ struct fz_batch_s {
     DevArena scratch;  // block sums of blocked scans
     DevArena memos;    // memo offsets and rows
     DevArena meta;     // jobs, tasks, memo jobs, params, item prefix, counters
+    DevArena runs;     // run-order memos: jobs, rows, class starts
     // scan launches: (first task, number of tasks) per launch, in order
     std::vector<std::pair<int, int>> scan_launches;
     ScanJob *jobs_dev = nullptr;
@@ -77,6 +83,8 @@ struct fz_batch_s {
     MemoJob *memo_jobs_dev = nullptr;
     int nmemo = 0;
     std::vector<MemoJob> memo_jobs;
+    RunJob *run_jobs_dev = nullptr;
+    int nrun = 0, run_inst = 0;
     void *params_dev = nullptr;       // EnumParams images (out = word offset)
     uint64_t *item0_dev = nullptr;
     unsigned long long *counter_dev = nullptr;
@@ -259,7 +267,9 @@ int batch_enqueue_rebuild(fz_batch_s *b, cudaStream_t s) {
         int rc = launch_scan_tasks(b->jobs_dev, b->tasks_dev + L.first, L.second, s);
         if (rc != FZ_OK) return rc;
     }
-    return launch_memo_cta_build(b->memo_jobs_dev, b->nmemo, b->status_dev, s);
+    int rc = launch_memo_cta_build(b->memo_jobs_dev, b->nmemo, b->status_dev, s);
+    if (rc != FZ_OK) return rc;
+    return launch_run_memo_batch(b->run_jobs_dev, b->nrun, b->status_dev, s);
 }
 
 __global__ void gather_kernel(const uint64_t *const *ptrs, uint64_t *out, int count) {
@@ -300,6 +310,56 @@ int gather(const std::vector<const uint64_t *> &ptrs, std::vector<uint64_t> &out
 // 3).  Otherwise the pair memo: depth 2, full, as the closed form of
 // Z(p, (g_{d-2}, g_{d-1})) -- no table to build, and its leaves are
 // evaluated 32 at a time.
+// Sum over i = 0..cnt-1 of floor((a i + b) / m), a, b >= 0, m >= 1 (the
+// Euclid-like reduction of floor sums: take out the whole parts of a / m and
+// b / m, then count the lattice points under the line the other way round).
+unsigned __int128 floor_sum(uint64_t cnt, uint64_t m, uint64_t a, uint64_t b) {
+    unsigned __int128 ans = 0;
+    for (;;) {
+        if (a >= m) {
+            ans += (unsigned __int128)cnt * (cnt - 1) / 2 * (a / m);
+            a %= m;
+        }
+        if (b >= m) {
+            ans += (unsigned __int128)cnt * (b / m);
+            b %= m;
+        }
+        const unsigned __int128 y = (unsigned __int128)a * cnt + b;
+        if (y < m) break;
+        cnt = (uint64_t)(y / m);
+        b = (uint64_t)(y % m);
+        const uint64_t t = m;
+        m = a;
+        a = t;
+    }
+    return ans;
+}
+
+// Rows of the pair's run-order memo up to element n: the points (x, y) >= 0
+// with t0 x + t1 y <= n, i.e. the sum over p <= n of |Z(p, (t0, t1))|
+// (saturated at 2^64 - 1).
+uint64_t pair_rows_upto(int64_t n, int64_t t0, int64_t t1) {
+    const uint64_t X = (uint64_t)(n / t0);
+    // sum over x <= X of floor((n - t0 x) / t1) + 1; with x' = X - x the
+    // numerator is (n mod t0) + t0 x'
+    const unsigned __int128 s =
+        floor_sum(X + 1, (uint64_t)t1, (uint64_t)t0, (uint64_t)(n % t0)) + X + 1;
+    return s > (unsigned __int128)~0ull ? ~0ull : (uint64_t)s;
+}
+
+// Estimated |Z(n, g)|: the volume n^(d-1) / ((d-1)! prod g).
+double volume_rows(const Inst &I, int n) {
+    double count = 1.0 / (double)I.g[I.d - 1];
+    for (int i = 0; i < I.d - 1; ++i) count *= (double)n / (double)(i + 1) / (double)I.g[i];
+    return count;
+}
+
+// Run-order memos of the pair's closed form are kept within this many times
+// the instance's estimated rows: they cost 16 bytes a row, built in one
+// fully parallel pass, and replace memo leaves of one to three rows that
+// cost about 12 warp instructions per output row.
+constexpr double RUN_PAIR_CAP = 2.0;
+
 void choose_batch_memo(Inst &I, int n_set) {
     I.K = 0;
     I.top = 0;
@@ -396,12 +456,30 @@ int fz_batch_create(const fz_instance_t *inst, int count, const fz_opts_t *opt,
         }
         if (I.K > 0 && I.top <= 0) I.K = 0;
         if (I.K == 0) I.top = 0;
+        // run order: a full memo of depth 1..3 under at least one walked
+        // coordinate, width <= 8 (the batch walk's run copy); the pair's
+        // closed form gets a run-order table when that stays small
+        I.run = false;
+        if (run_memo_enabled() && I.K >= 1 && I.K <= 3 && I.top > I.n && I.d <= 8 &&
+            I.d - I.K - 1 >= 1) {
+            if (!I.pair) {
+                I.run = true;
+            } else {
+                const int ns = n_set[std::vector<int32_t>(x.g, x.g + x.d)];
+                const int64_t t0 = I.g[I.d - 2], t1 = I.g[I.d - 1];
+                if ((int64_t)ns / t0 < (int64_t)BATCH_MEMO_MAX_ROWS) {
+                    const double rows = (double)pair_rows_upto(ns, t0, t1);
+                    I.run = rows <= BATCH_MEMO_MAX_ROWS &&
+                            rows <= RUN_PAIR_CAP * volume_rows(I, ns) + 4096.0;
+                }
+            }
+        }
         const size_t len = (size_t)I.n + 1;
         I.off_C = words;
         words += (size_t)(I.d + 1) * len;
         I.off_RT = (size_t)-1;
         if (I.d >= 2) {
-            balance_level(I.d, I.K, I.top, I.n, false, &I.lam_r, &I.W, &I.clamp_row);
+            balance_level(I.d, I.K, I.top, I.n, I.run, &I.lam_r, &I.W, &I.clamp_row);
             I.off_RT = words;
             words += (size_t)(I.lam_r + 1) * len;
         } else {
@@ -548,6 +626,88 @@ int fz_batch_create(const fz_instance_t *inst, int count, const fz_opts_t *opt,
         rc = launch_memo_cta_build(b->memo_jobs_dev, b->nmemo, b->status_dev, s);
         if (rc != FZ_OK) return fail(rc);
     }
+    // run-order memos, one per distinct (g_lam, tail) and source (memo or
+    // closed form), built for the largest element asked of it
+    {
+        std::map<std::vector<int32_t>, int> run_of;
+        std::vector<int> run_src;
+        for (int i = 0; i < count; ++i) {
+            Inst &I = b->inst[i];
+            if (!I.run) continue;
+            std::vector<int32_t> key(I.g + (I.d - I.K - 1), I.g + I.d);
+            key.push_back(I.pair ? -1 : I.K);
+            auto it = run_of.find(key);
+            if (it == run_of.end()) {
+                I.run_job = (int)run_src.size();
+                run_of[key] = I.run_job;
+                run_src.push_back(i);
+            } else {
+                I.run_job = it->second;
+                if (I.n > b->inst[run_src[I.run_job]].n) run_src[I.run_job] = i;
+            }
+            ++b->run_inst;
+        }
+        b->nrun = (int)run_src.size();
+        std::vector<RunJob> rj(b->nrun);
+        size_t bytes = a256((size_t)b->nrun * sizeof(RunJob));
+        for (int j = 0; j < b->nrun; ++j) {
+            const Inst &S = b->inst[run_src[j]];
+            RunJob &R = rj[j];
+            const int lam = S.d - S.K - 1;
+            const size_t len = (size_t)S.n + 1;
+            R.Clam = tb + S.off_C + (size_t)lam * len;
+            R.Cnext = tb + S.off_C + (size_t)(lam + 1) * len;
+            R.n = S.n;
+            R.g = S.g[lam];
+            R.G = (int32_t)std::min<int64_t>(R.g, (int64_t)S.n + 1);
+            R.k = S.K;
+            if (S.pair) {
+                R.t0 = S.g[S.d - 2];
+                R.t1 = S.g[S.d - 1];
+                int64_t g1;
+                pair_params(R.t0, R.t1, &R.e, &R.h1, &g1, &R.inv);
+                R.expect_rows = pair_rows_upto(S.n, R.t0, R.t1);
+                R.out_rows = R.expect_rows;
+            } else {
+                if (S.memo < 0 || b->memo_jobs[S.memo].top < S.n + 1 ||
+                    b->memo_jobs[S.memo].k != S.K)
+                    return fail(set_error(FZ_EINTERNAL, "run-order memo without its full memo"));
+                const MemoJob &M = b->memo_jobs[S.memo];
+                R.O = M.O;
+                R.rows = M.R;
+                R.out_rows = M.rows;
+            }
+            if (R.out_rows > MEMO_MAX_ROWS)
+                return fail(set_error(FZ_EINVAL, "batch run-order memo too large"));
+            bytes += a256((size_t)R.out_rows * 16 + 16) + a256(((size_t)R.G + 1) * 8);
+        }
+        if (b->nrun) {
+            rc = b->runs.alloc(bytes);
+            if (rc != FZ_OK) return fail(rc);
+            char *base = static_cast<char *>(b->runs.p);
+            size_t off = a256((size_t)b->nrun * sizeof(RunJob));
+            for (RunJob &R : rj) {
+                R.out = reinterpret_cast<int4 *>(base + off);
+                off += a256((size_t)R.out_rows * 16 + 16);
+                R.cls_beg = reinterpret_cast<uint64_t *>(base + off);
+                off += a256(((size_t)R.G + 1) * 8);
+            }
+            b->run_jobs_dev = reinterpret_cast<RunJob *>(base);
+            FZ_CUDA_TRY(cudaMemcpyAsync(b->run_jobs_dev, rj.data(), rj.size() * sizeof(RunJob),
+                                        cudaMemcpyHostToDevice, s));
+            rc = launch_run_memo_batch(b->run_jobs_dev, b->nrun, b->status_dev, s);
+            if (rc != FZ_OK) return fail(rc);
+            FZ_CUDA_TRY(cudaStreamSynchronize(s));  // rj is a host temporary
+        }
+        for (int i = 0; i < count; ++i) {
+            Inst &I = b->inst[i];
+            if (!I.run) continue;
+            const RunJob &R = rj[I.run_job];
+            I.run_memo = R.out;
+            I.cls_beg = R.cls_beg;
+            I.run_rows = R.out_rows;
+        }
+    }
     // counts and run totals
     std::vector<const uint64_t *> pc(count), pr(count);
     for (int i = 0; i < count; ++i) {
@@ -609,6 +769,12 @@ int fz_batch_create(const fz_instance_t *inst, int count, const fz_opts_t *opt,
             L.memo = b->memo_jobs[I.memo].R;
             L.memo_rows = b->memo_jobs[I.memo].rows;
         }
+        if (I.run) {
+            // the run copy reads the run-order rows only: memo_rows bounds them
+            L.run_memo = I.run_memo;
+            L.cls_beg = I.cls_beg;
+            L.memo_rows = I.run_rows;
+        }
         if (I.off_RT != (size_t)-1) {
             L.RT = tb + I.off_RT;
             L.W = I.W;
@@ -636,8 +802,11 @@ int fz_batch_info(fz_batch_t b, fz_batch_info_t *info) {
     info->memos = b->nmemo;
     info->total_rows = b->total_rows;
     info->total_words = b->total_words;
-    info->device_bytes = b->tables.bytes + b->scratch.bytes + b->memos.bytes + b->meta.bytes;
+    info->device_bytes =
+        b->tables.bytes + b->scratch.bytes + b->memos.bytes + b->meta.bytes + b->runs.bytes;
     info->work_items = b->nitems;
+    info->run_order = b->run_inst;
+    info->run_memos = b->nrun;
     return FZ_OK;
 }
 

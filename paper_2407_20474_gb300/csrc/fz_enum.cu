@@ -1064,6 +1064,167 @@ __global__ void __launch_bounds__(ENUM_THREADS, 4)
     __syncwarp();
 }
 
+// The run-order copy with the tuple width D <= 8 and the memo depth
+// 1 <= K <= 3 read at run time (batches): the rounds of runs_slice, with the
+// prefix a_0..a_{LAMF-1} (LAMF = D - K - 1 <= 6) kept in registers through
+// loops unrolled to their maxima and guarded by the run-time bounds.
+constexpr int RT_LAMF_MAX = 6;
+
+__device__ __forceinline__ void run_store_row_rt(int32_t *dst, const int (&a)[RT_LAMF_MAX], int D,
+                                                 int LAMF, int vmax, int4 m) {
+    int w[8];
+#pragma unroll
+    for (int c = 0; c < 8; ++c) {
+        const int t = c - LAMF;
+        int v = c < RT_LAMF_MAX ? a[c] : 0;
+        if (t == 0)
+            v = vmax - m.x;
+        else if (t == 1)
+            v = m.y;
+        else if (t == 2)
+            v = m.z;
+        else if (t == 3)
+            v = m.w;
+        w[c] = v;
+    }
+    if ((D & 3) == 0) {  // row starts 16-byte aligned
+#pragma unroll
+        for (int c = 0; c < 8; c += 4)
+            if (c < D)
+                *reinterpret_cast<int4 *>(dst + c) = make_int4(w[c], w[c + 1], w[c + 2], w[c + 3]);
+    } else if ((D & 1) == 0) {  // 8-byte aligned
+#pragma unroll
+        for (int c = 0; c < 8; c += 2)
+            if (c < D) *reinterpret_cast<int2 *>(dst + c) = make_int2(w[c], w[c + 1]);
+    } else {
+#pragma unroll
+        for (int c = 0; c < 8; ++c)
+            if (c < D) dst[c] = w[c];
+    }
+}
+
+__device__ __noinline__ bool runs_slice_rt(const EnumParams &P, int32_t *ring, uint32_t B,
+                                           uint64_t row0, uint64_t row1, uint64_t pol,
+                                           int lane) {
+    const int D = P.d;
+    const int LAMF = P.d - P.K - 1;
+    if (LAMF < 1 || D > 8 || P.K < 1 || P.K > 3) {  // shapes the host never sends here
+        if (lane == 0) atomicExch(P.status, (int)DEV_INTERNAL);
+        return false;
+    }
+    // unrank the first row: the prefix, its remainder and the offset in its run
+    int a[RT_LAMF_MAX];
+#pragma unroll
+    for (int c = 0; c < RT_LAMF_MAX; ++c) a[c] = 0;
+    uint64_t R = P.rank_begin + row0;
+    int rem = P.n;
+#pragma unroll 1
+    for (int j = 0; j < LAMF; ++j) {
+        int v;
+        uint64_t before;
+        find_child(P, j, rem, R, lane, v, before);
+        R -= before;
+        rem -= v * P.g[j];
+#pragma unroll
+        for (int c = 0; c < RT_LAMF_MAX; ++c)
+            if (c == j) a[c] = v;
+    }
+    uint64_t off = R;
+    uint64_t left = row1 - row0;
+    uint32_t hpos = 0, half = 0, nfull = 0;
+    const int glam = P.g[LAMF];
+    bool ok = true;
+    for (;;) {
+        const uint64_t run_rows = __ldg(P.C + (long long)LAMF * P.cs + rem);
+        if (off < run_rows) {
+            const int vmax = rem / glam;
+            const int cls = rem - vmax * glam;
+            const uint64_t src64 = __ldg(P.cls_beg + cls) + off;
+            uint64_t take64 = run_rows - off;
+            if (take64 > left) take64 = left;
+            if (src64 + take64 > P.memo_rows) {  // bounds guard: the run lies in the memo
+                if (lane == 0) atomicExch(P.status, (int)DEV_INTERNAL);
+                ok = false;
+                break;
+            }
+            left -= take64;
+            uint32_t src = (uint32_t)src64, take = (uint32_t)take64;
+            uint32_t c0 = take < 64u ? take : 64u;
+            if (c0 > B - hpos) c0 = B - hpos;
+            int4 x0 = make_int4(0, 0, 0, 0), x1 = x0, y0 = x0, y1 = x0;
+            {
+                const int4 *ms = P.run_memo + src;
+                if ((uint32_t)lane < c0) x0 = __ldg(ms + lane);
+                if ((uint32_t)lane + 32u < c0) x1 = __ldg(ms + 32 + lane);
+            }
+            auto round = [&](const int4 &cur0, const int4 &cur1, int4 &nxt0, int4 &nxt1) {
+                const uint32_t hp1 = hpos + c0 == B ? 0u : hpos + c0;
+                const uint32_t t1 = take - c0;
+                uint32_t c1 = t1 < 64u ? t1 : 64u;
+                if (c1 > B - hp1) c1 = B - hp1;
+                const int4 *ns = P.run_memo + (src + c0);
+                if ((uint32_t)lane < c1) nxt0 = __ldg(ns + lane);
+                if ((uint32_t)lane + 32u < c1) nxt1 = __ldg(ns + 32 + lane);
+                if (hpos == 0 && nfull >= 2) {
+                    if (lane == 0) bulk_wait_read<1>();
+                    __syncwarp();
+                }
+                int32_t *dst = ring + (size_t)(half * B + hpos + lane) * D;
+                if ((uint32_t)lane < c0) run_store_row_rt(dst, a, D, LAMF, vmax, cur0);
+                if ((uint32_t)lane + 32u < c0) run_store_row_rt(dst + 32 * D, a, D, LAMF, vmax, cur1);
+                if (hp1 == 0) {
+                    flush_rows(P, ring + (size_t)half * B * D, row0 + (uint64_t)nfull * B, B, D,
+                               lane, pol);
+                    ++nfull;
+                    half ^= 1u;
+                }
+                hpos = hp1;
+                src += c0;
+                take = t1;
+                c0 = c1;
+            };
+            for (;;) {
+                round(x0, x1, y0, y1);
+                if (take == 0) break;
+                round(y0, y1, x0, x1);
+                if (take == 0) break;
+            }
+            if (left == 0) break;
+        }
+        off = 0;
+        // the next prefix in descending order: decrement the deepest positive
+        // coordinate, reset the ones after it to their maxima (the remainder
+        // is carried forward from r_0 = n)
+        int jj = -1;
+#pragma unroll
+        for (int j = 0; j < RT_LAMF_MAX; ++j)
+            if (j < LAMF && a[j] > 0) jj = j;
+        if (jj < 0) {
+            if (lane == 0) atomicExch(P.status, (int)DEV_INTERNAL);
+            ok = false;
+            break;
+        }
+        int rr = P.n;
+#pragma unroll
+        for (int j = 0; j < RT_LAMF_MAX; ++j) {
+            if (j < LAMF) {
+                if (j == jj)
+                    a[j] -= 1;
+                else if (j > jj)
+                    a[j] = rr / P.g[j];
+                rr -= a[j] * P.g[j];
+            }
+        }
+        rem = rr;
+    }
+    if (hpos > 0)
+        flush_rows(P, ring + (size_t)half * B * D, row0 + (uint64_t)nfull * B, hpos, D, lane,
+                   pol);
+    if (lane == 0) bulk_wait_read_all();
+    __syncwarp();
+    return ok;
+}
+
 // ---------------------------------------------------------------------------
 // Many instances in one persistent launch.  Work items (instance, slice) are
 // numbered consecutively, instance i owning items [item0[i], item0[i+1]); a
@@ -1158,12 +1319,17 @@ __global__ void __launch_bounds__(ENUM_THREADS, 4)
             }
             continue;
         }
-        // one walk for every width up to 8 (row loops unrolled to 8), the
-        // 16-wide one beyond: two code paths at most, so warps of different
-        // instances share the instruction cache
-        const bool ok =
-            P.d <= 8 ? enum_slice<0, -1, 8>(P, wp, ring, (uint32_t)P.half_rows, row0, row1, pol, lane)
-                     : enum_slice<0, -1>(P, wp, ring, (uint32_t)P.half_rows, row0, row1, pol, lane);
+        // full memos in run order take the run copy; otherwise one walk for
+        // every width up to 8 (row loops unrolled to 8), the 16-wide one
+        // beyond: three code paths at most, so warps of different instances
+        // share the instruction cache
+        bool ok;
+        if (P.run_memo)
+            ok = runs_slice_rt(P, ring, (uint32_t)P.half_rows, row0, row1, pol, lane);
+        else if (P.d <= 8)
+            ok = enum_slice<0, -1, 8>(P, wp, ring, (uint32_t)P.half_rows, row0, row1, pol, lane);
+        else
+            ok = enum_slice<0, -1>(P, wp, ring, (uint32_t)P.half_rows, row0, row1, pol, lane);
         if (!ok) break;
     }
     cp_async_wait<0>();

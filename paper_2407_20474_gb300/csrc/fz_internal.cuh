@@ -302,6 +302,26 @@ int launch_run_memo(const uint64_t *C, int64_t cs, int lam, int32_t n, int32_t g
                     uint64_t *cls_beg, int4 *run_memo, int *status, cudaStream_t s);
 int launch_memo_cta_build(const MemoJob *jobs, int njobs, int *status, cudaStream_t s);
 
+// One run-order memo of a batch (the layout of launch_run_memo) for the
+// elements 0..n: its rows come from an element-order memo of depth k <= 3
+// (O, rows), or, with O null, from the closed form of the pair
+// (t0, t1) = (g_{d-2}, g_{d-1}) (k = 2): element p holds the a_{d-2} =
+// a_top - o h1 (o = 0, 1, ...) of the progression of launch_memo_closed.
+struct RunJob {
+    const uint64_t *Clam;   // count-table row lam of the source instance, n + 1 entries
+    const uint64_t *Cnext;  // row lam + 1: |Z(p, tail)|
+    const uint64_t *O;      // element-order memo offsets, or null (closed form)
+    const int32_t *rows;    // element-order memo rows (k int32 each), or null
+    uint64_t *cls_beg;      // G + 1 class starts
+    int4 *out;              // run-order rows
+    uint64_t out_rows;      // capacity of out (bounds guard)
+    uint64_t expect_rows;   // closed form: sum over p <= n of |Z(p, (t0, t1))|
+    int32_t n, g, G, k;     // last element, g_lam, G = min(g_lam, n + 1), depth
+    int64_t t0, t1, e, h1, inv;
+};
+// Builds every job's class starts, then its rows (two launches).
+int launch_run_memo_batch(const RunJob *jobs, int njobs, int *status, cudaStream_t s);
+
 // out[w] = w for w < words, 16-byte stores (fz_write_probe; fz_count.cu).
 int launch_write_probe(int32_t *out, uint64_t words, cudaStream_t s);
 
@@ -317,6 +337,7 @@ bool walk_progression_enabled();
 // and candidates evaluated 32 at a time cost W = 16.
 // *clamp_row >= 0: the table row whose entries below top are set to 1 (a
 // memo leaf is one unit, whatever lies under it), else -1.
+bool run_memo_enabled();
 void balance_level(int d, int K, int top, int n, bool run_order, int *lam_r, uint64_t *W,
                    int *clamp_row);
 

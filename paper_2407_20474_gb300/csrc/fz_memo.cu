@@ -683,7 +683,105 @@ __global__ void __launch_bounds__(THREADS) run_memo_kernel(
     }
 }
 
+// Batches: one CTA per run job for its class starts.  The total must be the
+// memo's rows up to n (O[n + 1]), or the closed form's count.
+__global__ void __launch_bounds__(RUN_CB_THREADS) run_class_begin_batch_kernel(
+    const RunJob *__restrict__ jobs, int *status) {
+    __shared__ uint64_t sums[33];
+    const RunJob &J = jobs[blockIdx.x];
+    const uint64_t *Clam = J.Clam;
+    const int32_t n = J.n, g = J.g, G = J.G;
+    uint64_t carry = 0;
+    for (int base = 0; base < G; base += blockDim.x) {
+        const int c = base + (int)threadIdx.x;
+        uint64_t v = 0;
+        if (c < G) {
+            const int64_t last = c + (int64_t)((n - c) / g) * g;
+            v = __ldg(Clam + last);
+        }
+        uint64_t total;
+        const uint64_t ex = block_exclusive_scan(v, sums, &total);
+        if (c < G) J.cls_beg[c] = carry + ex;
+        carry += total;
+    }
+    if (threadIdx.x == 0) {
+        J.cls_beg[G] = carry;
+        const uint64_t want = J.O ? __ldg(J.O + (int64_t)n + 1) : J.expect_rows;
+        if (carry != want || carry > J.out_rows) atomicExch(status, (int)DEV_INTERNAL);
+    }
+}
+
+// Batches: a thread per element (the batch memos hold a few rows per
+// element), jobs along y.  Rows from the element-order memo, or from the
+// pair's closed form (the progression of memo_closed_kernel).
+__global__ void __launch_bounds__(THREADS) run_rows_batch_kernel(const RunJob *__restrict__ jobs,
+                                                                 int njobs, int *status) {
+    for (int jb = blockIdx.y; jb < njobs; jb += gridDim.y) {
+        const RunJob &J = jobs[jb];
+        const int64_t g = J.g;
+        for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p <= J.n;
+             p += (int64_t)gridDim.x * blockDim.x) {
+            const int64_t q = p / g, c = p - q * g;
+            const uint64_t tail_rows = __ldg(J.Cnext + p);
+            const uint64_t dst = __ldg(J.cls_beg + c) + __ldg(J.Clam + p) - tail_rows;
+            if (dst + tail_rows > J.out_rows) {
+                atomicExch(status, (int)DEV_INTERNAL);
+                continue;
+            }
+            int4 *o = J.out + dst;
+            if (J.O) {
+                const uint64_t o0 = __ldg(J.O + p), len = __ldg(J.O + p + 1) - o0;
+                if (len != tail_rows) {
+                    atomicExch(status, (int)DEV_INTERNAL);
+                    continue;
+                }
+                const int k = J.k;
+                const int32_t *s = J.rows + o0 * (uint64_t)k;
+                for (uint64_t r = 0; r < len; ++r, s += k) {
+                    int4 v;
+                    v.x = (int)q;
+                    v.y = __ldg(s);
+                    v.z = k > 1 ? __ldg(s + 1) : 0;
+                    v.w = k > 2 ? __ldg(s + 2) : 0;
+                    o[r] = v;
+                }
+            } else {
+                int64_t atop = -1;
+                uint64_t want = 0;
+                if (p % J.e == 0) {
+                    const int64_t astar = ((p / J.e) % J.h1) * J.inv % J.h1;
+                    const int64_t q0 = p / J.t0;
+                    if (q0 >= astar) {
+                        atop = q0 - (q0 - astar) % J.h1;
+                        want = (uint64_t)(atop / J.h1) + 1;
+                    }
+                }
+                if (want != tail_rows) {
+                    atomicExch(status, (int)DEV_INTERNAL);
+                    continue;
+                }
+                for (uint64_t r = 0; r < want; ++r) {
+                    const int64_t a0 = atop - (int64_t)r * J.h1;
+                    o[r] = make_int4((int)q, (int)a0, (int)((p - a0 * J.t0) / J.t1), 0);
+                }
+            }
+        }
+    }
+}
+
 }  // namespace
+
+int launch_run_memo_batch(const RunJob *jobs, int njobs, int *status, cudaStream_t s) {
+    if (njobs <= 0) return FZ_OK;
+    if (!jobs || !status) return set_error(FZ_EINTERNAL, "run memo batch: missing device buffer");
+    run_class_begin_batch_kernel<<<njobs, RUN_CB_THREADS, 0, s>>>(jobs, status);
+    note_launch();
+    const dim3 grid(64, (unsigned)(njobs < 65535 ? njobs : 65535));
+    run_rows_batch_kernel<<<grid, THREADS, 0, s>>>(jobs, njobs, status);
+    note_launch();
+    FZ_CUDA_TRY(cudaGetLastError());
+    return FZ_OK;
+}
 
 int launch_run_memo(const uint64_t *C, int64_t cs, int lam, int32_t n, int32_t g_lam,
                     const uint64_t *O, const int32_t *rows, int k, uint64_t memo_rows,

@@ -71,6 +71,30 @@ def test_batch_pair_memo_leaves(fz):
         assert np.array_equal(got, oracle.enumerate_desc(g, n)), (g, n)
 
 
+def test_batch_run_order(fz):
+    """Full memos copied in run order inside the batch launch: the pair's
+    closed form (d >= 4) and memos of depth 1..3 (explicit k), prefixes of
+    one to six walked coordinates, generator sets repeated with several n
+    (one run-order memo for the largest), repeats and gcd > 1."""
+    gens = [(5, 9, 12, 18), (2, 3, 35, 49), (7, 11, 13, 17, 19), (6, 10, 15, 4),
+            (3, 5, 7, 9, 11, 13), (4, 4, 6, 9), (9, 6, 12, 15, 21, 10), (2, 3, 5, 7, 11, 13, 17, 19)]
+    inst = []
+    for g in gens:
+        for target in (700, 9_000, 40_000):
+            inst.append((g, workloads.find_n(oracle.count_upto, g, target, 64)))
+    inst.append((gens[0], inst[0][1] + 1))
+    b, segs = run_batch(fz, inst)
+    assert b.run_order > 0 and b.run_memos > 0, (b.run_order, b.run_memos)
+    for (g, n), got in zip(inst, segs):
+        assert np.array_equal(got, oracle.enumerate_desc(g, n)), (g, n)
+    for k in (1, 2, 3):
+        sub = [(g, n) for g, n in inst if len(g) >= k + 2]
+        b, segs = run_batch(fz, sub, k=k)
+        assert b.run_order > 0, k
+        for (g, n), got in zip(sub, segs):
+            assert np.array_equal(got, oracle.enumerate_desc(g, n)), (g, n, k)
+
+
 def test_batch_every_memo_depth(fz):
     inst = [x for x in small_instances(32, 60) if len(x[0]) >= 4]
     for k in (0, 1, 2, 3):
