@@ -300,8 +300,11 @@ int fz_plan_destroy(fz_plan_t plan);
  * remainders take the ordinary next-candidate step, Section 3.1; a memo of
  * depth 2 over the last two generators is kept as its closed form, with no
  * table), and one persistent enumeration launch over (instance, slice) work
- * items.  The memo depth of each generator set is chosen by the library
- * unless opts.k is given.
+ * items.  Full memos of depth 1..3 (widths d <= 8 with at least one walked
+ * coordinate above the memo) are also kept in run order, as in plans, so a
+ * prefix's whole subtree is one contiguous copy; for the closed form that
+ * table is computed from the formula when it stays small.  The memo depth
+ * of each generator set is chosen by the library unless opts.k is given.
  * Output: instance i's rows (d_i int32 each, descending lexicographic order)
  * start at word word_offsets[i] of the output buffer (multiples of 32 words,
  * so 128-byte aligned when the buffer is); word_offsets[count] is the total.
