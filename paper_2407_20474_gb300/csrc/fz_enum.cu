@@ -1432,16 +1432,16 @@ constexpr int ENUM_MAX_SMEM = 200 * 1024;
 
 template <typename Kern>
 static int launch_enum_kernel(Kern kern, const EnumParams &P, int D, cudaStream_t s, int sms,
-                              bool (&attr_set)[64]) {
+                              DeviceOnce &attr_set) {
     const size_t smem = (size_t)ENUM_WARPS * 2 * P.half_rows * D * 4 +
                         (size_t)ENUM_WARPS * sizeof(WarpPath);
     if (smem > (size_t)ENUM_MAX_SMEM) return set_error(FZ_EINTERNAL, "enumerate: ring too large");
     int dev = 0;
-    cudaGetDevice(&dev);
-    if (dev < 64 && !attr_set[dev]) {
+    FZ_CUDA_TRY(cudaGetDevice(&dev));
+    if (!attr_set.is_set(dev)) {
         FZ_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          ENUM_MAX_SMEM));
-        attr_set[dev] = true;
+        attr_set.set(dev);
     }
     int per_sm = 0;
     FZ_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, ENUM_THREADS, smem));
@@ -1460,13 +1460,13 @@ static int launch_enum_kernel(Kern kern, const EnumParams &P, int D, cudaStream_
 
 template <int D, int LAMF>
 static int launch_enum_dl(const EnumParams &P, cudaStream_t s, int sms) {
-    static bool attr_set[64] = {};
+    static DeviceOnce attr_set;
     return launch_enum_kernel(fz_enum_kernel<D, LAMF>, P, D, s, sms, attr_set);
 }
 
 template <int D, int LAMF, int K>
 static int launch_enum_runs(const EnumParams &P, cudaStream_t s, int sms) {
-    static bool attr_set[64] = {};
+    static DeviceOnce attr_set;
     return launch_enum_kernel(fz_enum_runs_kernel<D, LAMF, K>, P, D, s, sms, attr_set);
 }
 
@@ -1697,11 +1697,11 @@ int launch_enumerate_batch(const void *params_dev, const uint64_t *item0_dev, in
     int rc = device_props(&dp);
     if (rc != FZ_OK) return rc;
     const size_t smem = enum_batch_smem_bytes();
-    static bool attr_set[64] = {};
-    if (dp.device >= 0 && dp.device < 64 && !attr_set[dp.device]) {
+    static DeviceOnce attr_set;
+    if (!attr_set.is_set(dp.device)) {
         FZ_CUDA_TRY(cudaFuncSetAttribute(fz_enum_batch_kernel,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-        attr_set[dp.device] = true;
+        attr_set.set(dp.device);
     }
     int per_sm = 0;
     FZ_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fz_enum_batch_kernel,

@@ -5,6 +5,7 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <atomic>
 #include <string>
 #include <vector>
 
@@ -193,6 +194,19 @@ __device__ __forceinline__ bool grid_barrier_mono(unsigned *count, unsigned inde
 // ---------------------------------------------------------------------------
 // Host helpers.
 // ---------------------------------------------------------------------------
+// Per-device flags for host-side steps done once per kernel and device
+// (function attributes), safe when several host threads launch: the
+// serving thread and its callers.
+struct DeviceOnce {
+    std::atomic<bool> done[64];
+    bool is_set(int dev) const {
+        return dev >= 0 && dev < 64 && done[dev].load(std::memory_order_acquire);
+    }
+    void set(int dev) {
+        if (dev >= 0 && dev < 64) done[dev].store(true, std::memory_order_release);
+    }
+};
+
 struct DeviceProps {
     int device = -1;
     int sms = 0;

@@ -452,10 +452,12 @@ int coop_grid(const void *kernel, int threads) {
 template <int MAXT, int MINB>
 static int launch_fill_cluster_t(FillParams fp, int threads, cudaStream_t s) {
     auto kern = memo_fill_cluster_kernel<MAXT, MINB, false>;
-    static bool attr_set = false;
-    if (!attr_set) {
+    static DeviceOnce attr_set;
+    int dev = 0;
+    FZ_CUDA_TRY(cudaGetDevice(&dev));
+    if (!attr_set.is_set(dev)) {
         cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
-        attr_set = true;
+        attr_set.set(dev);
     }
     for (int csize : {16, 8}) {
         cudaLaunchConfig_t cfg = {};
