@@ -50,6 +50,8 @@ def parse():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--seed", type=int, default=0)
     ap.add_argument("--e2e-steps", type=int, default=2)
+    ap.add_argument("--pg-timeout", type=float, default=300.0,
+                    help="seconds a collective waits for a rank that has left (N > 1)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-graph", action="store_true",
@@ -148,6 +150,11 @@ class ClockSampler:
 
 # ------------------------------------------------------------ distributed
 def dist_setup(args):
+    """One process per GPU from the torchrun environment.  A collective
+    that waits on a rank that has left ends with an error after
+    args.pg_timeout seconds (or as soon as the peer's connection closes)
+    instead of hanging."""
+    import datetime
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
@@ -158,7 +165,8 @@ def dist_setup(args):
         if backend == "nccl":
             import torch
             torch.cuda.set_device(local)
-        dist.init_process_group(backend=backend)
+        dist.init_process_group(backend=backend,
+                                timeout=datetime.timedelta(seconds=float(args.pg_timeout)))
         pg = dist
     return world, rank, local, pg
 

@@ -3,7 +3,9 @@
 bench.py under torchrun runs one replica per rank and rank 0 alone prints;
 times are the maximum over ranks.  These tests run that path with
 world_size 2 on the CPU: the reference arm (the oracle, gloo) through
-torchrun, and the max-over-ranks reduction with two spawned processes.
+torchrun, the max-over-ranks reduction with two spawned processes, and a
+rank that leaves between steps (the other's next collective must end with
+an error, not hang).
 """
 import json
 import os
@@ -66,3 +68,53 @@ def test_max_over_ranks_gloo():
         p.join(timeout=60)
         assert p.exitcode == 0
     assert got == {0: 20.0, 1: 20.0}
+
+
+def _leaving_worker(rank, port, out):
+    import argparse
+    import torch.distributed as dist
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port), RANK=str(rank),
+                      WORLD_SIZE="2", LOCAL_RANK=str(rank))
+    sys.path.insert(0, ROOT)
+    import bench
+    args = argparse.Namespace(impl="reference", pg_timeout=10.0)
+    world, r, _, pg = bench.dist_setup(args)
+    assert world == 2 and r == rank
+    bench.barrier(pg)  # one step together
+    if rank == 1:
+        # leaves between steps, with nothing in flight
+        out.put((rank, "left"))
+        out.close()
+        out.join_thread()
+        os._exit(3)
+    import time
+    t0 = time.monotonic()
+    try:
+        bench.max_over_ranks(pg, 1.0)
+        res = "no error"
+    except Exception:
+        res = "error"
+    out.put((rank, res, time.monotonic() - t0))
+    out.close()
+    out.join_thread()
+    os._exit(0)
+
+
+def test_rank_leaving_ends_the_next_collective():
+    import multiprocessing as mp
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    port = free_port()
+    ps = [ctx.Process(target=_leaving_worker, args=(r, port, q)) for r in range(2)]
+    for p in ps:
+        p.start()
+    got = {}
+    for _ in ps:
+        item = q.get(timeout=120)
+        got[item[0]] = item[1:]
+    for p in ps:
+        p.join(timeout=60)
+    assert got[1] == ("left",)
+    assert got[0][0] == "error", got
+    assert got[0][1] < 60.0  # the process-group timeout (10 s) or the closed connection
+    assert ps[0].exitcode == 0 and ps[1].exitcode == 3
