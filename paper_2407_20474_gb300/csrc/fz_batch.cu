@@ -310,43 +310,6 @@ int gather(const std::vector<const uint64_t *> &ptrs, std::vector<uint64_t> &out
 // 3).  Otherwise the pair memo: depth 2, full, as the closed form of
 // Z(p, (g_{d-2}, g_{d-1})) -- no table to build, and its leaves are
 // evaluated 32 at a time.
-// Sum over i = 0..cnt-1 of floor((a i + b) / m), a, b >= 0, m >= 1 (the
-// Euclid-like reduction of floor sums: take out the whole parts of a / m and
-// b / m, then count the lattice points under the line the other way round).
-unsigned __int128 floor_sum(uint64_t cnt, uint64_t m, uint64_t a, uint64_t b) {
-    unsigned __int128 ans = 0;
-    for (;;) {
-        if (a >= m) {
-            ans += (unsigned __int128)cnt * (cnt - 1) / 2 * (a / m);
-            a %= m;
-        }
-        if (b >= m) {
-            ans += (unsigned __int128)cnt * (b / m);
-            b %= m;
-        }
-        const unsigned __int128 y = (unsigned __int128)a * cnt + b;
-        if (y < m) break;
-        cnt = (uint64_t)(y / m);
-        b = (uint64_t)(y % m);
-        const uint64_t t = m;
-        m = a;
-        a = t;
-    }
-    return ans;
-}
-
-// Rows of the pair's run-order memo up to element n: the points (x, y) >= 0
-// with t0 x + t1 y <= n, i.e. the sum over p <= n of |Z(p, (t0, t1))|
-// (saturated at 2^64 - 1).
-uint64_t pair_rows_upto(int64_t n, int64_t t0, int64_t t1) {
-    const uint64_t X = (uint64_t)(n / t0);
-    // sum over x <= X of floor((n - t0 x) / t1) + 1; with x' = X - x the
-    // numerator is (n mod t0) + t0 x'
-    const unsigned __int128 s =
-        floor_sum(X + 1, (uint64_t)t1, (uint64_t)t0, (uint64_t)(n % t0)) + X + 1;
-    return s > (unsigned __int128)~0ull ? ~0ull : (uint64_t)s;
-}
-
 // Estimated |Z(n, g)|: the volume n^(d-1) / ((d-1)! prod g).
 double volume_rows(const Inst &I, int n) {
     double count = 1.0 / (double)I.g[I.d - 1];

@@ -1499,28 +1499,6 @@ static int launch_unrank_d(const EnumParams &P, const uint64_t *ranks, uint64_t 
     return FZ_OK;
 }
 
-void pair_params(int64_t g, int64_t h, int64_t *e_out, int64_t *h1_out, int64_t *g1_out,
-                 int64_t *inv_out) {
-    // extended Euclid: x g + y h = e
-    int64_t r0 = g, r1 = h, x0 = 1, x1 = 0;
-    while (r1 != 0) {
-        const int64_t q = r0 / r1;
-        int64_t t = r0 - q * r1;
-        r0 = r1;
-        r1 = t;
-        t = x0 - q * x1;
-        x0 = x1;
-        x1 = t;
-    }
-    const int64_t e = r0, h1 = h / e;
-    int64_t inv = h1 > 1 ? x0 % h1 : 0;  // (g/e) x = 1 (mod h/e)
-    if (inv < 0) inv += h1;
-    *e_out = e;
-    *h1_out = h1;
-    *g1_out = g / e;
-    *inv_out = inv;
-}
-
 // FZ_WALK_PROGRESSION=0 evaluates walk leaves candidate by candidate as the
 // ordinary step does (tuning and testing only).
 bool walk_progression_enabled() {

@@ -10,6 +10,7 @@
 #include <vector>
 
 #include "../../include/fz.h"
+#include "fz_host_math.h"
 
 namespace fz {
 
@@ -256,9 +257,6 @@ enum ScanTaskKind : int {
     TK_PAIR = 6,    // rows d-2 and d-1 of a count table in closed form
     TK_LINEAR = 7   // out[x] = x / g + 1 (a runs-table row above the ones row)
 };
-// Extended Euclid for the last two generators (g, h): e = gcd, h1 = h / e,
-// g1 = g / e, inv = g1^-1 mod h1 (0 when h1 = 1).
-void pair_params(int64_t g, int64_t h, int64_t *e, int64_t *h1, int64_t *g1, int64_t *inv);
 struct ScanTask {
     int job;
     int kind;
