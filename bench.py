@@ -623,6 +623,10 @@ def run_batch_workload(args):
     ms = _event_time(torch, step, max(args.steps, 1), max(args.warmup, 1))
     b.sync()
     value = b.total_rows / (ms / 1e3)
+    # the two halves of the step, each timed alone (plain launches)
+    ms_rebuild = _event_time(torch, b.rebuild, max(args.steps, 1), 1)
+    ms_enum = _event_time(torch, lambda: b.enumerate(out), max(args.steps, 1), 1)
+    b.sync()
     # per-instance launches of the same instances
     plans = [fz.Plan(gg, n) for gg, n in inst]
     offs = [int(x) for x in b.word_offsets]
@@ -646,6 +650,7 @@ def run_batch_workload(args):
                       "total_rows": b.total_rows, "memos": b.memos,
                       "run_order_instances": b.run_order, "run_order_memos": b.run_memos,
                       "work_items": b.work_items, "cuda_graph": graph_ok,
+                      "rebuild_ms": ms_rebuild, "enumerate_ms": ms_enum,
                       "per_instance_ms_per_step": ms_pi,
                       "per_instance_value": b.total_rows / (ms_pi / 1e3),
                       "speedup_vs_per_instance": ms_pi / ms}}
