@@ -50,7 +50,7 @@ typedef enum fz_status {
     FZ_OK = 0,
     FZ_EINVAL = -1,     /* bad argument: d, g_i, n, k, top, null pointer, alignment */
     FZ_EOVERFLOW = -2,  /* a count or a byte size does not fit in 64 bits */
-    FZ_ENOSPC = -3,     /* output capacity smaller than needed (*written/*rows_needed still set) */
+    FZ_ENOSPC = -3,     /* output capacity smaller than needed (*written and *rows_needed still set) */
     FZ_ENOMEM = -4,     /* device or host allocation failed */
     FZ_EAGAIN = -5,     /* serving: request deferred, queue full */
     FZ_ETIMEOUT = -6,   /* a bounded device-side wait gave up */
