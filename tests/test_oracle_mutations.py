@@ -5,7 +5,6 @@ the kinds a reader could miss (a dropped term, a wrong index, an off-by-one
 bound, a reversed order, a transposed operand).  The checks of
 ``test_oracle_pins.py`` are run on each and must fail.  All of it is CPU-only.
 """
-import numpy as np
 import pytest
 
 import oracle
