@@ -937,7 +937,7 @@ int launch_memo_build(const int32_t *tail, int k, int32_t top, uint64_t rows,
     void *args[] = {&fp};
     FZ_CUDA_TRY(cudaLaunchCooperativeKernel((const void *)memo_fill_kernel, dim3(grid),
                                             dim3(GRID_THREADS), args, 0, s));
-                                            note_launch();
+    note_launch();
     return FZ_OK;
 }
 
