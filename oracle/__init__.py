@@ -73,6 +73,11 @@ def _load():
             ctypes.POINTER(ctypes.c_int32), ctypes.c_int, ctypes.c_int64,
             ctypes.POINTER(ctypes.c_int64), ctypes.c_int, ctypes.c_int,
             ctypes.POINTER(ctypes.c_uint64), ctypes.POINTER(ctypes.c_uint64)]
+        lib.fzo_digest_subtrees.restype = ctypes.c_int
+        lib.fzo_digest_subtrees.argtypes = [
+            ctypes.POINTER(ctypes.c_int32), ctypes.c_int, ctypes.c_int64,
+            ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_uint64), ctypes.c_int,
+            ctypes.c_int, ctypes.POINTER(ctypes.c_uint64), ctypes.POINTER(ctypes.c_uint64)]
         lib.fzo_lex_lists.restype = ctypes.c_int64
         lib.fzo_lex_lists.argtypes = [
             ctypes.POINTER(ctypes.c_int32), ctypes.c_int, ctypes.c_int64,
@@ -156,6 +161,42 @@ def sample_a1(g: Sequence[int], n: int, a1_values: Sequence[int],
     if used < 0:
         raise ValueError("oracle rejected its arguments")
     return int(rows.value), int(cs.value), int(used)
+
+
+def digest_parallel(g: Sequence[int], n: int, threads: int = 1) -> Tuple[int, int]:
+    """(rows, digest) of the whole of Z(n, g): the digest of ``digest`` (same
+    value), computed by walking the subtree of each first coordinate a_1 on
+    one of ``threads`` POSIX threads, each from its global rank.  The list is
+    descending in a_1 and the subtree of a_1 = v holds |Z(n - v g_1, (g_2..g_d))|
+    rows, so the subtree of v starts after those of every larger value."""
+    gg = _gens(g)
+    if gg.size == 1 or n < 0:
+        return digest(g, n)
+    T = count_table(gg[1:], n, exact=True)[0]
+    g1 = int(gg[0])
+    vals = list(range(n // g1, -1, -1))
+    sizes = [int(T[n - v * g1]) for v in vals]
+    first, acc = [], 0
+    for c in sizes:
+        first.append(acc)
+        acc += c
+    if acc >= 1 << 64:
+        raise ValueError("more than 2^64 rows")
+    # largest subtrees first, so the threads finish together
+    order = sorted(range(len(vals)), key=lambda j: -sizes[j])
+    v_arr = np.ascontiguousarray(np.array([vals[j] for j in order], dtype=np.int64))
+    f_arr = np.ascontiguousarray(np.array([first[j] for j in order], dtype=np.uint64))
+    lib = _load()
+    rows = ctypes.c_uint64(0)
+    cs = ctypes.c_uint64(0)
+    used = lib.fzo_digest_subtrees(gg.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)), gg.size,
+                                   n, v_arr.ctypes.data_as(ctypes.POINTER(ctypes.c_int64)),
+                                   f_arr.ctypes.data_as(ctypes.POINTER(ctypes.c_uint64)),
+                                   int(v_arr.size), int(threads), ctypes.byref(rows),
+                                   ctypes.byref(cs))
+    if used < 0:
+        raise ValueError("oracle rejected its arguments")
+    return int(rows.value), int(cs.value)
 
 
 # ---------------------------------------------------------------------------

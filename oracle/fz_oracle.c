@@ -136,6 +136,7 @@ typedef struct {
     int d;
     int64_t n;
     const int64_t *a1;
+    const uint64_t *first;  /* rank of each subtree's first row, or NULL (0) */
     int na1;
     int next;
     pthread_mutex_t mu;
@@ -161,6 +162,7 @@ static void *fzo_worker(void *arg)
         s.d = p->d;
         s.begin = 0;
         s.end = UINT64_MAX;
+        s.rank = p->first ? p->first[j] : 0;
         s.a[0] = v;
         if (p->d == 1) {
             if (rem == 0) fzo_emit(&s);
@@ -177,8 +179,9 @@ static void *fzo_worker(void *arg)
     return NULL;
 }
 
-int fzo_sample(const int32_t *g, int d, int64_t n, const int64_t *a1_values,
-               int na1, int nthreads, uint64_t *rows, uint64_t *checksum)
+static int fzo_pool_run(const int32_t *g, int d, int64_t n, const int64_t *a1_values,
+                        const uint64_t *first, int na1, int nthreads, uint64_t *rows,
+                        uint64_t *checksum)
 {
     if (fzo_check(g, d, n) || na1 < 0 || (na1 && !a1_values)) return -1;
     if (nthreads < 1) nthreads = 1;
@@ -189,6 +192,7 @@ int fzo_sample(const int32_t *g, int d, int64_t n, const int64_t *a1_values,
     p.d = d;
     p.n = n;
     p.a1 = a1_values;
+    p.first = first;
     p.na1 = na1;
     pthread_mutex_init(&p.mu, NULL);
     pthread_t *th = (pthread_t *)calloc((size_t)nthreads, sizeof(pthread_t));
@@ -205,6 +209,27 @@ int fzo_sample(const int32_t *g, int d, int64_t n, const int64_t *a1_values,
     if (rows) *rows = p.rows;
     if (checksum) *checksum = p.checksum;
     return started == 0 ? 1 : started;
+}
+
+int fzo_sample(const int32_t *g, int d, int64_t n, const int64_t *a1_values,
+               int na1, int nthreads, uint64_t *rows, uint64_t *checksum)
+{
+    return fzo_pool_run(g, d, n, a1_values, NULL, na1, nthreads, rows, checksum);
+}
+
+/*
+ * The order-sensitive digest of fzo_enumerate over whole subtrees walked in
+ * parallel: subtree j (a_1 = a1_values[j]) starts at global rank first[j],
+ * which the caller takes from the sizes of the subtrees of the larger a_1
+ * values (the list is descending, Lemma "disjlex").  The digest is a sum over
+ * rows, so the subtrees may run in any order.  Returns as fzo_sample.
+ */
+int fzo_digest_subtrees(const int32_t *g, int d, int64_t n, const int64_t *a1_values,
+                        const uint64_t *first, int na1, int nthreads, uint64_t *rows,
+                        uint64_t *checksum)
+{
+    if (!first && na1) return -1;
+    return fzo_pool_run(g, d, n, a1_values, first, na1, nthreads, rows, checksum);
 }
 
 /*

@@ -60,3 +60,30 @@ def check_csr_segments(offsets: torch.Tensor, rows: torch.Tensor, g, counts,
         lead = diff.gather(1, first).squeeze(1)
         ok = (~same) | (nz.any(dim=1) & (lead > 0))
         assert bool(ok.all()), "memo segment not strictly descending"
+
+
+_M64 = (1 << 64) - 1
+_K0 = 0x9E3779B97F4A7C15 - (1 << 64)  # the oracle's row-digest constants, as int64
+_K1 = 0x632BE59BD9B4E019
+_LSR2 = (1 << 62) - 1
+
+
+def rows_digest(rows: torch.Tensor, rank0: int = 0, chunk: int = 1 << 22) -> int:
+    """The oracle's order-sensitive digest (oracle.digest) of int32 rows of
+    any device, row r having rank rank0 + r: the sum mod 2^64 over rows of
+    h = rank * K0, then for each coordinate a, h ^= a + K1 + (h << 6) + (h >> 2)
+    (unsigned 64-bit; here int64 with wrap-around, << as a product and the
+    logical >> as an arithmetic one masked)."""
+    N, d = rows.shape
+    total = 0
+    start = 0
+    while start < N:
+        stop = min(N, start + chunk)
+        x = rows[start:stop].to(torch.int64)
+        h = torch.arange(rank0 + start, rank0 + stop, dtype=torch.int64, device=rows.device)
+        h = h * _K0
+        for i in range(d):
+            h = h ^ (x[:, i] + _K1 + h * 64 + ((h >> 2) & _LSR2))
+        total = (total + int(h.sum().item())) & _M64
+        start = stop
+    return total

@@ -4,13 +4,16 @@ Exact integer work: the comparison is bit-exact, tuple for tuple and in
 order, with no tolerance.  Small and medium cases are compared element by
 element; the full-size workloads are checked by properties that prove
 equality (sorted, valid, right count; see gpu_checks.py) plus sampled ranks
-the oracle computes one by one.
+the oracle computes one by one, and config 2 also by an order-sensitive
+digest of every row against the oracle's (its walk split over host cores).
 """
+import os
+
 import numpy as np
 import pytest
 
 import oracle
-from gpu_checks import check_csr_segments, check_sorted_solutions
+from gpu_checks import check_csr_segments, check_sorted_solutions, rows_digest
 from paper_2407_20474_gb300 import workloads
 
 torch = pytest.importorskip("torch")
@@ -439,6 +442,11 @@ def test_config2_full_size(fz):
         # the oracle's own walk over the first ranks
         head = oracle.enumerate_desc(g, n, 0, 50000)
         assert np.array_equal(rows[:50000].cpu().numpy(), head)
+        # every row: the order-sensitive digest of the whole output against
+        # the oracle's, its first-coordinate subtrees walked on all host cores
+        rows_o, dig = oracle.digest_parallel(g, n, threads=os.cpu_count() or 1)
+        assert rows_o == total
+        assert rows_digest(rows) == dig
         # the launch configuration bench.py times: the enumeration capped at
         # 3 or 2 CTAs per SM (larger rings) while another plan of the same
         # element rebuilds on a second stream; the bytes must not change
