@@ -489,3 +489,37 @@ def test_config3_full_memo_build(fz):
         ref = oracle.enumerate_desc(g, m)
         got = rows[int(o[m]):int(o[m + 1])].cpu().numpy()
         assert np.array_equal(got, ref), m
+
+
+def test_table1_instances_every_row(fz):
+    """The paper's own workload (Table 1: g = the first d of (13, 37, 38,
+    40..45), each n at the memo depth the paper used): every row of every
+    instance against the oracle by the order-sensitive digest, the count
+    against the printed one where it is a pin."""
+    path = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden",
+                        "table1_counts.txt")
+    cases = []
+    for line in open(path):
+        if line.startswith("#") or not line.strip():
+            continue
+        f = line.split()
+        cases.append((int(f[0]), int(f[1]), int(f[2]), int(f[3]), len(f) == 4))
+    assert len(cases) == 31
+    threads = os.cpu_count() or 1
+    oracle_digest = {}
+    for d, k, n, printed, pin in cases:
+        g = workloads.TABLE1_GENERATORS[:d]
+        c = fz.fz_count(g, n)
+        if pin:
+            assert c == printed, (d, n)
+        out = torch.empty((c + 16) * d, dtype=torch.int32, device="cuda")
+        out[c * d:].fill_(CANARY)
+        assert fz.fz_enumerate(g, n, out, k=k) == c
+        torch.cuda.synchronize()
+        assert bool((out[c * d:] == CANARY).all())
+        if (d, n) not in oracle_digest:
+            oracle_digest[(d, n)] = oracle.digest_parallel(g, n, threads=threads)
+        rows_o, dig = oracle_digest[(d, n)]
+        assert rows_o == c, (d, n)
+        assert rows_digest(out[:c * d].view(c, d)) == dig, (d, k, n)
+        del out
