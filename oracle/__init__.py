@@ -172,7 +172,7 @@ def digest_parallel(g: Sequence[int], n: int, threads: int = 1) -> Tuple[int, in
     gg = _gens(g)
     if gg.size == 1 or n < 0:
         return digest(g, n)
-    T = count_table(gg[1:], n, exact=True)[0]
+    T = count_table(gg[1:], n)[0]  # uint64 (exact: wrap-around is detected)
     g1 = int(gg[0])
     vals = list(range(n // g1, -1, -1))
     sizes = [int(T[n - v * g1]) for v in vals]
