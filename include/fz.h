@@ -56,7 +56,8 @@ typedef enum fz_status {
     FZ_ETIMEOUT = -6,   /* a bounded device-side wait gave up */
     FZ_ECUDA = -7,      /* other CUDA failure; see fz_last_error_string() */
     FZ_ENOTFOUND = -8,  /* unknown ticket or handle */
-    FZ_EINTERNAL = -9   /* a device-side consistency check failed */
+    FZ_EINTERNAL = -9,  /* a device-side consistency check failed */
+    FZ_ECANCELED = -10  /* serving: the request was cancelled before it ran */
 } fz_status;
 
 /* Implementation options.  Every field accepts FZ_AUTO (or 0 for slice_rows). */
@@ -136,9 +137,12 @@ int fz_count_upto(const int32_t *g, int d, int32_t n_max, uint64_t *counts,
  * GPU that loads the library until the process exits), so n_max is limited
  * to FZ_NOALLOC_MAX_N; larger n_max gives FZ_EINVAL.  The first call made
  * with a given device current looks up that array's device address
- * (cudaGetSymbolAddress); make that first call before any stream capture.
- * Every call shares the array: calls that overlap on the GPU (other streams
- * or host threads) race on it.  Asynchronous; calls no allocating routine.
+ * (cudaGetSymbolAddress), and so does the first call after that device's
+ * context was reset (cudaDeviceReset); make such a first call before any
+ * stream capture.  counts_dev must hold n_max + 1 uint64 (the call cannot
+ * check a raw pointer's size).  Every call shares the array: calls that
+ * overlap on the GPU (other streams or host threads) race on it.
+ * Asynchronous; calls no allocating routine.
  * Errors: FZ_EINVAL, FZ_ECUDA. */
 #define FZ_NOALLOC_MAX_N 262143
 int fz_count_upto_noalloc(const int32_t *g, int d, int32_t n_max,
@@ -347,6 +351,17 @@ int fz_batch_enumerate(fz_batch_t batch, int32_t *out_dev,
 int fz_batch_sync(fz_batch_t batch, void *stream);
 int fz_batch_destroy(fz_batch_t batch);
 
+/* The exact layout of a batch before any output exists: word_offsets (host,
+ * count + 1) and rows (host, count; may be NULL) receive what
+ * fz_enumerate_batch will use for the same instances and options, and
+ * *words_needed (may be NULL) the total.  Costs one fz_batch_create (the
+ * counts come from the batch's own tables); callers that go on to enumerate
+ * should keep a batch instead (fz_batch_create + fz_batch_layout).
+ * Synchronises.  Errors: as fz_batch_create. */
+int fz_plan_batch(const fz_instance_t *inst, int count, const fz_opts_t *opt,
+                  uint64_t *word_offsets, uint64_t *rows, uint64_t *words_needed,
+                  void *stream);
+
 /* One-shot: create + enumerate + sync + destroy.  word_offsets (host,
  * count + 1, may be NULL) and *words_needed receive the layout.  Errors: as
  * above; FZ_ENOSPC when out_capacity_words is too small (nothing written). */
@@ -368,6 +383,9 @@ int fz_enumerate_batch(const fz_instance_t *inst, int count, const fz_opts_t *op
  * free up, and their work overlaps on the GPU (continuous batching).  A
  * result stays valid until fz_serve_release.  Times are seconds on the host
  * steady clock; t_done is stamped when the request's stream reaches it.
+ * Each request in flight has its own device status word, read back with
+ * the request: a device-side check that fails marks that request's status
+ * FZ_EINTERNAL (or FZ_ETIMEOUT), not the server or other requests.
  * The paper serves no requests; this is the deployment layer around the
  * enumeration of Section 3.1.
  * ---------------------------------------------------------------------- */
@@ -387,7 +405,8 @@ typedef struct fz_server_s *fz_server_t;
 #define FZ_SERVE_RUNNING 2
 
 typedef struct fz_result {
-    int32_t status;          /* FZ_SERVE_DONE / QUEUED / RUNNING, or a negative fz_status */
+    int32_t status;          /* FZ_SERVE_DONE / QUEUED / RUNNING, or a negative fz_status
+                                (FZ_ECANCELED, FZ_EINTERNAL, FZ_ETIMEOUT, ...) */
     int32_t d;
     uint64_t count;          /* rows */
     const int32_t *rows_dev; /* count * d int32 (when done), owned by the server */
@@ -410,21 +429,39 @@ int fz_serve_register(fz_server_t srv, const int32_t *g, int d, int32_t n_max,
 /* Queue Z(n, set).  Errors: FZ_ENOTFOUND (set), FZ_EINVAL (n > n_max),
  * FZ_EAGAIN (queue full), FZ_ENOMEM (larger than the whole budget). */
 int fz_serve_submit(fz_server_t srv, int32_t set_id, int32_t n, uint64_t *ticket);
+/* Queue Z(n, g) by its generators (host, d entries, in the caller's order):
+ * the request goes to a registered set with the same generators in the same
+ * order and n_max >= n; when there is none, the set is first registered
+ * (synchronously, with n_max = n) and later queries reuse it.  This is the
+ * submit-by-instance form; fz_serve_submit with a set id skips the lookup.
+ * Errors: those of fz_serve_register and fz_serve_submit. */
+int fz_serve_submit_gens(fz_server_t srv, const int32_t *g, int d, int32_t n,
+                         uint64_t *ticket);
 /* Current state of a request (non-blocking). */
 int fz_serve_poll(fz_server_t srv, uint64_t ticket, fz_result_t *result);
-/* Block until the request is done (timeout_ms < 0: no limit; FZ_EAGAIN on
- * timeout). */
+/* Block until the request is done, failed or cancelled (timeout_ms < 0: no
+ * limit; FZ_EAGAIN on timeout; FZ_ENOTFOUND if another thread releases the
+ * ticket meanwhile). */
 int fz_serve_wait(fz_server_t srv, uint64_t ticket, int32_t timeout_ms,
                   fz_result_t *result);
 /* Copy a finished request's rows into dst (host or device memory, at least
  * count * d int32 words).  Synchronises `stream`.  Errors: FZ_ENOTFOUND,
- * FZ_EAGAIN (not done), FZ_ENOSPC (capacity_words too small), FZ_ECUDA. */
+ * FZ_EAGAIN (not done), FZ_ENOSPC (capacity_words too small), the request's
+ * own negative status if it failed or was cancelled, FZ_ECUDA. */
 int fz_serve_copy(fz_server_t srv, uint64_t ticket, int32_t *dst, uint64_t capacity_words,
                   void *stream);
-/* Free a finished request's output (FZ_EAGAIN while queued or running). */
+/* Free a finished, failed or cancelled request's output and forget its
+ * ticket (FZ_EAGAIN while queued or running). */
 int fz_serve_release(fz_server_t srv, uint64_t ticket);
+/* Cancel a queued request: it leaves the queue without running, its status
+ * becomes FZ_ECANCELED (release it as usual), and requests queued behind it
+ * may be admitted at once.  A request already on the device is not stopped:
+ * FZ_EAGAIN (wait for it, then release).  A finished request is left as it
+ * is (FZ_OK).  Errors: FZ_ENOTFOUND, FZ_EAGAIN. */
+int fz_serve_cancel(fz_server_t srv, uint64_t ticket);
 int fz_serve_stats(fz_server_t srv, fz_serve_stats_t *stats);
-/* Stop the loop, wait for running requests, free everything. */
+/* Stop the loop, wait for running requests, free everything.  Requests still
+ * queued are dropped. */
 int fz_serve_destroy(fz_server_t srv);
 
 /* ------------------------------------------------------------------------
@@ -437,14 +474,27 @@ int fz_enumerate(const int32_t *g, int d, int32_t n, const fz_opts_t *opt,
                  uint64_t rank_begin, uint64_t rank_end, int32_t *out_dev,
                  uint64_t out_capacity_rows, uint64_t *written, void *stream);
 
-/* As fz_enumerate, but out_host is host memory.  Page-locked (pinned,
- * mapped) memory is written by the enumeration kernel itself over the host
- * link; pageable memory gets the rows in device chunks that are copied back
- * while the next chunks are produced.  Synchronises. */
+/* As fz_enumerate, but out_host is host memory: the asynchronous form of
+ * the device-to-host buffer flushes of the paper's driver (Section 3.2).
+ * Page-locked (pinned, mapped) memory is written by the enumeration kernel
+ * itself over the host link.  Pageable memory is filled in chunks: each
+ * chunk is enumerated into one of three page-locked staging buffers while
+ * host threads copy the previous, finished chunks into out_host, so the
+ * output may be larger than device memory.  The staging buffers (3 chunks)
+ * are kept for later calls; a call that finds them in use by another
+ * thread pins its own.  Synchronises.
+ * Errors: those of fz_enumerate; FZ_ENOMEM (staging buffers). */
 int fz_enumerate_host(const int32_t *g, int d, int32_t n, const fz_opts_t *opt,
                       uint64_t rank_begin, uint64_t rank_end, int32_t *out_host,
                       uint64_t out_capacity_rows, uint64_t *written,
                       void *stream);
+
+/* fz_enumerate_host with the chunk size for pageable output given in rows
+ * (0 = the default, 128 MB of rows; ignored for page-locked output). */
+int fz_enumerate_host_chunks(const int32_t *g, int d, int32_t n, const fz_opts_t *opt,
+                             uint64_t rank_begin, uint64_t rank_end, int32_t *out_host,
+                             uint64_t out_capacity_rows, uint64_t chunk_rows,
+                             uint64_t *written, void *stream);
 
 #ifdef __cplusplus
 }

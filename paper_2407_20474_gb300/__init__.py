@@ -33,6 +33,7 @@ FZ_ETIMEOUT = -6
 FZ_ECUDA = -7
 FZ_ENOTFOUND = -8
 FZ_EINTERNAL = -9
+FZ_ECANCELED = -10
 
 # Every symbol include/fz.h declares (checked by the CPU tests).
 EXPORTS = (
@@ -46,11 +47,13 @@ EXPORTS = (
     "fz_plan_rebuild",
     "fz_plan_enumerate",
     "fz_plan_unrank", "fz_plan_sync", "fz_plan_destroy",
-    "fz_enumerate", "fz_enumerate_host",
+    "fz_enumerate", "fz_enumerate_host", "fz_enumerate_host_chunks",
     "fz_batch_create", "fz_batch_info", "fz_batch_layout", "fz_batch_rebuild",
     "fz_batch_enumerate", "fz_batch_sync", "fz_batch_destroy", "fz_enumerate_batch",
+    "fz_plan_batch",
     "fz_serve_create", "fz_serve_register", "fz_serve_submit", "fz_serve_poll",
     "fz_serve_wait", "fz_serve_copy", "fz_serve_release", "fz_serve_stats", "fz_serve_destroy",
+    "fz_serve_submit_gens", "fz_serve_cancel",
 )
 
 
@@ -155,6 +158,10 @@ _SIGS = {
     "fz_enumerate_host": (ctypes.c_int, [_I32P, ctypes.c_int, ctypes.c_int32,
                                          ctypes.POINTER(fz_opts_t), ctypes.c_uint64,
                                          ctypes.c_uint64, _P, ctypes.c_uint64, _U64P, _P]),
+    "fz_enumerate_host_chunks": (ctypes.c_int, [_I32P, ctypes.c_int, ctypes.c_int32,
+                                                ctypes.POINTER(fz_opts_t), ctypes.c_uint64,
+                                                ctypes.c_uint64, _P, ctypes.c_uint64,
+                                                ctypes.c_uint64, _U64P, _P]),
     "fz_batch_create": (ctypes.c_int, [ctypes.POINTER(fz_instance_t), ctypes.c_int,
                                        ctypes.POINTER(fz_opts_t), ctypes.POINTER(_P), _P]),
     "fz_batch_info": (ctypes.c_int, [_P, ctypes.POINTER(fz_batch_info_t)]),
@@ -163,12 +170,16 @@ _SIGS = {
     "fz_batch_enumerate": (ctypes.c_int, [_P, _P, ctypes.c_uint64, _P]),
     "fz_batch_sync": (ctypes.c_int, [_P, _P]),
     "fz_batch_destroy": (ctypes.c_int, [_P]),
+    "fz_plan_batch": (ctypes.c_int, [ctypes.POINTER(fz_instance_t), ctypes.c_int,
+                                     ctypes.POINTER(fz_opts_t), _U64P, _U64P, _U64P, _P]),
     "fz_enumerate_batch": (ctypes.c_int, [ctypes.POINTER(fz_instance_t), ctypes.c_int,
                                           ctypes.POINTER(fz_opts_t), _U64P, _P,
                                           ctypes.c_uint64, _U64P, _P]),
     "fz_serve_create": (ctypes.c_int, [ctypes.POINTER(fz_serve_cfg_t), ctypes.POINTER(_P)]),
     "fz_serve_register": (ctypes.c_int, [_P, _I32P, ctypes.c_int, ctypes.c_int32, _I32P]),
     "fz_serve_submit": (ctypes.c_int, [_P, ctypes.c_int32, ctypes.c_int32, _U64P]),
+    "fz_serve_submit_gens": (ctypes.c_int, [_P, _I32P, ctypes.c_int, ctypes.c_int32, _U64P]),
+    "fz_serve_cancel": (ctypes.c_int, [_P, ctypes.c_uint64]),
     "fz_serve_poll": (ctypes.c_int, [_P, ctypes.c_uint64, ctypes.POINTER(fz_result_t)]),
     "fz_serve_wait": (ctypes.c_int, [_P, ctypes.c_uint64, ctypes.c_int32,
                                      ctypes.POINTER(fz_result_t)]),
@@ -200,7 +211,8 @@ def lib():
 _STATUS_NAMES = {FZ_OK: "FZ_OK", FZ_EINVAL: "FZ_EINVAL", FZ_EOVERFLOW: "FZ_EOVERFLOW",
                  FZ_ENOSPC: "FZ_ENOSPC", FZ_ENOMEM: "FZ_ENOMEM", FZ_EAGAIN: "FZ_EAGAIN",
                  FZ_ETIMEOUT: "FZ_ETIMEOUT", FZ_ECUDA: "FZ_ECUDA",
-                 FZ_ENOTFOUND: "FZ_ENOTFOUND", FZ_EINTERNAL: "FZ_EINTERNAL"}
+                 FZ_ENOTFOUND: "FZ_ENOTFOUND", FZ_EINTERNAL: "FZ_EINTERNAL",
+                 FZ_ECANCELED: "FZ_ECANCELED"}
 
 
 def status_string(status: int) -> str:
@@ -241,6 +253,27 @@ def _ptr(x) -> Optional[int]:
     if hasattr(x, "data_ptr"):
         return x.data_ptr()
     return int(x)
+
+
+def _devbuf(x, itemsize: int, need: int, what: str) -> Optional[int]:
+    """Device address of ``x`` after checking, for a torch tensor, that it is
+    a contiguous CUDA tensor of ``itemsize``-byte elements holding at least
+    ``need`` of them (the C side writes ``need`` elements through the raw
+    pointer and cannot check).  Raw integer addresses are passed through:
+    their size is the caller's responsibility."""
+    if x is None or not hasattr(x, "data_ptr"):
+        return _ptr(x)
+    if need > 0:
+        if not getattr(x, "is_cuda", False):
+            raise FzError(FZ_EINVAL, "%s: expected a CUDA tensor" % what)
+        if x.element_size() != itemsize:
+            raise FzError(FZ_EINVAL, "%s: expected %d-byte elements, got %d"
+                          % (what, itemsize, x.element_size()))
+        if not x.is_contiguous():
+            raise FzError(FZ_EINVAL, "%s: tensor must be contiguous" % what)
+        if x.numel() < need:
+            raise FzError(FZ_EINVAL, "%s: %d elements, %d needed" % (what, x.numel(), need))
+    return x.data_ptr()
 
 
 def _opts(k=FZ_AUTO, top=FZ_AUTO, slice_rows=0):
@@ -298,13 +331,15 @@ def fz_count_upto_noalloc(g: Sequence[int], n_max: int, counts, stream=None) -> 
     a fixed array inside the library shared by all calls, so n_max is at most
     FZ_NOALLOC_MAX_N and overlapping calls race.  Asynchronous."""
     ga, d = _gens(g)
-    _check(lib().fz_count_upto_noalloc(ga, d, int(n_max), _ptr(counts), _stream(stream)))
+    ptr = _devbuf(counts, 8, int(n_max) + 1, "counts")
+    _check(lib().fz_count_upto_noalloc(ga, d, int(n_max), ptr, _stream(stream)))
 
 
 def fz_count_table(g: Sequence[int], n: int, table, stream=None) -> None:
     """Fill a device uint64 buffer of (d+1)*(n+1) entries with the count table."""
     ga, d = _gens(g)
-    _check(lib().fz_count_table(ga, d, int(n), _ptr(table), _stream(stream)))
+    ptr = _devbuf(table, 8, (d + 1) * (int(n) + 1), "table")
+    _check(lib().fz_count_table(ga, d, int(n), ptr, _stream(stream)))
 
 
 # -------------------------------------------------------------------- memo
@@ -321,7 +356,9 @@ def fz_build_memo_into(tail: Sequence[int], top: int, offsets, rows, rows_capaci
     (offsets: top+1 uint64; rows: rows_capacity*k int32).  Returns the rows."""
     ga, k = _gens(tail)
     need = ctypes.c_uint64(0)
-    _check(lib().fz_build_memo_into(ga, k, int(top), _ptr(offsets), _ptr(rows),
+    po = _devbuf(offsets, 8, int(top) + 1, "offsets")
+    pr = _devbuf(rows, 4, int(rows_capacity) * k, "rows")
+    _check(lib().fz_build_memo_into(ga, k, int(top), po, pr,
                                     int(rows_capacity), ctypes.byref(need), _stream(stream)))
     return int(need.value)
 
@@ -334,8 +371,10 @@ def fz_build_memo_schedule(tail: Sequence[int], top: int, schedule: int, offsets
     """fz_build_memo_into with an explicit launch schedule (FZ_MEMO_*)."""
     ga, k = _gens(tail)
     need = ctypes.c_uint64(0)
-    _check(lib().fz_build_memo_schedule(ga, k, int(top), int(schedule), _ptr(offsets),
-                                        _ptr(rows), int(rows_capacity), ctypes.byref(need),
+    po = _devbuf(offsets, 8, int(top) + 1, "offsets")
+    pr = _devbuf(rows, 4, int(rows_capacity) * k, "rows")
+    _check(lib().fz_build_memo_schedule(ga, k, int(top), int(schedule), po,
+                                        pr, int(rows_capacity), ctypes.byref(need),
                                         _stream(stream)))
     return int(need.value)
 
@@ -417,6 +456,8 @@ class Plan:
         if capacity_rows is None:
             capacity_rows = (out.numel() // self.d) if hasattr(out, "numel") else 0
         w = ctypes.c_uint64(0)
+        if hasattr(out, "element_size") and out.element_size() != 4:
+            raise FzError(FZ_EINVAL, "out: expected int32 elements")
         _check(lib().fz_plan_enumerate(self._h, int(rank_begin), end, _ptr(out),
                                        int(capacity_rows), ctypes.byref(w), _stream(stream)))
         return int(w.value)
@@ -424,7 +465,9 @@ class Plan:
     def unrank(self, ranks, out, stream=None):
         """Asynchronously write the tuples of device uint64 ``ranks`` into ``out``."""
         m = ranks.numel() if hasattr(ranks, "numel") else len(ranks)
-        _check(lib().fz_plan_unrank(self._h, _ptr(ranks), int(m), _ptr(out), _stream(stream)))
+        pr = _devbuf(ranks, 8, int(m), "ranks")
+        po = _devbuf(out, 4, int(m) * self.d, "out")
+        _check(lib().fz_plan_unrank(self._h, pr, int(m), po, _stream(stream)))
 
     def sync(self, stream=None):
         _check(lib().fz_plan_sync(self._h, _stream(stream)))
@@ -463,6 +506,8 @@ def fz_enumerate(g: Sequence[int], n: int, out, rank_begin: int = 0,
     if capacity_rows is None:
         capacity_rows = (out.numel() // d) if hasattr(out, "numel") else 0
     w = ctypes.c_uint64(0)
+    if hasattr(out, "element_size") and out.element_size() != 4:
+        raise FzError(FZ_EINVAL, "out: expected int32 elements")
     _check(lib().fz_enumerate(ga, d, int(n), ctypes.byref(o), int(rank_begin), end,
                               _ptr(out), int(capacity_rows), ctypes.byref(w),
                               _stream(stream)))
@@ -471,9 +516,10 @@ def fz_enumerate(g: Sequence[int], n: int, out, rank_begin: int = 0,
 
 def fz_enumerate_host(g: Sequence[int], n: int, out, rank_begin: int = 0,
                       rank_end: Optional[int] = None, k: int = FZ_AUTO, top: int = FZ_AUTO,
-                      slice_rows: int = 0, stream=None) -> int:
+                      slice_rows: int = 0, chunk_rows: int = 0, stream=None) -> int:
     """As fz_enumerate into host memory ``out`` (numpy int32 array or pinned
-    torch CPU tensor, at least rows*d entries)."""
+    torch CPU tensor, at least rows*d entries).  Pageable output is streamed
+    in chunks of ``chunk_rows`` rows (0 = the library's default)."""
     ga, d = _gens(g)
     o = _opts(k, top, slice_rows)
     end = (1 << 64) - 1 if rank_end is None else int(rank_end)
@@ -482,9 +528,12 @@ def fz_enumerate_host(g: Sequence[int], n: int, out, rank_begin: int = 0,
         ptr, cap = out.ctypes.data, out.size // d
     else:
         ptr, cap = out.data_ptr(), out.numel() // d
+    if hasattr(out, "element_size") and out.element_size() != 4:
+        raise FzError(FZ_EINVAL, "out: expected int32 elements")
     w = ctypes.c_uint64(0)
-    _check(lib().fz_enumerate_host(ga, d, int(n), ctypes.byref(o), int(rank_begin), end,
-                                   ptr, int(cap), ctypes.byref(w), _stream(stream)))
+    _check(lib().fz_enumerate_host_chunks(ga, d, int(n), ctypes.byref(o), int(rank_begin), end,
+                                          ptr, int(cap), int(chunk_rows), ctypes.byref(w),
+                                          _stream(stream)))
     return int(w.value)
 
 
@@ -560,6 +609,20 @@ class Batch:
         self.close()
 
 
+def fz_plan_batch(instances, k: int = FZ_AUTO, top: int = FZ_AUTO, stream=None):
+    """Exact layout of a batch before enumerating it: (word offsets, count + 1;
+    rows per instance), the offsets fz_enumerate_batch will use."""
+    arr, keep = _instances(instances)
+    o = _opts(k, top, 0)
+    offs = np.zeros(len(instances) + 1, dtype=np.uint64)
+    rows = np.zeros(max(len(instances), 1), dtype=np.uint64)
+    need = ctypes.c_uint64(0)
+    _check(lib().fz_plan_batch(arr, len(instances), ctypes.byref(o),
+                               offs.ctypes.data_as(_U64P), rows.ctypes.data_as(_U64P),
+                               ctypes.byref(need), _stream(stream)))
+    return offs, rows[:len(instances)]
+
+
 def fz_enumerate_batch(instances, out, k: int = FZ_AUTO, top: int = FZ_AUTO,
                        capacity_words: Optional[int] = None, stream=None) -> np.ndarray:
     """One-shot batch; returns the word offsets (count + 1)."""
@@ -597,6 +660,17 @@ class Server:
         t = ctypes.c_uint64(0)
         _check(lib().fz_serve_submit(self._h, int(set_id), int(n), ctypes.byref(t)))
         return int(t.value)
+
+    def submit_gens(self, g: Sequence[int], n: int) -> int:
+        """Queue Z(n, g) by its generators (registers the set on first use)."""
+        ga, d = _gens(g)
+        t = ctypes.c_uint64(0)
+        _check(lib().fz_serve_submit_gens(self._h, ga, d, int(n), ctypes.byref(t)))
+        return int(t.value)
+
+    def cancel(self, ticket: int):
+        """Cancel a queued request (FzError FZ_EAGAIN if it is already running)."""
+        _check(lib().fz_serve_cancel(self._h, int(ticket)))
 
     def poll(self, ticket: int) -> fz_result_t:
         r = fz_result_t()

@@ -5,11 +5,14 @@
 
 #include <algorithm>
 #include <atomic>
+#include <condition_variable>
 #include <cstdlib>
 #include <cstring>
+#include <deque>
 #include <map>
 #include <mutex>
 #include <string>
+#include <thread>
 #include <vector>
 
 #include "fz_internal.cuh"
@@ -464,6 +467,193 @@ uint64_t rows_in(const fz_plan_s *p, uint64_t b, uint64_t e) {
     return b < e ? e - b : 0;
 }
 
+// ---------------------------------------------------------------------------
+// Streamed delivery into pageable host memory (the role of the paper's
+// copyDeviceBufferToHostAndClear flushes, Section 3.2, made asynchronous).
+//
+// A kernel cannot write pageable memory, and a copy-engine transfer into
+// pageable memory returns only when it has finished, so the rows are made in
+// chunks: chunk i is written by the enumeration kernel straight into
+// page-locked, mapped staging buffer i mod HOST_STAGES (over the host link,
+// as for pinned output), and host worker threads copy every finished stage
+// into the caller's array while the GPU fills the next ones.  The host
+// enqueues chunk i only once the workers have emptied its stage (chunk
+// i - HOST_STAGES), so the GPU runs at most HOST_STAGES - 1 chunks ahead of
+// the host copies and the output may be far larger than device memory.
+// The staging buffers are kept between calls (one pool per process, grown
+// on demand: pinning memory costs far more than copying one chunk) and are
+// used by one call at a time; a call that finds the pool busy pins its own.
+// ---------------------------------------------------------------------------
+constexpr int HOST_STAGES = 3;
+
+struct StagePool {
+    std::mutex mu;  // held by the call using the pool
+    char *base = nullptr;
+    size_t bytes = 0;
+};
+StagePool g_stage_pool;
+
+int host_copy_threads() {
+    static const int t = [] {
+        const char *e = std::getenv("FZ_HOST_COPY_THREADS");
+        int v = e ? std::atoi(e) : 0;
+        if (v <= 0) {
+            const unsigned hc = std::thread::hardware_concurrency();
+            v = hc >= 4 ? (int)(hc / 2) : 1;
+            if (v > 8) v = 8;
+        }
+        return v > 64 ? 64 : v;
+    }();
+    return t;
+}
+
+// Default chunk: 128 MB of rows.
+uint64_t default_host_chunk_rows(int d) {
+    return std::max<uint64_t>(1u << 14, (128ull << 20) / (4ull * (uint64_t)d));
+}
+
+struct CopyJob {
+    const char *src;
+    char *dst;
+    size_t bytes;
+    int stage;
+    cudaEvent_t ev;
+};
+
+int stream_to_pageable(fz_plan_s *p, uint64_t rank_begin, uint64_t rows, int32_t *out_host,
+                       uint64_t chunk_rows, cudaStream_t s) {
+    const int d = p->d;
+    if (chunk_rows == 0) chunk_rows = default_host_chunk_rows(d);
+    if (chunk_rows > rows) chunk_rows = rows;
+    const size_t stage_bytes = align256(chunk_rows * (size_t)d * 4);
+    const size_t pool_bytes = HOST_STAGES * stage_bytes;
+
+    // staging buffers: the process pool when it is free, else this call's own
+    std::unique_lock<std::mutex> pool_lk(g_stage_pool.mu, std::try_to_lock);
+    char *base = nullptr;
+    bool own = false;
+    if (pool_lk.owns_lock()) {
+        if (g_stage_pool.bytes < pool_bytes) {
+            if (g_stage_pool.base) cudaFreeHost(g_stage_pool.base);
+            g_stage_pool.base = nullptr;
+            g_stage_pool.bytes = 0;
+            void *h = nullptr;
+            if (cudaHostAlloc(&h, pool_bytes, cudaHostAllocMapped | cudaHostAllocPortable) !=
+                cudaSuccess) {
+                cudaGetLastError();
+                return set_error(FZ_ENOMEM, "cudaHostAlloc (staging buffers)");
+            }
+            g_stage_pool.base = static_cast<char *>(h);
+            g_stage_pool.bytes = pool_bytes;
+        }
+        base = g_stage_pool.base;
+    } else {
+        void *h = nullptr;
+        if (cudaHostAlloc(&h, pool_bytes, cudaHostAllocMapped | cudaHostAllocPortable) !=
+            cudaSuccess) {
+            cudaGetLastError();
+            return set_error(FZ_ENOMEM, "cudaHostAlloc (staging buffers)");
+        }
+        base = static_cast<char *>(h);
+        own = true;
+    }
+    void *dbase_v = nullptr;
+    cudaEvent_t ev[HOST_STAGES] = {};
+    int rc = FZ_OK;
+    if (cudaHostGetDevicePointer(&dbase_v, base, 0) != cudaSuccess)
+        rc = set_error(FZ_ECUDA, "cudaHostGetDevicePointer (staging buffers)");
+    for (int j = 0; j < HOST_STAGES && rc == FZ_OK; ++j)
+        if (cudaEventCreateWithFlags(&ev[j], cudaEventDisableTiming | cudaEventBlockingSync) !=
+            cudaSuccess)
+            rc = set_error(FZ_ECUDA, "cudaEventCreate");
+    char *dbase = static_cast<char *>(dbase_v);
+
+    std::mutex mu;
+    std::condition_variable cv_work, cv_free;
+    std::deque<CopyJob> jobs;
+    int pending[HOST_STAGES] = {};
+    bool stop = false;
+    int worker_err = FZ_OK;
+    std::vector<std::thread> workers;
+    auto work = [&] {
+        for (;;) {
+            CopyJob job;
+            {
+                std::unique_lock<std::mutex> lk(mu);
+                cv_work.wait(lk, [&] { return stop || !jobs.empty(); });
+                if (jobs.empty()) return;
+                job = jobs.front();
+                jobs.pop_front();
+            }
+            const bool ok = cudaEventSynchronize(job.ev) == cudaSuccess;
+            if (ok) std::memcpy(job.dst, job.src, job.bytes);
+            {
+                std::lock_guard<std::mutex> lk(mu);
+                if (!ok && worker_err == FZ_OK) worker_err = FZ_ECUDA;
+                if (--pending[job.stage] == 0 || !ok) cv_free.notify_all();
+            }
+        }
+    };
+    const int nthreads = host_copy_threads();
+    if (rc == FZ_OK)
+        for (int t = 0; t < nthreads; ++t) workers.emplace_back(work);
+
+    DeviceProps dp;
+    if (rc == FZ_OK) rc = device_props(&dp);
+    EnumLaunch L = launch_of(p);
+    L.plain_stores = true;
+    uint64_t done = 0;
+    for (uint64_t i = 0; rc == FZ_OK && done < rows; ++i) {
+        const int j = (int)(i % HOST_STAGES);
+        const uint64_t now = std::min(chunk_rows, rows - done);
+        {
+            std::unique_lock<std::mutex> lk(mu);
+            cv_free.wait(lk, [&] { return pending[j] == 0 || worker_err != FZ_OK; });
+            if (worker_err != FZ_OK) {
+                rc = set_error(worker_err, "staging copy: event wait failed");
+                break;
+            }
+        }
+        const uint64_t slice = std::min<uint64_t>(p->slice_rows, default_slice_rows(now, dp.sms));
+        rc = launch_enumerate(L, rank_begin + done, now,
+                              reinterpret_cast<int32_t *>(dbase + (size_t)j * stage_bytes), slice,
+                              s);
+        if (rc != FZ_OK) break;
+        if (cudaEventRecord(ev[j], s) != cudaSuccess) {
+            rc = set_error(FZ_ECUDA, "cudaEventRecord");
+            break;
+        }
+        // one job per worker, each a multiple of 4 KB (the last takes the rest)
+        const size_t bytes = (size_t)now * d * 4;
+        const char *src = base + (size_t)j * stage_bytes;
+        char *dst = reinterpret_cast<char *>(out_host) + (size_t)done * d * 4;
+        size_t part = (bytes + nthreads - 1) / nthreads;
+        part = (part + 4095) & ~size_t(4095);
+        if (part < (1u << 20)) part = 1u << 20;
+        {
+            std::lock_guard<std::mutex> lk(mu);
+            for (size_t off = 0; off < bytes; off += part) {
+                jobs.push_back({src + off, dst + off, std::min(part, bytes - off), j, ev[j]});
+                pending[j]++;
+            }
+        }
+        cv_work.notify_all();
+        done += now;
+    }
+    {
+        std::lock_guard<std::mutex> lk(mu);
+        stop = true;
+    }
+    cv_work.notify_all();
+    for (std::thread &t : workers) t.join();
+    if (rc == FZ_OK && worker_err != FZ_OK)
+        rc = set_error(worker_err, "staging copy: event wait failed");
+    for (int j = 0; j < HOST_STAGES; ++j)
+        if (ev[j]) cudaEventDestroy(ev[j]);
+    if (own) cudaFreeHost(base);
+    return rc;
+}
+
 }  // namespace
 
 int plan_launch_for(fz_plan_t p, int32_t n, EnumLaunch *L) {
@@ -560,6 +750,7 @@ const char *fz_status_string(int status) {
         case FZ_ECUDA: return "FZ_ECUDA";
         case FZ_ENOTFOUND: return "FZ_ENOTFOUND";
         case FZ_EINTERNAL: return "FZ_EINTERNAL";
+        case FZ_ECANCELED: return "FZ_ECANCELED";
         default: return "FZ_UNKNOWN";
     }
 }
@@ -985,6 +1176,14 @@ int fz_enumerate(const int32_t *g, int d, int32_t n, const fz_opts_t *opt, uint6
 int fz_enumerate_host(const int32_t *g, int d, int32_t n, const fz_opts_t *opt,
                       uint64_t rank_begin, uint64_t rank_end, int32_t *out_host,
                       uint64_t out_capacity_rows, uint64_t *written, void *stream) {
+    return fz_enumerate_host_chunks(g, d, n, opt, rank_begin, rank_end, out_host,
+                                    out_capacity_rows, 0, written, stream);
+}
+
+int fz_enumerate_host_chunks(const int32_t *g, int d, int32_t n, const fz_opts_t *opt,
+                             uint64_t rank_begin, uint64_t rank_end, int32_t *out_host,
+                             uint64_t out_capacity_rows, uint64_t chunk_rows,
+                             uint64_t *written, void *stream) {
     fz_plan_t p = nullptr;
     int rc = fz_plan_create(g, d, n, opt, &p, stream);
     if (rc != FZ_OK) return rc;
@@ -1012,54 +1211,9 @@ int fz_enumerate_host(const int32_t *g, int d, int32_t n, const fz_opts_t *opt,
         return rc;
     }
     cudaGetLastError();  // pageable memory: the query above may have set an error
-    // Pageable host memory: device chunks, enumerate chunk i while the
-    // previous ones are copied back on NCOPY copy streams.
-    constexpr int NBUF = 3;
-    const uint64_t chunk = std::min<uint64_t>(rows, std::max<uint64_t>(1ull << 20,
-                                                  (512ull << 20) / (4ull * d)));
-    const size_t cbytes = align256(chunk * (size_t)d * 4);
-    DevBuf bufs;
-    rc = bufs.alloc(NBUF * cbytes);
-    cudaStream_t copy[NBUF] = {};
-    cudaEvent_t made[NBUF] = {}, copied[NBUF] = {};
-    for (int i = 0; i < NBUF && rc == FZ_OK; ++i) {
-        if (cudaStreamCreateWithFlags(&copy[i], cudaStreamNonBlocking) != cudaSuccess ||
-            cudaEventCreateWithFlags(&made[i], cudaEventDisableTiming) != cudaSuccess ||
-            cudaEventCreateWithFlags(&copied[i], cudaEventDisableTiming) != cudaSuccess)
-            rc = set_error(FZ_ECUDA, "stream/event create");
-    }
-    uint64_t done = 0;
-    int i = 0;
-    while (rc == FZ_OK && done < rows) {
-        const int k = i % NBUF;
-        const uint64_t now = std::min(chunk, rows - done);
-        int32_t *dbuf = reinterpret_cast<int32_t *>(bufs.as<char>() + (size_t)k * cbytes);
-        if (i >= NBUF && cudaStreamWaitEvent(s, copied[k], 0) != cudaSuccess) {
-            rc = set_error(FZ_ECUDA, "stream wait");
-            break;
-        }
-        uint64_t w = 0;
-        rc = fz_plan_enumerate(p, rank_begin + done, rank_begin + done + now, dbuf, now, &w, s);
-        if (rc != FZ_OK) break;
-        if (cudaEventRecord(made[k], s) != cudaSuccess ||
-            cudaStreamWaitEvent(copy[k], made[k], 0) != cudaSuccess ||
-            cudaMemcpyAsync(out_host + done * (uint64_t)d, dbuf, now * (size_t)d * 4,
-                            cudaMemcpyDeviceToHost, copy[k]) != cudaSuccess ||
-            cudaEventRecord(copied[k], copy[k]) != cudaSuccess) {
-            rc = set_error(FZ_ECUDA, "chunk copy");
-            break;
-        }
-        done += now;
-        ++i;
-    }
-    for (int j = 0; j < NBUF; ++j)
-        if (copy[j]) cudaStreamSynchronize(copy[j]);
-    if (rc == FZ_OK) rc = fz_plan_sync(p, stream);
-    for (int j = 0; j < NBUF; ++j) {
-        if (made[j]) cudaEventDestroy(made[j]);
-        if (copied[j]) cudaEventDestroy(copied[j]);
-        if (copy[j]) cudaStreamDestroy(copy[j]);
-    }
+    rc = stream_to_pageable(p, rank_begin, rows, out_host, chunk_rows, s);
+    const int rc2 = fz_plan_sync(p, stream);
+    if (rc == FZ_OK) rc = rc2;
     fz_plan_destroy(p);
     return rc;
 }

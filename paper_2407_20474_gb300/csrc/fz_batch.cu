@@ -823,6 +823,18 @@ int fz_batch_destroy(fz_batch_t b) {
     return FZ_OK;
 }
 
+int fz_plan_batch(const fz_instance_t *inst, int count, const fz_opts_t *opt,
+                  uint64_t *word_offsets, uint64_t *rows, uint64_t *words_needed,
+                  void *stream) {
+    fz_batch_t b = nullptr;
+    int rc = fz_batch_create(inst, count, opt, &b, stream);
+    if (rc != FZ_OK) return rc;
+    if (words_needed) *words_needed = b->total_words;
+    fz_batch_layout(b, rows, word_offsets, nullptr, nullptr);
+    fz_batch_destroy(b);
+    return FZ_OK;
+}
+
 int fz_enumerate_batch(const fz_instance_t *inst, int count, const fz_opts_t *opt,
                        uint64_t *word_offsets, int32_t *out_dev, uint64_t out_capacity_words,
                        uint64_t *words_needed, void *stream) {

@@ -10,8 +10,12 @@
 // out of one device allocation) are free, and launches each admitted request
 // on the next of several streams: requests admitted while others run
 // overlap on the GPU.  Completion is recorded by a host callback on the
-// request's stream (cudaLaunchHostFunc), which frees the slot and stamps the
-// completion time; the output stays valid until the client releases it.
+// request's stream (cudaLaunchHostFunc), which frees the slot, stamps the
+// completion time and reads the request's own device status word (copied to
+// page-locked host memory just before the callback), so a device-side check
+// that failed marks that request, and only it, as failed.  The output stays
+// valid until the client releases it.  A queued request can be cancelled;
+// one already on the device runs to completion.
 #include <cuda_runtime.h>
 
 #include <atomic>
@@ -91,6 +95,7 @@ struct SetRec {
     fz_plan_t plan = nullptr;
     int d = 0;
     int32_t n_max = 0;
+    std::vector<int32_t> g;           // generators, in the caller's order
     std::vector<uint64_t> count_row;  // |Z(r)|, r = 0..n_max
     std::vector<uint64_t> runs_row;   // runs under the root, r = 0..n_max (if any)
 };
@@ -108,7 +113,7 @@ struct Req {
     int32_t n = 0;
     uint64_t count = 0, bytes = 0, off = 0;
     int slot = -1;
-    int status = FZ_SERVE_QUEUED;
+    int status = FZ_SERVE_QUEUED;  // or FZ_SERVE_RUNNING / DONE, or a negative fz_status
     bool has_mem = false;
     double t_submit = 0, t_admit = 0, t_done = 0;
     CallbackCtx cb;
@@ -131,8 +136,9 @@ struct fz_server_s {
     int next_stream = 0;
     void *arena_base = nullptr;
     Arena arena;
-    unsigned long long *counters = nullptr;  // one per slot
-    int *status = nullptr;
+    unsigned long long *counters = nullptr;  // work-item counter, one per slot
+    int *slot_status = nullptr;              // device status word, one per slot
+    int *slot_status_host = nullptr;         // page-locked copies, read by on_done
     std::vector<int> free_slots;
     std::vector<SetRec> sets;
     std::deque<Req *> queue;
@@ -151,7 +157,15 @@ void CUDART_CB on_done(void *p) {
     {
         std::lock_guard<std::mutex> lk(s->mu);
         c->req->t_done = now_s();
-        c->req->status = FZ_SERVE_DONE;
+        // the status word of this request's slot, copied back on its stream
+        // before this callback (no CUDA call is allowed in here)
+        const int dev = s->slot_status_host[c->req->slot];
+        if (dev == DEV_OK) {
+            c->req->status = FZ_SERVE_DONE;
+        } else {
+            c->req->status = dev == DEV_TIMEOUT ? FZ_ETIMEOUT : FZ_EINTERNAL;
+            s->launch_error = c->req->status;
+        }
         s->free_slots.push_back(c->req->slot);
         c->req->slot = -1;
         s->completed++;
@@ -167,12 +181,15 @@ int launch_request(fz_server_s *s, Req *r, cudaStream_t st) {
     int rc = fz_plan_info(S.plan, &info);
     if (rc != FZ_OK) return rc;
     int32_t *out = reinterpret_cast<int32_t *>(static_cast<char *>(s->arena_base) + r->off);
+    // the slot is free, so no copy into its host word is pending
+    s->slot_status_host[r->slot] = DEV_OK;
     if (r->count > 0) {
         EnumLaunch L;
         rc = plan_launch_for(S.plan, r->n, &L);
         if (rc != FZ_OK) return rc;
         L.slice_counter = s->counters + r->slot;
-        L.status = s->status;
+        L.status = s->slot_status + r->slot;
+        FZ_CUDA_TRY(cudaMemsetAsync(L.status, 0, sizeof(int), st));
         if (L.RT) {
             L.total_rows = r->count;
             L.total_cost = r->count + L.W * S.runs_row[r->n];
@@ -182,6 +199,8 @@ int launch_request(fz_server_s *s, Req *r, cudaStream_t st) {
         if (rc != FZ_OK) return rc;
         rc = launch_enumerate(L, 0, r->count, out, default_slice_rows(r->count, dp.sms), st);
         if (rc != FZ_OK) return rc;
+        FZ_CUDA_TRY(cudaMemcpyAsync(s->slot_status_host + r->slot, L.status, sizeof(int),
+                                    cudaMemcpyDeviceToHost, st));
     }
     r->cb.srv = s;
     r->cb.req = r;
@@ -247,6 +266,7 @@ int fz_serve_create(const fz_serve_cfg_t *cfg, fz_server_t *srv) {
         for (cudaStream_t st : s->streams) cudaStreamDestroy(st);
         if (s->arena_base) cudaFree(s->arena_base);
         if (s->counters) cudaFree(s->counters);
+        if (s->slot_status_host) cudaFreeHost(s->slot_status_host);
         delete s;
         return rc;
     };
@@ -261,10 +281,16 @@ int fz_serve_create(const fz_serve_cfg_t *cfg, fz_server_t *srv) {
     e = cudaMalloc(&s->arena_base, mem);
     if (e != cudaSuccess) return fail(cuda_error(e, "cudaMalloc (serve arena)"));
     s->arena.init(mem);
-    e = cudaMalloc((void **)&s->counters, 256 + (size_t)cfg->max_in_flight * 8);
+    const size_t cbytes = (size_t)cfg->max_in_flight * (8 + 4);
+    e = cudaMalloc((void **)&s->counters, cbytes);
     if (e != cudaSuccess) return fail(cuda_error(e, "cudaMalloc (serve counters)"));
-    s->status = reinterpret_cast<int *>(s->counters + cfg->max_in_flight);
-    cudaMemset(s->counters, 0, 256 + (size_t)cfg->max_in_flight * 8);
+    s->slot_status = reinterpret_cast<int *>(s->counters + cfg->max_in_flight);
+    e = cudaMemset(s->counters, 0, cbytes);
+    if (e != cudaSuccess) return fail(cuda_error(e, "cudaMemset (serve counters)"));
+    e = cudaHostAlloc((void **)&s->slot_status_host, (size_t)cfg->max_in_flight * 4,
+                      cudaHostAllocDefault);
+    if (e != cudaSuccess) return fail(cuda_error(e, "cudaHostAlloc (serve status)"));
+    for (int i = 0; i < cfg->max_in_flight; ++i) s->slot_status_host[i] = DEV_OK;
     for (int i = 0; i < cfg->streams; ++i) {
         cudaStream_t st;
         e = cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking);
@@ -282,6 +308,7 @@ int fz_serve_register(fz_server_t s, const int32_t *g, int d, int32_t n_max, int
     SetRec rec;
     rec.d = d;
     rec.n_max = n_max;
+    if (g && d > 0 && d <= FZ_MAX_D) rec.g.assign(g, g + d);
     fz_opts_t opt{FZ_AUTO, FZ_AUTO, 0, 0};
     int rc = fz_plan_create(g, d, n_max, &opt, &rec.plan, s->streams[0]);
     if (rc != FZ_OK) return rc;
@@ -329,6 +356,55 @@ int fz_serve_submit(fz_server_t s, int32_t set_id, int32_t n, uint64_t *ticket) 
     return FZ_OK;
 }
 
+int fz_serve_submit_gens(fz_server_t s, const int32_t *g, int d, int32_t n, uint64_t *ticket) {
+    if (!s || !ticket) return set_error(FZ_EINVAL, "null pointer");
+    int rc = validate_gens(g, d);
+    if (rc != FZ_OK) return rc;
+    if (n < 0) return set_error(FZ_EINVAL, "n must be >= 0");
+    int32_t set_id = -1;
+    {
+        // a registered set with the same generators, in the same order
+        // (the order defines the lexicographic order), covering n
+        std::lock_guard<std::mutex> lk(s->mu);
+        for (size_t i = 0; i < s->sets.size() && set_id < 0; ++i) {
+            const SetRec &S = s->sets[i];
+            if (S.d != d || S.n_max < n) continue;
+            bool same = true;
+            for (int j = 0; j < d && same; ++j) same = S.g[j] == g[j];
+            if (same) set_id = (int32_t)i;
+        }
+    }
+    if (set_id < 0) {
+        rc = fz_serve_register(s, g, d, n, &set_id);
+        if (rc != FZ_OK) return rc;
+    }
+    return fz_serve_submit(s, set_id, n, ticket);
+}
+
+int fz_serve_cancel(fz_server_t s, uint64_t ticket) {
+    if (!s) return set_error(FZ_EINVAL, "null pointer");
+    {
+        std::lock_guard<std::mutex> lk(s->mu);
+        auto it = s->reqs.find(ticket);
+        if (it == s->reqs.end()) return set_error(FZ_ENOTFOUND, "unknown ticket");
+        Req *r = it->second;
+        if (r->status == FZ_SERVE_RUNNING)
+            return set_error(FZ_EAGAIN, "request already on the device; wait, then release");
+        if (r->status != FZ_SERVE_QUEUED) return FZ_OK;  // finished or failed: nothing to do
+        for (auto q = s->queue.begin(); q != s->queue.end(); ++q) {
+            if (*q == r) {
+                s->queue.erase(q);
+                break;
+            }
+        }
+        r->status = FZ_ECANCELED;
+        r->t_done = now_s();
+    }
+    s->done_cv.notify_all();
+    s->cv.notify_one();  // the request may have been blocking admission of later ones
+    return FZ_OK;
+}
+
 static void fill_result(fz_server_t s, const Req *r, fz_result_t *out) {
     out->status = r->status;
     out->d = s->sets[r->set].d;
@@ -353,16 +429,31 @@ int fz_serve_poll(fz_server_t s, uint64_t ticket, fz_result_t *res) {
 int fz_serve_wait(fz_server_t s, uint64_t ticket, int32_t timeout_ms, fz_result_t *res) {
     if (!s || !res) return set_error(FZ_EINVAL, "null pointer");
     std::unique_lock<std::mutex> lk(s->mu);
-    auto it = s->reqs.find(ticket);
-    if (it == s->reqs.end()) return set_error(FZ_ENOTFOUND, "unknown ticket");
-    Req *r = it->second;
-    auto pred = [&] { return r->status <= 0; };
-    if (timeout_ms < 0)
-        s->done_cv.wait(lk, pred);
-    else if (!s->done_cv.wait_for(lk, std::chrono::milliseconds(timeout_ms), pred))
-        return set_error(FZ_EAGAIN, "not done yet");
-    fill_result(s, r, res);
-    return FZ_OK;
+    const auto deadline =
+        std::chrono::steady_clock::now() + std::chrono::milliseconds(timeout_ms < 0 ? 0 : timeout_ms);
+    for (;;) {
+        // looked up again after every wakeup: another thread may have
+        // released (and so freed) the request meanwhile
+        auto it = s->reqs.find(ticket);
+        if (it == s->reqs.end()) return set_error(FZ_ENOTFOUND, "unknown or released ticket");
+        if (it->second->status <= 0) {
+            fill_result(s, it->second, res);
+            return FZ_OK;
+        }
+        if (timeout_ms < 0)
+            s->done_cv.wait(lk);
+        else if (s->done_cv.wait_until(lk, deadline) == std::cv_status::timeout &&
+                 std::chrono::steady_clock::now() >= deadline) {
+            auto again = s->reqs.find(ticket);
+            if (again == s->reqs.end())
+                return set_error(FZ_ENOTFOUND, "unknown or released ticket");
+            if (again->second->status <= 0) {
+                fill_result(s, again->second, res);
+                return FZ_OK;
+            }
+            return set_error(FZ_EAGAIN, "not done yet");
+        }
+    }
 }
 
 int fz_serve_copy(fz_server_t s, uint64_t ticket, int32_t *dst, uint64_t capacity_words,
@@ -375,6 +466,7 @@ int fz_serve_copy(fz_server_t s, uint64_t ticket, int32_t *dst, uint64_t capacit
         auto it = s->reqs.find(ticket);
         if (it == s->reqs.end()) return set_error(FZ_ENOTFOUND, "unknown ticket");
         const Req *r = it->second;
+        if (r->status < 0) return set_error(r->status, "request failed or was cancelled");
         if (r->status != FZ_SERVE_DONE) return set_error(FZ_EAGAIN, "request not done");
         words = r->count * (uint64_t)s->sets[r->set].d;
         src = static_cast<char *>(s->arena_base) + r->off;
@@ -429,14 +521,14 @@ int fz_serve_destroy(fz_server_t s) {
         cudaStreamSynchronize(st);
         cudaStreamDestroy(st);
     }
-    int h = 0;
-    cudaMemcpy(&h, s->status, 4, cudaMemcpyDeviceToHost);
     for (auto &kv : s->reqs) delete kv.second;
     for (SetRec &r : s->sets) fz_plan_destroy(r.plan);
     cudaFree(s->arena_base);
     cudaFree(s->counters);
+    cudaFreeHost(s->slot_status_host);
     delete s;
-    return h ? set_error(FZ_EINTERNAL, "device-side check failed while serving") : FZ_OK;
+    // device-side failures were reported on the requests they hit
+    return FZ_OK;
 }
 
 }  // extern "C"

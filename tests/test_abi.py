@@ -83,3 +83,42 @@ def test_missing_or_broken_library_fails_loudly(tmp_path):
     r = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, timeout=120)
     assert r.returncode == 0, r.stdout + r.stderr
     assert r.stdout.count("raised") == 2
+
+
+class _FakeDeviceTensor:
+    """Stands in for a CUDA tensor: the binding's size checks read only these."""
+
+    def __init__(self, numel, itemsize, contiguous=True, cuda=True):
+        self._n, self._s, self._c, self.is_cuda = numel, itemsize, contiguous, cuda
+
+    def data_ptr(self):
+        return 0x1000
+
+    def numel(self):
+        return self._n
+
+    def element_size(self):
+        return self._s
+
+    def is_contiguous(self):
+        return self._c
+
+
+def test_binding_checks_device_buffer_sizes():
+    """Calls that write a caller buffer of implied size through a raw pointer
+    reject, before any library call, a tensor that is too short, has the
+    wrong element size, is not contiguous or is not on the device."""
+    import paper_2407_20474_gb300 as fz
+    bad = [_FakeDeviceTensor(100, 8), _FakeDeviceTensor(101, 4),
+           _FakeDeviceTensor(101, 8, contiguous=False), _FakeDeviceTensor(101, 8, cuda=False)]
+    for t in bad:
+        with pytest.raises(fz.FzError) as e:
+            fz.fz_count_upto_noalloc((3, 5), 100, t)
+        assert e.value.status == fz.FZ_EINVAL
+    with pytest.raises(fz.FzError) as e:
+        fz.fz_count_table((3, 5), 10, _FakeDeviceTensor(3 * 11 - 1, 8))
+    assert e.value.status == fz.FZ_EINVAL
+    with pytest.raises(fz.FzError) as e:
+        fz.fz_build_memo_into((3, 5), 10, _FakeDeviceTensor(11, 8), _FakeDeviceTensor(9, 4), 5)
+    assert e.value.status == fz.FZ_EINVAL
+    assert fz._devbuf(_FakeDeviceTensor(101, 8), 8, 101, "counts") == 0x1000

@@ -55,6 +55,26 @@ def test_batch_matches_oracle(fz):
         assert np.array_equal(got, oracle.enumerate_desc(g, n)), (g, n)
 
 
+def test_plan_batch_layout(fz):
+    """fz_plan_batch gives the exact layout the one-shot batch call then uses:
+    rows are the oracle's counts, each instance starts on a multiple of 32
+    words after the previous one's rows."""
+    inst = small_instances(37, 40)
+    offs, rows = fz.fz_plan_batch(inst)
+    assert [int(r) for r in rows] == [oracle.count(g, n) for g, n in inst]
+    for i, (g, n) in enumerate(inst):
+        a, b = int(offs[i]), int(offs[i + 1])
+        assert a % 32 == 0 and b - a >= int(rows[i]) * len(g) and b - a < int(rows[i]) * len(g) + 32
+    out = torch.full((int(offs[-1]) + 16,), CANARY, dtype=torch.int32, device="cuda")
+    offs2 = fz.fz_enumerate_batch(inst, out)
+    assert np.array_equal(offs, offs2)
+    host = out.cpu().numpy()
+    for i, (g, n) in enumerate(inst):
+        a, r = int(offs[i]), int(rows[i])
+        assert np.array_equal(host[a:a + r * len(g)].reshape(r, len(g)),
+                              oracle.enumerate_desc(g, n)), (g, n)
+
+
 def test_batch_pair_memo_leaves(fz):
     """Instances whose memo is the closed form of the last two generators
     (no full memo of depth >= 3 fits): last pair coprime, with a common

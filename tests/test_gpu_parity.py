@@ -342,6 +342,53 @@ def test_enumerate_host_pinned_direct(fz):
     assert np.array_equal(out.numpy()[4:4 + w2 * 4].reshape(w2, 4), ref[7:1000])
 
 
+@pytest.mark.parametrize("g,n,chunk,begin,end", [
+    # 3 staging buffers: 7+ chunks wrap the ring twice, the last chunk is short
+    ((5, 8, 11, 14), 700, 997, 0, None),
+    ((5, 8, 11, 14), 700, 613, 1234, 9001),          # window not starting at 0
+    ((3, 7, 8, 10, 13, 20), 260, 4099, 11, None),    # d = 6, odd chunk
+    ((2, 5), 50001, 1, 3, 40),                        # one row per chunk
+])
+def test_enumerate_host_streamed_many_chunks(fz, g, n, chunk, begin, end):
+    """Pageable host output streamed through the page-locked staging ring:
+    many chunks (ring wrap, short last chunk, rank windows), byte for byte
+    against the oracle, nothing written outside the window's rows."""
+    ref = oracle.enumerate_desc(g, n)
+    stop = ref.shape[0] if end is None else min(end, ref.shape[0])
+    want = ref[begin:stop]
+    d = len(g)
+    chunks = -(-want.shape[0] // chunk)
+    assert chunks >= 7 or want.shape[0] < 7 * chunk
+    out = np.full(want.size + 2 * d + 5, CANARY, dtype=np.int32)
+    w = fz.fz_enumerate_host(g, n, out[d:], rank_begin=begin, rank_end=end, chunk_rows=chunk)
+    assert w == want.shape[0]
+    assert (out[:d] == CANARY).all(), "write before the output"
+    assert np.array_equal(out[d:d + want.size].reshape(want.shape), want)
+    assert (out[d + want.size:] == CANARY).all(), "write past the output"
+    # a second call reuses the staging pool and gives the same bytes
+    again = np.full(want.size, CANARY, dtype=np.int32)
+    assert fz.fz_enumerate_host(g, n, again, rank_begin=begin, rank_end=end,
+                                chunk_rows=chunk) == want.shape[0]
+    assert np.array_equal(again.reshape(want.shape), want)
+
+
+def test_enumerate_host_streamed_large(fz):
+    """A streamed output of 1.09 GB (45,216,350 rows) with the default chunk:
+    nine chunks of 128 MB through the three staging buffers, every row checked
+    against the oracle's digest, plus the first rows element by element."""
+    g = (56, 90, 96, 127, 146, 178)
+    n = 24000
+    total = oracle.count(g, n)
+    out = np.empty(total * len(g), dtype=np.int32)
+    w = fz.fz_enumerate_host(g, n, out)
+    assert w == total
+    rows = out.reshape(total, len(g))
+    head = oracle.enumerate_desc(g, n, 0, 20000)
+    assert np.array_equal(rows[:20000], head)
+    dev = torch.from_numpy(rows).cuda()
+    assert rows_digest(dev) == oracle.digest_parallel(g, n, threads=os.cpu_count() or 1)[1]
+
+
 # --------------------------------------------------------------------------
 # memo build (the dynamic FactorizationsUpToElement pass)
 # --------------------------------------------------------------------------

@@ -99,15 +99,92 @@ def test_admission_by_exact_bytes_and_queue_limit(fz):
 
 
 def test_config5_sets_large_requests(fz):
+    """Requests at the upper sizes of the served workload (|Z| about 10^6 and
+    10^7 rows, generator sets of the served workload's draw), several in
+    flight at once: every served result equals the oracle's list, checked by
+    its count and an order-sensitive digest of every row against the
+    oracle's walk, and the 10^6-row results also equal the same query run
+    alone."""
+    import os
+    from gpu_checks import rows_digest
     stream = workloads.config5_stream(3, n_sets=4, rate=2000.0, duration_s=0.05)
+    threads = os.cpu_count() or 1
     with fz.Server(max_in_flight=32, streams=8) as srv:
         for g in stream.sets:
-            counts = fz.fz_count_upto(g, 4096)
-            n = int(np.argmax(counts >= 200_000)) if (counts >= 200_000).any() else 4096
-            sid = srv.register(g, n)
-            ts = [srv.submit(sid, m) for m in (n, n // 2, n - 1, 0)]
-            for m, t in zip((n, n // 2, n - 1, 0), ts):
-                r = srv.wait(t, 60000)
+            n7 = workloads.find_n(oracle.count_upto, g, 10_000_000, n_hint=1024)
+            n6 = workloads.find_n(oracle.count_upto, g, 1_000_000, n_hint=1024)
+            sid = srv.register(g, n7)
+            ns = (n7, n6, n7 - 1, 0)
+            ts = [srv.submit(sid, m) for m in ns]
+            for m, t in zip(ns, ts):
+                r = srv.wait(t, 120000)
                 assert r.status == fz.FZ_SERVE_DONE
-                assert np.array_equal(rows_of(srv, t, r), alone(fz, g, m)), (g, m)
+                assert int(r.count) == oracle.count(g, m)
+                words = int(r.count) * len(g)
+                dev = torch.empty(max(words, 1), dtype=torch.int32, device="cuda")
+                srv.copy(t, dev)
+                rows = dev[:words].view(int(r.count), len(g))
+                assert rows_digest(rows) == oracle.digest_parallel(g, m, threads)[1], (g, m)
+                if m == n6:
+                    assert np.array_equal(rows.cpu().numpy(), alone(fz, g, m)), (g, m)
                 srv.release(t)
+
+
+def test_cancel_queued_request(fz):
+    """A queued request can be cancelled: it never runs, reports FZ_ECANCELED,
+    and the request queued behind it is admitted once memory frees up."""
+    g = (7, 9, 11, 13, 17)
+    n = 300
+    c = fz.fz_count(g, n)
+    budget = ((c * len(g) * 4 + 255) // 256) * 256   # room for exactly one result
+    with fz.Server(memory_bytes=budget, max_in_flight=8, streams=2, max_queue=8) as srv:
+        sid = srv.register(g, n)
+        t1 = srv.submit(sid, n)
+        r1 = srv.wait(t1, 60000)
+        assert r1.status == fz.FZ_SERVE_DONE
+        t2 = srv.submit(sid, n)                    # queued: t1 holds the memory
+        t3 = srv.submit(sid, n)
+        assert srv.poll(t2).status == fz.FZ_SERVE_QUEUED
+        srv.cancel(t2)
+        r2 = srv.poll(t2)
+        assert r2.status == fz.FZ_ECANCELED and r2.t_done >= r2.t_submit
+        with pytest.raises(fz.FzError) as e:
+            srv.copy(t2, torch.empty(c * len(g), dtype=torch.int32))
+        assert e.value.status == fz.FZ_ECANCELED
+        srv.release(t2)                            # a cancelled ticket is released as usual
+        with pytest.raises(fz.FzError) as e:
+            srv.poll(t2)
+        assert e.value.status == fz.FZ_ENOTFOUND
+        ref = rows_of(srv, t1, r1)
+        srv.release(t1)                            # t3 (behind the cancelled t2) runs
+        r3 = srv.wait(t3, 60000)
+        assert r3.status == fz.FZ_SERVE_DONE
+        assert np.array_equal(rows_of(srv, t3, r3), ref)
+        assert np.array_equal(ref, oracle.enumerate_desc(g, n))
+        srv.cancel(t3)                             # finished: left as it is
+        assert srv.poll(t3).status == fz.FZ_SERVE_DONE
+        srv.release(t3)
+        st = srv.stats()
+        assert st.bytes_in_use == 0 and st.queued == 0
+        assert st.completed == 2                   # t1 and t3; t2 never ran
+
+
+def test_submit_by_generators(fz):
+    """fz_serve_submit_gens registers a set on first use and reuses it for
+    queries it covers; results equal the oracle."""
+    with fz.Server(max_in_flight=8, streams=2) as srv:
+        g = (6, 9, 20)
+        t1 = srv.submit_gens(g, 500)
+        t2 = srv.submit_gens(g, 450)                # covered by the first registration
+        assert srv.stats().sets == 1
+        t3 = srv.submit_gens((9, 6, 20), 450)       # another order is another set
+        t4 = srv.submit_gens(g, 800)                # beyond n_max: a new registration
+        assert srv.stats().sets == 3
+        for t, gg, n in ((t1, g, 500), (t2, g, 450), (t3, (9, 6, 20), 450), (t4, g, 800)):
+            r = srv.wait(t, 60000)
+            assert r.status == fz.FZ_SERVE_DONE
+            assert np.array_equal(rows_of(srv, t, r), oracle.enumerate_desc(gg, n)), (gg, n)
+            srv.release(t)
+        with pytest.raises(fz.FzError) as e:
+            srv.wait(t1, 10)                        # released: unknown ticket
+        assert e.value.status == fz.FZ_ENOTFOUND
