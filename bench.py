@@ -38,8 +38,8 @@ if ROOT not in sys.path:
 METRIC = "Factorizations/s (exact, lex order) vs HBM roofline; served p50/p99 latency"
 UNIT = "factorizations/s"
 WORKLOAD = ("single large element: d=6 generators uniform in [50,200] (seed 0, distinct, "
-            "sorted, gcd 1), n = smallest with |Z(n)| >= 5e8, int32 tuples, memo depth "
-            "autotuned")
+            "sorted, gcd 1), n = smallest with |Z(n)| >= 5e8, int32 tuples, memo depth and "
+            "work-item size chosen by fz_autotune_report (measured in the warm-up)")
 
 
 def parse():
@@ -54,6 +54,10 @@ def parse():
                     help="seconds a collective waits for a rank that has left (N > 1)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-autotune", action="store_true",
+                    help="memo depth by the library's size rule instead of measuring")
+    ap.add_argument("--no-secondary", action="store_true",
+                    help="skip the batch / serve / memo records appended to the line")
     ap.add_argument("--no-graph", action="store_true",
                     help="launch every step's kernels directly instead of replaying a graph")
     ap.add_argument("--no-pipeline", action="store_true",
@@ -267,6 +271,23 @@ def run_ours(args):
     dev = torch.cuda.current_device()
     g, n = resolve_instance(lambda gg, nm: fz.fz_count_upto(gg, nm), args.seed, args.target)
     d = len(g)
+    # memo depth k and work-item size: measured (fz_autotune_report times
+    # every depth whose memo fits, at three work-item sizes, and the plan
+    # below picks up the fastest) unless given on the command line
+    k_choice = None
+    if args.k == -1 and not args.no_autotune:
+        t0 = time.perf_counter()
+        (k_best, sl_best, ms_best), cands = fz.fz_autotune_report(g, n)
+        k_choice = {"by": "fz_autotune_report: rebuild + enumeration of 4 sample windows "
+                          "per candidate, scaled to |Z| (measured in the warm-up)",
+                    "k": k_best, "slice_rows": sl_best, "est_ms": ms_best,
+                    "seconds": time.perf_counter() - t0,
+                    "candidates": [{kk: (round(vv, 4) if isinstance(vv, float) else vv)
+                                    for kk, vv in c.items()} for c in cands]}
+    elif args.k == -1:
+        k_choice = {"by": "size rule (choose_k: deepest k <= 4 whose memo stays small)"}
+    else:
+        k_choice = {"by": "command line"}
     plan = fz.Plan(g, n, k=args.k, slice_rows=args.slice_rows)
     count = plan.count
     out = torch.empty(count * d, dtype=torch.int32, device="cuda")
@@ -477,6 +498,44 @@ def run_ours(args):
                "note": "fz_enumerate_host: plan (count + memo), enumeration and D2H of "
                        "every tuple into pinned host memory, %d steps" % E}
         del host
+        # the same call into pageable memory (a plain numpy array): streamed
+        # through the library's page-locked staging buffers
+        import numpy as np
+        page = np.empty(count * d, dtype=np.int32)
+        page.fill(0)                     # touch every page once, outside the timing
+        fz.fz_enumerate_host(g, n, page)  # warm-up (staging pool, page-in)
+        barrier(pg, torch)
+        t0 = time.perf_counter()
+        for _ in range(E):
+            fz.fz_enumerate_host(g, n, page)
+        t = time.perf_counter() - t0
+        t = max_over_ranks(pg, t, torch)
+        e2e["pageable"] = {"value": world * E * count / t, "unit": UNIT,
+                           "d2h_GBps": E * count * d * 4 / t / 1e9,
+                           "note": "fz_enumerate_host into a pageable numpy array: chunks "
+                                   "enumerated into page-locked staging buffers and copied "
+                                   "by host threads while the next chunks are made"}
+        e2e["pinned_d2h_GBps"] = e2e["value"] / world * d * 4 / 1e9
+        del page
+
+    # the secondary workloads, bounded (about a minute together): batch,
+    # serving (with a sweep of offered rates) and the config-3 memo build
+    secondary = None
+    if rank == 0 and world == 1 and not args.no_secondary:
+        secondary = {}
+        for name, fn in (
+                ("memo", lambda: measure_memo(torch, fz, 20, 3)),
+                ("batch", lambda: measure_batch(torch, fz, 10, 3, 4096, 0, pi_steps=1)),
+                ("serve", lambda: measure_serve(torch, fz, seconds=3.0,
+                                                sweep_rates=(8000, 32000, 128000),
+                                                sweep_requests=4000))):
+            t0 = time.perf_counter()
+            try:
+                secondary[name] = fn()
+            except Exception as e:  # reported, never hides the main line
+                secondary[name] = {"error": repr(e)[:300]}
+            secondary[name]["wall_s"] = time.perf_counter() - t0
+        torch.cuda.synchronize()
 
     base = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -489,7 +548,8 @@ def run_ours(args):
             "warmup": args.warmup, "ms_per_step": ms / K, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "int32", "data": "synthetic",
             "config": {"workload": WORKLOAD, "g": list(g), "n": n, "count": count,
-                       "k": plan.k, "top": plan.top, "memo_rows": plan.memo_rows,
+                       "k": plan.k, "k_choice": k_choice, "top": plan.top,
+                       "memo_rows": plan.memo_rows,
                        "slice_rows": plan.slice_rows, "bytes_per_step": bytes_per_launch,
                        "parallelism": "replicas (one instance per GPU)",
                        "cuda_graph": graph is not None,
@@ -517,6 +577,8 @@ def run_ours(args):
             "clocks": clocks,
             "gpu_launches": launches,
         }
+        if secondary is not None:
+            rec["secondary"] = secondary
         print(json.dumps(rec))
     plan.close()
     if pg is not None:
@@ -586,21 +648,23 @@ def _event_time(torch, fn, steps, warmup):
     return a.elapsed_time(b) / steps
 
 
-def run_batch_workload(args):
-    """4096 instances (d 3..8, generators in [2,300], |Z| log-uniform in
-    [1e2,1e6]) in one persistent launch (the step -- batched counting tables,
-    memos and enumeration -- replayed as a captured CUDA graph), against the
-    same instances launched one plan at a time."""
-    torch, fz = _gpu_env()
+def measure_batch(torch, fz, steps, warmup, count=4096, only_d=0, pi_steps=5):
+    """Config 4: ``count`` instances (d 3..8, generators in [2,300], |Z|
+    log-uniform in [1e2,1e6]) in one persistent launch -- the step (batched
+    counting tables, memos and enumeration) replayed as a captured CUDA
+    graph -- against the same instances launched one plan at a time.
+    Returns a record (dict)."""
     from paper_2407_20474_gb300 import workloads
-    insts = workloads.config4_instances(2, args.batch_count)
-    if args.batch_d:
-        insts = [x for x in insts if len(x.g) == args.batch_d]
+    t_setup = time.perf_counter()
+    insts = workloads.config4_instances(2, count)
+    if only_d:
+        insts = [x for x in insts if len(x.g) == only_d]
     inst = [(x.g, workloads.find_n(fz.fz_count_upto, x.g, x.target, 64)) for x in insts]
     b = fz.Batch(inst)
     out = torch.empty(int(b.total_words) + 16, dtype=torch.int32, device="cuda")
     side = torch.cuda.Stream()
     graph_ok = True
+    graph_err = None
     try:
         cg = torch.cuda.CUDAGraph()
         side.wait_stream(torch.cuda.current_stream())
@@ -620,13 +684,13 @@ def run_batch_workload(args):
         def step():
             b.rebuild()
             b.enumerate(out)
-    ms = _event_time(torch, step, max(args.steps, 1), max(args.warmup, 1))
+    ms = _event_time(torch, step, max(steps, 1), max(warmup, 1))
     b.sync()
-    value = b.total_rows / (ms / 1e3)
     # the two halves of the step, each timed alone (plain launches)
-    ms_rebuild = _event_time(torch, b.rebuild, max(args.steps, 1), 1)
-    ms_enum = _event_time(torch, lambda: b.enumerate(out), max(args.steps, 1), 1)
+    ms_rebuild = _event_time(torch, b.rebuild, max(steps, 1), 1)
+    ms_enum = _event_time(torch, lambda: b.enumerate(out), max(steps, 1), 1)
     b.sync()
+    bytes_out = sum(int(r) * len(g) * 4 for (g, _), r in zip(inst, b.rows))
     # per-instance launches of the same instances
     plans = [fz.Plan(gg, n) for gg, n in inst]
     offs = [int(x) for x in b.word_offsets]
@@ -636,63 +700,92 @@ def run_batch_workload(args):
             if p.count:
                 p.rebuild()
                 p.enumerate(out[offs[i]:], capacity_rows=p.count)
-    steps_pi = max(1, min(args.steps, 5))
-    ms_pi = _event_time(torch, per_instance, steps_pi, 1)
+    ms_pi = _event_time(torch, per_instance, max(1, pi_steps), 1)
     for p in plans:
         p.close()
-    rec = {"metric": "Factorizations/s, batched (%d instances, one persistent launch)" % len(inst),
-           "value": value, "unit": UNIT, "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
-           "ms_per_step": ms, "higher_is_better": True, "dtype": "int32", "data": "synthetic",
-           "config": {"workload": "batched: %d instances, d uniform 3..8, generators uniform "
-                                  "[2,300] (distinct, gcd 1), |Z| log-uniform [1e2,1e6], "
-                                  "seed 2%s" % (len(inst), (", only d = %d" % args.batch_d)
-                                                if args.batch_d else ""),
-                      "total_rows": b.total_rows, "memos": b.memos,
-                      "run_order_instances": b.run_order, "run_order_memos": b.run_memos,
-                      "work_items": b.work_items, "cuda_graph": graph_ok,
-                      "rebuild_ms": ms_rebuild, "enumerate_ms": ms_enum,
-                      "per_instance_ms_per_step": ms_pi,
-                      "per_instance_value": b.total_rows / (ms_pi / 1e3),
-                      "speedup_vs_per_instance": ms_pi / ms}}
-    if not graph_ok:
-        rec["config"]["graph_error"] = graph_err
+    peak = _hbm_peak()
+    rec = {"workload": "batched: %d instances, d uniform 3..8, generators uniform [2,300] "
+                       "(distinct, gcd 1), |Z| log-uniform [1e2,1e6], seed 2%s"
+                       % (len(inst), (", only d = %d" % only_d) if only_d else ""),
+           "instances": len(inst), "total_rows": int(b.total_rows), "bytes_out": bytes_out,
+           "ms_per_step": ms, "value": b.total_rows / (ms / 1e3), "unit": UNIT,
+           "memos": b.memos, "run_order_instances": b.run_order,
+           "run_order_memos": b.run_memos, "work_items": b.work_items,
+           "cuda_graph": graph_ok, "rebuild_ms": ms_rebuild, "enumerate_ms": ms_enum,
+           "per_instance_ms_per_step": ms_pi,
+           "per_instance_value": b.total_rows / (ms_pi / 1e3),
+           "speedup_vs_per_instance": ms_pi / ms,
+           "roofline_enumeration": {
+               "bound": "hbm", "kernel": "fz_enum_batch_kernel",
+               "achieved": bytes_out / (ms_enum / 1e3) / 1e9, "peak": peak[0],
+               "unit": "GB/s", "frac": bytes_out / (ms_enum / 1e3) / 1e9 / peak[0],
+               "peak_source": peak[1]},
+           "setup_s": time.perf_counter() - t_setup}
+    if graph_err:
+        rec["graph_error"] = graph_err
+    b.close()
+    return rec
+
+
+def run_batch_workload(args):
+    torch, fz = _gpu_env()
+    r = measure_batch(torch, fz, args.steps, args.warmup, args.batch_count, args.batch_d)
+    rec = {"metric": "Factorizations/s, batched (%d instances, one persistent launch)"
+                     % r["instances"],
+           "value": r["value"], "unit": UNIT, "n_gpus": 1, "steps": args.steps,
+           "warmup": args.warmup, "ms_per_step": r["ms_per_step"], "higher_is_better": True,
+           "dtype": "int32", "data": "synthetic",
+           "config": {k: v for k, v in r.items() if k not in ("value", "unit", "ms_per_step")}}
     print(json.dumps(rec))
 
 
-def run_serve_workload(args):
-    """Open-loop Poisson stream (2000 req/s) of queries over 64 resident
-    generator sets (d 4..7, generators in [5,500]), |Z| log-uniform in
-    [1e3,1e7]; continuous batching against one-request-at-a-time serving."""
+def _hbm_peak():
+    pp = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(pp):
+        v = json.load(open(pp)).get("hbm_gbs")
+        if v:
+            return float(v), "measured"
+    return 6800.0, "fallback"
+
+
+def measure_serve(torch, fz, seconds=10.0, sweep_rates=(), sweep_requests=4000,
+                  serial=True):
+    """Config 5: an open-loop Poisson stream (2000 req/s) of queries over 64
+    resident generator sets (d 4..7, generators in [5,500]), |Z| log-uniform
+    in [1e3,1e7]; continuous batching against one-request-at-a-time serving.
+    ``sweep_rates`` replays the same query mix at higher offered rates,
+    ``sweep_requests`` requests each, in both modes, to find the sustainable
+    rate.
+    Returns a record (dict)."""
     import threading
     import numpy as np
-    torch, fz = _gpu_env()
     from paper_2407_20474_gb300 import workloads
-    st = workloads.config5_stream(3, duration_s=args.serve_seconds)
+    t_setup = time.perf_counter()
+    base = workloads.config5_stream(3, duration_s=seconds)
+    sets = base.sets
     # per set: counts up to the element of the largest target, then each
     # request's n = the smallest element reaching its target
-    set_counts, n_of = [], np.zeros(len(st.targets), dtype=np.int64)
-    n_max = []
-    for g in st.sets:
-        nm = workloads.find_n(fz.fz_count_upto, g, int(st.targets.max()), 1024)
-        c = fz.fz_count_upto(g, nm).astype(np.float64)
-        set_counts.append(c)
+    n_max, set_counts = [], []
+    for g in sets:
+        nm = workloads.find_n(fz.fz_count_upto, g, int(base.targets.max()), 1024)
+        set_counts.append(fz.fz_count_upto(g, nm).astype(np.float64))
         n_max.append(nm)
-    for i, (s_i, t) in enumerate(zip(st.set_index, st.targets)):
-        c = set_counts[s_i]
-        n_of[i] = int(np.argmax(c >= t))
 
-    def replay(max_in_flight, streams):
-        srv = fz.Server(max_in_flight=max_in_flight, streams=streams)
-        ids = [srv.register(g, nm) for g, nm in zip(st.sets, n_max)]
-        tickets = [None] * len(n_of)
-        lat = np.zeros(len(n_of))
-        rows = np.zeros(len(n_of))
-        done_t = np.zeros(len(n_of))
-        sub_t = np.zeros(len(n_of))
+    def n_for(set_index, targets):
+        return np.array([int(np.argmax(set_counts[s_i] >= t))
+                         for s_i, t in zip(set_index, targets)], dtype=np.int64)
+
+    def replay(srv, ids, arrivals, set_index, ns):
+        m = len(ns)
+        tickets = [None] * m
+        lat = np.zeros(m)
+        rows = np.zeros(m)
+        done_t = np.zeros(m)
+        sub_t = np.zeros(m)
         ready = threading.Semaphore(0)
 
         def drain():
-            for i in range(len(n_of)):
+            for i in range(m):
                 ready.acquire()
                 r = srv.wait(tickets[i], -1)
                 lat[i] = r.t_done - r.t_submit
@@ -704,76 +797,140 @@ def run_serve_workload(args):
         th = threading.Thread(target=drain)
         th.start()
         t0 = time.perf_counter()
-        for i, (s_i, at) in enumerate(zip(st.set_index, st.arrivals_s)):
-            delay = t0 + at - time.perf_counter()
+        late = 0.0
+        for i in range(m):
+            delay = t0 + arrivals[i] - time.perf_counter()
             if delay > 0:
                 time.sleep(delay)
-            tickets[i] = srv.submit(ids[s_i], int(n_of[i]))
+            else:
+                late = max(late, -delay)
+            tickets[i] = srv.submit(ids[set_index[i]], int(ns[i]))
             ready.release()
         th.join()
-        srv.close()
-        span = done_t.max() - sub_t.min()
+        span = float(done_t.max() - sub_t.min()) if m else 0.0
+        offered_span = float(arrivals[-1]) if m else 0.0
         return {"p50_ms": 1e3 * float(np.percentile(lat, 50)),
                 "p99_ms": 1e3 * float(np.percentile(lat, 99)),
                 "mean_ms": 1e3 * float(lat.mean()),
-                "throughput": float(rows.sum() / span), "requests": int(len(n_of)),
-                "rows": float(rows.sum())}
+                "throughput": float(rows.sum() / span) if span > 0 else 0.0,
+                "requests": int(m), "rows": float(rows.sum()),
+                "offered_req_per_s": m / offered_span if offered_span > 0 else 0.0,
+                "achieved_req_per_s": m / span if span > 0 else 0.0,
+                "max_submit_lag_ms": 1e3 * late}
 
-    cont = replay(64, 8)
-    serial = replay(1, 1)
+    def server(max_in_flight, streams):
+        srv = fz.Server(max_in_flight=max_in_flight, streams=streams)
+        ids = [srv.register(g, nm) for g, nm in zip(sets, n_max)]
+        return srv, ids
+
+    modes = {"continuous": (64, 8)}
+    if serial:
+        modes["serial_one_at_a_time"] = (1, 1)
+    res = {}
+    servers = {k: server(*v) for k, v in modes.items()}
+    t_setup = time.perf_counter() - t_setup
+    st = workloads.config5_stream(3, duration_s=seconds)
+    ns = n_for(st.set_index, st.targets)
+    for name, (srv, ids) in servers.items():
+        replay(srv, ids, st.arrivals_s[:64], st.set_index[:64], ns[:64])  # warm-up
+        res[name] = replay(srv, ids, st.arrivals_s, st.set_index, ns)
+    sweep = {}
+    for rate in sweep_rates:
+        sw = workloads.config5_stream(3, rate=float(rate),
+                                      duration_s=1.2 * sweep_requests / float(rate) + 0.01)
+        m = min(sweep_requests, len(sw.arrivals_s))
+        # targets above the largest the sets were sized for are clipped to it
+        tg = np.minimum(sw.targets[:m], base.targets.max())
+        nsw = n_for(sw.set_index[:m], tg)
+        for name, (srv, ids) in servers.items():
+            sweep.setdefault(name, []).append(
+                dict(rate=float(rate),
+                     **replay(srv, ids, sw.arrivals_s[:m], sw.set_index[:m], nsw)))
+    for srv, _ in servers.values():
+        srv.close()
+    rec = {"workload": "served: Poisson %.0f req/s for %.1f s over 64 resident sets (d 4..7, "
+                       "generators [5,500], gcd 1), |Z| log-uniform [1e3,1e7], seed 3"
+                       % (st.rate, st.duration_s),
+           "value": res["continuous"]["throughput"], "unit": UNIT,
+           "p50_ms": res["continuous"]["p50_ms"], "p99_ms": res["continuous"]["p99_ms"],
+           "setup_s": t_setup}
+    rec.update(res)
+    if sweep:
+        sat = {}
+        for name, pts in sweep.items():
+            # sustainable: the request rate keeps up with the offered rate
+            # (>= 95 %) and p99 stays within 10x of its value at 2000 req/s
+            ok = [p for p in pts if p["achieved_req_per_s"] >= 0.95 * p["offered_req_per_s"]
+                  and p["p99_ms"] <= 10.0 * res[name]["p99_ms"]]
+            best = max(ok, key=lambda p: p["rate"]) if ok else None
+            sat[name] = {"sustainable_rate": best["rate"] if best else None,
+                         "throughput_at_sustainable": best["throughput"] if best else None,
+                         "max_throughput": max(p["throughput"] for p in pts),
+                         "points": pts}
+        rec["saturation"] = sat
+    return rec
+
+
+def run_serve_workload(args):
+    torch, fz = _gpu_env()
+    r = measure_serve(torch, fz, args.serve_seconds,
+                      sweep_rates=(4000, 8000, 16000, 32000, 64000, 128000),
+                      sweep_requests=8000)
     rec = {"metric": "Served factorizations/s with p50/p99 latency (Poisson 2000 req/s)",
-           "value": cont["throughput"], "unit": UNIT, "n_gpus": 1, "higher_is_better": True,
+           "value": r["value"], "unit": UNIT, "n_gpus": 1, "higher_is_better": True,
            "dtype": "int32", "data": "synthetic",
-           "p50_ms": cont["p50_ms"], "p99_ms": cont["p99_ms"],
-           "config": {"workload": "served: Poisson %.0f req/s for %.1f s over 64 resident sets "
-                                  "(d 4..7, generators [5,500], gcd 1), |Z| log-uniform "
-                                  "[1e3,1e7], seed 3" % (st.rate, st.duration_s),
-                      "continuous": cont, "serial_one_at_a_time": serial}}
+           "p50_ms": r["p50_ms"], "p99_ms": r["p99_ms"],
+           "config": {k: v for k, v in r.items() if k not in ("value", "unit")}}
     print(json.dumps(rec))
 
 
-def run_memo_workload(args):
-    """Dynamic FactorizationsUpToElement build of all Z(0..1500) for d = 5
-    generators in [3,40] (seed 1): the full CSR, elementwise in batches of
-    min(g) elements.  Timed on the device as the rebuild of a plan whose memo
-    is that CSR (k = d, top = N + 1: count table, offsets, gather map and the
-    batched fill, no allocation), CUDA events over the steps; the one-shot
+def measure_memo(torch, fz, steps, warmup):
+    """Config 3: dynamic FactorizationsUpToElement build of all Z(0..1500) for
+    d = 5 generators in [3,40] (seed 1): the full CSR, elementwise in batches
+    of min(g) elements.  Timed on the device as the rebuild of a plan whose
+    memo is that CSR (k = d, top = N + 1: count table, offsets, gather map and
+    the batched fill, no allocation), CUDA events over the steps; the one-shot
     host call fz_build_memo_into (which allocates its work buffers and
-    synchronises) is timed beside it."""
-    torch, fz = _gpu_env()
+    synchronises) is timed beside it.  Returns a record (dict)."""
     from paper_2407_20474_gb300 import workloads
     g = workloads.config3_generators(1)
     N = workloads.CONFIG3_N
     rows = fz.fz_memo_rows(g, N + 1)
     with fz.Plan(g, N, k=len(g), top=N + 1) as plan:
         assert plan.memo_rows == rows
-        ms = _event_time(torch, plan.rebuild, max(args.steps, 1), max(args.warmup, 1))
+        ms = _event_time(torch, plan.rebuild, max(steps, 1), max(warmup, 1))
         plan.sync()
     off = torch.zeros(N + 2, dtype=torch.int64, device="cuda")
     buf = torch.empty(rows * len(g) + 16, dtype=torch.int32, device="cuda")
     ts = []
-    for i in range(max(args.warmup, 1) + max(min(args.steps, 20), 1)):
+    for i in range(max(warmup, 1) + max(min(steps, 20), 1)):
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         fz.fz_build_memo_into(g, N + 1, off, buf, rows)
         torch.cuda.synchronize()
-        if i >= max(args.warmup, 1):
+        if i >= max(warmup, 1):
             ts.append(time.perf_counter() - t0)
     t_host = statistics.median(ts)
     nbatch = -(-(N + 1) // min(g))
+    return {"workload": "d=5 generators %s (seed 1), N=%d" % (list(g), N),
+            "value": rows / (ms / 1e3), "unit": "rows/s", "ms_per_step": ms,
+            "rows": rows, "bytes_written": rows * len(g) * 4,
+            "write_GBps": rows * len(g) * 4 / (ms / 1e3) / 1e9,
+            "dependent_batches": nbatch, "us_per_batch": 1e3 * ms / nbatch,
+            "bound": "latency (one grid barrier per elementwise batch)",
+            "host_call_ms": 1e3 * t_host,
+            "note": "value: device time of a plan rebuild (CUDA events); "
+                    "host_call_ms: fz_build_memo_into incl. its allocations"}
+
+
+def run_memo_workload(args):
+    torch, fz = _gpu_env()
+    r = measure_memo(torch, fz, args.steps, args.warmup)
     rec = {"metric": "Memo rows/s, dynamic build of all Z(0..N) (FactorizationsUpToElement)",
-           "value": rows / (ms / 1e3), "unit": "rows/s", "n_gpus": 1, "higher_is_better": True,
-           "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "dtype": "int32",
-           "data": "synthetic",
-           "config": {"workload": "d=5 generators %s (seed 1), N=%d" % (list(g), N),
-                      "rows": rows, "bytes_written": rows * len(g) * 4,
-                      "write_GBps": rows * len(g) * 4 / (ms / 1e3) / 1e9,
-                      "dependent_batches": nbatch,
-                      "us_per_batch": 1e3 * ms / nbatch,
-                      "bound": "latency (one grid barrier per elementwise batch)",
-                      "host_call_ms": 1e3 * t_host,
-                      "note": "value: device time of a plan rebuild (CUDA events); "
-                              "host_call_ms: fz_build_memo_into incl. its allocations"}}
+           "value": r["value"], "unit": "rows/s", "n_gpus": 1, "higher_is_better": True,
+           "steps": args.steps, "warmup": args.warmup, "ms_per_step": r["ms_per_step"],
+           "dtype": "int32", "data": "synthetic",
+           "config": {k: v for k, v in r.items() if k not in ("value", "unit", "ms_per_step")}}
     print(json.dumps(rec))
 
 

@@ -272,6 +272,27 @@ int fz_plan_set_enum_ctas_per_sm(fz_plan_t plan, int32_t ctas);
 int fz_autotune(const int32_t *g, int d, int32_t n, fz_opts_t *best, double *best_ms,
                 void *stream);
 
+/* One measured candidate of the tuning above. */
+typedef struct fz_tune_entry {
+    int32_t k;          /* memo depth */
+    int32_t slice_rows; /* rows per work item */
+    int32_t run_order;  /* 1 when the memo is kept in run order */
+    int32_t reserved;
+    uint64_t memo_rows;
+    double build_ms;    /* rebuild: count tables + memo (measured) */
+    double enum_ms;     /* enumeration of the whole set (measured on the
+                           sample windows, scaled by rows) */
+    double total_ms;    /* build_ms + enum_ms: what the choice minimises */
+} fz_tune_entry_t;
+
+/* fz_autotune that also reports every candidate it timed: up to `capacity`
+ * entries into `entries` (host; may be NULL when capacity is 0), their
+ * number into *n_entries (may be NULL).  Same choice, same memory of it.
+ * Errors: as fz_autotune; FZ_EINVAL (entries null with capacity > 0). */
+int fz_autotune_report(const int32_t *g, int d, int32_t n, fz_tune_entry_t *entries,
+                       int capacity, int *n_entries, fz_opts_t *best, double *best_ms,
+                       void *stream);
+
 /* Recompute the count table and rebuild the memo in the plan's buffers.
  * Asynchronous (no host synchronisation), so it can be captured in a CUDA
  * graph.  Errors surface at fz_plan_sync. */

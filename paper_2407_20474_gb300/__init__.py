@@ -43,7 +43,7 @@ EXPORTS = (
     "fz_memo_rows", "fz_build_memo_into", "fz_build_memo_schedule", "fz_build_memo",
     "fz_memo_info",
     "fz_memo_release",
-    "fz_autotune", "fz_plan_create", "fz_plan_info", "fz_plan_set_enum_ctas_per_sm",
+    "fz_autotune", "fz_autotune_report", "fz_plan_create", "fz_plan_info", "fz_plan_set_enum_ctas_per_sm",
     "fz_plan_rebuild",
     "fz_plan_enumerate",
     "fz_plan_unrank", "fz_plan_sync", "fz_plan_destroy",
@@ -66,6 +66,13 @@ class FzError(RuntimeError):
 class fz_opts_t(ctypes.Structure):
     _fields_ = [("k", ctypes.c_int32), ("top", ctypes.c_int32),
                 ("slice_rows", ctypes.c_int32), ("flags", ctypes.c_int32)]
+
+
+class fz_tune_entry_t(ctypes.Structure):
+    _fields_ = [("k", ctypes.c_int32), ("slice_rows", ctypes.c_int32),
+                ("run_order", ctypes.c_int32), ("reserved", ctypes.c_int32),
+                ("memo_rows", ctypes.c_uint64), ("build_ms", ctypes.c_double),
+                ("enum_ms", ctypes.c_double), ("total_ms", ctypes.c_double)]
 
 
 class fz_plan_info_t(ctypes.Structure):
@@ -145,6 +152,11 @@ _SIGS = {
     "fz_plan_info": (ctypes.c_int, [_P, ctypes.POINTER(fz_plan_info_t)]),
     "fz_autotune": (ctypes.c_int, [_I32P, ctypes.c_int, ctypes.c_int32,
                                    ctypes.POINTER(fz_opts_t), ctypes.POINTER(ctypes.c_double), _P]),
+    "fz_autotune_report": (ctypes.c_int, [_I32P, ctypes.c_int, ctypes.c_int32,
+                                          ctypes.POINTER(fz_tune_entry_t), ctypes.c_int,
+                                          ctypes.POINTER(ctypes.c_int),
+                                          ctypes.POINTER(fz_opts_t),
+                                          ctypes.POINTER(ctypes.c_double), _P]),
     "fz_plan_rebuild": (ctypes.c_int, [_P, _P]),
     "fz_plan_set_enum_ctas_per_sm": (ctypes.c_int, [_P, ctypes.c_int32]),
     "fz_plan_enumerate": (ctypes.c_int, [_P, ctypes.c_uint64, ctypes.c_uint64, _P,
@@ -418,6 +430,24 @@ def fz_autotune(g: Sequence[int], n: int, stream=None):
     _check(lib().fz_autotune(ga, d, int(n), ctypes.byref(o), ctypes.byref(ms),
                              _stream(stream)))
     return int(o.k), int(o.slice_rows), float(ms.value)
+
+
+def fz_autotune_report(g: Sequence[int], n: int, stream=None):
+    """fz_autotune plus every timed candidate: ((k, slice_rows, est_ms),
+    [dict(k, slice_rows, run_order, memo_rows, build_ms, enum_ms, total_ms)])."""
+    ga, d = _gens(g)
+    cap = 64
+    arr = (fz_tune_entry_t * cap)()
+    got = ctypes.c_int(0)
+    o = fz_opts_t(0, 0, 0, 0)
+    ms = ctypes.c_double(0.0)
+    _check(lib().fz_autotune_report(ga, d, int(n), arr, cap, ctypes.byref(got), ctypes.byref(o),
+                                    ctypes.byref(ms), _stream(stream)))
+    entries = [dict(k=int(e.k), slice_rows=int(e.slice_rows), run_order=int(e.run_order),
+                    memo_rows=int(e.memo_rows), build_ms=float(e.build_ms),
+                    enum_ms=float(e.enum_ms), total_ms=float(e.total_ms))
+               for e in arr[:got.value]]
+    return (int(o.k), int(o.slice_rows), float(ms.value)), entries
 
 
 class Plan:

@@ -1013,9 +1013,13 @@ static int time_plan(fz_plan_t p, int32_t *buf, uint64_t wrows, int windows, cud
     return rc;
 }
 
-int fz_autotune(const int32_t *g, int d, int32_t n, fz_opts_t *best, double *best_ms,
-                void *stream) {
+int fz_autotune_report(const int32_t *g, int d, int32_t n, fz_tune_entry_t *entries,
+                       int capacity, int *n_entries, fz_opts_t *best, double *best_ms,
+                       void *stream) {
     if (!best) return set_error(FZ_EINVAL, "best: null pointer");
+    if (capacity < 0 || (capacity > 0 && !entries))
+        return set_error(FZ_EINVAL, "entries: null pointer");
+    if (n_entries) *n_entries = 0;
     cudaStream_t s = as_stream(stream);
     // the heuristic plan gives the count and the depths worth trying
     fz_plan_t p0 = nullptr;
@@ -1042,6 +1046,7 @@ int fz_autotune(const int32_t *g, int d, int32_t n, fz_opts_t *best, double *bes
     if (rc != FZ_OK) return rc;
     double best_t = 1e300;
     fz_opts_t best_o = *best;
+    int found = 0;
     std::vector<int> ks;
     for (int k = 0; k <= std::min(d - 1, 4); ++k) ks.push_back(k);
     for (int k : ks) {
@@ -1063,6 +1068,17 @@ int fz_autotune(const int32_t *g, int d, int32_t n, fz_opts_t *best, double *bes
                 return rc;
             }
             const double t = b_ms + e_row * (double)count;
+            if (found < capacity) {
+                fz_tune_entry_t &E = entries[found];
+                E.k = k;
+                E.slice_rows = (int32_t)p->slice_rows;
+                E.run_order = p->run_memo ? 1 : 0;
+                E.memo_rows = p->memo_rows;
+                E.build_ms = b_ms;
+                E.enum_ms = e_row * (double)count;
+                E.total_ms = t;
+            }
+            ++found;
             if (t < best_t) {
                 best_t = t;
                 best_o = fz_opts_t{k, FZ_AUTO, (int32_t)p->slice_rows, 0};
@@ -1070,11 +1086,17 @@ int fz_autotune(const int32_t *g, int d, int32_t n, fz_opts_t *best, double *bes
         }
         fz_plan_destroy(p);
     }
+    if (n_entries) *n_entries = std::min(found, capacity);
     *best = best_o;
     if (best_ms) *best_ms = best_t;
     std::lock_guard<std::mutex> lk(g_tune_mu);
     g_tune[tune_key(g, d, n)] = best_o;
     return FZ_OK;
+}
+
+int fz_autotune(const int32_t *g, int d, int32_t n, fz_opts_t *best, double *best_ms,
+                void *stream) {
+    return fz_autotune_report(g, d, n, nullptr, 0, nullptr, best, best_ms, stream);
 }
 
 // -------------------------------------------------------------------- plans
