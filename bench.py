@@ -78,6 +78,8 @@ def parse():
                          "Z(0..1500); table1: the paper's Table 1 instances")
     ap.add_argument("--serve-seconds", type=float, default=10.0)
     ap.add_argument("--batch-count", type=int, default=4096)
+    ap.add_argument("--batch-pi-steps", type=int, default=5,
+                    help="steps of the per-instance comparison (0: skip it)")
     ap.add_argument("--batch-d", type=int, default=0,
                     help="batch workload: keep only the instances with this many generators")
     return ap.parse_args()
@@ -278,8 +280,8 @@ def run_ours(args):
     if args.k == -1 and not args.no_autotune:
         t0 = time.perf_counter()
         (k_best, sl_best, ms_best), cands = fz.fz_autotune_report(g, n)
-        k_choice = {"by": "fz_autotune_report: rebuild + enumeration of 4 sample windows "
-                          "per candidate, scaled to |Z| (measured in the warm-up)",
+        k_choice = {"by": "fz_autotune_report: rebuild + enumeration of the whole set per "
+                          "candidate, mean of 2 passes (measured in the warm-up)",
                     "k": k_best, "slice_rows": sl_best, "est_ms": ms_best,
                     "seconds": time.perf_counter() - t0,
                     "candidates": [{kk: (round(vv, 4) if isinstance(vv, float) else vv)
@@ -498,23 +500,29 @@ def run_ours(args):
                "note": "fz_enumerate_host: plan (count + memo), enumeration and D2H of "
                        "every tuple into pinned host memory, %d steps" % E}
         del host
-        # the same call into pageable memory (a plain numpy array): streamed
-        # through the library's page-locked staging buffers
+        # the same call into pageable memory (a plain numpy array): written
+        # by the kernel where the device reaches pageable memory through the
+        # host's page tables, else through the page-locked staging ring; the
+        # ring alone is timed beside it (128 MB chunks)
         import numpy as np
         page = np.empty(count * d, dtype=np.int32)
         page.fill(0)                     # touch every page once, outside the timing
-        fz.fz_enumerate_host(g, n, page)  # warm-up (staging pool, page-in)
-        barrier(pg, torch)
-        t0 = time.perf_counter()
-        for _ in range(E):
-            fz.fz_enumerate_host(g, n, page)
-        t = time.perf_counter() - t0
-        t = max_over_ranks(pg, t, torch)
-        e2e["pageable"] = {"value": world * E * count / t, "unit": UNIT,
-                           "d2h_GBps": E * count * d * 4 / t / 1e9,
-                           "note": "fz_enumerate_host into a pageable numpy array: chunks "
-                                   "enumerated into page-locked staging buffers and copied "
-                                   "by host threads while the next chunks are made"}
+        for label, chunk in (("pageable", 0),
+                             ("pageable_staged", (128 << 20) // (4 * d))):
+            fz.fz_enumerate_host(g, n, page, chunk_rows=chunk)  # warm-up
+            barrier(pg, torch)
+            t0 = time.perf_counter()
+            for _ in range(E):
+                fz.fz_enumerate_host(g, n, page, chunk_rows=chunk)
+            t = time.perf_counter() - t0
+            t = max_over_ranks(pg, t, torch)
+            e2e[label] = {"value": world * E * count / t, "unit": UNIT,
+                          "d2h_GBps": E * count * d * 4 / t / 1e9,
+                          "note": ("fz_enumerate_host into a pageable numpy array (default "
+                                   "path)" if chunk == 0 else
+                                   "fz_enumerate_host_chunks into a pageable numpy array: "
+                                   "128 MB chunks enumerated into page-locked staging buffers "
+                                   "and copied by host threads while the next are made")}
         e2e["pinned_d2h_GBps"] = e2e["value"] / world * d * 4 / 1e9
         del page
 
@@ -692,17 +700,19 @@ def measure_batch(torch, fz, steps, warmup, count=4096, only_d=0, pi_steps=5):
     b.sync()
     bytes_out = sum(int(r) * len(g) * 4 for (g, _), r in zip(inst, b.rows))
     # per-instance launches of the same instances
-    plans = [fz.Plan(gg, n) for gg, n in inst]
-    offs = [int(x) for x in b.word_offsets]
+    ms_pi = None
+    if pi_steps > 0:
+        plans = [fz.Plan(gg, n) for gg, n in inst]
+        offs = [int(x) for x in b.word_offsets]
 
-    def per_instance():
-        for i, p in enumerate(plans):
-            if p.count:
-                p.rebuild()
-                p.enumerate(out[offs[i]:], capacity_rows=p.count)
-    ms_pi = _event_time(torch, per_instance, max(1, pi_steps), 1)
-    for p in plans:
-        p.close()
+        def per_instance():
+            for i, p in enumerate(plans):
+                if p.count:
+                    p.rebuild()
+                    p.enumerate(out[offs[i]:], capacity_rows=p.count)
+        ms_pi = _event_time(torch, per_instance, pi_steps, 1)
+        for p in plans:
+            p.close()
     peak = _hbm_peak()
     rec = {"workload": "batched: %d instances, d uniform 3..8, generators uniform [2,300] "
                        "(distinct, gcd 1), |Z| log-uniform [1e2,1e6], seed 2%s"
@@ -713,8 +723,8 @@ def measure_batch(torch, fz, steps, warmup, count=4096, only_d=0, pi_steps=5):
            "run_order_memos": b.run_memos, "work_items": b.work_items,
            "cuda_graph": graph_ok, "rebuild_ms": ms_rebuild, "enumerate_ms": ms_enum,
            "per_instance_ms_per_step": ms_pi,
-           "per_instance_value": b.total_rows / (ms_pi / 1e3),
-           "speedup_vs_per_instance": ms_pi / ms,
+           "per_instance_value": b.total_rows / (ms_pi / 1e3) if ms_pi else None,
+           "speedup_vs_per_instance": ms_pi / ms if ms_pi else None,
            "roofline_enumeration": {
                "bound": "hbm", "kernel": "fz_enum_batch_kernel",
                "achieved": bytes_out / (ms_enum / 1e3) / 1e9, "peak": peak[0],
@@ -729,7 +739,8 @@ def measure_batch(torch, fz, steps, warmup, count=4096, only_d=0, pi_steps=5):
 
 def run_batch_workload(args):
     torch, fz = _gpu_env()
-    r = measure_batch(torch, fz, args.steps, args.warmup, args.batch_count, args.batch_d)
+    r = measure_batch(torch, fz, args.steps, args.warmup, args.batch_count, args.batch_d,
+                      pi_steps=args.batch_pi_steps)
     rec = {"metric": "Factorizations/s, batched (%d instances, one persistent launch)"
                      % r["instances"],
            "value": r["value"], "unit": UNIT, "n_gpus": 1, "steps": args.steps,

@@ -264,25 +264,28 @@ int fz_plan_set_enum_ctas_per_sm(fz_plan_t plan, int32_t ctas);
 /* Empirical tuning of the implementation options for Z(n, g): each memo
  * depth k = 0..min(d-1, 4) whose memo fits (and three work-item sizes for
  * each) is built and timed on the device -- its rebuild plus the
- * enumeration of four rank windows spread over the set, extrapolated to the
- * whole set.  The fastest is written to *best (and its estimated ms per
- * step to *best_ms, may be NULL) and remembered for this (g, n) and device:
- * later plans created with k = FZ_AUTO use it.  Synchronises.
- * Errors: as fz_plan_create. */
+ * enumeration of the whole set into a scratch buffer (of the whole output
+ * when it fits in a third of the free device memory, else windows of that
+ * size), averaged over two passes after a first pass that also screens:
+ * a candidate whose first pass, scaled to the set, takes over four times
+ * the best time so far is not timed further.  The fastest is written to
+ * *best (and its ms per step to *best_ms, may be NULL) and remembered for
+ * this (g, n) and device: later plans created with k = FZ_AUTO use it.
+ * Synchronises.  Errors: as fz_plan_create. */
 int fz_autotune(const int32_t *g, int d, int32_t n, fz_opts_t *best, double *best_ms,
                 void *stream);
 
 /* One measured candidate of the tuning above. */
 typedef struct fz_tune_entry {
-    int32_t k;          /* memo depth */
-    int32_t slice_rows; /* rows per work item */
-    int32_t run_order;  /* 1 when the memo is kept in run order */
-    int32_t reserved;
+    int32_t k;            /* memo depth */
+    int32_t slice_rows;   /* rows per work item */
+    int32_t run_order;    /* 1 when the memo is kept in run order */
+    int32_t screened_out; /* 1: timed once only (over 4x the best so far) */
     uint64_t memo_rows;
-    double build_ms;    /* rebuild: count tables + memo (measured) */
-    double enum_ms;     /* enumeration of the whole set (measured on the
-                           sample windows, scaled by rows) */
-    double total_ms;    /* build_ms + enum_ms: what the choice minimises */
+    double build_ms;      /* rebuild: count tables + memo (measured) */
+    double enum_ms;       /* enumeration of the whole set (measured; for a
+                             screened-out candidate its first window, scaled) */
+    double total_ms;      /* build_ms + enum_ms: what the choice minimises */
 } fz_tune_entry_t;
 
 /* fz_autotune that also reports every candidate it timed: up to `capacity`
@@ -498,9 +501,12 @@ int fz_enumerate(const int32_t *g, int d, int32_t n, const fz_opts_t *opt,
 /* As fz_enumerate, but out_host is host memory: the asynchronous form of
  * the device-to-host buffer flushes of the paper's driver (Section 3.2).
  * Page-locked (pinned, mapped) memory is written by the enumeration kernel
- * itself over the host link.  Pageable memory is filled in chunks: each
- * chunk is enumerated into one of three page-locked staging buffers while
- * host threads copy the previous, finished chunks into out_host, so the
+ * itself over the host link, and so is pageable memory on devices that
+ * reach it through the host's page tables (cudaDevAttrPageableMemoryAccess
+ * and cudaDevAttrPageableMemoryAccessUsesHostPageTables both 1, as on
+ * Grace-Blackwell).  Other pageable memory is filled in chunks: each chunk
+ * is enumerated into one of three page-locked staging buffers while host
+ * threads copy the previous, finished chunks into out_host.  Either way the
  * output may be larger than device memory.  The staging buffers (3 chunks)
  * are kept for later calls; a call that finds them in use by another
  * thread pins its own.  Synchronises.
@@ -510,8 +516,10 @@ int fz_enumerate_host(const int32_t *g, int d, int32_t n, const fz_opts_t *opt,
                       uint64_t out_capacity_rows, uint64_t *written,
                       void *stream);
 
-/* fz_enumerate_host with the chunk size for pageable output given in rows
- * (0 = the default, 128 MB of rows; ignored for page-locked output). */
+/* fz_enumerate_host with the chunk size for pageable output given in rows:
+ * chunk_rows > 0 always takes the staging ring with chunks of that many
+ * rows; 0 = the default (direct writes where the device can make them,
+ * else the ring with 128 MB chunks).  Ignored for page-locked output. */
 int fz_enumerate_host_chunks(const int32_t *g, int d, int32_t n, const fz_opts_t *opt,
                              uint64_t rank_begin, uint64_t rank_end, int32_t *out_host,
                              uint64_t out_capacity_rows, uint64_t chunk_rows,

@@ -70,7 +70,7 @@ class fz_opts_t(ctypes.Structure):
 
 class fz_tune_entry_t(ctypes.Structure):
     _fields_ = [("k", ctypes.c_int32), ("slice_rows", ctypes.c_int32),
-                ("run_order", ctypes.c_int32), ("reserved", ctypes.c_int32),
+                ("run_order", ctypes.c_int32), ("screened_out", ctypes.c_int32),
                 ("memo_rows", ctypes.c_uint64), ("build_ms", ctypes.c_double),
                 ("enum_ms", ctypes.c_double), ("total_ms", ctypes.c_double)]
 
@@ -433,8 +433,9 @@ def fz_autotune(g: Sequence[int], n: int, stream=None):
 
 
 def fz_autotune_report(g: Sequence[int], n: int, stream=None):
-    """fz_autotune plus every timed candidate: ((k, slice_rows, est_ms),
-    [dict(k, slice_rows, run_order, memo_rows, build_ms, enum_ms, total_ms)])."""
+    """fz_autotune plus every timed candidate: ((k, slice_rows, ms),
+    [dict(k, slice_rows, run_order, screened_out, memo_rows, build_ms, enum_ms,
+    total_ms)])."""
     ga, d = _gens(g)
     cap = 64
     arr = (fz_tune_entry_t * cap)()
@@ -444,6 +445,7 @@ def fz_autotune_report(g: Sequence[int], n: int, stream=None):
     _check(lib().fz_autotune_report(ga, d, int(n), arr, cap, ctypes.byref(got), ctypes.byref(o),
                                     ctypes.byref(ms), _stream(stream)))
     entries = [dict(k=int(e.k), slice_rows=int(e.slice_rows), run_order=int(e.run_order),
+                    screened_out=int(e.screened_out),
                     memo_rows=int(e.memo_rows), build_ms=float(e.build_ms),
                     enum_ms=float(e.enum_ms), total_ms=float(e.total_ms))
                for e in arr[:got.value]]

@@ -486,6 +486,27 @@ uint64_t rows_in(const fz_plan_s *p, uint64_t b, uint64_t e) {
 // ---------------------------------------------------------------------------
 constexpr int HOST_STAGES = 3;
 
+// True when the current device reads and writes pageable host memory through
+// the host's page tables (cudaDevAttrPageableMemoryAccess and
+// ...UsesHostPageTables both 1).  FZ_HOST_DIRECT=0 turns the direct path off
+// (tuning and testing only).
+bool pageable_direct_ok() {
+    static const bool allowed = [] {
+        const char *e = std::getenv("FZ_HOST_DIRECT");
+        return !(e && e[0] == '0');
+    }();
+    if (!allowed) return false;
+    int dev = 0, pma = 0, hpt = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&pma, cudaDevAttrPageableMemoryAccess, dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&hpt, cudaDevAttrPageableMemoryAccessUsesHostPageTables, dev) !=
+            cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return pma == 1 && hpt == 1;
+}
+
 struct StagePool {
     std::mutex mu;  // held by the call using the pool
     char *base = nullptr;
@@ -971,45 +992,33 @@ int fz_memo_release(fz_memo_t memo) {
 }
 
 // ----------------------------------------------------------------- tuning
-// Time one plan: its rebuild (count tables + memo), then the enumeration of
-// `windows` rank windows of `wrows` rows spread evenly over the set, in ms.
-static int time_plan(fz_plan_t p, int32_t *buf, uint64_t wrows, int windows, cudaStream_t s,
-                     double *build_ms, double *enum_ms_per_row) {
+// One timed pass of a plan: its rebuild (count tables + memo), then the
+// enumeration of ranks [0, rows) in windows of at most `wrows` rows, all
+// written to the same buffer (each window a full launch over the GPU).
+static int time_pass(fz_plan_t p, int32_t *buf, uint64_t wrows, uint64_t rows, cudaStream_t s,
+                     double *build_ms, double *enum_ms) {
     cudaEvent_t e0, e1, e2;
     FZ_CUDA_TRY(cudaEventCreate(&e0));
     FZ_CUDA_TRY(cudaEventCreate(&e1));
     FZ_CUDA_TRY(cudaEventCreate(&e2));
-    int rc = FZ_OK;
-    double bsum = 0, esum = 0;
-    uint64_t rows_done = 0;
-    for (int rep = 0; rep < 3 && rc == FZ_OK; ++rep) {  // rep 0 warms up
-        cudaEventRecord(e0, s);
-        rc = fz_plan_rebuild(p, s);
-        cudaEventRecord(e1, s);
-        uint64_t rows = 0;
-        for (int w = 0; w < windows && rc == FZ_OK; ++w) {
-            const uint64_t span = p->count > wrows ? p->count - wrows : 0;
-            const uint64_t b = windows > 1 ? span * (uint64_t)w / (uint64_t)(windows - 1) : 0;
-            uint64_t got = 0;
-            rc = fz_plan_enumerate(p, b & ~31ull, (b & ~31ull) + wrows, buf, wrows, &got, s);
-            rows += got;
-        }
-        cudaEventRecord(e2, s);
-        if (rc == FZ_OK) rc = fz_plan_sync(p, s);
-        float b_ms = 0, e_ms = 0;
-        cudaEventElapsedTime(&b_ms, e0, e1);
-        cudaEventElapsedTime(&e_ms, e1, e2);
-        if (rep > 0) {
-            bsum += b_ms;
-            esum += e_ms;
-            rows_done += rows;
-        }
+    cudaEventRecord(e0, s);
+    int rc = fz_plan_rebuild(p, s);
+    cudaEventRecord(e1, s);
+    for (uint64_t b = 0; b < rows && rc == FZ_OK; b += wrows) {
+        uint64_t got = 0;
+        const uint64_t e = std::min(rows, b + wrows);
+        rc = fz_plan_enumerate(p, b, e, buf, wrows, &got, s);
     }
+    cudaEventRecord(e2, s);
+    if (rc == FZ_OK) rc = fz_plan_sync(p, s);
+    float b_ms = 0, en_ms = 0;
+    cudaEventElapsedTime(&b_ms, e0, e1);
+    cudaEventElapsedTime(&en_ms, e1, e2);
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     cudaEventDestroy(e2);
-    *build_ms = bsum / 2;
-    *enum_ms_per_row = rows_done ? esum / (double)rows_done : 0.0;
+    *build_ms = b_ms;
+    *enum_ms = en_ms;
     return rc;
 }
 
@@ -1021,7 +1030,7 @@ int fz_autotune_report(const int32_t *g, int d, int32_t n, fz_tune_entry_t *entr
         return set_error(FZ_EINVAL, "entries: null pointer");
     if (n_entries) *n_entries = 0;
     cudaStream_t s = as_stream(stream);
-    // the heuristic plan gives the count and the depths worth trying
+    // the heuristic plan gives the count and the first depth to try
     fz_plan_t p0 = nullptr;
     fz_opts_t o0{FZ_AUTO, FZ_AUTO, 0, 0};
     {
@@ -1036,10 +1045,13 @@ int fz_autotune_report(const int32_t *g, int d, int32_t n, fz_tune_entry_t *entr
     *best = fz_opts_t{k0, FZ_AUTO, 0, 0};
     if (best_ms) *best_ms = 0;
     if (count == 0 || d == 1) return FZ_OK;
-    // sample: four windows, at most 2^24 rows and 256 MB in total
-    const int windows = 4;
-    uint64_t wrows = std::min<uint64_t>(count / windows, (1ull << 22));
-    wrows = std::min<uint64_t>(wrows, (256ull << 20) / (4ull * d * windows));
+    // Candidates are timed on the whole set: a sample of small windows
+    // leaves most warps idle and favours small work items.  The output goes
+    // to one scratch buffer of the whole set when it fits in a third of the
+    // free device memory, else to windows of that size.
+    size_t fr = 0, tot = 0;
+    FZ_CUDA_TRY(cudaMemGetInfo(&fr, &tot));
+    uint64_t wrows = std::min<uint64_t>(count, (uint64_t)(fr / 3) / (4ull * d));
     wrows = std::max<uint64_t>(32, wrows & ~31ull);
     DevBuf buf;
     rc = buf.alloc(wrows * (size_t)d * 4 + 256);
@@ -1047,42 +1059,66 @@ int fz_autotune_report(const int32_t *g, int d, int32_t n, fz_tune_entry_t *entr
     double best_t = 1e300;
     fz_opts_t best_o = *best;
     int found = 0;
-    std::vector<int> ks;
-    for (int k = 0; k <= std::min(d - 1, 4); ++k) ks.push_back(k);
+    // the size rule's depth first (a good time early lets slow candidates
+    // be screened out after one pass), then every other depth that fits
+    std::vector<int> ks{k0};
+    for (int k = std::min(d - 1, 4); k >= 0; --k)
+        if (k != k0) ks.push_back(k);
     for (int k : ks) {
         fz_opts_t o{k, FZ_AUTO, 0, 0};
         fz_plan_t p = nullptr;
-        if (fz_plan_create(g, d, n, &o, &p, stream) != FZ_OK) continue;  // memo too large
+        if (fz_plan_create(g, d, n, &o, &p, stream) != FZ_OK) {  // memo too large
+            cudaGetLastError();
+            continue;
+        }
         if (p->memo_rows * (uint64_t)(4 * k + 8) > std::max<uint64_t>(64ull << 20, count * d)) {
             fz_plan_destroy(p);
             continue;
         }
         const uint64_t base_slice = p->slice_rows;
-        for (uint64_t sl : {base_slice / 2, base_slice, base_slice * 2}) {
+        for (uint64_t sl : {base_slice, base_slice / 2, base_slice * 2}) {
             if (sl < 1024) continue;
             p->slice_rows = (sl + 31) & ~31ull;
-            double b_ms = 0, e_row = 0;
-            rc = time_plan(p, buf.as<int32_t>(), wrows, windows, s, &b_ms, &e_row);
+            // screening pass (also the warm-up): one window, scaled to the set
+            double b_ms = 0, e_ms = 0;
+            const uint64_t first = std::min(count, wrows);
+            rc = time_pass(p, buf.as<int32_t>(), wrows, first, s, &b_ms, &e_ms);
             if (rc != FZ_OK) {
                 fz_plan_destroy(p);
                 return rc;
             }
-            const double t = b_ms + e_row * (double)count;
+            const double screen = b_ms + e_ms * (double)count / (double)first;
+            double t = screen, bsum = 0, esum = 0;
+            const bool hopeless = best_t < 1e300 && screen > 4.0 * best_t;
+            if (!hopeless) {
+                for (int rep = 0; rep < 2 && rc == FZ_OK; ++rep) {
+                    rc = time_pass(p, buf.as<int32_t>(), wrows, count, s, &b_ms, &e_ms);
+                    bsum += b_ms;
+                    esum += e_ms;
+                }
+                if (rc != FZ_OK) {
+                    fz_plan_destroy(p);
+                    return rc;
+                }
+                t = (bsum + esum) / 2;
+            }
             if (found < capacity) {
                 fz_tune_entry_t &E = entries[found];
                 E.k = k;
                 E.slice_rows = (int32_t)p->slice_rows;
                 E.run_order = p->run_memo ? 1 : 0;
+                E.screened_out = hopeless ? 1 : 0;
                 E.memo_rows = p->memo_rows;
-                E.build_ms = b_ms;
-                E.enum_ms = e_row * (double)count;
+                E.build_ms = hopeless ? b_ms : bsum / 2;
+                E.enum_ms = hopeless ? e_ms * (double)count / (double)first : esum / 2;
                 E.total_ms = t;
             }
             ++found;
-            if (t < best_t) {
+            if (!hopeless && t < best_t) {
                 best_t = t;
                 best_o = fz_opts_t{k, FZ_AUTO, (int32_t)p->slice_rows, 0};
             }
+            if (hopeless) break;  // other work-item sizes will not rescue this depth
         }
         fz_plan_destroy(p);
     }
@@ -1233,6 +1269,19 @@ int fz_enumerate_host_chunks(const int32_t *g, int d, int32_t n, const fz_opts_t
         return rc;
     }
     cudaGetLastError();  // pageable memory: the query above may have set an error
+    // Devices that reach pageable host memory through the host's own page
+    // tables (address translation services over a coherent link, as on
+    // Grace-Blackwell) are written directly by the kernel, as pinned memory
+    // is; elsewhere, or when a chunk size is asked for, the rows go through
+    // the staging ring.
+    if (chunk_rows == 0 && pageable_direct_ok()) {
+        EnumLaunch L = launch_of(p);
+        L.plain_stores = true;
+        rc = launch_enumerate(L, rank_begin, rows, out_host, p->slice_rows, s);
+        if (rc == FZ_OK) rc = fz_plan_sync(p, stream);
+        fz_plan_destroy(p);
+        return rc;
+    }
     rc = stream_to_pageable(p, rank_begin, rows, out_host, chunk_rows, s);
     const int rc2 = fz_plan_sync(p, stream);
     if (rc == FZ_OK) rc = rc2;

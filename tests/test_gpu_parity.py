@@ -163,6 +163,25 @@ def test_measured_autotune(fz):
         assert np.array_equal(run_enum(fz, g, n), oracle.enumerate_desc(g, n)), (g, n)
 
 
+def test_autotune_report(fz):
+    """Every candidate the tuner timed is reported; the best one is the
+    fastest candidate not screened out, and plans then use it."""
+    g = (56, 90, 96, 127, 146, 178)
+    n = 16000
+    (k, slice_rows, ms), cands = fz.fz_autotune_report(g, n)
+    assert cands, "no candidate timed"
+    timed = [c for c in cands if not c["screened_out"]]
+    fastest = min(timed, key=lambda c: c["total_ms"])
+    assert (k, slice_rows) == (fastest["k"], fastest["slice_rows"])
+    assert abs(ms - fastest["total_ms"]) < 1e-9
+    for c in cands:
+        assert c["build_ms"] >= 0 and c["enum_ms"] > 0
+        assert abs(c["total_ms"] - c["build_ms"] - c["enum_ms"]) < 1e-6 * max(1.0, c["total_ms"])
+    with fz.Plan(g, n) as plan:
+        assert (plan.k, plan.slice_rows) == (k, slice_rows)
+    assert np.array_equal(run_enum(fz, g, n), oracle.enumerate_desc(g, n))
+
+
 @pytest.mark.parametrize("d", [2, 3, 5, 6, 7, 9, 12, 16])
 def test_small_slices_ring_boundaries(fz, d):
     """Tiny slices and many ring halves: every flush path, every tuple width."""
@@ -372,15 +391,18 @@ def test_enumerate_host_streamed_many_chunks(fz, g, n, chunk, begin, end):
     assert np.array_equal(again.reshape(want.shape), want)
 
 
-def test_enumerate_host_streamed_large(fz):
-    """A streamed output of 1.09 GB (45,216,350 rows) with the default chunk:
-    nine chunks of 128 MB through the three staging buffers, every row checked
-    against the oracle's digest, plus the first rows element by element."""
+@pytest.mark.parametrize("chunk", [0, 5_000_000])
+def test_enumerate_host_streamed_large(fz, chunk):
+    """A pageable output of 1.09 GB (45,216,350 rows): the default path
+    (direct writes where the device reaches pageable memory through the
+    host's page tables, else 128 MB chunks through the staging ring) and the
+    ring with nine chunks of 5,000,000 rows; every row checked against the
+    oracle's digest, plus the first rows element by element."""
     g = (56, 90, 96, 127, 146, 178)
     n = 24000
     total = oracle.count(g, n)
     out = np.empty(total * len(g), dtype=np.int32)
-    w = fz.fz_enumerate_host(g, n, out)
+    w = fz.fz_enumerate_host(g, n, out, chunk_rows=chunk)
     assert w == total
     rows = out.reshape(total, len(g))
     head = oracle.enumerate_desc(g, n, 0, 20000)
