@@ -656,7 +656,7 @@ def _event_time(torch, fn, steps, warmup):
     return a.elapsed_time(b) / steps
 
 
-def measure_batch(torch, fz, steps, warmup, count=4096, only_d=0, pi_steps=5):
+def measure_batch(torch, fz, steps, warmup, count=4096, only_d=0, pi_steps=5, autotune=True):
     """Config 4: ``count`` instances (d 3..8, generators in [2,300], |Z|
     log-uniform in [1e2,1e6]) in one persistent launch -- the step (batched
     counting tables, memos and enumeration) replayed as a captured CUDA
@@ -668,6 +668,18 @@ def measure_batch(torch, fz, steps, warmup, count=4096, only_d=0, pi_steps=5):
     if only_d:
         insts = [x for x in insts if len(x.g) == only_d]
     inst = [(x.g, workloads.find_n(fz.fz_count_upto, x.g, x.target, 64)) for x in insts]
+    tune = None
+    if autotune:
+        # memo depth policy and layout per tuple width, measured on samples
+        t0 = time.perf_counter()
+        cands, chosen = fz.fz_batch_autotune(inst)
+        tune = {"by": "fz_batch_autotune: rebuild + enumeration of up to 256 sampled "
+                      "instances per width under each candidate (measured)",
+                "seconds": time.perf_counter() - t0,
+                "chosen": {str(d): {"cap_rows": c, "run_order": r}
+                           for d, (c, r) in chosen.items()},
+                "candidates": [{k: (round(v, 4) if isinstance(v, float) else v)
+                                for k, v in c.items()} for c in cands]}
     b = fz.Batch(inst)
     out = torch.empty(int(b.total_words) + 16, dtype=torch.int32, device="cuda")
     side = torch.cuda.Stream()
@@ -730,6 +742,7 @@ def measure_batch(torch, fz, steps, warmup, count=4096, only_d=0, pi_steps=5):
                "achieved": bytes_out / (ms_enum / 1e3) / 1e9, "peak": peak[0],
                "unit": "GB/s", "frac": bytes_out / (ms_enum / 1e3) / 1e9 / peak[0],
                "peak_source": peak[1]},
+           "memo_policy": tune if tune else "hand-set rule (cap 4x rows at d >= 6, 1x below)",
            "setup_s": time.perf_counter() - t_setup}
     if graph_err:
         rec["graph_error"] = graph_err
@@ -740,7 +753,7 @@ def measure_batch(torch, fz, steps, warmup, count=4096, only_d=0, pi_steps=5):
 def run_batch_workload(args):
     torch, fz = _gpu_env()
     r = measure_batch(torch, fz, args.steps, args.warmup, args.batch_count, args.batch_d,
-                      pi_steps=args.batch_pi_steps)
+                      pi_steps=args.batch_pi_steps, autotune=not args.no_autotune)
     rec = {"metric": "Factorizations/s, batched (%d instances, one persistent launch)"
                      % r["instances"],
            "value": r["value"], "unit": UNIT, "n_gpus": 1, "steps": args.steps,

@@ -386,6 +386,41 @@ int fz_plan_batch(const fz_instance_t *inst, int count, const fz_opts_t *opt,
                   uint64_t *word_offsets, uint64_t *rows, uint64_t *words_needed,
                   void *stream);
 
+/* Measured choice of memos for batches (the memo depth, Section 3.1's
+ * memoDim, and the memo layout).  A batch chooses per generator set the
+ * deepest full memo whose estimated rows stay within cap_rows times the
+ * instance's estimated rows (else a partial depth-3 memo for d >= 5, else
+ * the closed form of the last two generators), and keeps full memos of
+ * depth <= 3 in run order when run_order is set; both are per tuple width.
+ * fz_batch_autotune times, on the device, a sample of up to 256 of the
+ * given instances of each width >= 3 under cap_rows in {0, 1/4, 1, 4, 16}
+ * with run order on and off (rebuild + enumeration, mean of 3 after a
+ * warm-up; candidates that choose the same memos are timed once) and keeps
+ * the fastest per width for later fz_batch_create calls on this device
+ * (with opts.k = FZ_AUTO).  Up to `capacity` timed candidates go to
+ * `entries` (host, may be NULL when capacity is 0), their number to
+ * *n_entries.  Synchronises.  Errors: as fz_batch_create. */
+typedef struct fz_batch_tune_entry {
+    int32_t d;          /* tuple width of the sample */
+    int32_t run_order;  /* layout candidate: 1 = run order allowed */
+    int32_t instances;  /* sampled instances */
+    int32_t memos;      /* distinct memos built */
+    double cap_rows;    /* depth candidate: memo rows per instance row */
+    uint64_t rows;      /* output rows of the sample */
+    uint64_t memo_rows; /* memo rows built */
+    double build_ms;    /* rebuild: tables + memos (measured) */
+    double enum_ms;     /* enumeration (measured) */
+    double total_ms;
+} fz_batch_tune_entry_t;
+int fz_batch_autotune(const fz_instance_t *inst, int count, fz_batch_tune_entry_t *entries,
+                      int capacity, int *n_entries, void *stream);
+/* The policy in force for width d on the current device (measured by
+ * fz_batch_autotune, else the hand-set default: cap_rows 4 for d >= 6, 1
+ * below, run order on).  Either pointer may be NULL.  Errors: FZ_EINVAL. */
+int fz_batch_policy(int32_t d, double *cap_rows, int32_t *run_order);
+/* Forget the measured policy of the current device (back to the default). */
+int fz_batch_policy_reset(void);
+
 /* One-shot: create + enumerate + sync + destroy.  word_offsets (host,
  * count + 1, may be NULL) and *words_needed receive the layout.  Errors: as
  * above; FZ_ENOSPC when out_capacity_words is too small (nothing written). */

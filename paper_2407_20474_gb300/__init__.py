@@ -50,7 +50,7 @@ EXPORTS = (
     "fz_enumerate", "fz_enumerate_host", "fz_enumerate_host_chunks",
     "fz_batch_create", "fz_batch_info", "fz_batch_layout", "fz_batch_rebuild",
     "fz_batch_enumerate", "fz_batch_sync", "fz_batch_destroy", "fz_enumerate_batch",
-    "fz_plan_batch",
+    "fz_plan_batch", "fz_batch_autotune", "fz_batch_policy", "fz_batch_policy_reset",
     "fz_serve_create", "fz_serve_register", "fz_serve_submit", "fz_serve_poll",
     "fz_serve_wait", "fz_serve_copy", "fz_serve_release", "fz_serve_stats", "fz_serve_destroy",
     "fz_serve_submit_gens", "fz_serve_cancel",
@@ -90,6 +90,14 @@ class fz_memo_info_t(ctypes.Structure):
 class fz_instance_t(ctypes.Structure):
     _fields_ = [("g", ctypes.POINTER(ctypes.c_int32)), ("d", ctypes.c_int32),
                 ("n", ctypes.c_int32)]
+
+
+class fz_batch_tune_entry_t(ctypes.Structure):
+    _fields_ = [("d", ctypes.c_int32), ("run_order", ctypes.c_int32),
+                ("instances", ctypes.c_int32), ("memos", ctypes.c_int32),
+                ("cap_rows", ctypes.c_double), ("rows", ctypes.c_uint64),
+                ("memo_rows", ctypes.c_uint64), ("build_ms", ctypes.c_double),
+                ("enum_ms", ctypes.c_double), ("total_ms", ctypes.c_double)]
 
 
 class fz_batch_info_t(ctypes.Structure):
@@ -182,6 +190,12 @@ _SIGS = {
     "fz_batch_enumerate": (ctypes.c_int, [_P, _P, ctypes.c_uint64, _P]),
     "fz_batch_sync": (ctypes.c_int, [_P, _P]),
     "fz_batch_destroy": (ctypes.c_int, [_P]),
+    "fz_batch_autotune": (ctypes.c_int, [ctypes.POINTER(fz_instance_t), ctypes.c_int,
+                                         ctypes.POINTER(fz_batch_tune_entry_t), ctypes.c_int,
+                                         ctypes.POINTER(ctypes.c_int), _P]),
+    "fz_batch_policy": (ctypes.c_int, [ctypes.c_int32, ctypes.POINTER(ctypes.c_double),
+                                       ctypes.POINTER(ctypes.c_int32)]),
+    "fz_batch_policy_reset": (ctypes.c_int, []),
     "fz_plan_batch": (ctypes.c_int, [ctypes.POINTER(fz_instance_t), ctypes.c_int,
                                      ctypes.POINTER(fz_opts_t), _U64P, _U64P, _U64P, _P]),
     "fz_enumerate_batch": (ctypes.c_int, [ctypes.POINTER(fz_instance_t), ctypes.c_int,
@@ -639,6 +653,39 @@ class Batch:
 
     def __exit__(self, *a):
         self.close()
+
+
+def fz_batch_autotune(instances, stream=None):
+    """Measure the memo policy per tuple width on a sample of ``instances``
+    ([(g, n), ...]); later batches on this device use it.  Returns the timed
+    candidates as dicts and the chosen policy {d: (cap_rows, run_order)}."""
+    arr, keep = _instances(instances)
+    cap = 256
+    ent = (fz_batch_tune_entry_t * cap)()
+    got = ctypes.c_int(0)
+    _check(lib().fz_batch_autotune(arr, len(instances), ent, cap, ctypes.byref(got),
+                                   _stream(stream)))
+    rows = [dict(d=int(e.d), run_order=int(e.run_order), instances=int(e.instances),
+                 memos=int(e.memos), cap_rows=float(e.cap_rows), rows=int(e.rows),
+                 memo_rows=int(e.memo_rows), build_ms=float(e.build_ms),
+                 enum_ms=float(e.enum_ms), total_ms=float(e.total_ms))
+            for e in ent[:got.value]]
+    chosen = {}
+    for d in sorted({len(g) for g, _ in instances}):
+        chosen[d] = fz_batch_policy(d)
+    return rows, chosen
+
+
+def fz_batch_policy(d: int):
+    """(cap_rows, run_order) of the batch memo policy for width d."""
+    c = ctypes.c_double(0.0)
+    r = ctypes.c_int32(0)
+    _check(lib().fz_batch_policy(int(d), ctypes.byref(c), ctypes.byref(r)))
+    return float(c.value), bool(r.value)
+
+
+def fz_batch_policy_reset():
+    _check(lib().fz_batch_policy_reset())
 
 
 def fz_plan_batch(instances, k: int = FZ_AUTO, top: int = FZ_AUTO, stream=None):

@@ -14,6 +14,7 @@
 #include <algorithm>
 #include <cstring>
 #include <map>
+#include <mutex>
 #include <vector>
 
 #include "fz_internal.cuh"
@@ -28,6 +29,9 @@ struct DevArena {
         if (p) cudaFree(p);
     }
     int alloc(size_t b) {
+        if (p) cudaFree(p);
+        p = nullptr;
+        bytes = 0;
         if (b == 0) b = 256;
         cudaError_t e = cudaMalloc(&p, b);
         if (e != cudaSuccess) {
@@ -323,7 +327,41 @@ double volume_rows(const Inst &I, int n) {
 // cost about 12 warp instructions per output row.
 constexpr double RUN_PAIR_CAP = 2.0;
 
-void choose_batch_memo(Inst &I, int n_set) {
+// How a batch chooses memos, per tuple width d: the memo rows allowed per
+// estimated instance row (cap_rows, see choose_batch_memo) and whether full
+// memos of depth <= 3 are also kept in run order.  The defaults are the
+// hand-set rule; fz_batch_autotune replaces them per device by the fastest
+// measured candidates.
+struct BatchPolicy {
+    double cap_rows[FZ_MAX_D + 1];
+    bool run_order[FZ_MAX_D + 1];
+};
+
+BatchPolicy default_policy() {
+    BatchPolicy P;
+    for (int d = 0; d <= FZ_MAX_D; ++d) {
+        // the batch walk pays per memo leaf, so deeper memos (fewer, larger
+        // leaves) repaid their build at d >= 6 up to ~4x the instance's rows
+        // (config 4: d = 6..8 enumeration 11.9 -> 4.1 ms for 1.6 ms more
+        // build); at d <= 5 they did not
+        P.cap_rows[d] = d >= 6 ? 4.0 : 1.0;
+        P.run_order[d] = true;
+    }
+    return P;
+}
+
+std::mutex g_policy_mu;
+std::map<int, BatchPolicy> g_policy;  // by device ordinal, set by fz_batch_autotune
+
+BatchPolicy current_policy() {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    std::lock_guard<std::mutex> lk(g_policy_mu);
+    auto it = g_policy.find(dev);
+    return it == g_policy.end() ? default_policy() : it->second;
+}
+
+void choose_batch_memo(Inst &I, int n_set, double cap_rows) {
     I.K = 0;
     I.top = 0;
     I.pair = false;
@@ -331,11 +369,6 @@ void choose_batch_memo(Inst &I, int n_set) {
     double count = 1.0 / (double)I.g[I.d - 1];
     for (int i = 0; i < I.d - 1; ++i) count *= (double)n_set / (double)(i + 1) / (double)I.g[i];
     int64_t part_top = 0;
-    // memo rows allowed per estimated instance row: the batch walk pays per
-    // memo leaf, so deeper memos (fewer, larger leaves) repay their build at
-    // d >= 6 up to ~4x the instance's rows (config 4: d = 6..8 enumeration
-    // 11.9 -> 4.1 ms for 1.6 ms more build); at d <= 5 they did not
-    const double cap_rows = I.d >= 6 ? 4.0 : 1.0;
     for (int k = I.d - 1; k >= 3; --k) {
         int32_t tmin = I.g[I.d - k];
         double prod = 1.0;
@@ -370,12 +403,31 @@ void choose_batch_memo(Inst &I, int n_set) {
 
 extern "C" {
 
+namespace fz {
+namespace {
+
+int batch_create_impl(const fz_instance_t *inst, int count, const fz_opts_t *opt,
+                      const BatchPolicy &pol, fz_batch_t *batch, cudaStream_t s);
+
+}  // namespace
+}  // namespace fz
+
 int fz_batch_create(const fz_instance_t *inst, int count, const fz_opts_t *opt,
                     fz_batch_t *batch, void *stream) {
+    return batch_create_impl(inst, count, opt, current_policy(), batch,
+                             static_cast<cudaStream_t>(stream));
+}
+
+}  // extern "C"
+
+namespace fz {
+namespace {
+
+int batch_create_impl(const fz_instance_t *inst, int count, const fz_opts_t *opt,
+                      const BatchPolicy &pol, fz_batch_t *batch, cudaStream_t s) {
     if (!batch) return set_error(FZ_EINVAL, "batch: null pointer");
     if (count < 0 || (count > 0 && !inst)) return set_error(FZ_EINVAL, "instances");
     if (opt && opt->flags != 0) return set_error(FZ_EINVAL, "opts.flags must be 0");
-    cudaStream_t s = static_cast<cudaStream_t>(stream);
     fz_batch_s *b = new (std::nothrow) fz_batch_s;
     if (!b) return set_error(FZ_ENOMEM, "host allocation");
     auto fail = [&](int rc) {
@@ -403,7 +455,7 @@ int fz_batch_create(const fz_instance_t *inst, int count, const fz_opts_t *opt,
         I.d = x.d;
         I.n = x.n;
         for (int j = 0; j < x.d; ++j) I.g[j] = x.g[j];
-        choose_batch_memo(I, n_set[std::vector<int32_t>(x.g, x.g + x.d)]);
+        choose_batch_memo(I, n_set[std::vector<int32_t>(x.g, x.g + x.d)], pol.cap_rows[x.d]);
         if (opt && opt->k != FZ_AUTO) {
             if (opt->k < 0 || opt->k > x.d - 1)
                 return fail(set_error(FZ_EINVAL, "opts.k must be in 0..d-1 for every instance"));
@@ -423,7 +475,8 @@ int fz_batch_create(const fz_instance_t *inst, int count, const fz_opts_t *opt,
         // coordinate, width <= 8 (the batch walk's run copy); the pair's
         // closed form gets a run-order table when that stays small
         I.run = false;
-        if (run_memo_enabled() && I.K >= 1 && I.K <= 3 && I.top > I.n && I.d <= 8 &&
+        if (run_memo_enabled() && pol.run_order[I.d] && I.K >= 1 && I.K <= 3 && I.top > I.n &&
+            I.d <= 8 &&
             I.d - I.K - 1 >= 1) {
             if (!I.pair) {
                 I.run = true;
@@ -759,6 +812,11 @@ int fz_batch_create(const fz_instance_t *inst, int count, const fz_opts_t *opt,
     return FZ_OK;
 }
 
+}  // namespace
+}  // namespace fz
+
+extern "C" {
+
 int fz_batch_info(fz_batch_t b, fz_batch_info_t *info) {
     if (!b || !info) return set_error(FZ_EINVAL, "null pointer");
     info->count = b->count;
@@ -847,6 +905,153 @@ int fz_enumerate_batch(const fz_instance_t *inst, int count, const fz_opts_t *op
     if (rc == FZ_OK) rc = fz_batch_sync(b, stream);
     fz_batch_destroy(b);
     return rc;
+}
+
+int fz_batch_autotune(const fz_instance_t *inst, int count, fz_batch_tune_entry_t *entries,
+                      int capacity, int *n_entries, void *stream) {
+    if (count < 0 || (count > 0 && !inst)) return set_error(FZ_EINVAL, "instances");
+    if (capacity < 0 || (capacity > 0 && !entries))
+        return set_error(FZ_EINVAL, "entries: null pointer");
+    if (n_entries) *n_entries = 0;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    for (int i = 0; i < count; ++i) {
+        int rc = validate_gens(inst[i].g, inst[i].d);
+        if (rc != FZ_OK) return rc;
+        if (inst[i].n < 0) return set_error(FZ_EINVAL, "n must be >= 0");
+    }
+    BatchPolicy tuned = current_policy();
+    const BatchPolicy base = tuned;
+    static const double caps[] = {0.0, 0.25, 1.0, 4.0, 16.0};
+    int found = 0;
+    cudaEvent_t e0, e1, e2;
+    FZ_CUDA_TRY(cudaEventCreate(&e0));
+    FZ_CUDA_TRY(cudaEventCreate(&e1));
+    FZ_CUDA_TRY(cudaEventCreate(&e2));
+    int rc = FZ_OK;
+    DevArena out;
+    for (int d = 3; d <= FZ_MAX_D && rc == FZ_OK; ++d) {
+        // a sample of this width: up to 256 instances spread over the list
+        std::vector<fz_instance_t> all;
+        for (int i = 0; i < count; ++i)
+            if (inst[i].d == d) all.push_back(inst[i]);
+        if (all.empty()) continue;
+        std::vector<fz_instance_t> sub;
+        const size_t step = (all.size() + 255) / 256;
+        for (size_t i = 0; i < all.size(); i += step) sub.push_back(all[i]);
+        double best_t = 1e300;
+        double best_cap = base.cap_rows[d];
+        bool best_run = base.run_order[d];
+        std::vector<std::pair<double, bool>> cands;
+        for (double c : caps) cands.push_back({c, true});
+        for (double c : caps) cands.push_back({c, false});
+        std::vector<std::vector<int>> seen;  // memo depth and layout choices already timed
+        for (auto &cand : cands) {
+            BatchPolicy pol = tuned;
+            pol.cap_rows[d] = cand.first;
+            pol.run_order[d] = cand.second;
+            fz_batch_t b = nullptr;
+            rc = batch_create_impl(sub.data(), (int)sub.size(), nullptr, pol, &b, s);
+            if (rc == FZ_ENOMEM || rc == FZ_EINVAL) {  // too large for this device: skip
+                cudaGetLastError();
+                rc = FZ_OK;
+                continue;
+            }
+            if (rc != FZ_OK) break;
+            // candidates that choose the same memos as one already timed are
+            // not timed again
+            std::vector<int> key;
+            for (const Inst &I : b->inst) {
+                key.push_back(I.K);
+                key.push_back(I.top);
+                key.push_back(I.pair ? 1 : 0);
+                key.push_back(I.run ? 1 : 0);
+            }
+            bool dup = false;
+            for (auto &k : seen) dup = dup || k == key;
+            if (dup) {
+                fz_batch_destroy(b);
+                continue;
+            }
+            seen.push_back(key);
+            if (out.bytes < b->total_words * 4 + 256) {
+                rc = out.alloc(b->total_words * 4 + 256);
+                if (rc != FZ_OK) {
+                    fz_batch_destroy(b);
+                    break;
+                }
+            }
+            double bsum = 0, esum = 0;
+            for (int rep = 0; rep < 4 && rc == FZ_OK; ++rep) {  // rep 0 warms up
+                cudaEventRecord(e0, s);
+                rc = fz_batch_rebuild(b, s);
+                cudaEventRecord(e1, s);
+                if (rc == FZ_OK)
+                    rc = fz_batch_enumerate(b, static_cast<int32_t *>(out.p), b->total_words, s);
+                cudaEventRecord(e2, s);
+                if (rc == FZ_OK) rc = fz_batch_sync(b, s);
+                float b_ms = 0, e_ms = 0;
+                cudaEventElapsedTime(&b_ms, e0, e1);
+                cudaEventElapsedTime(&e_ms, e1, e2);
+                if (rep > 0) {
+                    bsum += b_ms;
+                    esum += e_ms;
+                }
+            }
+            if (rc == FZ_OK) {
+                const double t = (bsum + esum) / 3;
+                if (found < capacity) {
+                    fz_batch_tune_entry_t &E = entries[found];
+                    E.d = d;
+                    E.run_order = cand.second ? 1 : 0;
+                    E.instances = (int32_t)sub.size();
+                    E.memos = b->nmemo;
+                    E.cap_rows = cand.first;
+                    E.rows = b->total_rows;
+                    uint64_t mr = 0;
+                    for (const MemoJob &J : b->memo_jobs) mr += J.rows;
+                    E.memo_rows = mr;
+                    E.build_ms = bsum / 3;
+                    E.enum_ms = esum / 3;
+                    E.total_ms = t;
+                }
+                ++found;
+                if (t < best_t) {
+                    best_t = t;
+                    best_cap = cand.first;
+                    best_run = cand.second;
+                }
+            }
+            fz_batch_destroy(b);
+        }
+        tuned.cap_rows[d] = best_cap;
+        tuned.run_order[d] = best_run;
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    cudaEventDestroy(e2);
+    if (rc != FZ_OK) return rc;
+    if (n_entries) *n_entries = std::min(found, capacity);
+    int dev = 0;
+    cudaGetDevice(&dev);
+    std::lock_guard<std::mutex> lk(g_policy_mu);
+    g_policy[dev] = tuned;
+    return FZ_OK;
+}
+
+int fz_batch_policy(int32_t d, double *cap_rows, int32_t *run_order) {
+    if (d < 1 || d > FZ_MAX_D) return set_error(FZ_EINVAL, "d out of range");
+    const BatchPolicy P = current_policy();
+    if (cap_rows) *cap_rows = P.cap_rows[d];
+    if (run_order) *run_order = P.run_order[d] ? 1 : 0;
+    return FZ_OK;
+}
+
+int fz_batch_policy_reset(void) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    std::lock_guard<std::mutex> lk(g_policy_mu);
+    g_policy.erase(dev);
+    return FZ_OK;
 }
 
 }  // extern "C"

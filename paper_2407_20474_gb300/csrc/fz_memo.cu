@@ -547,16 +547,30 @@ __global__ void __launch_bounds__(MB_THREADS) memo_sizes_kernel(const MemoJob *_
     if (threadIdx.x == 0) rows_out[blockIdx.x] = total;
 }
 
-// One CTA of MB_BUILD_THREADS per memo.  Inside an elementwise batch each
-// warp copies whole (element, generator) blocks as flat word copies; a lane
-// loads MB_ILP words before it stores them, so a block of W words costs
-// about W / (32 MB_ILP) L2 round trips.
+// One CTA of MB_BUILD_THREADS per memo.  Inside an elementwise batch the
+// elements are spread over the warps (several warps per element when the
+// batch has fewer elements than warps).  An element's rows are one
+// contiguous range of the memo, the concatenation of its k blocks
+// incr_i(Z_{>=i}(m - t_i)); its warps copy that range as one flat run of
+// words: lane words are consecutive (coalesced stores), each word finds its
+// block in the element's k block descriptors (shared memory, filled by
+// lanes 0..k-1 with one round of parallel loads) and its source word in the
+// suffix block of Z(m - t_i), adding one to coordinate i.  A lane loads
+// MB_ILP words before it stores them, so an element of W words costs one
+// round of descriptor loads plus about W / (32 MB_ILP warps) L2 round trips.
 constexpr int MB_BUILD_THREADS = 1024;
 constexpr int MB_ILP = 8;
+constexpr int MB_WARPS = MB_BUILD_THREADS / 32;
+
+struct MemoBlockDesc {
+    uint64_t end;  // end row of the block in the element (exclusive prefix of lengths)
+    uint64_t src;  // first source row: the suffix Z_{>=i}(m - t_i) of Z(m - t_i)
+};
 
 __global__ void __launch_bounds__(MB_BUILD_THREADS) memo_cta_build_kernel(
     const MemoJob *__restrict__ jobs, int *status) {
     __shared__ uint64_t sums[33];
+    __shared__ MemoBlockDesc desc[MB_WARPS][FZ_MAX_D];
     const MemoJob J = jobs[blockIdx.x];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int nwarps = blockDim.x >> 5;
@@ -577,45 +591,86 @@ __global__ void __launch_bounds__(MB_BUILD_THREADS) memo_cta_build_kernel(
         if (threadIdx.x == 0) atomicExch(status, (int)DEV_INTERNAL);
         return;
     }
+    if (k < 1 || k > FZ_MAX_D) {
+        if (threadIdx.x == 0) atomicExch(status, (int)DEV_INTERNAL);
+        return;
+    }
+    MemoBlockDesc *dsc = desc[warp];
     // elementwise batches of b elements
     for (int m0 = 0; m0 < J.top; m0 += J.b) {
         const int m1 = m0 + J.b < J.top ? m0 + J.b : J.top;
-        for (int m = m0 + warp; m < m1; m += nwarps) {
-            uint64_t dst = J.O[m];
-            if (m == 0) {
-                if (lane < k) J.R[lane] = 0;
+        const int nb = m1 - m0;
+        const int wpe = nb >= nwarps ? 1 : nwarps / nb;  // warps per element
+        const int groups = nwarps / wpe;
+        const int sub = warp % wpe;
+        // a lane's word index grows by 32 wpe: rows by rstep, coordinates by cstep
+        const uint64_t wstep = 32ull * (uint64_t)wpe;
+        const uint64_t rstep = wstep / (uint64_t)k;
+        const uint32_t cstep = (uint32_t)(wstep - rstep * (uint64_t)k);
+        for (int e = warp / wpe; e < nb && warp < groups * wpe; e += groups) {
+            const int m = m0 + e;
+            const uint64_t dst0 = J.O[m];
+            if (m == 0) {  // Z(0) = {0}
+                if (sub == 0 && lane < k) J.R[lane] = 0;
                 continue;
             }
-            for (int i = 0; i < k; ++i) {
-                const int src_m = m - J.t[i];
-                if (src_m < 0) continue;
-                const uint64_t len = __ldg(J.Ct + (int64_t)i * J.cs + src_m);
-                if (len == 0) continue;
-                const uint64_t src = J.O[src_m + 1] - len;  // suffix Z_{>=i}(src_m)
-                // the block is a flat copy of len * k words with one added to
-                // every word of coordinate i: word w of the block is
-                // coordinate w mod k of row w div k
-                const uint64_t W = len * (uint64_t)k;
-                const int32_t *a = J.R + src * (uint64_t)k;
-                int32_t *b = J.R + dst * (uint64_t)k;
-                const uint32_t step = (uint32_t)(32 % k);
-                uint32_t c0 = (uint32_t)(lane % k);  // coordinate of word lane
-                for (uint64_t w0 = lane; w0 < W; w0 += 32 * MB_ILP) {
-                    int32_t v[MB_ILP];
-#pragma unroll
-                    for (int u = 0; u < MB_ILP; ++u)
-                        if (w0 + 32 * u < W) v[u] = a[w0 + 32 * u];
-                    uint32_t c = c0;
-#pragma unroll
-                    for (int u = 0; u < MB_ILP; ++u) {
-                        if (w0 + 32 * u < W) b[w0 + 32 * u] = v[u] + (c == (uint32_t)i ? 1 : 0);
-                        c += step;
-                        if (c >= (uint32_t)k) c -= (uint32_t)k;
-                    }
-                    c0 = c;
+            // block descriptors: lane i < k holds block i
+            uint64_t len = 0, src = 0;
+            if (lane < k) {
+                const int sm = m - J.t[lane];
+                if (sm >= 0) {
+                    len = __ldg(J.Ct + (int64_t)lane * J.cs + sm);
+                    src = J.O[sm + 1] - len;  // the suffix block of Z(sm)
                 }
-                dst += len;
             }
+            const uint64_t incl = warp_incl_scan(len, lane);
+            const uint64_t total = shfl_u64(incl, 31);
+            if (lane < k) dsc[lane] = MemoBlockDesc{incl, src};
+            __syncwarp();
+            if (total != J.O[m + 1] - dst0) {  // the block sizes must fill Z(m)
+                if (lane == 0) atomicExch(status, (int)DEV_INTERNAL);
+                __syncwarp();
+                continue;
+            }
+            const uint64_t W = total * (uint64_t)k;
+            int32_t *out = J.R + dst0 * (uint64_t)k;
+            // word w = lane + 32 (sub + wpe t): row r = w div k, coordinate c
+            uint64_t w = (uint64_t)lane + 32ull * (uint64_t)sub;
+            uint64_t r = w / (uint64_t)k;
+            uint32_t c = (uint32_t)(w - r * (uint64_t)k);
+            int j = 0;  // block of row r (rows only grow along a lane)
+            uint64_t jbeg = 0, jend = dsc[0].end, jsrc = dsc[0].src;
+            while (w < W) {
+                int32_t v[MB_ILP];
+                const uint64_t w0 = w;
+#pragma unroll
+                for (int u = 0; u < MB_ILP; ++u) {
+                    v[u] = 0;
+                    if (w < W) {
+                        while (r >= jend) {  // next non-empty block
+                            ++j;
+                            jbeg = jend;
+                            jend = dsc[j].end;
+                            jsrc = dsc[j].src;
+                        }
+                        const uint64_t sw = (jsrc + (r - jbeg)) * (uint64_t)k + c;
+                        v[u] = J.R[sw] + (c == (uint32_t)j ? 1 : 0);
+                    }
+                    w += wstep;
+                    r += rstep;
+                    c += cstep;
+                    if (c >= (uint32_t)k) {
+                        c -= (uint32_t)k;
+                        ++r;
+                    }
+                }
+#pragma unroll
+                for (int u = 0; u < MB_ILP; ++u) {
+                    const uint64_t wu = w0 + (uint64_t)u * wstep;
+                    if (wu < W) out[wu] = v[u];
+                }
+            }
+            __syncwarp();  // dsc is reused by the warp's next element
         }
         __syncthreads();
     }

@@ -75,6 +75,30 @@ def test_plan_batch_layout(fz):
                               oracle.enumerate_desc(g, n)), (g, n)
 
 
+def test_batch_autotune(fz):
+    """The measured memo policy: every width's chosen (cap, layout) is its
+    fastest timed candidate, and batches created under it equal the oracle."""
+    inst = small_instances(43, 150)
+    try:
+        rows, chosen = fz.fz_batch_autotune(inst)
+        assert rows, "no candidate timed"
+        for d, (cap, run) in chosen.items():
+            cands = [r for r in rows if r["d"] == d]
+            if not cands:
+                continue
+            best = min(cands, key=lambda r: r["total_ms"])
+            assert (best["cap_rows"], bool(best["run_order"])) == (cap, run), d
+            for r in cands:
+                assert r["rows"] > 0 and r["total_ms"] > 0
+        b, segs = run_batch(fz, inst)
+        for (g, n), got in zip(inst, segs):
+            assert np.array_equal(got, oracle.enumerate_desc(g, n)), (g, n)
+    finally:
+        fz.fz_batch_policy_reset()
+    assert fz.fz_batch_policy(7) == (4.0, True)
+    assert fz.fz_batch_policy(4) == (1.0, True)
+
+
 def test_batch_pair_memo_leaves(fz):
     """Instances whose memo is the closed form of the last two generators
     (no full memo of depth >= 3 fits): last pair coprime, with a common
