@@ -12,6 +12,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <cstdlib>
 #include <cstring>
 #include <map>
 #include <mutex>
@@ -224,7 +225,10 @@ int build_scan_plan(fz_batch_s *b, uint64_t *table_base, std::vector<ScanJob> &j
             ScanJob &J = jobs[ji];
             const int64_t T = (J.len + J.g - 1) / J.g;
             if (T > DIRECT) {
-                const int64_t nrb = (T + RBk - 1) / RBk;
+                // blocks of at least RBk entries, more for long chains, so
+                // that each chain of block sums is scanned directly
+                J.rb = std::max<int64_t>(RBk, (T + DIRECT - 1) / DIRECT);
+                const int64_t nrb = (T + J.rb - 1) / J.rb;
                 J.slen = nrb * J.g;
                 J.S = reinterpret_cast<uint64_t *>(sw);  // offset, fixed up below
                 J.Sincl = reinterpret_cast<uint64_t *>(sw + (size_t)J.slen);
@@ -326,6 +330,16 @@ double volume_rows(const Inst &I, int n) {
 // fully parallel pass, and replace memo leaves of one to three rows that
 // cost about 12 warp instructions per output row.
 constexpr double RUN_PAIR_CAP = 2.0;
+
+// FZ_BATCH_ORDER=0 numbers the work items in the caller's instance order
+// (tuning only; see the item numbering in batch_create_impl).
+bool batch_item_order_enabled() {
+    static const bool on = [] {
+        const char *e = getenv("FZ_BATCH_ORDER");
+        return !(e && e[0] == '0');
+    }();
+    return on;
+}
 
 // How a batch chooses memos, per tuple width d: the memo rows allowed per
 // estimated instance row (cap_rows, see choose_batch_memo) and whether full
@@ -529,7 +543,9 @@ int batch_create_impl(const fz_instance_t *inst, int count, const fz_opts_t *opt
     std::vector<int> memo_src;  // instance whose table rows feed the memo
     for (int i = 0; i < count; ++i) {
         Inst &I = b->inst[i];
-        if (I.K <= 0 || I.pair) continue;
+        // run-order instances take their rows from the tail's closed form
+        // (depth <= 3): no element-order memo
+        if (I.K <= 0 || I.pair || I.run) continue;
         std::vector<int32_t> key(I.g + (I.d - I.K), I.g + I.d);
         auto it = memo_of.find(key);
         int m;
@@ -677,22 +693,31 @@ int batch_create_impl(const fz_instance_t *inst, int count, const fz_opts_t *opt
             R.g = S.g[lam];
             R.G = (int32_t)std::min<int64_t>(R.g, (int64_t)S.n + 1);
             R.k = S.K;
-            if (S.pair) {
+            // the tail's closed form: k = 1, one row when ta divides p;
+            // k = 2, the pair (t0, t1); k = 3, ta over the pair (t0, t1)
+            if (S.K >= 2) {
                 R.t0 = S.g[S.d - 2];
                 R.t1 = S.g[S.d - 1];
                 int64_t g1;
                 pair_params(R.t0, R.t1, &R.e, &R.h1, &g1, &R.inv);
-                R.expect_rows = pair_rows_upto(S.n, R.t0, R.t1);
-                R.out_rows = R.expect_rows;
-            } else {
-                if (S.memo < 0 || b->memo_jobs[S.memo].top < S.n + 1 ||
-                    b->memo_jobs[S.memo].k != S.K)
-                    return fail(set_error(FZ_EINTERNAL, "run-order memo without its full memo"));
-                const MemoJob &M = b->memo_jobs[S.memo];
-                R.O = M.O;
-                R.rows = M.R;
-                R.out_rows = M.rows;
             }
+            if (S.K == 1 || S.K == 3) R.ta = S.g[S.d - S.K];
+            if (S.K == 1) {
+                R.expect_rows = (uint64_t)(S.n / R.ta) + 1;
+            } else if (S.K == 2) {
+                R.expect_rows = pair_rows_upto(S.n, R.t0, R.t1);
+            } else if (S.K == 3) {
+                // sum over a of the pair's rows up to n - a ta
+                if ((int64_t)S.n / R.ta > (1 << 22))
+                    return fail(set_error(FZ_EINVAL, "batch run-order memo too large"));
+                uint64_t tot = 0;
+                for (int64_t a = 0; a * R.ta <= S.n; ++a)
+                    tot += pair_rows_upto(S.n - a * R.ta, R.t0, R.t1);
+                R.expect_rows = tot;
+            } else {
+                return fail(set_error(FZ_EINTERNAL, "run-order memo of depth > 3"));
+            }
+            R.out_rows = R.expect_rows;
             if (R.out_rows > MEMO_MAX_ROWS)
                 return fail(set_error(FZ_EINVAL, "batch run-order memo too large"));
             bytes += a256((size_t)R.out_rows * 16 + 16) + a256(((size_t)R.G + 1) * 8);
@@ -762,13 +787,29 @@ int batch_create_impl(const fz_instance_t *inst, int count, const fz_opts_t *opt
     const uint64_t target = std::max<uint64_t>(4096, total_cost / (warps * 8 + 1));
     std::vector<uint64_t> item0(count + 1, 0);
     b->params_host.resize((size_t)count * pbytes);
-    for (int i = 0; i < count; ++i) {
+    // Work items are numbered instance by instance in an order grouped by
+    // code path (run copy, walk up to width 8, wider walk) and then by width,
+    // so that warps taking consecutive items run the same code: warps of
+    // one SM mixing the paths evict each other's instructions.  The output
+    // layout (word offsets) keeps the caller's order.
+    std::vector<int> order(count);
+    for (int i = 0; i < count; ++i) order[i] = i;
+    if (batch_item_order_enabled()) {
+        auto path = [&](const Inst &I) { return I.run ? 0 : (I.d <= 8 ? 1 : 2); };
+        std::stable_sort(order.begin(), order.end(), [&](int x, int y) {
+            const Inst &A = b->inst[x], &B = b->inst[y];
+            if (path(A) != path(B)) return path(A) < path(B);
+            return A.d < B.d;
+        });
+    }
+    for (int pos = 0; pos < count; ++pos) {
+        const int i = order[pos];
         Inst &I = b->inst[i];
         const uint64_t cost = I.count + I.W * I.runs;
         I.items = I.count == 0 ? 0 : std::max<uint64_t>(1, (cost + target - 1) / target);
         I.slice_cost = I.items ? (cost + I.items - 1) / I.items : 64;
         I.slice_rows = I.items ? std::max<uint64_t>(4, (I.count + I.items - 1) / I.items) : 4;
-        item0[i + 1] = item0[i] + I.items;
+        item0[pos + 1] = item0[pos] + I.items;
         EnumLaunch L;
         L.C = tb + I.off_C;
         L.cs = (int64_t)I.n + 1;
@@ -798,7 +839,7 @@ int batch_create_impl(const fz_instance_t *inst, int count, const fz_opts_t *opt
         }
         // out holds the word offset; the kernel adds the output base
         fill_batch_params(L, reinterpret_cast<int32_t *>(I.word_off * 4), I.count, I.slice_rows,
-                          I.slice_cost, b->params_host.data() + (size_t)i * pbytes);
+                          I.slice_cost, b->params_host.data() + (size_t)pos * pbytes);
     }
     b->nitems = item0[count];
     if (count) {

@@ -253,33 +253,52 @@ __global__ void __launch_bounds__(THREADS) scan_tasks_kernel(const ScanJob *__re
             for (int64_t rho = t.begin + warp; rho < t.end; rho += nwarps)
                 chain_scan_warp(J.S, J.Sincl, J.slen, J.g, rho, lane);
             break;
-        case TK_BSUM:
+        case TK_BSUM: {
+            const int64_t rb = J.rb > 0 ? J.rb : RB;
             for (int64_t i = t.begin + threadIdx.x; i < t.end; i += blockDim.x) {
                 const int64_t b = i / J.g, rho = i - b * J.g;
-                const int64_t r0 = (b * RB) * J.g + rho;
+                const int64_t r0 = (b * rb) * J.g + rho;
                 uint64_t acc = 0;
-                for (int u = 0; u < RB; ++u) {
-                    const int64_t r = r0 + (int64_t)u * J.g;
-                    if (r < J.len) acc = sat_add(acc, __ldg(J.in + off + r * es));
+                for (int64_t u0 = 0; u0 < rb; u0 += 8) {
+                    uint64_t v[8];
+#pragma unroll
+                    for (int u = 0; u < 8; ++u) {
+                        const int64_t r = r0 + (u0 + u) * J.g;
+                        v[u] = (u0 + u < rb && r < J.len) ? __ldg(J.in + off + r * es) : 0ull;
+                    }
+#pragma unroll
+                    for (int u = 0; u < 8; ++u) acc = sat_add(acc, v[u]);
                 }
                 J.S[i] = acc;
             }
             break;
-        case TK_APPLY:
+        }
+        case TK_APPLY: {
+            const int64_t rb = J.rb > 0 ? J.rb : RB;
             for (int64_t i = t.begin + threadIdx.x; i < t.end; i += blockDim.x) {
                 const int64_t b = i / J.g, rho = i - b * J.g;
                 uint64_t acc = b > 0 ? J.Sincl[i - J.g] : 0ull;
-                const int64_t r0 = (b * RB) * J.g + rho;
-                for (int u = 0; u < RB; ++u) {
-                    const int64_t r = r0 + (int64_t)u * J.g;
-                    if (r < J.len) {
-                        const int64_t x = off + r * es;
-                        acc = sat_add(acc, __ldg(J.in + x));
-                        J.out[x] = x < J.ones_below ? 1ull : acc;
+                const int64_t r0 = (b * rb) * J.g + rho;
+                for (int64_t u0 = 0; u0 < rb; u0 += 8) {
+                    uint64_t v[8];
+#pragma unroll
+                    for (int u = 0; u < 8; ++u) {
+                        const int64_t r = r0 + (u0 + u) * J.g;
+                        v[u] = (u0 + u < rb && r < J.len) ? __ldg(J.in + off + r * es) : 0ull;
+                    }
+#pragma unroll
+                    for (int u = 0; u < 8; ++u) {
+                        const int64_t r = r0 + (u0 + u) * J.g;
+                        if (u0 + u < rb && r < J.len) {
+                            const int64_t x = off + r * es;
+                            acc = sat_add(acc, v[u]);
+                            J.out[x] = x < J.ones_below ? 1ull : acc;
+                        }
                     }
                 }
             }
             break;
+        }
         case TK_DELTA:
             for (int64_t i = t.begin + threadIdx.x; i < t.end; i += blockDim.x)
                 J.out[off + i * es] = (off + i * es == 0) ? 1ull : 0ull;

@@ -246,6 +246,10 @@ struct ScanJob {
     // h1 = 1)
     int64_t h, e, h1, g1, inv;
     int64_t off, es;
+    // entries per block of a blocked scan (0: scan_block_rows()); long
+    // chains take larger blocks so their chains of block sums stay within
+    // the direct-scan limit
+    int64_t rb;
 };
 enum ScanTaskKind : int {
     TK_DIRECT = 0,  // chains [begin, end) of in -> out, one warp each
@@ -316,9 +320,11 @@ int launch_memo_cta_build(const MemoJob *jobs, int njobs, int *status, cudaStrea
 
 // One run-order memo of a batch (the layout of launch_run_memo) for the
 // elements 0..n: its rows come from an element-order memo of depth k <= 3
-// (O, rows), or, with O null, from the closed form of the pair
-// (t0, t1) = (g_{d-2}, g_{d-1}) (k = 2): element p holds the a_{d-2} =
-// a_top - o h1 (o = 0, 1, ...) of the progression of launch_memo_closed.
+// (O, rows), or, with O null, from the closed form of the tail: k = 1, the
+// one row p / ta when ta divides p; k = 2, the pair (t0, t1) = (g_{d-2},
+// g_{d-1}), whose rows for element p have a_{d-2} = a_top - o h1 (o = 0, 1,
+// ...) as in launch_memo_closed; k = 3, for each a_{d-3} = p div ta down to
+// 0 (ta = g_{d-3}) the pair's rows of p - a_{d-3} ta.
 struct RunJob {
     const uint64_t *Clam;   // count-table row lam of the source instance, n + 1 entries
     const uint64_t *Cnext;  // row lam + 1: |Z(p, tail)|
@@ -327,9 +333,10 @@ struct RunJob {
     uint64_t *cls_beg;      // G + 1 class starts
     int4 *out;              // run-order rows
     uint64_t out_rows;      // capacity of out (bounds guard)
-    uint64_t expect_rows;   // closed form: sum over p <= n of |Z(p, (t0, t1))|
+    uint64_t expect_rows;   // closed form: sum over p <= n of |Z(p, tail)|
     int32_t n, g, G, k;     // last element, g_lam, G = min(g_lam, n + 1), depth
     int64_t t0, t1, e, h1, inv;
+    int64_t ta;             // closed form, k = 1 or 3: the first tail generator
 };
 // Builds every job's class starts, then its rows (two launches).
 int launch_run_memo_batch(const RunJob *jobs, int njobs, int *status, cudaStream_t s);
