@@ -634,6 +634,40 @@ __global__ void __launch_bounds__(MB_BUILD_THREADS) memo_cta_build_kernel(
             }
             const uint64_t W = total * (uint64_t)k;
             int32_t *out = J.R + dst0 * (uint64_t)k;
+            if (W > (uint64_t)(32 * MB_ILP * wpe)) {
+                // large element: block by block, a flat copy of len_i k words
+                // from the suffix block with one added to every k-th word
+                // (the cheapest loop per word; blocks are long here)
+                uint64_t bstart = 0;
+                for (int i = 0; i < k; ++i) {
+                    const uint64_t bl = shfl_u64(len, i);
+                    const uint64_t bs = shfl_u64(src, i);
+                    if (bl == 0) continue;
+                    const uint64_t BW = bl * (uint64_t)k;
+                    const int32_t *a = J.R + bs * (uint64_t)k;
+                    int32_t *bdst = out + bstart * (uint64_t)k;
+                    const uint64_t first = (uint64_t)lane + 32ull * (uint64_t)sub;
+                    uint32_t c0 = (uint32_t)(first % (uint64_t)k);  // coordinate of word `first`
+                    for (uint64_t w0 = first; w0 < BW; w0 += wstep * MB_ILP) {
+                        int32_t v[MB_ILP];
+#pragma unroll
+                        for (int u = 0; u < MB_ILP; ++u)
+                            if (w0 + wstep * u < BW) v[u] = a[w0 + wstep * u];
+                        uint32_t c = c0;
+#pragma unroll
+                        for (int u = 0; u < MB_ILP; ++u) {
+                            if (w0 + wstep * u < BW)
+                                bdst[w0 + wstep * u] = v[u] + (c == (uint32_t)i ? 1 : 0);
+                            c += cstep;
+                            if (c >= (uint32_t)k) c -= (uint32_t)k;
+                        }
+                        c0 = c;
+                    }
+                    bstart += bl;
+                }
+                __syncwarp();
+                continue;
+            }
             // word w = lane + 32 (sub + wpe t): row r = w div k, coordinate c
             uint64_t w = (uint64_t)lane + 32ull * (uint64_t)sub;
             uint64_t r = w / (uint64_t)k;
