@@ -673,8 +673,8 @@ def measure_batch(torch, fz, steps, warmup, count=4096, only_d=0, pi_steps=5, au
         # memo depth policy and layout per tuple width, measured on samples
         t0 = time.perf_counter()
         cands, chosen = fz.fz_batch_autotune(inst)
-        tune = {"by": "fz_batch_autotune: rebuild + enumeration of up to 256 sampled "
-                      "instances per width under each candidate (measured)",
+        tune = {"by": "fz_batch_autotune: rebuild + enumeration of the instances of each "
+                      "width (up to 1024) under each candidate (measured)",
                 "seconds": time.perf_counter() - t0,
                 "chosen": {str(d): {"cap_rows": c, "run_order": r}
                            for d, (c, r) in chosen.items()},

@@ -392,8 +392,9 @@ int fz_plan_batch(const fz_instance_t *inst, int count, const fz_opts_t *opt,
  * instance's estimated rows (else a partial depth-3 memo for d >= 5, else
  * the closed form of the last two generators), and keeps full memos of
  * depth <= 3 in run order when run_order is set; both are per tuple width.
- * fz_batch_autotune times, on the device, a sample of up to 256 of the
- * given instances of each width >= 3 under cap_rows in {0, 1/4, 1, 4, 16}
+ * fz_batch_autotune times, on the device, the given instances of each width
+ * >= 3 (up to 1024 of them, spread over the list) under cap_rows in
+ * {0, 1/4, 1, 4, 16}
  * with run order on and off (rebuild + enumeration, mean of 3 after a
  * warm-up; candidates that choose the same memos are timed once) and keeps
  * the fastest per width for later fz_batch_create calls on this device

@@ -90,6 +90,7 @@ struct fz_batch_s {
     std::vector<MemoJob> memo_jobs;
     RunJob *run_jobs_dev = nullptr;
     int nrun = 0, run_inst = 0;
+    int max_n3 = -1;  // largest n of the depth-3 closed-form run jobs (-1: none)
     void *params_dev = nullptr;       // EnumParams images (out = word offset)
     uint64_t *item0_dev = nullptr;
     unsigned long long *counter_dev = nullptr;
@@ -277,7 +278,7 @@ int batch_enqueue_rebuild(fz_batch_s *b, cudaStream_t s) {
     }
     int rc = launch_memo_cta_build(b->memo_jobs_dev, b->nmemo, b->status_dev, s);
     if (rc != FZ_OK) return rc;
-    return launch_run_memo_batch(b->run_jobs_dev, b->nrun, b->status_dev, s);
+    return launch_run_memo_batch(b->run_jobs_dev, b->nrun, b->max_n3, b->status_dev, s);
 }
 
 __global__ void gather_kernel(const uint64_t *const *ptrs, uint64_t *out, int count) {
@@ -736,7 +737,10 @@ int batch_create_impl(const fz_instance_t *inst, int count, const fz_opts_t *opt
             b->run_jobs_dev = reinterpret_cast<RunJob *>(base);
             FZ_CUDA_TRY(cudaMemcpyAsync(b->run_jobs_dev, rj.data(), rj.size() * sizeof(RunJob),
                                         cudaMemcpyHostToDevice, s));
-            rc = launch_run_memo_batch(b->run_jobs_dev, b->nrun, b->status_dev, s);
+            b->max_n3 = -1;
+            for (const RunJob &R : rj)
+                if (!R.O && R.k == 3) b->max_n3 = std::max(b->max_n3, (int)R.n);
+            rc = launch_run_memo_batch(b->run_jobs_dev, b->nrun, b->max_n3, b->status_dev, s);
             if (rc != FZ_OK) return fail(rc);
             FZ_CUDA_TRY(cudaStreamSynchronize(s));  // rj is a host temporary
         }
@@ -971,13 +975,16 @@ int fz_batch_autotune(const fz_instance_t *inst, int count, fz_batch_tune_entry_
     int rc = FZ_OK;
     DevArena out;
     for (int d = 3; d <= FZ_MAX_D && rc == FZ_OK; ++d) {
-        // a sample of this width: up to 256 instances spread over the list
+        // the instances of this width (up to 1024, spread over the list):
+        // memo builds run one CTA per memo in waves and the enumeration's
+        // tail depends on the work available, so timings of small samples
+        // do not add up to the whole batch; whole widths nearly do
         std::vector<fz_instance_t> all;
         for (int i = 0; i < count; ++i)
             if (inst[i].d == d) all.push_back(inst[i]);
         if (all.empty()) continue;
         std::vector<fz_instance_t> sub;
-        const size_t step = (all.size() + 255) / 256;
+        const size_t step = (all.size() + 1023) / 1024;
         for (size_t i = 0; i < all.size(); i += step) sub.push_back(all[i]);
         double best_t = 1e300;
         double best_cap = base.cap_rows[d];

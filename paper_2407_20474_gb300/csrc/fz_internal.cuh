@@ -338,8 +338,11 @@ struct RunJob {
     int64_t t0, t1, e, h1, inv;
     int64_t ta;             // closed form, k = 1 or 3: the first tail generator
 };
-// Builds every job's class starts, then its rows (two launches).
-int launch_run_memo_batch(const RunJob *jobs, int njobs, int *status, cudaStream_t s);
+// Builds every job's class starts, then its rows (two launches, three when
+// some job is a closed form of depth 3; max_n3 = the largest n of those
+// jobs, or -1 when there is none).
+int launch_run_memo_batch(const RunJob *jobs, int njobs, int max_n3, int *status,
+                          cudaStream_t s);
 
 // out[w] = w for w < words, 16-byte stores (fz_write_probe; fz_count.cu).
 int launch_write_probe(int32_t *out, uint64_t words, cudaStream_t s);

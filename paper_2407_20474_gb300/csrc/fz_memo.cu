@@ -802,30 +802,92 @@ __global__ void __launch_bounds__(RUN_CB_THREADS) run_class_begin_batch_kernel(
     }
 }
 
-// Batches: a warp per element (jobs along y), lanes on consecutive rows, so
-// every store of a warp is coalesced.  Rows come from the element-order memo
-// (O, rows), or from the closed form of the tail: k = 1, the one row p / ta
-// when ta divides p; k = 2, the progression of the pair (t0, t1); k = 3, for
-// a = p div ta down to 0 the pair progression of p - a ta, 32 values of a at
-// a time (each lane counts one, a warp scan places their rows).
-__device__ __forceinline__ uint64_t pair_first(const RunJob &J, int64_t r, int64_t *atop) {
-    // rows of Z(r, (t0, t1)): b = atop, atop - h1, ..., >= 0 (none if atop < 0)
+// Batches, run-order rows of the tails of depth 1 and 2 and of element-order
+// memos: a thread per element (jobs along y; these elements hold a few rows
+// each).  Rows come from the element-order memo (O, rows), or from the
+// closed form: k = 1, the one row p / ta when ta divides p; k = 2, the
+// progression of the pair (t0, t1).  Jobs of depth 3 are left to the next
+// kernel.
+__device__ __forceinline__ uint32_t pair_first(const RunJob &J, int64_t r, int64_t *atop) {
+    // rows of Z(r, (t0, t1)): a_{d-2} = atop, atop - h1, ..., >= 0 (none if
+    // atop < 0); r, t0 and h1 fit in 32 bits
     *atop = -1;
-    if (r < 0 || r % J.e != 0) return 0;
-    const int64_t astar = ((r / J.e) % J.h1) * J.inv % J.h1;
-    const int64_t q0 = r / J.t0;
+    if (r < 0) return 0;
+    const uint32_t ru = (uint32_t)r, e = (uint32_t)J.e, h1 = (uint32_t)J.h1;
+    const uint32_t re = ru / e;
+    if (re * e != ru) return 0;
+    const uint32_t astar = (uint32_t)((uint64_t)(re % h1) * (uint64_t)J.inv % h1);
+    const uint32_t q0 = ru / (uint32_t)J.t0;
     if (q0 < astar) return 0;
-    *atop = q0 - (q0 - astar) % J.h1;
-    return (uint64_t)(*atop / J.h1) + 1;
+    const uint32_t top = q0 - (q0 - astar) % h1;
+    *atop = top;
+    return top / h1 + 1u;
 }
 
 __global__ void __launch_bounds__(THREADS) run_rows_batch_kernel(const RunJob *__restrict__ jobs,
                                                                  int njobs, int *status) {
+    for (int jb = blockIdx.y; jb < njobs; jb += gridDim.y) {
+        const RunJob &J = jobs[jb];
+        if (!J.O && J.k == 3) continue;  // run_rows3_batch_kernel
+        const int64_t g = J.g;
+        for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p <= J.n;
+             p += (int64_t)gridDim.x * blockDim.x) {
+            const int64_t q = p / g, c = p - q * g;
+            const uint64_t tail_rows = __ldg(J.Cnext + p);
+            const uint64_t dst = __ldg(J.cls_beg + c) + __ldg(J.Clam + p) - tail_rows;
+            if (dst + tail_rows > J.out_rows) {
+                atomicExch(status, (int)DEV_INTERNAL);
+                continue;
+            }
+            int4 *o = J.out + dst;
+            if (J.O) {
+                const uint64_t o0 = __ldg(J.O + p), len = __ldg(J.O + p + 1) - o0;
+                if (len != tail_rows) {
+                    atomicExch(status, (int)DEV_INTERNAL);
+                    continue;
+                }
+                const int k = J.k;
+                const int32_t *s = J.rows + o0 * (uint64_t)k;
+                for (uint64_t r = 0; r < len; ++r, s += k)
+                    o[r] = make_int4((int)q, __ldg(s), k > 1 ? __ldg(s + 1) : 0,
+                                     k > 2 ? __ldg(s + 2) : 0);
+            } else if (J.k == 1) {
+                const uint64_t want = p % J.ta == 0 ? 1u : 0u;
+                if (want != tail_rows) {
+                    atomicExch(status, (int)DEV_INTERNAL);
+                    continue;
+                }
+                if (want) o[0] = make_int4((int)q, (int)(p / J.ta), 0, 0);
+            } else {
+                int64_t atop;
+                const uint64_t want = pair_first(J, p, &atop);
+                if (want != tail_rows) {
+                    atomicExch(status, (int)DEV_INTERNAL);
+                    continue;
+                }
+                for (uint64_t r = 0; r < want; ++r) {
+                    const int64_t a0 = atop - (int64_t)r * J.h1;
+                    o[r] = make_int4((int)q, (int)a0, (int)((p - a0 * J.t0) / J.t1), 0);
+                }
+            }
+        }
+    }
+}
+
+// Batches, run-order rows of tails of depth 3 from their closed form: a warp
+// per element (elements hold up to thousands of rows), lanes on consecutive
+// rows so every store of a warp is coalesced.  For a = p div ta down to 0,
+// 32 values at a time (one per lane: each counts its pair rows of p - a ta,
+// a warp scan places them), each row finds its lane by a binary search over
+// the 32 running totals.
+__global__ void __launch_bounds__(THREADS) run_rows3_batch_kernel(const RunJob *__restrict__ jobs,
+                                                                  int njobs, int *status) {
     const int lane = threadIdx.x & 31;
     const int64_t wid = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
     for (int jb = blockIdx.y; jb < njobs; jb += gridDim.y) {
         const RunJob &J = jobs[jb];
+        if (J.O || J.k != 3) continue;
         const int64_t g = J.g;
         for (int64_t p = wid; p <= J.n; p += nw) {
             const int64_t q = p / g, c = p - q * g;
@@ -836,75 +898,44 @@ __global__ void __launch_bounds__(THREADS) run_rows_batch_kernel(const RunJob *_
                 continue;
             }
             int4 *o = J.out + dst;
-            if (J.O) {
-                const uint64_t o0 = __ldg(J.O + p), len = __ldg(J.O + p + 1) - o0;
-                if (len != tail_rows) {
-                    if (lane == 0) atomicExch(status, (int)DEV_INTERNAL);
-                    continue;
-                }
-                const int k = J.k;
-                for (uint64_t r = lane; r < len; r += 32) {
-                    const int32_t *s = J.rows + (o0 + r) * (uint64_t)k;
-                    o[r] = make_int4((int)q, __ldg(s), k > 1 ? __ldg(s + 1) : 0,
-                                     k > 2 ? __ldg(s + 2) : 0);
-                }
-            } else if (J.k == 1) {
-                const uint64_t want = p % J.ta == 0 ? 1u : 0u;
-                if (want != tail_rows) {
-                    if (lane == 0) atomicExch(status, (int)DEV_INTERNAL);
-                    continue;
-                }
-                if (want && lane == 0) o[0] = make_int4((int)q, (int)(p / J.ta), 0, 0);
-            } else if (J.k == 2) {
-                int64_t atop;
-                const uint64_t want = pair_first(J, p, &atop);
-                if (want != tail_rows) {
-                    if (lane == 0) atomicExch(status, (int)DEV_INTERNAL);
-                    continue;
-                }
-                for (uint64_t r = lane; r < want; r += 32) {
-                    const int64_t a0 = atop - (int64_t)r * J.h1;
-                    o[r] = make_int4((int)q, (int)a0, (int)((p - a0 * J.t0) / J.t1), 0);
-                }
-            } else {  // k == 3: a over the first tail generator, pairs below
-                uint64_t base = 0;
-                for (int64_t a0 = p / J.ta; a0 >= 0; a0 -= 32) {
-                    const int64_t a = a0 - lane;
-                    const int64_t ra = a >= 0 ? p - a * J.ta : -1;
-                    int64_t btop = -1;
-                    const uint64_t cnt = a >= 0 ? pair_first(J, ra, &btop) : 0u;
-                    const uint64_t incl = warp_incl_scan(cnt, lane);
-                    const uint64_t tot = shfl_u64(incl, 31);
-                    for (uint64_t rr0 = 0; rr0 < tot; rr0 += 32) {
-                        const uint64_t rr = rr0 + (uint64_t)lane;
-                        // lane l of the group holding row rr: lanes with incl <= rr
-                        int l = 0;
+            uint64_t base = 0;
+            for (int64_t a0 = p / J.ta; a0 >= 0; a0 -= 32) {
+                const int64_t a = a0 - lane;
+                const int64_t ra = a >= 0 ? p - a * J.ta : -1;
+                int64_t btop = -1;
+                const uint64_t cnt = a >= 0 ? pair_first(J, ra, &btop) : 0u;
+                const uint64_t incl = warp_incl_scan(cnt, lane);
+                const uint64_t tot = shfl_u64(incl, 31);
+                for (uint64_t rr0 = 0; rr0 < tot; rr0 += 32) {
+                    const uint64_t rr = rr0 + (uint64_t)lane;
+                    // lane l of the group holding row rr: lanes with incl <= rr
+                    int l = 0;
 #pragma unroll
-                        for (int sft = 16; sft >= 1; sft >>= 1) {
-                            const uint64_t e = shfl_u64(incl, l + sft - 1);
-                            if (e <= rr) l += sft;
-                        }
-                        uint64_t ex = shfl_u64(incl, l > 0 ? l - 1 : 0);
-                        if (l == 0) ex = 0;
-                        const int64_t bt = (int64_t)shfl_u64((uint64_t)btop, l);
-                        const int64_t rl = (int64_t)shfl_u64((uint64_t)ra, l);
-                        if (rr < tot && base + rr < tail_rows) {
-                            const int64_t b = bt - (int64_t)(rr - ex) * J.h1;
-                            o[base + rr] = make_int4((int)q, (int)(a0 - l), (int)b,
-                                                     (int)((rl - b * J.t0) / J.t1));
-                        }
+                    for (int sft = 16; sft >= 1; sft >>= 1) {
+                        const uint64_t e = shfl_u64(incl, l + sft - 1);
+                        if (e <= rr) l += sft;
                     }
-                    base += tot;
+                    uint64_t ex = shfl_u64(incl, l > 0 ? l - 1 : 0);
+                    if (l == 0) ex = 0;
+                    const int64_t bt = (int64_t)shfl_u64((uint64_t)btop, l);
+                    const int64_t rl = (int64_t)shfl_u64((uint64_t)ra, l);
+                    if (rr < tot && base + rr < tail_rows) {
+                        const int64_t b = bt - (int64_t)(rr - ex) * J.h1;
+                        const uint32_t cc = (uint32_t)(rl - b * J.t0) / (uint32_t)J.t1;
+                        o[base + rr] = make_int4((int)q, (int)(a0 - l), (int)b, (int)cc);
+                    }
                 }
-                if (base != tail_rows && lane == 0) atomicExch(status, (int)DEV_INTERNAL);
+                base += tot;
             }
+            if (base != tail_rows && lane == 0) atomicExch(status, (int)DEV_INTERNAL);
         }
     }
 }
 
 }  // namespace
 
-int launch_run_memo_batch(const RunJob *jobs, int njobs, int *status, cudaStream_t s) {
+int launch_run_memo_batch(const RunJob *jobs, int njobs, int max_n3, int *status,
+                          cudaStream_t s) {
     if (njobs <= 0) return FZ_OK;
     if (!jobs || !status) return set_error(FZ_EINTERNAL, "run memo batch: missing device buffer");
     run_class_begin_batch_kernel<<<njobs, RUN_CB_THREADS, 0, s>>>(jobs, status);
@@ -912,6 +943,14 @@ int launch_run_memo_batch(const RunJob *jobs, int njobs, int *status, cudaStream
     const dim3 grid(64, (unsigned)(njobs < 65535 ? njobs : 65535));
     run_rows_batch_kernel<<<grid, THREADS, 0, s>>>(jobs, njobs, status);
     note_launch();
+    if (max_n3 >= 0) {
+        // a warp per element of the largest depth-3 job
+        const int64_t want = ((int64_t)max_n3 + 1 + THREADS / 32 - 1) / (THREADS / 32);
+        const dim3 grid3((unsigned)std::min<int64_t>(std::max<int64_t>(want, 1), 2048),
+                         (unsigned)(njobs < 65535 ? njobs : 65535));
+        run_rows3_batch_kernel<<<grid3, THREADS, 0, s>>>(jobs, njobs, status);
+        note_launch();
+    }
     FZ_CUDA_TRY(cudaGetLastError());
     return FZ_OK;
 }
