@@ -90,7 +90,7 @@ struct fz_batch_s {
     std::vector<MemoJob> memo_jobs;
     RunJob *run_jobs_dev = nullptr;
     int nrun = 0, run_inst = 0;
-    int max_n3 = -1;  // largest n of the depth-3 closed-form run jobs (-1: none)
+    uint64_t run_blocks_t = 0, run_blocks_w = 0;  // blocks of the two run-row kernels
     void *params_dev = nullptr;       // EnumParams images (out = word offset)
     uint64_t *item0_dev = nullptr;
     unsigned long long *counter_dev = nullptr;
@@ -278,7 +278,8 @@ int batch_enqueue_rebuild(fz_batch_s *b, cudaStream_t s) {
     }
     int rc = launch_memo_cta_build(b->memo_jobs_dev, b->nmemo, b->status_dev, s);
     if (rc != FZ_OK) return rc;
-    return launch_run_memo_batch(b->run_jobs_dev, b->nrun, b->max_n3, b->status_dev, s);
+    return launch_run_memo_batch(b->run_jobs_dev, b->nrun, b->run_blocks_t, b->run_blocks_w,
+                                 b->status_dev, s);
 }
 
 __global__ void gather_kernel(const uint64_t *const *ptrs, uint64_t *out, int count) {
@@ -734,13 +735,28 @@ int batch_create_impl(const fz_instance_t *inst, int count, const fz_opts_t *opt
                 R.cls_beg = reinterpret_cast<uint64_t *>(base + off);
                 off += a256(((size_t)R.G + 1) * 8);
             }
+            // block ranges of the two row kernels (256 threads a block):
+            // a thread per element, or a warp per element for depth 3
+            uint64_t bt = 0, bw = 0;
+            for (RunJob &R : rj) {
+                const uint64_t elems = (uint64_t)R.n + 1;
+                const bool w = !R.O && R.k == 3;
+                R.blk0_t = bt;
+                R.blk0_w = bw;
+                if (w)
+                    bw += (elems + 7) / 8;
+                else
+                    bt += (elems + 255) / 256;
+            }
+            if (bt > 0x7fffffffull || bw > 0x7fffffffull)
+                return fail(set_error(FZ_EINVAL, "batch run-order memos too large"));
+            b->run_blocks_t = bt;
+            b->run_blocks_w = bw;
             b->run_jobs_dev = reinterpret_cast<RunJob *>(base);
             FZ_CUDA_TRY(cudaMemcpyAsync(b->run_jobs_dev, rj.data(), rj.size() * sizeof(RunJob),
                                         cudaMemcpyHostToDevice, s));
-            b->max_n3 = -1;
-            for (const RunJob &R : rj)
-                if (!R.O && R.k == 3) b->max_n3 = std::max(b->max_n3, (int)R.n);
-            rc = launch_run_memo_batch(b->run_jobs_dev, b->nrun, b->max_n3, b->status_dev, s);
+            rc = launch_run_memo_batch(b->run_jobs_dev, b->nrun, b->run_blocks_t,
+                                       b->run_blocks_w, b->status_dev, s);
             if (rc != FZ_OK) return fail(rc);
             FZ_CUDA_TRY(cudaStreamSynchronize(s));  // rj is a host temporary
         }

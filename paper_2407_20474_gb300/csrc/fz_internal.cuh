@@ -337,12 +337,17 @@ struct RunJob {
     int32_t n, g, G, k;     // last element, g_lam, G = min(g_lam, n + 1), depth
     int64_t t0, t1, e, h1, inv;
     int64_t ta;             // closed form, k = 1 or 3: the first tail generator
+    // first block of this job in the row kernels: a thread per element
+    // (closed forms of depth 1 and 2, element-order memos) and a warp per
+    // element (closed forms of depth 3); a job owns ceil((n + 1) / 256),
+    // resp. ceil((n + 1) / 8), blocks of its kernel and none of the other
+    uint64_t blk0_t, blk0_w;
 };
-// Builds every job's class starts, then its rows (two launches, three when
-// some job is a closed form of depth 3; max_n3 = the largest n of those
-// jobs, or -1 when there is none).
-int launch_run_memo_batch(const RunJob *jobs, int njobs, int max_n3, int *status,
-                          cudaStream_t s);
+// Builds every job's class starts, then its rows: blocks_t blocks of the
+// thread-per-element kernel and blocks_w of the warp-per-element kernel
+// (the totals of the jobs' block ranges; zero skips the launch).
+int launch_run_memo_batch(const RunJob *jobs, int njobs, uint64_t blocks_t, uint64_t blocks_w,
+                          int *status, cudaStream_t s);
 
 // out[w] = w for w < words, 16-byte stores (fz_write_probe; fz_count.cu).
 int launch_write_probe(int32_t *out, uint64_t words, cudaStream_t s);

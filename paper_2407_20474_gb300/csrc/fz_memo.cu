@@ -824,27 +824,47 @@ __device__ __forceinline__ uint32_t pair_first(const RunJob &J, int64_t r, int64
     return top / h1 + 1u;
 }
 
+// The job of block `blk` for a kernel whose jobs own the consecutive block
+// ranges [blk0(j), blk0(j + 1)) (blk0 non-decreasing; jobs owning no block
+// have equal starts): the last job whose range starts at or before blk.
+template <class F>
+__device__ __forceinline__ int job_of_block(int njobs, uint64_t blk, F blk0) {
+    int lo = 0, hi = njobs;  // blk0(lo) <= blk < blk0(hi) (blk0(njobs) = total)
+    while (hi - lo > 1) {
+        const int mid = (lo + hi) >> 1;
+        if (blk0(mid) <= blk)
+            lo = mid;
+        else
+            hi = mid;
+    }
+    return lo;
+}
+
 __global__ void __launch_bounds__(THREADS) run_rows_batch_kernel(const RunJob *__restrict__ jobs,
                                                                  int njobs, int *status) {
-    for (int jb = blockIdx.y; jb < njobs; jb += gridDim.y) {
-        const RunJob &J = jobs[jb];
-        if (!J.O && J.k == 3) continue;  // run_rows3_batch_kernel
+    __shared__ int s_job;
+    if (threadIdx.x == 0)
+        s_job = job_of_block(njobs, blockIdx.x, [&](int j) { return jobs[j].blk0_t; });
+    __syncthreads();
+    {
+        const RunJob &J = jobs[s_job];
+        if (!J.O && J.k == 3) return;  // (owns no block here) run_rows3_batch_kernel
         const int64_t g = J.g;
-        for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p <= J.n;
-             p += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t p = (int64_t)(blockIdx.x - J.blk0_t) * blockDim.x + threadIdx.x;
+        if (p <= J.n) {
             const int64_t q = p / g, c = p - q * g;
             const uint64_t tail_rows = __ldg(J.Cnext + p);
             const uint64_t dst = __ldg(J.cls_beg + c) + __ldg(J.Clam + p) - tail_rows;
             if (dst + tail_rows > J.out_rows) {
                 atomicExch(status, (int)DEV_INTERNAL);
-                continue;
+                return;
             }
             int4 *o = J.out + dst;
             if (J.O) {
                 const uint64_t o0 = __ldg(J.O + p), len = __ldg(J.O + p + 1) - o0;
                 if (len != tail_rows) {
                     atomicExch(status, (int)DEV_INTERNAL);
-                    continue;
+                    return;
                 }
                 const int k = J.k;
                 const int32_t *s = J.rows + o0 * (uint64_t)k;
@@ -855,7 +875,7 @@ __global__ void __launch_bounds__(THREADS) run_rows_batch_kernel(const RunJob *_
                 const uint64_t want = p % J.ta == 0 ? 1u : 0u;
                 if (want != tail_rows) {
                     atomicExch(status, (int)DEV_INTERNAL);
-                    continue;
+                    return;
                 }
                 if (want) o[0] = make_int4((int)q, (int)(p / J.ta), 0, 0);
             } else {
@@ -863,7 +883,7 @@ __global__ void __launch_bounds__(THREADS) run_rows_batch_kernel(const RunJob *_
                 const uint64_t want = pair_first(J, p, &atop);
                 if (want != tail_rows) {
                     atomicExch(status, (int)DEV_INTERNAL);
-                    continue;
+                    return;
                 }
                 for (uint64_t r = 0; r < want; ++r) {
                     const int64_t a0 = atop - (int64_t)r * J.h1;
@@ -883,19 +903,22 @@ __global__ void __launch_bounds__(THREADS) run_rows_batch_kernel(const RunJob *_
 __global__ void __launch_bounds__(THREADS) run_rows3_batch_kernel(const RunJob *__restrict__ jobs,
                                                                   int njobs, int *status) {
     const int lane = threadIdx.x & 31;
-    const int64_t wid = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
-    for (int jb = blockIdx.y; jb < njobs; jb += gridDim.y) {
-        const RunJob &J = jobs[jb];
-        if (J.O || J.k != 3) continue;
+    __shared__ int s_job;
+    if (threadIdx.x == 0)
+        s_job = job_of_block(njobs, blockIdx.x, [&](int j) { return jobs[j].blk0_w; });
+    __syncthreads();
+    {
+        const RunJob &J = jobs[s_job];
+        if (J.O || J.k != 3) return;  // owns no block here
         const int64_t g = J.g;
-        for (int64_t p = wid; p <= J.n; p += nw) {
+        const int64_t p = (int64_t)(blockIdx.x - J.blk0_w) * (blockDim.x >> 5) + (threadIdx.x >> 5);
+        if (p <= J.n) {
             const int64_t q = p / g, c = p - q * g;
             const uint64_t tail_rows = __ldg(J.Cnext + p);
             const uint64_t dst = __ldg(J.cls_beg + c) + __ldg(J.Clam + p) - tail_rows;
             if (dst + tail_rows > J.out_rows) {
                 if (lane == 0) atomicExch(status, (int)DEV_INTERNAL);
-                continue;
+                return;
             }
             int4 *o = J.out + dst;
             uint64_t base = 0;
@@ -934,21 +957,18 @@ __global__ void __launch_bounds__(THREADS) run_rows3_batch_kernel(const RunJob *
 
 }  // namespace
 
-int launch_run_memo_batch(const RunJob *jobs, int njobs, int max_n3, int *status,
-                          cudaStream_t s) {
+int launch_run_memo_batch(const RunJob *jobs, int njobs, uint64_t blocks_t, uint64_t blocks_w,
+                          int *status, cudaStream_t s) {
     if (njobs <= 0) return FZ_OK;
     if (!jobs || !status) return set_error(FZ_EINTERNAL, "run memo batch: missing device buffer");
     run_class_begin_batch_kernel<<<njobs, RUN_CB_THREADS, 0, s>>>(jobs, status);
     note_launch();
-    const dim3 grid(64, (unsigned)(njobs < 65535 ? njobs : 65535));
-    run_rows_batch_kernel<<<grid, THREADS, 0, s>>>(jobs, njobs, status);
-    note_launch();
-    if (max_n3 >= 0) {
-        // a warp per element of the largest depth-3 job
-        const int64_t want = ((int64_t)max_n3 + 1 + THREADS / 32 - 1) / (THREADS / 32);
-        const dim3 grid3((unsigned)std::min<int64_t>(std::max<int64_t>(want, 1), 2048),
-                         (unsigned)(njobs < 65535 ? njobs : 65535));
-        run_rows3_batch_kernel<<<grid3, THREADS, 0, s>>>(jobs, njobs, status);
+    if (blocks_t > 0) {
+        run_rows_batch_kernel<<<(unsigned)blocks_t, THREADS, 0, s>>>(jobs, njobs, status);
+        note_launch();
+    }
+    if (blocks_w > 0) {
+        run_rows3_batch_kernel<<<(unsigned)blocks_w, THREADS, 0, s>>>(jobs, njobs, status);
         note_launch();
     }
     FZ_CUDA_TRY(cudaGetLastError());
