@@ -333,6 +333,16 @@ double volume_rows(const Inst &I, int n) {
 // cost about 12 warp instructions per output row.
 constexpr double RUN_PAIR_CAP = 2.0;
 
+// FZ_RUN_CLOSED3=0 builds the run-order rows of depth-3 tails from an
+// element-order memo instead of the closed form (tuning only).
+bool run_closed3_enabled() {
+    static const bool on = [] {
+        const char *e = getenv("FZ_RUN_CLOSED3");
+        return !(e && e[0] == '0');
+    }();
+    return on;
+}
+
 // FZ_BATCH_ORDER=0 numbers the work items in the caller's instance order
 // (tuning only; see the item numbering in batch_create_impl).
 bool batch_item_order_enabled() {
@@ -547,7 +557,7 @@ int batch_create_impl(const fz_instance_t *inst, int count, const fz_opts_t *opt
         Inst &I = b->inst[i];
         // run-order instances take their rows from the tail's closed form
         // (depth <= 3): no element-order memo
-        if (I.K <= 0 || I.pair || I.run) continue;
+        if (I.K <= 0 || I.pair || (I.run && (I.K != 3 || run_closed3_enabled()))) continue;
         std::vector<int32_t> key(I.g + (I.d - I.K), I.g + I.d);
         auto it = memo_of.find(key);
         int m;
@@ -708,6 +718,14 @@ int batch_create_impl(const fz_instance_t *inst, int count, const fz_opts_t *opt
                 R.expect_rows = (uint64_t)(S.n / R.ta) + 1;
             } else if (S.K == 2) {
                 R.expect_rows = pair_rows_upto(S.n, R.t0, R.t1);
+            } else if (S.K == 3 && !run_closed3_enabled()) {
+                // rows copied from the element-order memo
+                if (S.memo < 0 || b->memo_jobs[S.memo].top < S.n + 1)
+                    return fail(set_error(FZ_EINTERNAL, "run-order memo without its full memo"));
+                const MemoJob &M = b->memo_jobs[S.memo];
+                R.O = M.O;
+                R.rows = M.R;
+                R.expect_rows = M.rows;
             } else if (S.K == 3) {
                 // sum over a of the pair's rows up to n - a ta
                 if ((int64_t)S.n / R.ta > (1 << 22))

@@ -710,6 +710,77 @@ __global__ void __launch_bounds__(MB_BUILD_THREADS) memo_cta_build_kernel(
     }
 }
 
+// The same memos copied (element, generator) block by block, each warp
+// loading a block's length and offset before copying it (the descriptor
+// loads of an element's k blocks are dependent round trips).  Kept for
+// comparison behind FZ_MEMO_CTA=blocks (tuning only).
+__global__ void __launch_bounds__(MB_BUILD_THREADS) memo_cta_build_blocks_kernel(
+    const MemoJob *__restrict__ jobs, int *status) {
+    __shared__ uint64_t sums[33];
+    const MemoJob J = jobs[blockIdx.x];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int nwarps = blockDim.x >> 5;
+    const int k = J.k;
+    // offsets: O[0] = 0, O[m+1] = O[m] + |Z(m, tail)| (chunked block scan)
+    uint64_t carry = 0;
+    for (int base = 0; base < J.top; base += blockDim.x) {
+        const int m = base + threadIdx.x;
+        const uint64_t v = m < J.top ? __ldg(J.Ct + m) : 0ull;
+        uint64_t tot;
+        const uint64_t ex = block_exclusive_scan(v, sums, &tot);
+        if (m < J.top) J.O[m] = carry + ex;
+        carry += tot;
+    }
+    if (threadIdx.x == 0) J.O[J.top] = carry;
+    __syncthreads();
+    if (carry != J.rows) {
+        if (threadIdx.x == 0) atomicExch(status, (int)DEV_INTERNAL);
+        return;
+    }
+    // elementwise batches of b elements
+    for (int m0 = 0; m0 < J.top; m0 += J.b) {
+        const int m1 = m0 + J.b < J.top ? m0 + J.b : J.top;
+        for (int m = m0 + warp; m < m1; m += nwarps) {
+            uint64_t dst = J.O[m];
+            if (m == 0) {
+                if (lane < k) J.R[lane] = 0;
+                continue;
+            }
+            for (int i = 0; i < k; ++i) {
+                const int src_m = m - J.t[i];
+                if (src_m < 0) continue;
+                const uint64_t len = __ldg(J.Ct + (int64_t)i * J.cs + src_m);
+                if (len == 0) continue;
+                const uint64_t src = J.O[src_m + 1] - len;  // suffix Z_{>=i}(src_m)
+                // the block is a flat copy of len * k words with one added to
+                // every word of coordinate i: word w of the block is
+                // coordinate w mod k of row w div k
+                const uint64_t W = len * (uint64_t)k;
+                const int32_t *a = J.R + src * (uint64_t)k;
+                int32_t *b = J.R + dst * (uint64_t)k;
+                const uint32_t step = (uint32_t)(32 % k);
+                uint32_t c0 = (uint32_t)(lane % k);  // coordinate of word lane
+                for (uint64_t w0 = lane; w0 < W; w0 += 32 * MB_ILP) {
+                    int32_t v[MB_ILP];
+#pragma unroll
+                    for (int u = 0; u < MB_ILP; ++u)
+                        if (w0 + 32 * u < W) v[u] = a[w0 + 32 * u];
+                    uint32_t c = c0;
+#pragma unroll
+                    for (int u = 0; u < MB_ILP; ++u) {
+                        if (w0 + 32 * u < W) b[w0 + 32 * u] = v[u] + (c == (uint32_t)i ? 1 : 0);
+                        c += step;
+                        if (c >= (uint32_t)k) c -= (uint32_t)k;
+                    }
+                    c0 = c;
+                }
+                dst += len;
+            }
+        }
+        __syncthreads();
+    }
+}
+
 // ---------------------------------------------------------------------------
 // The memo in run order (declared in fz_internal.cuh).  The element p of
 // class c = p mod g_lam, q = p div g_lam, starts at
@@ -1004,9 +1075,22 @@ int launch_memo_sizes(const MemoJob *jobs, int njobs, uint64_t *rows_out, cudaSt
     return FZ_OK;
 }
 
+// FZ_MEMO_CTA=blocks builds batch memos with the block-by-block kernel
+// (tuning only).
+static bool memo_cta_blocks() {
+    static const bool on = [] {
+        const char *e = getenv("FZ_MEMO_CTA");
+        return e && std::strcmp(e, "blocks") == 0;
+    }();
+    return on;
+}
+
 int launch_memo_cta_build(const MemoJob *jobs, int njobs, int *status, cudaStream_t s) {
     if (njobs <= 0) return FZ_OK;
-    memo_cta_build_kernel<<<njobs, MB_BUILD_THREADS, 0, s>>>(jobs, status);
+    if (memo_cta_blocks())
+        memo_cta_build_blocks_kernel<<<njobs, MB_BUILD_THREADS, 0, s>>>(jobs, status);
+    else
+        memo_cta_build_kernel<<<njobs, MB_BUILD_THREADS, 0, s>>>(jobs, status);
     note_launch();
     FZ_CUDA_TRY(cudaGetLastError());
     return FZ_OK;
