@@ -842,14 +842,17 @@ def measure_serve(torch, fz, seconds=10.0, sweep_rates=(), sweep_requests=4000,
                 "achieved_req_per_s": m / span if span > 0 else 0.0,
                 "max_submit_lag_ms": 1e3 * late}
 
-    def server(max_in_flight, streams):
-        srv = fz.Server(max_in_flight=max_in_flight, streams=streams)
+    def server(max_in_flight, streams, per_request):
+        srv = fz.Server(max_in_flight=max_in_flight, streams=streams, per_request=per_request)
         ids = [srv.register(g, nm) for g, nm in zip(sets, n_max)]
         return srv, ids
 
-    modes = {"continuous": (64, 8)}
+    # continuous: the requests admitted together form one launch (default);
+    # continuous_per_request: the same admission, one launch per request;
+    # serial: one request on the device at a time
+    modes = {"continuous": (64, 8, False), "continuous_per_request": (64, 8, True)}
     if serial:
-        modes["serial_one_at_a_time"] = (1, 1)
+        modes["serial_one_at_a_time"] = (1, 1, True)
     res = {}
     servers = {k: server(*v) for k, v in modes.items()}
     t_setup = time.perf_counter() - t_setup

@@ -438,9 +438,10 @@ int fz_enumerate_batch(const fz_instance_t *inst, int count, const fz_opts_t *op
  * row on the host, so fz_serve_submit knows the exact output bytes of a
  * query at once.  A background thread admits queued requests in arrival
  * order as soon as a slot (max_in_flight) and the exact bytes are free in the
- * output budget, and launches each on the next of `streams` CUDA streams:
+ * output budget, and launches them on the next of `streams` CUDA streams:
  * requests that arrive while others run are admitted as slots and memory
- * free up, and their work overlaps on the GPU (continuous batching).  A
+ * free up, and their work overlaps on the GPU (continuous batching).  The
+ * requests admitted together are one launch (see FZ_SERVE_PER_REQUEST).  A
  * result stays valid until fz_serve_release.  Times are seconds on the host
  * steady clock; t_done is stamped when the request's stream reaches it.
  * Each request in flight has its own device status word, read back with
@@ -453,10 +454,18 @@ typedef struct fz_serve_cfg {
     uint64_t memory_bytes;  /* device bytes for request outputs; 0 = a quarter
                                of the free memory at creation */
     int32_t max_in_flight;  /* requests on the device at once (slots) */
-    int32_t streams;        /* CUDA streams the server launches on */
+    int32_t streams;        /* CUDA streams the server launches on (grouped
+                               mode: at most one group in flight on each) */
     int32_t max_queue;      /* queued requests before FZ_EAGAIN */
-    int32_t flags;          /* reserved, 0 */
+    int32_t flags;          /* 0 or FZ_SERVE_PER_REQUEST */
 } fz_serve_cfg_t;
+
+/* fz_serve_cfg_t.flags: launch every request on its own instead of in
+ * groups.  By default (flags 0) the requests admitted in one pass of the
+ * server loop are launched together: one launch of the batch enumeration
+ * kernel with a range of work items per request, one transfer of their
+ * parameters and one completion callback per group. */
+#define FZ_SERVE_PER_REQUEST 1
 
 typedef struct fz_server_s *fz_server_t;
 

@@ -126,6 +126,8 @@ class fz_serve_stats_t(ctypes.Structure):
                 ("last_error", ctypes.c_int32)]
 
 
+FZ_SERVE_PER_REQUEST = 1
+
 FZ_SERVE_DONE = 0
 FZ_SERVE_QUEUED = 1
 FZ_SERVE_RUNNING = 2
@@ -722,9 +724,11 @@ class Server:
     """Request loop over resident generator sets (continuous batching)."""
 
     def __init__(self, memory_bytes: int = 0, max_in_flight: int = 64, streams: int = 8,
-                 max_queue: int = 1 << 20):
+                 max_queue: int = 1 << 20, per_request: bool = False):
+        """``per_request``: launch every request on its own (FZ_SERVE_PER_REQUEST)
+        instead of the requests admitted together as one launch."""
         cfg = fz_serve_cfg_t(int(memory_bytes), int(max_in_flight), int(streams),
-                             int(max_queue), 0)
+                             int(max_queue), FZ_SERVE_PER_REQUEST if per_request else 0)
         h = _P()
         _check(lib().fz_serve_create(ctypes.byref(cfg), ctypes.byref(h)))
         self._h = h

@@ -7,9 +7,15 @@
 // of any later query is known at submission without touching the device.
 // A background thread admits queued requests in arrival order whenever a
 // slot and enough output memory (exact bytes, from a first-fit arena carved
-// out of one device allocation) are free, and launches each admitted request
-// on the next of several streams: requests admitted while others run
-// overlap on the GPU.  Completion is recorded by a host callback on the
+// out of one device allocation) are free.  By default every request admitted
+// in one pass of the loop is launched as one group: one persistent launch of
+// the batch enumeration kernel with a work-item range per request (its
+// parameters and item prefix staged in page-locked memory and copied in one
+// transfer), one copy back of the group's status words and one completion
+// callback, on the next of several streams, so groups admitted while others
+// run overlap on the GPU.  With FZ_SERVE_PER_REQUEST every request is its
+// own launch of the single-instance kernel (and so is a request whose plan
+// the batch kernel does not serve: run order wider than 8).  Completion is recorded by a host callback on the
 // request's stream (cudaLaunchHostFunc), which frees the slot, stamps the
 // completion time and reads the request's own device status word (copied to
 // page-locked host memory just before the callback), so a device-side check
@@ -107,12 +113,25 @@ struct CallbackCtx {
     Req *req;
 };
 
+// A launch group (grouped mode): device and page-locked staging buffers for
+// up to max_group requests, used by one launch at a time.
+struct Group {
+    cudaStream_t st = nullptr;
+    char *dev = nullptr;      // params | item0 | status | counter
+    char *stage = nullptr;    // page-locked: params | item0 | status (zeros), copied up
+    int *status_host = nullptr;  // page-locked: the status words, copied back
+    size_t o_item0 = 0, o_status = 0, o_counter = 0, bytes = 0;
+    std::vector<Req *> reqs;
+    fz_server_s *srv = nullptr;
+    int index = 0;
+};
+
 struct Req {
     uint64_t ticket = 0;
     int set = 0;
     int32_t n = 0;
     uint64_t count = 0, bytes = 0, off = 0;
-    int slot = -1;
+    int slot = -1;   // per-request mode: its slot; grouped mode: its group
     int status = FZ_SERVE_QUEUED;  // or FZ_SERVE_RUNNING / DONE, or a negative fz_status
     bool has_mem = false;
     double t_submit = 0, t_admit = 0, t_done = 0;
@@ -146,6 +165,10 @@ struct fz_server_s {
     uint64_t next_ticket = 1;
     uint64_t admitted = 0, completed = 0;
     int launch_error = FZ_OK;
+    bool grouped = true;
+    int max_group = 0, in_flight = 0;
+    std::vector<Group> groups;
+    std::vector<int> free_groups;
 };
 
 namespace fz {
@@ -208,8 +231,169 @@ int launch_request(fz_server_s *s, Req *r, cudaStream_t st) {
     return FZ_OK;
 }
 
+// Grouped mode: the completion of a group (its status words were copied
+// back on the group's stream before this callback).
+void CUDART_CB on_group_done(void *p) {
+    Group *G = static_cast<Group *>(p);
+    fz_server_s *s = G->srv;
+    {
+        std::lock_guard<std::mutex> lk(s->mu);
+        const double t = now_s();
+        for (size_t j = 0; j < G->reqs.size(); ++j) {
+            Req *r = G->reqs[j];
+            r->t_done = t;
+            const int dev = G->status_host[j];
+            if (dev == DEV_OK) {
+                r->status = FZ_SERVE_DONE;
+            } else {
+                r->status = dev == DEV_TIMEOUT ? FZ_ETIMEOUT : FZ_EINTERNAL;
+                s->launch_error = r->status;
+            }
+            r->slot = -1;
+            s->completed++;
+        }
+        s->in_flight -= (int)G->reqs.size();
+        G->reqs.clear();
+        s->free_groups.push_back(G->index);
+    }
+    s->cv.notify_one();
+    s->done_cv.notify_all();
+}
+
+// Whether the batch kernel serves a launch of this shape (its run-order
+// copy takes widths up to 8 with at least one walked coordinate).
+bool batch_kernel_serves(const EnumLaunch &L) {
+    if (!L.run_memo) return true;
+    return L.d <= 8 && L.d - L.K - 1 >= 1 && L.K >= 1 && L.K <= 3;
+}
+
+// Enqueue a group of admitted requests (called by the server thread, lock
+// not held): one batch launch over all of them (request j's items follow
+// request j-1's, equal-cost items as in batches), requests the batch kernel
+// does not serve launched one by one after it, then the status words back
+// and the completion callback.
+int launch_group(fz_server_s *s, Group &G) {
+    const size_t pb = enum_params_bytes();
+    const int m = (int)G.reqs.size();
+    DeviceProps dp;
+    int rc = device_props(&dp);
+    if (rc != FZ_OK) return rc;
+    std::vector<EnumLaunch> Ls(m);
+    std::vector<uint64_t> cost(m, 0);
+    std::vector<char> direct(m, 0);
+    uint64_t total_cost = 0;
+    for (int j = 0; j < m; ++j) {
+        const Req *r = G.reqs[j];
+        const SetRec &S = s->sets[r->set];
+        rc = plan_launch_for(S.plan, r->n, &Ls[j]);
+        if (rc != FZ_OK) return rc;
+        EnumLaunch &L = Ls[j];
+        L.status = reinterpret_cast<int *>(G.dev + G.o_status) + j;
+        L.slice_counter = reinterpret_cast<unsigned long long *>(G.dev + G.o_counter);
+        cost[j] = r->count;
+        if (L.RT) {
+            L.total_rows = r->count;
+            L.total_cost = r->count + L.W * S.runs_row[r->n];
+            cost[j] = L.total_cost;
+        }
+        direct[j] = batch_kernel_serves(L) ? 0 : 1;
+        if (!direct[j]) total_cost += cost[j];
+    }
+    const uint64_t warps = (uint64_t)dp.sms * 16;
+    const uint64_t target = std::max<uint64_t>(4096, total_cost / (warps * 8 + 1));
+    uint64_t *item0 = reinterpret_cast<uint64_t *>(G.stage + G.o_item0);
+    item0[0] = 0;
+    for (int j = 0; j < m; ++j) {
+        const Req *r = G.reqs[j];
+        uint64_t items = 0, slice_cost = 64, slice_rows = 4;
+        if (!direct[j] && r->count > 0) {
+            items = std::max<uint64_t>(1, (cost[j] + target - 1) / target);
+            slice_cost = (cost[j] + items - 1) / items;
+            slice_rows = std::max<uint64_t>(4, (r->count + items - 1) / items);
+        }
+        // out holds the byte offset of the request's rows in the arena
+        fill_batch_params(Ls[j], reinterpret_cast<int32_t *>((uintptr_t)r->off), r->count,
+                          slice_rows, slice_cost, G.stage + (size_t)j * pb);
+        item0[j + 1] = item0[j] + items;
+        reinterpret_cast<int *>(G.stage + G.o_status)[j] = DEV_OK;
+    }
+    // parameters, item prefix and zeroed status words: one transfer
+    FZ_CUDA_TRY(cudaMemcpyAsync(G.dev, G.stage, G.o_status + (size_t)m * sizeof(int),
+                                cudaMemcpyHostToDevice, G.st));
+    int32_t *base = static_cast<int32_t *>(s->arena_base);
+    rc = launch_enumerate_batch(G.dev, reinterpret_cast<const uint64_t *>(G.dev + G.o_item0), m,
+                                item0[m], reinterpret_cast<unsigned long long *>(G.dev + G.o_counter),
+                                base, G.st);
+    if (rc != FZ_OK) return rc;
+    for (int j = 0; j < m; ++j) {
+        if (!direct[j] || G.reqs[j]->count == 0) continue;
+        const Req *r = G.reqs[j];
+        int32_t *out = reinterpret_cast<int32_t *>(static_cast<char *>(s->arena_base) + r->off);
+        rc = launch_enumerate(Ls[j], 0, r->count, out, default_slice_rows(r->count, dp.sms), G.st);
+        if (rc != FZ_OK) return rc;
+    }
+    FZ_CUDA_TRY(cudaMemcpyAsync(G.status_host, G.dev + G.o_status, (size_t)m * sizeof(int),
+                                cudaMemcpyDeviceToHost, G.st));
+    FZ_CUDA_TRY(cudaLaunchHostFunc(G.st, on_group_done, &G));
+    return FZ_OK;
+}
+
+void server_loop_grouped(fz_server_s *s) {
+    std::unique_lock<std::mutex> lk(s->mu);
+    while (!s->stop) {
+        bool launched = false;
+        // admit in arrival order into a free group while requests may be in
+        // flight and the exact output bytes are free
+        while (!s->free_groups.empty() && !s->queue.empty() &&
+               s->in_flight < s->cfg.max_in_flight) {
+            const int gi = s->free_groups.back();
+            Group &G = s->groups[gi];
+            G.reqs.clear();
+            while (!s->queue.empty() && (int)G.reqs.size() < s->max_group &&
+                   s->in_flight < s->cfg.max_in_flight) {
+                Req *r = s->queue.front();
+                uint64_t off = 0;
+                if (!s->arena.alloc(r->bytes, &off)) break;
+                s->queue.pop_front();
+                r->off = off;
+                r->has_mem = true;
+                r->slot = gi;
+                r->status = FZ_SERVE_RUNNING;
+                r->t_admit = now_s();
+                s->admitted++;
+                s->in_flight++;
+                G.reqs.push_back(r);
+            }
+            if (G.reqs.empty()) break;  // waiting for output memory
+            s->free_groups.pop_back();
+            lk.unlock();
+            const int rc = launch_group(s, G);
+            lk.lock();
+            if (rc != FZ_OK) {
+                // nothing of this group reaches its callback: fail its requests
+                for (Req *r : G.reqs) {
+                    r->status = rc;
+                    r->t_done = now_s();
+                    r->slot = -1;
+                }
+                s->in_flight -= (int)G.reqs.size();
+                G.reqs.clear();
+                s->free_groups.push_back(gi);
+                s->launch_error = rc;
+                s->done_cv.notify_all();
+            }
+            launched = true;
+        }
+        if (!launched) s->cv.wait_for(lk, std::chrono::microseconds(200));
+    }
+}
+
 void server_loop(fz_server_s *s) {
     cudaSetDevice(s->device);
+    if (s->grouped) {
+        server_loop_grouped(s);
+        return;
+    }
     std::unique_lock<std::mutex> lk(s->mu);
     while (!s->stop) {
         // admit in arrival order while a slot and the exact output bytes are free
@@ -257,16 +441,23 @@ extern "C" {
 
 int fz_serve_create(const fz_serve_cfg_t *cfg, fz_server_t *srv) {
     if (!cfg || !srv) return set_error(FZ_EINVAL, "null pointer");
-    if (cfg->flags != 0 || cfg->max_in_flight < 1 || cfg->streams < 1 || cfg->max_queue < 1)
+    if ((cfg->flags & ~FZ_SERVE_PER_REQUEST) != 0 || cfg->max_in_flight < 1 || cfg->streams < 1 ||
+        cfg->max_queue < 1)
         return set_error(FZ_EINVAL, "serve config");
     fz_server_s *s = new (std::nothrow) fz_server_s;
     if (!s) return set_error(FZ_ENOMEM, "host allocation");
     s->cfg = *cfg;
+    s->grouped = (cfg->flags & FZ_SERVE_PER_REQUEST) == 0;
     auto fail = [&](int rc) {
         for (cudaStream_t st : s->streams) cudaStreamDestroy(st);
         if (s->arena_base) cudaFree(s->arena_base);
         if (s->counters) cudaFree(s->counters);
         if (s->slot_status_host) cudaFreeHost(s->slot_status_host);
+        for (Group &G : s->groups) {
+            if (G.dev) cudaFree(G.dev);
+            if (G.stage) cudaFreeHost(G.stage);
+            if (G.status_host) cudaFreeHost(G.status_host);
+        }
         delete s;
         return rc;
     };
@@ -298,6 +489,30 @@ int fz_serve_create(const fz_serve_cfg_t *cfg, fz_server_t *srv) {
         s->streams.push_back(st);
     }
     for (int i = cfg->max_in_flight - 1; i >= 0; --i) s->free_slots.push_back(i);
+    if (s->grouped) {
+        // one launch group per stream, each for up to max_in_flight requests
+        s->max_group = cfg->max_in_flight;
+        const size_t pb = enum_params_bytes();
+        s->groups.resize(cfg->streams);
+        for (int i = 0; i < cfg->streams; ++i) {
+            Group &G = s->groups[i];
+            G.st = s->streams[i];
+            G.srv = s;
+            G.index = i;
+            G.o_item0 = ((size_t)s->max_group * pb + 255) & ~size_t(255);
+            G.o_status = (G.o_item0 + ((size_t)s->max_group + 1) * 8 + 255) & ~size_t(255);
+            G.o_counter = (G.o_status + (size_t)s->max_group * 4 + 255) & ~size_t(255);
+            G.bytes = G.o_counter + 256;
+            e = cudaMalloc((void **)&G.dev, G.bytes);
+            if (e != cudaSuccess) return fail(cuda_error(e, "cudaMalloc (serve group)"));
+            e = cudaHostAlloc((void **)&G.stage, G.o_counter, cudaHostAllocDefault);
+            if (e != cudaSuccess) return fail(cuda_error(e, "cudaHostAlloc (serve group)"));
+            e = cudaHostAlloc((void **)&G.status_host, (size_t)s->max_group * 4,
+                              cudaHostAllocDefault);
+            if (e != cudaSuccess) return fail(cuda_error(e, "cudaHostAlloc (serve group)"));
+        }
+        for (int i = cfg->streams - 1; i >= 0; --i) s->free_groups.push_back(i);
+    }
     s->th = std::thread(server_loop, s);
     *srv = s;
     return FZ_OK;
@@ -526,6 +741,11 @@ int fz_serve_destroy(fz_server_t s) {
     cudaFree(s->arena_base);
     cudaFree(s->counters);
     cudaFreeHost(s->slot_status_host);
+    for (Group &G : s->groups) {
+        cudaFree(G.dev);
+        cudaFreeHost(G.stage);
+        cudaFreeHost(G.status_host);
+    }
     delete s;
     // device-side failures were reported on the requests they hit
     return FZ_OK;

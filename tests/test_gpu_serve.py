@@ -36,11 +36,14 @@ def alone(fz, g, n):
     return out[:c * len(g)].cpu().numpy().reshape(c, len(g))
 
 
-def test_mix_equals_alone(fz):
+@pytest.mark.parametrize("per_request", [False, True])
+def test_mix_equals_alone(fz, per_request):
+    """Requests launched in groups (default) or one by one: every result
+    equals the same query run alone, and the oracle's list where small."""
     rng = np.random.Generator(np.random.PCG64(41))
     sets = [workloads.draw_generators(rng, int(rng.integers(4, 8)), 5, 60) for _ in range(5)]
     n_max = 700
-    with fz.Server(max_in_flight=16, streams=4) as srv:
+    with fz.Server(max_in_flight=16, streams=4, per_request=per_request) as srv:
         ids = [srv.register(g, n_max) for g in sets]
         reqs = []
         for _ in range(150):
