@@ -90,7 +90,7 @@ struct fz_batch_s {
     std::vector<MemoJob> memo_jobs;
     RunJob *run_jobs_dev = nullptr;
     int nrun = 0, run_inst = 0;
-    uint64_t run_blocks_t = 0, run_blocks_w = 0;  // blocks of the two run-row kernels
+    uint64_t run_blocks = 0;  // blocks of the run-row kernel
     void *params_dev = nullptr;       // EnumParams images (out = word offset)
     uint64_t *item0_dev = nullptr;
     unsigned long long *counter_dev = nullptr;
@@ -278,8 +278,7 @@ int batch_enqueue_rebuild(fz_batch_s *b, cudaStream_t s) {
     }
     int rc = launch_memo_cta_build(b->memo_jobs_dev, b->nmemo, b->status_dev, s);
     if (rc != FZ_OK) return rc;
-    return launch_run_memo_batch(b->run_jobs_dev, b->nrun, b->run_blocks_t, b->run_blocks_w,
-                                 b->status_dev, s);
+    return launch_run_memo_batch(b->run_jobs_dev, b->nrun, b->run_blocks, b->status_dev, s);
 }
 
 __global__ void gather_kernel(const uint64_t *const *ptrs, uint64_t *out, int count) {
@@ -332,16 +331,6 @@ double volume_rows(const Inst &I, int n) {
 // fully parallel pass, and replace memo leaves of one to three rows that
 // cost about 12 warp instructions per output row.
 constexpr double RUN_PAIR_CAP = 2.0;
-
-// FZ_RUN_CLOSED3=0 builds the run-order rows of depth-3 tails from an
-// element-order memo instead of the closed form (tuning only).
-bool run_closed3_enabled() {
-    static const bool on = [] {
-        const char *e = getenv("FZ_RUN_CLOSED3");
-        return !(e && e[0] == '0');
-    }();
-    return on;
-}
 
 // FZ_BATCH_ORDER=0 numbers the work items in the caller's instance order
 // (tuning only; see the item numbering in batch_create_impl).
@@ -555,9 +544,9 @@ int batch_create_impl(const fz_instance_t *inst, int count, const fz_opts_t *opt
     std::vector<int> memo_src;  // instance whose table rows feed the memo
     for (int i = 0; i < count; ++i) {
         Inst &I = b->inst[i];
-        // run-order instances take their rows from the tail's closed form
-        // (depth <= 3): no element-order memo
-        if (I.K <= 0 || I.pair || (I.run && (I.K != 3 || run_closed3_enabled()))) continue;
+        // run-order instances of depth 1 and 2 take their rows from the
+        // tail's closed form: no element-order memo
+        if (I.K <= 0 || I.pair || (I.run && I.K <= 2)) continue;
         std::vector<int32_t> key(I.g + (I.d - I.K), I.g + I.d);
         auto it = memo_of.find(key);
         int m;
@@ -705,35 +694,25 @@ int batch_create_impl(const fz_instance_t *inst, int count, const fz_opts_t *opt
             R.g = S.g[lam];
             R.G = (int32_t)std::min<int64_t>(R.g, (int64_t)S.n + 1);
             R.k = S.K;
-            // the tail's closed form: k = 1, one row when ta divides p;
-            // k = 2, the pair (t0, t1); k = 3, ta over the pair (t0, t1)
-            if (S.K >= 2) {
+            // depth 1 and 2: the tail's closed form (k = 1, one row when ta
+            // divides p; k = 2, the pair (t0, t1)); depth 3: rows copied from
+            // the element-order memo
+            if (S.K == 2) {
                 R.t0 = S.g[S.d - 2];
                 R.t1 = S.g[S.d - 1];
                 int64_t g1;
                 pair_params(R.t0, R.t1, &R.e, &R.h1, &g1, &R.inv);
-            }
-            if (S.K == 1 || S.K == 3) R.ta = S.g[S.d - S.K];
-            if (S.K == 1) {
-                R.expect_rows = (uint64_t)(S.n / R.ta) + 1;
-            } else if (S.K == 2) {
                 R.expect_rows = pair_rows_upto(S.n, R.t0, R.t1);
-            } else if (S.K == 3 && !run_closed3_enabled()) {
-                // rows copied from the element-order memo
+            } else if (S.K == 1) {
+                R.ta = S.g[S.d - 1];
+                R.expect_rows = (uint64_t)(S.n / R.ta) + 1;
+            } else if (S.K == 3) {
                 if (S.memo < 0 || b->memo_jobs[S.memo].top < S.n + 1)
                     return fail(set_error(FZ_EINTERNAL, "run-order memo without its full memo"));
                 const MemoJob &M = b->memo_jobs[S.memo];
                 R.O = M.O;
                 R.rows = M.R;
                 R.expect_rows = M.rows;
-            } else if (S.K == 3) {
-                // sum over a of the pair's rows up to n - a ta
-                if ((int64_t)S.n / R.ta > (1 << 22))
-                    return fail(set_error(FZ_EINVAL, "batch run-order memo too large"));
-                uint64_t tot = 0;
-                for (int64_t a = 0; a * R.ta <= S.n; ++a)
-                    tot += pair_rows_upto(S.n - a * R.ta, R.t0, R.t1);
-                R.expect_rows = tot;
             } else {
                 return fail(set_error(FZ_EINTERNAL, "run-order memo of depth > 3"));
             }
@@ -753,28 +732,20 @@ int batch_create_impl(const fz_instance_t *inst, int count, const fz_opts_t *opt
                 R.cls_beg = reinterpret_cast<uint64_t *>(base + off);
                 off += a256(((size_t)R.G + 1) * 8);
             }
-            // block ranges of the two row kernels (256 threads a block):
-            // a thread per element, or a warp per element for depth 3
-            uint64_t bt = 0, bw = 0;
+            // block ranges of the row kernel (256 threads a block, a thread
+            // per element)
+            uint64_t bt = 0;
             for (RunJob &R : rj) {
-                const uint64_t elems = (uint64_t)R.n + 1;
-                const bool w = !R.O && R.k == 3;
-                R.blk0_t = bt;
-                R.blk0_w = bw;
-                if (w)
-                    bw += (elems + 7) / 8;
-                else
-                    bt += (elems + 255) / 256;
+                R.blk0 = bt;
+                bt += ((uint64_t)R.n + 256) / 256;
             }
-            if (bt > 0x7fffffffull || bw > 0x7fffffffull)
+            if (bt > 0x7fffffffull)
                 return fail(set_error(FZ_EINVAL, "batch run-order memos too large"));
-            b->run_blocks_t = bt;
-            b->run_blocks_w = bw;
+            b->run_blocks = bt;
             b->run_jobs_dev = reinterpret_cast<RunJob *>(base);
             FZ_CUDA_TRY(cudaMemcpyAsync(b->run_jobs_dev, rj.data(), rj.size() * sizeof(RunJob),
                                         cudaMemcpyHostToDevice, s));
-            rc = launch_run_memo_batch(b->run_jobs_dev, b->nrun, b->run_blocks_t,
-                                       b->run_blocks_w, b->status_dev, s);
+            rc = launch_run_memo_batch(b->run_jobs_dev, b->nrun, b->run_blocks, b->status_dev, s);
             if (rc != FZ_OK) return fail(rc);
             FZ_CUDA_TRY(cudaStreamSynchronize(s));  // rj is a host temporary
         }

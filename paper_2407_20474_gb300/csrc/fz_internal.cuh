@@ -321,10 +321,9 @@ int launch_memo_cta_build(const MemoJob *jobs, int njobs, int *status, cudaStrea
 // One run-order memo of a batch (the layout of launch_run_memo) for the
 // elements 0..n: its rows come from an element-order memo of depth k <= 3
 // (O, rows), or, with O null, from the closed form of the tail: k = 1, the
-// one row p / ta when ta divides p; k = 2, the pair (t0, t1) = (g_{d-2},
-// g_{d-1}), whose rows for element p have a_{d-2} = a_top - o h1 (o = 0, 1,
-// ...) as in launch_memo_closed; k = 3, for each a_{d-3} = p div ta down to
-// 0 (ta = g_{d-3}) the pair's rows of p - a_{d-3} ta.
+// one row p / ta when ta divides p (ta = g_{d-1}); k = 2, the pair (t0, t1)
+// = (g_{d-2}, g_{d-1}), whose rows for element p have a_{d-2} = a_top - o h1
+// (o = 0, 1, ...) as in launch_memo_closed.
 struct RunJob {
     const uint64_t *Clam;   // count-table row lam of the source instance, n + 1 entries
     const uint64_t *Cnext;  // row lam + 1: |Z(p, tail)|
@@ -336,18 +335,14 @@ struct RunJob {
     uint64_t expect_rows;   // closed form: sum over p <= n of |Z(p, tail)|
     int32_t n, g, G, k;     // last element, g_lam, G = min(g_lam, n + 1), depth
     int64_t t0, t1, e, h1, inv;
-    int64_t ta;             // closed form, k = 1 or 3: the first tail generator
-    // first block of this job in the row kernels: a thread per element
-    // (closed forms of depth 1 and 2, element-order memos) and a warp per
-    // element (closed forms of depth 3); a job owns ceil((n + 1) / 256),
-    // resp. ceil((n + 1) / 8), blocks of its kernel and none of the other
-    uint64_t blk0_t, blk0_w;
+    int64_t ta;             // closed form, k = 1: the tail's generator
+    uint64_t blk0;          // first block of this job in the row kernel
 };
-// Builds every job's class starts, then its rows: blocks_t blocks of the
-// thread-per-element kernel and blocks_w of the warp-per-element kernel
-// (the totals of the jobs' block ranges; zero skips the launch).
-int launch_run_memo_batch(const RunJob *jobs, int njobs, uint64_t blocks_t, uint64_t blocks_w,
-                          int *status, cudaStream_t s);
+// Builds every job's class starts, then its rows: `blocks` blocks of 256
+// threads, job j owning ceil((n_j + 1) / 256) of them from blk0 on (zero
+// skips the launch).
+int launch_run_memo_batch(const RunJob *jobs, int njobs, uint64_t blocks, int *status,
+                          cudaStream_t s);
 
 // out[w] = w for w < words, 16-byte stores (fz_write_probe; fz_count.cu).
 int launch_write_probe(int32_t *out, uint64_t words, cudaStream_t s);

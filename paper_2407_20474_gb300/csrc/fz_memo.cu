@@ -547,174 +547,14 @@ __global__ void __launch_bounds__(MB_THREADS) memo_sizes_kernel(const MemoJob *_
     if (threadIdx.x == 0) rows_out[blockIdx.x] = total;
 }
 
-// One CTA of MB_BUILD_THREADS per memo.  Inside an elementwise batch the
-// elements are spread over the warps (several warps per element when the
-// batch has fewer elements than warps).  An element's rows are one
-// contiguous range of the memo, the concatenation of its k blocks
-// incr_i(Z_{>=i}(m - t_i)); its warps copy that range as one flat run of
-// words: lane words are consecutive (coalesced stores), each word finds its
-// block in the element's k block descriptors (shared memory, filled by
-// lanes 0..k-1 with one round of parallel loads) and its source word in the
-// suffix block of Z(m - t_i), adding one to coordinate i.  A lane loads
-// MB_ILP words before it stores them, so an element of W words costs one
-// round of descriptor loads plus about W / (32 MB_ILP warps) L2 round trips.
+// One CTA of MB_BUILD_THREADS per memo.  Inside an elementwise batch each
+// warp copies whole (element, generator) blocks as flat word copies; a lane
+// loads MB_ILP words before it stores them, so a block of W words costs
+// about W / (32 MB_ILP) L2 round trips.
 constexpr int MB_BUILD_THREADS = 1024;
 constexpr int MB_ILP = 8;
-constexpr int MB_WARPS = MB_BUILD_THREADS / 32;
-
-struct MemoBlockDesc {
-    uint64_t end;  // end row of the block in the element (exclusive prefix of lengths)
-    uint64_t src;  // first source row: the suffix Z_{>=i}(m - t_i) of Z(m - t_i)
-};
 
 __global__ void __launch_bounds__(MB_BUILD_THREADS) memo_cta_build_kernel(
-    const MemoJob *__restrict__ jobs, int *status) {
-    __shared__ uint64_t sums[33];
-    __shared__ MemoBlockDesc desc[MB_WARPS][FZ_MAX_D];
-    const MemoJob J = jobs[blockIdx.x];
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const int nwarps = blockDim.x >> 5;
-    const int k = J.k;
-    // offsets: O[0] = 0, O[m+1] = O[m] + |Z(m, tail)| (chunked block scan)
-    uint64_t carry = 0;
-    for (int base = 0; base < J.top; base += blockDim.x) {
-        const int m = base + threadIdx.x;
-        const uint64_t v = m < J.top ? __ldg(J.Ct + m) : 0ull;
-        uint64_t tot;
-        const uint64_t ex = block_exclusive_scan(v, sums, &tot);
-        if (m < J.top) J.O[m] = carry + ex;
-        carry += tot;
-    }
-    if (threadIdx.x == 0) J.O[J.top] = carry;
-    __syncthreads();
-    if (carry != J.rows) {
-        if (threadIdx.x == 0) atomicExch(status, (int)DEV_INTERNAL);
-        return;
-    }
-    if (k < 1 || k > FZ_MAX_D) {
-        if (threadIdx.x == 0) atomicExch(status, (int)DEV_INTERNAL);
-        return;
-    }
-    MemoBlockDesc *dsc = desc[warp];
-    // elementwise batches of b elements
-    for (int m0 = 0; m0 < J.top; m0 += J.b) {
-        const int m1 = m0 + J.b < J.top ? m0 + J.b : J.top;
-        const int nb = m1 - m0;
-        const int wpe = nb >= nwarps ? 1 : nwarps / nb;  // warps per element
-        const int groups = nwarps / wpe;
-        const int sub = warp % wpe;
-        // a lane's word index grows by 32 wpe: rows by rstep, coordinates by cstep
-        const uint64_t wstep = 32ull * (uint64_t)wpe;
-        const uint64_t rstep = wstep / (uint64_t)k;
-        const uint32_t cstep = (uint32_t)(wstep - rstep * (uint64_t)k);
-        for (int e = warp / wpe; e < nb && warp < groups * wpe; e += groups) {
-            const int m = m0 + e;
-            const uint64_t dst0 = J.O[m];
-            if (m == 0) {  // Z(0) = {0}
-                if (sub == 0 && lane < k) J.R[lane] = 0;
-                continue;
-            }
-            // block descriptors: lane i < k holds block i
-            uint64_t len = 0, src = 0;
-            if (lane < k) {
-                const int sm = m - J.t[lane];
-                if (sm >= 0) {
-                    len = __ldg(J.Ct + (int64_t)lane * J.cs + sm);
-                    src = J.O[sm + 1] - len;  // the suffix block of Z(sm)
-                }
-            }
-            const uint64_t incl = warp_incl_scan(len, lane);
-            const uint64_t total = shfl_u64(incl, 31);
-            if (lane < k) dsc[lane] = MemoBlockDesc{incl, src};
-            __syncwarp();
-            if (total != J.O[m + 1] - dst0) {  // the block sizes must fill Z(m)
-                if (lane == 0) atomicExch(status, (int)DEV_INTERNAL);
-                __syncwarp();
-                continue;
-            }
-            const uint64_t W = total * (uint64_t)k;
-            int32_t *out = J.R + dst0 * (uint64_t)k;
-            if (W > (uint64_t)(32 * MB_ILP * wpe)) {
-                // large element: block by block, a flat copy of len_i k words
-                // from the suffix block with one added to every k-th word
-                // (the cheapest loop per word; blocks are long here)
-                uint64_t bstart = 0;
-                for (int i = 0; i < k; ++i) {
-                    const uint64_t bl = shfl_u64(len, i);
-                    const uint64_t bs = shfl_u64(src, i);
-                    if (bl == 0) continue;
-                    const uint64_t BW = bl * (uint64_t)k;
-                    const int32_t *a = J.R + bs * (uint64_t)k;
-                    int32_t *bdst = out + bstart * (uint64_t)k;
-                    const uint64_t first = (uint64_t)lane + 32ull * (uint64_t)sub;
-                    uint32_t c0 = (uint32_t)(first % (uint64_t)k);  // coordinate of word `first`
-                    for (uint64_t w0 = first; w0 < BW; w0 += wstep * MB_ILP) {
-                        int32_t v[MB_ILP];
-#pragma unroll
-                        for (int u = 0; u < MB_ILP; ++u)
-                            if (w0 + wstep * u < BW) v[u] = a[w0 + wstep * u];
-                        uint32_t c = c0;
-#pragma unroll
-                        for (int u = 0; u < MB_ILP; ++u) {
-                            if (w0 + wstep * u < BW)
-                                bdst[w0 + wstep * u] = v[u] + (c == (uint32_t)i ? 1 : 0);
-                            c += cstep;
-                            if (c >= (uint32_t)k) c -= (uint32_t)k;
-                        }
-                        c0 = c;
-                    }
-                    bstart += bl;
-                }
-                __syncwarp();
-                continue;
-            }
-            // word w = lane + 32 (sub + wpe t): row r = w div k, coordinate c
-            uint64_t w = (uint64_t)lane + 32ull * (uint64_t)sub;
-            uint64_t r = w / (uint64_t)k;
-            uint32_t c = (uint32_t)(w - r * (uint64_t)k);
-            int j = 0;  // block of row r (rows only grow along a lane)
-            uint64_t jbeg = 0, jend = dsc[0].end, jsrc = dsc[0].src;
-            while (w < W) {
-                int32_t v[MB_ILP];
-                const uint64_t w0 = w;
-#pragma unroll
-                for (int u = 0; u < MB_ILP; ++u) {
-                    v[u] = 0;
-                    if (w < W) {
-                        while (r >= jend) {  // next non-empty block
-                            ++j;
-                            jbeg = jend;
-                            jend = dsc[j].end;
-                            jsrc = dsc[j].src;
-                        }
-                        const uint64_t sw = (jsrc + (r - jbeg)) * (uint64_t)k + c;
-                        v[u] = J.R[sw] + (c == (uint32_t)j ? 1 : 0);
-                    }
-                    w += wstep;
-                    r += rstep;
-                    c += cstep;
-                    if (c >= (uint32_t)k) {
-                        c -= (uint32_t)k;
-                        ++r;
-                    }
-                }
-#pragma unroll
-                for (int u = 0; u < MB_ILP; ++u) {
-                    const uint64_t wu = w0 + (uint64_t)u * wstep;
-                    if (wu < W) out[wu] = v[u];
-                }
-            }
-            __syncwarp();  // dsc is reused by the warp's next element
-        }
-        __syncthreads();
-    }
-}
-
-// The same memos copied (element, generator) block by block, each warp
-// loading a block's length and offset before copying it (the descriptor
-// loads of an element's k blocks are dependent round trips).  Kept for
-// comparison behind FZ_MEMO_CTA=blocks (tuning only).
-__global__ void __launch_bounds__(MB_BUILD_THREADS) memo_cta_build_blocks_kernel(
     const MemoJob *__restrict__ jobs, int *status) {
     __shared__ uint64_t sums[33];
     const MemoJob J = jobs[blockIdx.x];
@@ -873,12 +713,11 @@ __global__ void __launch_bounds__(RUN_CB_THREADS) run_class_begin_batch_kernel(
     }
 }
 
-// Batches, run-order rows of the tails of depth 1 and 2 and of element-order
-// memos: a thread per element (jobs along y; these elements hold a few rows
-// each).  Rows come from the element-order memo (O, rows), or from the
-// closed form: k = 1, the one row p / ta when ta divides p; k = 2, the
-// progression of the pair (t0, t1).  Jobs of depth 3 are left to the next
-// kernel.
+// Batches: a thread per element (these elements hold a few rows each), each
+// job owning the blocks [blk0, blk0 + ceil((n + 1) / 256)) of the launch.
+// Rows come from the element-order memo (O, rows), or from the closed form:
+// k = 1, the one row p / ta when ta divides p; k = 2, the progression of the
+// pair (t0, t1).
 __device__ __forceinline__ uint32_t pair_first(const RunJob &J, int64_t r, int64_t *atop) {
     // rows of Z(r, (t0, t1)): a_{d-2} = atop, atop - h1, ..., >= 0 (none if
     // atop < 0); r, t0 and h1 fit in 32 bits
@@ -915,13 +754,12 @@ __global__ void __launch_bounds__(THREADS) run_rows_batch_kernel(const RunJob *_
                                                                  int njobs, int *status) {
     __shared__ int s_job;
     if (threadIdx.x == 0)
-        s_job = job_of_block(njobs, blockIdx.x, [&](int j) { return jobs[j].blk0_t; });
+        s_job = job_of_block(njobs, blockIdx.x, [&](int j) { return jobs[j].blk0; });
     __syncthreads();
     {
         const RunJob &J = jobs[s_job];
-        if (!J.O && J.k == 3) return;  // (owns no block here) run_rows3_batch_kernel
         const int64_t g = J.g;
-        const int64_t p = (int64_t)(blockIdx.x - J.blk0_t) * blockDim.x + threadIdx.x;
+        const int64_t p = (int64_t)(blockIdx.x - J.blk0) * blockDim.x + threadIdx.x;
         if (p <= J.n) {
             const int64_t q = p / g, c = p - q * g;
             const uint64_t tail_rows = __ldg(J.Cnext + p);
@@ -965,81 +803,16 @@ __global__ void __launch_bounds__(THREADS) run_rows_batch_kernel(const RunJob *_
     }
 }
 
-// Batches, run-order rows of tails of depth 3 from their closed form: a warp
-// per element (elements hold up to thousands of rows), lanes on consecutive
-// rows so every store of a warp is coalesced.  For a = p div ta down to 0,
-// 32 values at a time (one per lane: each counts its pair rows of p - a ta,
-// a warp scan places them), each row finds its lane by a binary search over
-// the 32 running totals.
-__global__ void __launch_bounds__(THREADS) run_rows3_batch_kernel(const RunJob *__restrict__ jobs,
-                                                                  int njobs, int *status) {
-    const int lane = threadIdx.x & 31;
-    __shared__ int s_job;
-    if (threadIdx.x == 0)
-        s_job = job_of_block(njobs, blockIdx.x, [&](int j) { return jobs[j].blk0_w; });
-    __syncthreads();
-    {
-        const RunJob &J = jobs[s_job];
-        if (J.O || J.k != 3) return;  // owns no block here
-        const int64_t g = J.g;
-        const int64_t p = (int64_t)(blockIdx.x - J.blk0_w) * (blockDim.x >> 5) + (threadIdx.x >> 5);
-        if (p <= J.n) {
-            const int64_t q = p / g, c = p - q * g;
-            const uint64_t tail_rows = __ldg(J.Cnext + p);
-            const uint64_t dst = __ldg(J.cls_beg + c) + __ldg(J.Clam + p) - tail_rows;
-            if (dst + tail_rows > J.out_rows) {
-                if (lane == 0) atomicExch(status, (int)DEV_INTERNAL);
-                return;
-            }
-            int4 *o = J.out + dst;
-            uint64_t base = 0;
-            for (int64_t a0 = p / J.ta; a0 >= 0; a0 -= 32) {
-                const int64_t a = a0 - lane;
-                const int64_t ra = a >= 0 ? p - a * J.ta : -1;
-                int64_t btop = -1;
-                const uint64_t cnt = a >= 0 ? pair_first(J, ra, &btop) : 0u;
-                const uint64_t incl = warp_incl_scan(cnt, lane);
-                const uint64_t tot = shfl_u64(incl, 31);
-                for (uint64_t rr0 = 0; rr0 < tot; rr0 += 32) {
-                    const uint64_t rr = rr0 + (uint64_t)lane;
-                    // lane l of the group holding row rr: lanes with incl <= rr
-                    int l = 0;
-#pragma unroll
-                    for (int sft = 16; sft >= 1; sft >>= 1) {
-                        const uint64_t e = shfl_u64(incl, l + sft - 1);
-                        if (e <= rr) l += sft;
-                    }
-                    uint64_t ex = shfl_u64(incl, l > 0 ? l - 1 : 0);
-                    if (l == 0) ex = 0;
-                    const int64_t bt = (int64_t)shfl_u64((uint64_t)btop, l);
-                    const int64_t rl = (int64_t)shfl_u64((uint64_t)ra, l);
-                    if (rr < tot && base + rr < tail_rows) {
-                        const int64_t b = bt - (int64_t)(rr - ex) * J.h1;
-                        const uint32_t cc = (uint32_t)(rl - b * J.t0) / (uint32_t)J.t1;
-                        o[base + rr] = make_int4((int)q, (int)(a0 - l), (int)b, (int)cc);
-                    }
-                }
-                base += tot;
-            }
-            if (base != tail_rows && lane == 0) atomicExch(status, (int)DEV_INTERNAL);
-        }
-    }
-}
-
 }  // namespace
 
-int launch_run_memo_batch(const RunJob *jobs, int njobs, uint64_t blocks_t, uint64_t blocks_w,
-                          int *status, cudaStream_t s) {
+int launch_run_memo_batch(const RunJob *jobs, int njobs, uint64_t blocks, int *status,
+                          cudaStream_t s) {
     if (njobs <= 0) return FZ_OK;
     if (!jobs || !status) return set_error(FZ_EINTERNAL, "run memo batch: missing device buffer");
     run_class_begin_batch_kernel<<<njobs, RUN_CB_THREADS, 0, s>>>(jobs, status);
     note_launch();
-    if (blocks_t > 0) {
-        run_rows_batch_kernel<<<(unsigned)blocks_t, THREADS, 0, s>>>(jobs, njobs, status);
-        note_launch();
-    }
-    if (blocks_w > 0) {
-        run_rows3_batch_kernel<<<(unsigned)blocks_w, THREADS, 0, s>>>(jobs, njobs, status);
+    if (blocks > 0) {
+        run_rows_batch_kernel<<<(unsigned)blocks, THREADS, 0, s>>>(jobs, njobs, status);
         note_launch();
     }
     FZ_CUDA_TRY(cudaGetLastError());
@@ -1075,22 +848,9 @@ int launch_memo_sizes(const MemoJob *jobs, int njobs, uint64_t *rows_out, cudaSt
     return FZ_OK;
 }
 
-// FZ_MEMO_CTA=blocks builds batch memos with the block-by-block kernel
-// (tuning only).
-static bool memo_cta_blocks() {
-    static const bool on = [] {
-        const char *e = getenv("FZ_MEMO_CTA");
-        return e && std::strcmp(e, "blocks") == 0;
-    }();
-    return on;
-}
-
 int launch_memo_cta_build(const MemoJob *jobs, int njobs, int *status, cudaStream_t s) {
     if (njobs <= 0) return FZ_OK;
-    if (memo_cta_blocks())
-        memo_cta_build_blocks_kernel<<<njobs, MB_BUILD_THREADS, 0, s>>>(jobs, status);
-    else
-        memo_cta_build_kernel<<<njobs, MB_BUILD_THREADS, 0, s>>>(jobs, status);
+    memo_cta_build_kernel<<<njobs, MB_BUILD_THREADS, 0, s>>>(jobs, status);
     note_launch();
     FZ_CUDA_TRY(cudaGetLastError());
     return FZ_OK;
