@@ -979,6 +979,35 @@ int fz_batch_autotune(const fz_instance_t *inst, int count, fz_batch_tune_entry_
     FZ_CUDA_TRY(cudaEventCreate(&e2));
     int rc = FZ_OK;
     DevArena out;
+    // rebuild + enumeration of a created batch, mean of 3 after a warm-up
+    auto time_batch = [&](fz_batch_s *b, double *build_ms, double *enum_ms) -> int {
+        if (out.bytes < b->total_words * 4 + 256) {
+            const int r = out.alloc(b->total_words * 4 + 256);
+            if (r != FZ_OK) return r;
+        }
+        double bsum = 0, esum = 0;
+        int r = FZ_OK;
+        for (int rep = 0; rep < 4 && r == FZ_OK; ++rep) {  // rep 0 warms up
+            cudaEventRecord(e0, s);
+            r = fz_batch_rebuild(b, s);
+            cudaEventRecord(e1, s);
+            if (r == FZ_OK)
+                r = fz_batch_enumerate(b, static_cast<int32_t *>(out.p), b->total_words, s);
+            cudaEventRecord(e2, s);
+            if (r == FZ_OK) r = fz_batch_sync(b, s);
+            float b_ms = 0, e_ms = 0;
+            cudaEventElapsedTime(&b_ms, e0, e1);
+            cudaEventElapsedTime(&e_ms, e1, e2);
+            if (rep > 0) {
+                bsum += b_ms;
+                esum += e_ms;
+            }
+        }
+        *build_ms = bsum / 3;
+        *enum_ms = esum / 3;
+        return r;
+    };
+    BatchPolicy margin = base;  // per-width fastest where >= 10 % faster than the default
     for (int d = 3; d <= FZ_MAX_D && rc == FZ_OK; ++d) {
         // the instances of this width (up to 1024, spread over the list):
         // memo builds run one CTA per memo in waves and the enumeration's
@@ -991,13 +1020,28 @@ int fz_batch_autotune(const fz_instance_t *inst, int count, fz_batch_tune_entry_
         std::vector<fz_instance_t> sub;
         const size_t step = (all.size() + 1023) / 1024;
         for (size_t i = 0; i < all.size(); i += step) sub.push_back(all[i]);
-        double best_t = 1e300;
+        double best_t = 1e300, base_t = -1;
         double best_cap = base.cap_rows[d];
         bool best_run = base.run_order[d];
         std::vector<std::pair<double, bool>> cands;
         for (double c : caps) cands.push_back({c, true});
         for (double c : caps) cands.push_back({c, false});
         std::vector<std::vector<int>> seen;  // memo depth and layout choices already timed
+        std::vector<double> seen_t;
+        std::vector<int> base_key;
+        {
+            fz_batch_t b0 = nullptr;
+            if (batch_create_impl(sub.data(), (int)sub.size(), nullptr, base, &b0, s) == FZ_OK) {
+                for (const Inst &I : b0->inst) {
+                    base_key.push_back(I.K);
+                    base_key.push_back(I.top);
+                    base_key.push_back(I.pair ? 1 : 0);
+                    base_key.push_back(I.run ? 1 : 0);
+                }
+                fz_batch_destroy(b0);
+            }
+            cudaGetLastError();
+        }
         for (auto &cand : cands) {
             BatchPolicy pol = tuned;
             pol.cap_rows[d] = cand.first;
@@ -1025,33 +1069,13 @@ int fz_batch_autotune(const fz_instance_t *inst, int count, fz_batch_tune_entry_
                 fz_batch_destroy(b);
                 continue;
             }
-            seen.push_back(key);
-            if (out.bytes < b->total_words * 4 + 256) {
-                rc = out.alloc(b->total_words * 4 + 256);
-                if (rc != FZ_OK) {
-                    fz_batch_destroy(b);
-                    break;
-                }
-            }
-            double bsum = 0, esum = 0;
-            for (int rep = 0; rep < 4 && rc == FZ_OK; ++rep) {  // rep 0 warms up
-                cudaEventRecord(e0, s);
-                rc = fz_batch_rebuild(b, s);
-                cudaEventRecord(e1, s);
-                if (rc == FZ_OK)
-                    rc = fz_batch_enumerate(b, static_cast<int32_t *>(out.p), b->total_words, s);
-                cudaEventRecord(e2, s);
-                if (rc == FZ_OK) rc = fz_batch_sync(b, s);
-                float b_ms = 0, e_ms = 0;
-                cudaEventElapsedTime(&b_ms, e0, e1);
-                cudaEventElapsedTime(&e_ms, e1, e2);
-                if (rep > 0) {
-                    bsum += b_ms;
-                    esum += e_ms;
-                }
-            }
+            double b_ms = 0, e_ms = 0;
+            rc = time_batch(b, &b_ms, &e_ms);
             if (rc == FZ_OK) {
-                const double t = (bsum + esum) / 3;
+                const double t = b_ms + e_ms;
+                seen.push_back(key);
+                seen_t.push_back(t);
+                if (key == base_key) base_t = t;
                 if (found < capacity) {
                     fz_batch_tune_entry_t &E = entries[found];
                     E.d = d;
@@ -1063,8 +1087,8 @@ int fz_batch_autotune(const fz_instance_t *inst, int count, fz_batch_tune_entry_
                     uint64_t mr = 0;
                     for (const MemoJob &J : b->memo_jobs) mr += J.rows;
                     E.memo_rows = mr;
-                    E.build_ms = bsum / 3;
-                    E.enum_ms = esum / 3;
+                    E.build_ms = b_ms;
+                    E.enum_ms = e_ms;
                     E.total_ms = t;
                 }
                 ++found;
@@ -1078,7 +1102,64 @@ int fz_batch_autotune(const fz_instance_t *inst, int count, fz_batch_tune_entry_
         }
         tuned.cap_rows[d] = best_cap;
         tuned.run_order[d] = best_run;
+        if (base_t > 0 && best_t <= 0.9 * base_t) {
+            margin.cap_rows[d] = best_cap;
+            margin.run_order[d] = best_run;
+        }
     }
+    // The widths' fastest choices need not combine: the enumeration of a
+    // mixed batch shares the GPU, its L2 and its instruction cache among
+    // widths.  So the whole batch is timed under the default policy, the
+    // per-width fastest and the per-width fastest that beat the default by
+    // 10 % or more, and the fastest of those is kept.
+    const BatchPolicy whole[3] = {base, tuned, margin};
+    int keep = 0;
+    double keep_t = 1e300;
+    for (int c = 0; c < 3 && rc == FZ_OK; ++c) {
+        bool same = false;
+        for (int c2 = 0; c2 < c; ++c2) {
+            bool eq = true;
+            for (int d = 0; d <= FZ_MAX_D; ++d)
+                eq = eq && whole[c].cap_rows[d] == whole[c2].cap_rows[d] &&
+                     whole[c].run_order[d] == whole[c2].run_order[d];
+            same = same || eq;
+        }
+        if (same) continue;
+        fz_batch_t b = nullptr;
+        rc = batch_create_impl(inst, count, nullptr, whole[c], &b, s);
+        if (rc == FZ_ENOMEM || rc == FZ_EINVAL) {
+            cudaGetLastError();
+            rc = FZ_OK;
+            continue;
+        }
+        if (rc != FZ_OK) break;
+        double b_ms = 0, e_ms = 0;
+        rc = time_batch(b, &b_ms, &e_ms);
+        if (rc == FZ_OK) {
+            if (found < capacity) {
+                fz_batch_tune_entry_t &E = entries[found];
+                E.d = 0;           // the whole batch
+                E.run_order = c;   // which policy (see fz.h)
+                E.instances = count;
+                E.memos = b->nmemo;
+                E.cap_rows = -1.0;
+                E.rows = b->total_rows;
+                uint64_t mr = 0;
+                for (const MemoJob &J : b->memo_jobs) mr += J.rows;
+                E.memo_rows = mr;
+                E.build_ms = b_ms;
+                E.enum_ms = e_ms;
+                E.total_ms = b_ms + e_ms;
+            }
+            ++found;
+            if (b_ms + e_ms < keep_t) {
+                keep_t = b_ms + e_ms;
+                keep = c;
+            }
+        }
+        fz_batch_destroy(b);
+    }
+    tuned = whole[keep];
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     cudaEventDestroy(e2);

@@ -76,20 +76,33 @@ def test_plan_batch_layout(fz):
 
 
 def test_batch_autotune(fz):
-    """The measured memo policy: every width's chosen (cap, layout) is its
-    fastest timed candidate, and batches created under it equal the oracle."""
+    """The measured memo policy: each width's candidates are timed, then the
+    whole batch under the default policy, the widths' fastest and the
+    fastest where 10 % better; the kept policy is the fastest whole-batch
+    one, and batches created under it equal the oracle."""
     inst = small_instances(43, 150)
+    default = {d: fz.fz_batch_policy(d) for d in range(3, 9)}
     try:
         rows, chosen = fz.fz_batch_autotune(inst)
-        assert rows, "no candidate timed"
-        for d, (cap, run) in chosen.items():
-            cands = [r for r in rows if r["d"] == d]
-            if not cands:
-                continue
-            best = min(cands, key=lambda r: r["total_ms"])
-            assert (best["cap_rows"], bool(best["run_order"])) == (cap, run), d
-            for r in cands:
+        per_width = [r for r in rows if r["d"] > 0]
+        whole = [r for r in rows if r["d"] == 0]
+        assert per_width and whole, "no candidate timed"
+        fastest = {}
+        for d in {r["d"] for r in per_width}:
+            best = min((r for r in per_width if r["d"] == d), key=lambda r: r["total_ms"])
+            fastest[d] = (best["cap_rows"], bool(best["run_order"]))
+            for r in per_width:
                 assert r["rows"] > 0 and r["total_ms"] > 0
+        kept = min(whole, key=lambda r: r["total_ms"])["run_order"]
+        for d, pol in chosen.items():
+            if d not in fastest:
+                continue
+            if kept == 0:
+                assert pol == default[d], d
+            elif kept == 1:
+                assert pol == fastest[d], d
+            else:
+                assert pol in (default[d], fastest[d]), d
         b, segs = run_batch(fz, inst)
         for (g, n), got in zip(inst, segs):
             assert np.array_equal(got, oracle.enumerate_desc(g, n)), (g, n)
