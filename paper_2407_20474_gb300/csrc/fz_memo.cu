@@ -547,14 +547,17 @@ __global__ void __launch_bounds__(MB_THREADS) memo_sizes_kernel(const MemoJob *_
     if (threadIdx.x == 0) rows_out[blockIdx.x] = total;
 }
 
-// One CTA of MB_BUILD_THREADS per memo.  Inside an elementwise batch each
-// warp copies whole (element, generator) blocks as flat word copies; a lane
-// loads MB_ILP words before it stores them, so a block of W words costs
-// about W / (32 MB_ILP) L2 round trips.
-constexpr int MB_BUILD_THREADS = 1024;
+// One CTA of T threads per memo.  Inside an elementwise batch each warp
+// copies whole (element, generator) blocks as flat word copies; a lane loads
+// MB_ILP words before it stores them, so a block of W words costs about
+// W / (32 MB_ILP) L2 round trips.  The kernel needs 57 registers a thread
+// (64 allocated), so 1024 threads fit on an SM: one CTA of 1024, or several
+// smaller CTAs, each building its own memo.
 constexpr int MB_ILP = 8;
+constexpr int MB_CTA_THREADS_DEFAULT = 1024;
 
-__global__ void __launch_bounds__(MB_BUILD_THREADS) memo_cta_build_kernel(
+template <int T>
+__global__ void __launch_bounds__(T, 1024 / T) memo_cta_build_kernel(
     const MemoJob *__restrict__ jobs, int *status) {
     __shared__ uint64_t sums[33];
     const MemoJob J = jobs[blockIdx.x];
@@ -848,9 +851,24 @@ int launch_memo_sizes(const MemoJob *jobs, int njobs, uint64_t *rows_out, cudaSt
     return FZ_OK;
 }
 
+// CTA size of the batch memo build: FZ_MEMO_CTA_THREADS=256|512|1024
+// (tuning only).
+static int memo_cta_threads() {
+    static const int t = [] {
+        const char *e = getenv("FZ_MEMO_CTA_THREADS");
+        const int v = e ? atoi(e) : 0;
+        return (v == 256 || v == 512 || v == 1024) ? v : MB_CTA_THREADS_DEFAULT;
+    }();
+    return t;
+}
+
 int launch_memo_cta_build(const MemoJob *jobs, int njobs, int *status, cudaStream_t s) {
     if (njobs <= 0) return FZ_OK;
-    memo_cta_build_kernel<<<njobs, MB_BUILD_THREADS, 0, s>>>(jobs, status);
+    switch (memo_cta_threads()) {
+        case 256: memo_cta_build_kernel<256><<<njobs, 256, 0, s>>>(jobs, status); break;
+        case 512: memo_cta_build_kernel<512><<<njobs, 512, 0, s>>>(jobs, status); break;
+        default: memo_cta_build_kernel<1024><<<njobs, 1024, 0, s>>>(jobs, status); break;
+    }
     note_launch();
     FZ_CUDA_TRY(cudaGetLastError());
     return FZ_OK;
