@@ -397,15 +397,17 @@ int fz_plan_batch(const fz_instance_t *inst, int count, const fz_opts_t *opt,
  * {0, 1/4, 1, 4, 16}
  * with run order on and off (rebuild + enumeration, mean of 3 after a
  * warm-up; candidates that choose the same memos are timed once).  The
- * widths' fastest choices need not combine well, so it then times the whole
- * batch of the given instances under (0) the policy in force before the
- * call, (1) every width's fastest candidate and (2) the fastest candidate
- * only for widths where it beat (0) by 10 % or more, and keeps the fastest
- * of these for later fz_batch_create calls on this device (with opts.k =
- * FZ_AUTO).  Up to `capacity` timed candidates go to `entries` (host, may
- * be NULL when capacity is 0), their number to *n_entries; the whole-batch
- * timings are the entries with d = 0, run_order = 0, 1 or 2 naming the
- * policy and cap_rows = -1.  Synchronises.  Errors: as fz_batch_create. */
+ * widths' fastest choices need not combine well, so they are then applied
+ * greedily on the whole batch of the given instances: starting from the
+ * policy in force before the call, each width's fastest choice (widths in
+ * decreasing order of their own gain) is tried on top of the choices kept
+ * so far and kept only if the whole batch gets 1 % faster or more.  The
+ * result is kept for later fz_batch_create calls on this device (with
+ * opts.k = FZ_AUTO).  Up to `capacity` timed candidates go to `entries`
+ * (host, may be NULL when capacity is 0), their number to *n_entries; the
+ * whole-batch timings are the entries with d = 0 and cap_rows = -1, with
+ * run_order = 0 for the starting policy and w after trying width w's
+ * choice.  Synchronises.  Errors: as fz_batch_create. */
 typedef struct fz_batch_tune_entry {
     int32_t d;          /* tuple width of the sample */
     int32_t run_order;  /* layout candidate: 1 = run order allowed */

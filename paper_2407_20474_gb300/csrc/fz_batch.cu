@@ -1007,7 +1007,8 @@ int fz_batch_autotune(const fz_instance_t *inst, int count, fz_batch_tune_entry_
         *enum_ms = esum / 3;
         return r;
     };
-    BatchPolicy margin = base;  // per-width fastest where >= 10 % faster than the default
+    // per width: the default's time and the fastest candidate's
+    std::vector<double> width_gain(FZ_MAX_D + 1, 0.0);
     for (int d = 3; d <= FZ_MAX_D && rc == FZ_OK; ++d) {
         // the instances of this width (up to 1024, spread over the list):
         // memo builds run one CTA per memo in waves and the enumeration's
@@ -1102,44 +1103,32 @@ int fz_batch_autotune(const fz_instance_t *inst, int count, fz_batch_tune_entry_
         }
         tuned.cap_rows[d] = best_cap;
         tuned.run_order[d] = best_run;
-        if (base_t > 0 && best_t <= 0.9 * base_t) {
-            margin.cap_rows[d] = best_cap;
-            margin.run_order[d] = best_run;
-        }
+        if (base_t > 0 && best_t < base_t) width_gain[d] = base_t - best_t;
     }
     // The widths' fastest choices need not combine: the enumeration of a
     // mixed batch shares the GPU, its L2 and its instruction cache among
-    // widths.  So the whole batch is timed under the default policy, the
-    // per-width fastest and the per-width fastest that beat the default by
-    // 10 % or more, and the fastest of those is kept.
-    const BatchPolicy whole[3] = {base, tuned, margin};
-    int keep = 0;
-    double keep_t = 1e300;
-    for (int c = 0; c < 3 && rc == FZ_OK; ++c) {
-        bool same = false;
-        for (int c2 = 0; c2 < c; ++c2) {
-            bool eq = true;
-            for (int d = 0; d <= FZ_MAX_D; ++d)
-                eq = eq && whole[c].cap_rows[d] == whole[c2].cap_rows[d] &&
-                     whole[c].run_order[d] == whole[c2].run_order[d];
-            same = same || eq;
-        }
-        if (same) continue;
+    // widths.  So they are applied greedily on the whole batch: starting
+    // from the policy in force, each width's fastest choice (widths in
+    // decreasing order of their own gain, gains of 3 % or more) is tried on
+    // top of the choices kept so far and kept only if the whole batch's
+    // rebuild + enumeration gets faster by 1 % or more.
+    auto time_whole = [&](const BatchPolicy &pol, int tag, double *t) -> int {
+        *t = 1e300;
         fz_batch_t b = nullptr;
-        rc = batch_create_impl(inst, count, nullptr, whole[c], &b, s);
-        if (rc == FZ_ENOMEM || rc == FZ_EINVAL) {
+        int r = batch_create_impl(inst, count, nullptr, pol, &b, s);
+        if (r == FZ_ENOMEM || r == FZ_EINVAL) {  // too large for this device
             cudaGetLastError();
-            rc = FZ_OK;
-            continue;
+            return FZ_OK;
         }
-        if (rc != FZ_OK) break;
+        if (r != FZ_OK) return r;
         double b_ms = 0, e_ms = 0;
-        rc = time_batch(b, &b_ms, &e_ms);
-        if (rc == FZ_OK) {
+        r = time_batch(b, &b_ms, &e_ms);
+        if (r == FZ_OK) {
+            *t = b_ms + e_ms;
             if (found < capacity) {
                 fz_batch_tune_entry_t &E = entries[found];
-                E.d = 0;           // the whole batch
-                E.run_order = c;   // which policy (see fz.h)
+                E.d = 0;            // the whole batch
+                E.run_order = tag;  // 0: the starting policy; w: after trying width w
                 E.instances = count;
                 E.memos = b->nmemo;
                 E.cap_rows = -1.0;
@@ -1149,17 +1138,35 @@ int fz_batch_autotune(const fz_instance_t *inst, int count, fz_batch_tune_entry_
                 E.memo_rows = mr;
                 E.build_ms = b_ms;
                 E.enum_ms = e_ms;
-                E.total_ms = b_ms + e_ms;
+                E.total_ms = *t;
             }
             ++found;
-            if (b_ms + e_ms < keep_t) {
-                keep_t = b_ms + e_ms;
-                keep = c;
-            }
         }
         fz_batch_destroy(b);
+        return r;
+    };
+    BatchPolicy kept = base;
+    double kept_t = 1e300;
+    if (rc == FZ_OK) rc = time_whole(kept, 0, &kept_t);
+    std::vector<int> order;
+    for (int d = 3; d <= FZ_MAX_D; ++d)
+        if (width_gain[d] > 0) order.push_back(d);
+    std::sort(order.begin(), order.end(),
+              [&](int x, int y) { return width_gain[x] > width_gain[y]; });
+    for (int d : order) {
+        if (rc != FZ_OK || kept_t >= 1e300) break;
+        if (width_gain[d] < 0.03 * kept_t / 6.0) continue;  // small next to a width's share
+        BatchPolicy trial = kept;
+        trial.cap_rows[d] = tuned.cap_rows[d];
+        trial.run_order[d] = tuned.run_order[d];
+        double t = 1e300;
+        rc = time_whole(trial, d, &t);
+        if (rc == FZ_OK && t < 0.99 * kept_t) {
+            kept = trial;
+            kept_t = t;
+        }
     }
-    tuned = whole[keep];
+    tuned = kept;
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     cudaEventDestroy(e2);

@@ -14,6 +14,8 @@
 // chains are cut into blocks of RB entries, the block sums are scanned by the
 // same routine (they form a strided array of the same shape), and the blocks
 // are then re-walked with their carries.  All sums saturate at 2^64 - 1.
+#include <cstdlib>
+
 #include "fz_internal.cuh"
 
 namespace fz {
@@ -236,8 +238,13 @@ __device__ __forceinline__ void chain_scan_warp(const uint64_t *__restrict__ in,
     }
 }
 
-__global__ void __launch_bounds__(THREADS) scan_tasks_kernel(const ScanJob *__restrict__ jobs,
-                                                             const ScanTask *__restrict__ tasks) {
+constexpr int SCAN_MINB_DEFAULT = 4;
+
+// MINB: CTAs per SM the register budget is set for (3 fit without a bound:
+// 76 registers; 4 at 64 registers; 6 at 40 registers with a few spills).
+template <int MINB>
+__global__ void __launch_bounds__(THREADS, MINB) scan_tasks_kernel(const ScanJob *__restrict__ jobs,
+                                                                   const ScanTask *__restrict__ tasks) {
     const ScanTask t = tasks[blockIdx.x];
     const ScanJob J = jobs[t.job];
     const int lane = threadIdx.x & 31;
@@ -335,9 +342,23 @@ __global__ void __launch_bounds__(THREADS) scan_tasks_kernel(const ScanJob *__re
     }
 }
 
+// FZ_SCAN_MINB=1|4|6: the register budget of the batched scans (tuning only).
+static int scan_minb() {
+    static const int v = [] {
+        const char *e = getenv("FZ_SCAN_MINB");
+        const int x = e ? atoi(e) : 0;
+        return (x == 1 || x == 4 || x == 6) ? x : SCAN_MINB_DEFAULT;
+    }();
+    return v;
+}
+
 int launch_scan_tasks(const ScanJob *jobs, const ScanTask *tasks, int ntasks, cudaStream_t s) {
     if (ntasks <= 0) return FZ_OK;
-    scan_tasks_kernel<<<ntasks, THREADS, 0, s>>>(jobs, tasks);
+    switch (scan_minb()) {
+        case 1: scan_tasks_kernel<1><<<ntasks, THREADS, 0, s>>>(jobs, tasks); break;
+        case 6: scan_tasks_kernel<6><<<ntasks, THREADS, 0, s>>>(jobs, tasks); break;
+        default: scan_tasks_kernel<4><<<ntasks, THREADS, 0, s>>>(jobs, tasks); break;
+    }
     note_launch();
     FZ_CUDA_TRY(cudaGetLastError());
     return FZ_OK;

@@ -554,9 +554,12 @@ __global__ void __launch_bounds__(MB_THREADS) memo_sizes_kernel(const MemoJob *_
 // (64 allocated), so 1024 threads fit on an SM: one CTA of 1024, or several
 // smaller CTAs, each building its own memo.
 constexpr int MB_ILP = 8;
-constexpr int MB_CTA_THREADS_DEFAULT = 1024;
+constexpr int MB_CTA_THREADS_DEFAULT = 512;
 
-template <int T>
+// PAR: lanes 0..k-1 load the lengths and source offsets of an element's k
+// blocks at once (one round of loads per element) instead of each block's
+// before its copy (two dependent rounds per block).
+template <int T, bool PAR>
 __global__ void __launch_bounds__(T, 1024 / T) memo_cta_build_kernel(
     const MemoJob *__restrict__ jobs, int *status) {
     __shared__ uint64_t sums[33];
@@ -589,12 +592,27 @@ __global__ void __launch_bounds__(T, 1024 / T) memo_cta_build_kernel(
                 if (lane < k) J.R[lane] = 0;
                 continue;
             }
+            uint64_t plen = 0, psrc = 0;
+            if (PAR && lane < k) {
+                const int sm = m - J.t[lane];
+                if (sm >= 0) {
+                    plen = __ldg(J.Ct + (int64_t)lane * J.cs + sm);
+                    psrc = J.O[sm + 1] - plen;  // suffix Z_{>=lane}(sm)
+                }
+            }
             for (int i = 0; i < k; ++i) {
-                const int src_m = m - J.t[i];
-                if (src_m < 0) continue;
-                const uint64_t len = __ldg(J.Ct + (int64_t)i * J.cs + src_m);
-                if (len == 0) continue;
-                const uint64_t src = J.O[src_m + 1] - len;  // suffix Z_{>=i}(src_m)
+                uint64_t len, src;
+                if (PAR) {
+                    len = shfl_u64(plen, i);
+                    src = shfl_u64(psrc, i);
+                    if (len == 0) continue;
+                } else {
+                    const int src_m = m - J.t[i];
+                    if (src_m < 0) continue;
+                    len = __ldg(J.Ct + (int64_t)i * J.cs + src_m);
+                    if (len == 0) continue;
+                    src = J.O[src_m + 1] - len;  // suffix Z_{>=i}(src_m)
+                }
                 // the block is a flat copy of len * k words with one added to
                 // every word of coordinate i: word w of the block is
                 // coordinate w mod k of row w div k
@@ -851,6 +869,16 @@ int launch_memo_sizes(const MemoJob *jobs, int njobs, uint64_t *rows_out, cudaSt
     return FZ_OK;
 }
 
+// Descriptor loads of the batch memo build: FZ_MEMO_DESC=serial loads each
+// block's before its copy (tuning only).
+static bool memo_desc_parallel() {
+    static const bool on = [] {
+        const char *e = getenv("FZ_MEMO_DESC");
+        return !(e && strcmp(e, "serial") == 0);
+    }();
+    return on;
+}
+
 // CTA size of the batch memo build: FZ_MEMO_CTA_THREADS=256|512|1024
 // (tuning only).
 static int memo_cta_threads() {
@@ -864,10 +892,20 @@ static int memo_cta_threads() {
 
 int launch_memo_cta_build(const MemoJob *jobs, int njobs, int *status, cudaStream_t s) {
     if (njobs <= 0) return FZ_OK;
+    const bool par = memo_desc_parallel();
     switch (memo_cta_threads()) {
-        case 256: memo_cta_build_kernel<256><<<njobs, 256, 0, s>>>(jobs, status); break;
-        case 512: memo_cta_build_kernel<512><<<njobs, 512, 0, s>>>(jobs, status); break;
-        default: memo_cta_build_kernel<1024><<<njobs, 1024, 0, s>>>(jobs, status); break;
+        case 256:
+            if (par) memo_cta_build_kernel<256, true><<<njobs, 256, 0, s>>>(jobs, status);
+            else memo_cta_build_kernel<256, false><<<njobs, 256, 0, s>>>(jobs, status);
+            break;
+        case 1024:
+            if (par) memo_cta_build_kernel<1024, true><<<njobs, 1024, 0, s>>>(jobs, status);
+            else memo_cta_build_kernel<1024, false><<<njobs, 1024, 0, s>>>(jobs, status);
+            break;
+        default:
+            if (par) memo_cta_build_kernel<512, true><<<njobs, 512, 0, s>>>(jobs, status);
+            else memo_cta_build_kernel<512, false><<<njobs, 512, 0, s>>>(jobs, status);
+            break;
     }
     note_launch();
     FZ_CUDA_TRY(cudaGetLastError());
