@@ -1008,7 +1008,7 @@ int fz_batch_autotune(const fz_instance_t *inst, int count, fz_batch_tune_entry_
         return r;
     };
     // per width: the default's time and the fastest candidate's
-    std::vector<double> width_gain(FZ_MAX_D + 1, 0.0);
+    std::vector<double> width_gain(FZ_MAX_D + 1, 0.0), width_base(FZ_MAX_D + 1, 0.0);
     for (int d = 3; d <= FZ_MAX_D && rc == FZ_OK; ++d) {
         // the instances of this width (up to 1024, spread over the list):
         // memo builds run one CTA per memo in waves and the enumeration's
@@ -1103,7 +1103,10 @@ int fz_batch_autotune(const fz_instance_t *inst, int count, fz_batch_tune_entry_
         }
         tuned.cap_rows[d] = best_cap;
         tuned.run_order[d] = best_run;
-        if (base_t > 0 && best_t < base_t) width_gain[d] = base_t - best_t;
+        if (base_t > 0 && best_t < base_t) {
+            width_gain[d] = base_t - best_t;
+            width_base[d] = base_t;
+        }
     }
     // The widths' fastest choices need not combine: the enumeration of a
     // mixed batch shares the GPU, its L2 and its instruction cache among
@@ -1155,7 +1158,7 @@ int fz_batch_autotune(const fz_instance_t *inst, int count, fz_batch_tune_entry_
               [&](int x, int y) { return width_gain[x] > width_gain[y]; });
     for (int d : order) {
         if (rc != FZ_OK || kept_t >= 1e300) break;
-        if (width_gain[d] < 0.03 * kept_t / 6.0) continue;  // small next to a width's share
+        if (width_gain[d] < 0.03 * width_base[d]) continue;  // under 3 % of the width's time
         BatchPolicy trial = kept;
         trial.cap_rows[d] = tuned.cap_rows[d];
         trial.run_order[d] = tuned.run_order[d];
