@@ -191,3 +191,26 @@ def test_submit_by_generators(fz):
         with pytest.raises(fz.FzError) as e:
             srv.wait(t1, 10)                        # released: unknown ticket
         assert e.value.status == fz.FZ_ENOTFOUND
+
+
+def test_grouped_server_wide_run_order_plan(fz):
+    """A width-9 set whose plan keeps a depth-2 memo in run order (the deeper
+    memos exceed the plan's memo budget): the batch kernel's run copy serves
+    widths up to 8, so the grouped server launches these requests on their
+    own after its group kernel.  Mixed with requests of a narrow set, every
+    result equals the oracle's list."""
+    wide = (1000, 1001, 1002, 1003, 1004, 3, 4, 5, 7)
+    narrow = (6, 9, 20)
+    with fz.Plan(wide, 1200) as p:
+        assert p.d == 9 and p.k == 2 and p.run_order, (p.k, p.run_order)
+    with fz.Server(max_in_flight=16, streams=2) as srv:
+        w = srv.register(wide, 1200)
+        s = srv.register(narrow, 600)
+        reqs = [(wide, w, 1200), (narrow, s, 600), (wide, w, 1000), (narrow, s, 0),
+                (wide, w, 3), (narrow, s, 599), (wide, w, 1199)]
+        ts = [(g, n, srv.submit(sid, n)) for g, sid, n in reqs]
+        for g, n, t in ts:
+            r = srv.wait(t, 60000)
+            assert r.status == fz.FZ_SERVE_DONE, (g, n, r.status)
+            assert np.array_equal(rows_of(srv, t, r), oracle.enumerate_desc(g, n)), (g, n)
+            srv.release(t)
