@@ -48,7 +48,15 @@ size_t a256(size_t x) { return (x + 255) & ~size_t(255); }
 
 // Elementwise batches a batch memo may take (its top is cut to this many
 // batches of min(tail) elements; larger remainders take the ordinary step).
-constexpr int64_t BATCH_MEMO_BATCHES = 512;
+// FZ_BATCH_MEMO_BATCHES=b overrides it (tuning only).
+int64_t batch_memo_batches() {
+    static const int64_t v = [] {
+        const char *e = getenv("FZ_BATCH_MEMO_BATCHES");
+        const long long x = e ? atoll(e) : 0;
+        return x >= 16 && x <= 65536 ? (int64_t)x : (int64_t)512;
+    }();
+    return v;
+}
 constexpr double BATCH_MEMO_MAX_ROWS = 1 << 20;
 
 struct Inst {
@@ -308,7 +316,7 @@ int gather(const std::vector<const uint64_t *> &ptrs, std::vector<uint64_t> &out
 // Memo depth of a batch instance, chosen for the largest element n_set
 // asked of the same generators in the batch (so instances of one generator
 // set share one memo).  A memo's rows are estimated by the volume
-// top^K / (K! prod tail), with top = min(n_set + 1, BATCH_MEMO_BATCHES
+// top^K / (K! prod tail), with top = min(n_set + 1, batch_memo_batches()
 // elementwise batches of min(tail) elements).  Preferred: the deepest full
 // memo (top > n_set) of depth >= 3 within BATCH_MEMO_MAX_ROWS rows and
 // cap_rows times the instance's estimated rows (volume n^(d-1) / ((d-1)!
@@ -391,7 +399,7 @@ void choose_batch_memo(Inst &I, int n_set, double cap_rows) {
             tmin = std::min(tmin, I.g[i]);
             prod *= I.g[i];
         }
-        const int64_t top = std::min<int64_t>((int64_t)n_set + 1, BATCH_MEMO_BATCHES * tmin);
+        const int64_t top = std::min<int64_t>((int64_t)n_set + 1, batch_memo_batches() * tmin);
         double rows = 1.0;
         for (int i = 0; i < k; ++i) rows *= (double)top / (i + 1);
         rows /= prod;
@@ -478,7 +486,7 @@ int batch_create_impl(const fz_instance_t *inst, int count, const fz_opts_t *opt
             I.K = opt->k;
             int32_t tmin = I.K ? I.g[I.d - I.K] : 1;
             for (int j = I.d - I.K; j < I.d; ++j) tmin = std::min(tmin, I.g[j]);
-            I.top = I.K ? (int)std::min<int64_t>((int64_t)I.n + 1, BATCH_MEMO_BATCHES * tmin) : 0;
+            I.top = I.K ? (int)std::min<int64_t>((int64_t)I.n + 1, batch_memo_batches() * tmin) : 0;
         }
         if (opt && opt->top != FZ_AUTO && I.K > 0) {
             I.top = std::min(I.top, opt->top);
