@@ -536,6 +536,20 @@ int fz_serve_release(fz_server_t srv, uint64_t ticket);
  * is (FZ_OK).  Errors: FZ_ENOTFOUND, FZ_EAGAIN. */
 int fz_serve_cancel(fz_server_t srv, uint64_t ticket);
 int fz_serve_stats(fz_server_t srv, fz_serve_stats_t *stats);
+/* Measurement utility (the paper has no counterpart): replays a request
+ * stream against the server from native threads, so that a client's own
+ * overhead does not bound the measured rate.  Request i (set set_ids[i],
+ * element ns[i]) is submitted at arrival_s[i] seconds after the call starts
+ * (busy wait; a full queue is retried); a second thread waits for the
+ * requests in submission order and releases them.  latency_s[i] receives
+ * t_done - t_submit, rows[i] (may be NULL) the request's row count, and
+ * *span_s (may be NULL) the time from the first submission to the last
+ * completion.  All arrays are host memory of `count` entries.  Returns when
+ * every request is done.  Errors: FZ_EINVAL, those of fz_serve_submit, and
+ * the status of a request that failed. */
+int fz_serve_replay(fz_server_t srv, const int32_t *set_ids, const int32_t *ns,
+                    const double *arrival_s, int count, double *latency_s, uint64_t *rows,
+                    double *span_s);
 /* Stop the loop, wait for running requests, free everything.  Requests still
  * queued are dropped. */
 int fz_serve_destroy(fz_server_t srv);

@@ -53,7 +53,7 @@ EXPORTS = (
     "fz_plan_batch", "fz_batch_autotune", "fz_batch_policy", "fz_batch_policy_reset",
     "fz_serve_create", "fz_serve_register", "fz_serve_submit", "fz_serve_poll",
     "fz_serve_wait", "fz_serve_copy", "fz_serve_release", "fz_serve_stats", "fz_serve_destroy",
-    "fz_serve_submit_gens", "fz_serve_cancel",
+    "fz_serve_submit_gens", "fz_serve_cancel", "fz_serve_replay",
 )
 
 
@@ -208,6 +208,9 @@ _SIGS = {
     "fz_serve_submit": (ctypes.c_int, [_P, ctypes.c_int32, ctypes.c_int32, _U64P]),
     "fz_serve_submit_gens": (ctypes.c_int, [_P, _I32P, ctypes.c_int, ctypes.c_int32, _U64P]),
     "fz_serve_cancel": (ctypes.c_int, [_P, ctypes.c_uint64]),
+    "fz_serve_replay": (ctypes.c_int, [_P, _I32P, _I32P, ctypes.POINTER(ctypes.c_double),
+                                       ctypes.c_int, ctypes.POINTER(ctypes.c_double), _U64P,
+                                       ctypes.POINTER(ctypes.c_double)]),
     "fz_serve_poll": (ctypes.c_int, [_P, ctypes.c_uint64, ctypes.POINTER(fz_result_t)]),
     "fz_serve_wait": (ctypes.c_int, [_P, ctypes.c_uint64, ctypes.c_int32,
                                      ctypes.POINTER(fz_result_t)]),
@@ -750,6 +753,25 @@ class Server:
         t = ctypes.c_uint64(0)
         _check(lib().fz_serve_submit_gens(self._h, ga, d, int(n), ctypes.byref(t)))
         return int(t.value)
+
+    def replay(self, set_ids, ns, arrivals_s):
+        """Replay a request stream from native threads (fz_serve_replay):
+        request i of set set_ids[i] and element ns[i] is submitted at
+        arrivals_s[i] s.  Returns (latency seconds, rows, span seconds)."""
+        sid = np.ascontiguousarray(np.asarray(set_ids, dtype=np.int32))
+        nn = np.ascontiguousarray(np.asarray(ns, dtype=np.int32))
+        at = np.ascontiguousarray(np.asarray(arrivals_s, dtype=np.float64))
+        m = int(sid.size)
+        if nn.size != m or at.size != m:
+            raise FzError(FZ_EINVAL, "replay: arrays of different lengths")
+        lat = np.zeros(m, dtype=np.float64)
+        rows = np.zeros(m, dtype=np.uint64)
+        span = ctypes.c_double(0.0)
+        _check(lib().fz_serve_replay(self._h, sid.ctypes.data_as(_I32P), nn.ctypes.data_as(_I32P),
+                                     at.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), m,
+                                     lat.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
+                                     rows.ctypes.data_as(_U64P), ctypes.byref(span)))
+        return lat, rows, float(span.value)
 
     def cancel(self, ticket: int):
         """Cancel a queued request (FzError FZ_EAGAIN if it is already running)."""

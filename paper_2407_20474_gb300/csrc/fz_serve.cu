@@ -711,6 +711,55 @@ int fz_serve_release(fz_server_t s, uint64_t ticket) {
     return FZ_OK;
 }
 
+int fz_serve_replay(fz_server_t s, const int32_t *set_ids, const int32_t *ns,
+                    const double *arrival_s, int count, double *latency_s, uint64_t *rows,
+                    double *span_s) {
+    if (!s || count < 0 || (count > 0 && (!set_ids || !ns || !arrival_s || !latency_s)))
+        return set_error(FZ_EINVAL, "null pointer");
+    std::vector<uint64_t> tickets((size_t)count, 0);
+    std::atomic<int> submitted{0};
+    std::atomic<int> drain_rc{FZ_OK};
+    double first_submit = 0, last_done = 0;
+    // drain: wait for the requests in submission order, record, release
+    std::thread drain([&] {
+        for (int i = 0; i < count; ++i) {
+            while (submitted.load(std::memory_order_acquire) <= i) {
+                if (drain_rc.load() != FZ_OK) return;
+                std::this_thread::yield();
+            }
+            fz_result_t r;
+            int rc = fz_serve_wait(s, tickets[i], -1, &r);
+            if (rc != FZ_OK || r.status != FZ_SERVE_DONE) {
+                drain_rc.store(rc != FZ_OK ? rc : r.status);
+                return;
+            }
+            latency_s[i] = r.t_done - r.t_submit;
+            if (rows) rows[i] = r.count;
+            if (i == 0) first_submit = r.t_submit;
+            if (r.t_done > last_done) last_done = r.t_done;
+            fz_serve_release(s, tickets[i]);
+        }
+    });
+    const double t0 = now_s();
+    int rc = FZ_OK;
+    for (int i = 0; i < count && rc == FZ_OK; ++i) {
+        while (now_s() < t0 + arrival_s[i]) {
+        }
+        for (;;) {
+            rc = fz_serve_submit(s, set_ids[i], ns[i], &tickets[i]);
+            if (rc != FZ_EAGAIN) break;  // queue full: retry
+            std::this_thread::yield();
+        }
+        if (rc == FZ_OK) submitted.store(i + 1, std::memory_order_release);
+    }
+    if (rc != FZ_OK) drain_rc.store(rc);
+    drain.join();
+    if (rc != FZ_OK) return rc;
+    if (drain_rc.load() != FZ_OK) return set_error(drain_rc.load(), "replayed request failed");
+    if (span_s) *span_s = count > 0 ? last_done - first_submit : 0.0;
+    return FZ_OK;
+}
+
 int fz_serve_stats(fz_server_t s, fz_serve_stats_t *st) {
     if (!s || !st) return set_error(FZ_EINVAL, "null pointer");
     std::lock_guard<std::mutex> lk(s->mu);

@@ -214,3 +214,22 @@ def test_grouped_server_wide_run_order_plan(fz):
             assert r.status == fz.FZ_SERVE_DONE, (g, n, r.status)
             assert np.array_equal(rows_of(srv, t, r), oracle.enumerate_desc(g, n)), (g, n)
             srv.release(t)
+
+
+def test_native_replay(fz):
+    """fz_serve_replay submits a stream from native threads: every request
+    completes, its row count is the oracle's, latencies are positive, and
+    the server is empty afterwards."""
+    g1, g2 = (7, 11, 13, 17), (5, 8, 11, 14)
+    with fz.Server(max_in_flight=8, streams=2) as srv:
+        a = srv.register(g1, 400)
+        b = srv.register(g2, 500)
+        ids = [a, b] * 20
+        ns = [int(x) for x in np.linspace(0, 400, 40)]
+        arr = np.arange(40) * 1e-4
+        lat, rows, span = srv.replay(ids, ns, arr)
+        gs = [g1, g2] * 20
+        assert [int(r) for r in rows] == [oracle.count(g, n) for g, n in zip(gs, ns)]
+        assert (lat > 0).all() and span > 0
+        st = srv.stats()
+        assert st.completed == 40 and st.bytes_in_use == 0 and st.queued == 0
