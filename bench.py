@@ -875,7 +875,7 @@ def measure_serve(torch, fz, seconds=10.0, sweep_rates=(), sweep_requests=4000,
 def run_serve_workload(args):
     torch, fz = _gpu_env()
     r = measure_serve(torch, fz, args.serve_seconds,
-                      sweep_rates=(4000, 8000, 16000, 32000, 64000, 128000),
+                      sweep_rates=(4000, 8000, 16000, 32000, 64000, 128000, 256000),
                       sweep_requests=8000)
     rec = {"metric": "Served factorizations/s with p50/p99 latency (Poisson 2000 req/s)",
            "value": r["value"], "unit": UNIT, "n_gpus": 1, "higher_is_better": True,
