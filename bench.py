@@ -656,7 +656,8 @@ def _event_time(torch, fn, steps, warmup):
     return a.elapsed_time(b) / steps
 
 
-def measure_batch(torch, fz, steps, warmup, count=4096, only_d=0, pi_steps=5, autotune=True):
+def measure_batch(torch, fz, steps, warmup, count=4096, only_d=0, pi_steps=5, autotune=True,
+                  pipeline=True):
     """Config 4: ``count`` instances (d 3..8, generators in [2,300], |Z|
     log-uniform in [1e2,1e6]) in one persistent launch -- the step (batched
     counting tables, memos and enumeration) replayed as a captured CUDA
@@ -710,6 +711,59 @@ def measure_batch(torch, fz, steps, warmup, count=4096, only_d=0, pi_steps=5, au
     ms_rebuild = _event_time(torch, b.rebuild, max(steps, 1), 1)
     ms_enum = _event_time(torch, lambda: b.enumerate(out), max(steps, 1), 1)
     b.sync()
+    ms_serial = ms
+    pipe = None
+    if pipeline:
+        # Pipelined steps, as for config 2: two batches of the same instances
+        # take turns; one's rebuild (tables and memos, latency-bound) runs on
+        # its own stream while the other's enumeration runs on another, the
+        # enumeration capped at 4, 3 or 2 blocks per SM (chosen in the
+        # warm-up) so the rebuild's blocks fit beside it.  Every step still
+        # rebuilds all tables and memos and enumerates every instance.
+        bs = [b, fz.Batch(inst)]
+        s_bs = [torch.cuda.Stream() for _ in bs]
+        s_e = torch.cuda.Stream()
+        built = [torch.cuda.Event() for _ in bs]
+        done = [torch.cuda.Event() for _ in bs]
+
+        def pipelined(count):
+            st0 = torch.cuda.Event(enable_timing=True)
+            st1 = torch.cuda.Event(enable_timing=True)
+            st0.record(s_e)
+            for sb in s_bs:
+                sb.wait_event(st0)
+            for i in range(count):
+                j = i % 2
+                if i >= 2:
+                    s_bs[j].wait_event(done[j])
+                bs[j].rebuild(stream=s_bs[j])
+                built[j].record(s_bs[j])
+                s_e.wait_event(built[j])
+                bs[j].enumerate(out, stream=s_e)
+                done[j].record(s_e)
+            st1.record(s_e)
+            torch.cuda.synchronize()
+            return st0.elapsed_time(st1) / count
+
+        trials = {}
+        for cap in (4, 3, 2):
+            for x in bs:
+                x.set_enum_ctas_per_sm(cap)
+            pipelined(3)
+            trials[cap] = pipelined(max(warmup, 3) + 2)
+        cap = min(trials, key=trials.get)
+        for x in bs:
+            x.set_enum_ctas_per_sm(cap)
+        pipelined(3)
+        ms_pipe = pipelined(max(steps, 1))
+        for x in bs:
+            x.sync()
+            x.set_enum_ctas_per_sm(0)
+        bs[1].close()
+        pipe = {"ms_per_step": ms_pipe, "enum_ctas_per_sm": cap,
+                "trials_ms_per_step": {str(k): round(v, 4) for k, v in trials.items()}}
+        if ms_pipe < ms:
+            ms = ms_pipe
     bytes_out = sum(int(r) * len(g) * 4 for (g, _), r in zip(inst, b.rows))
     # per-instance launches of the same instances
     ms_pi = None
@@ -733,7 +787,8 @@ def measure_batch(torch, fz, steps, warmup, count=4096, only_d=0, pi_steps=5, au
            "ms_per_step": ms, "value": b.total_rows / (ms / 1e3), "unit": UNIT,
            "memos": b.memos, "run_order_instances": b.run_order,
            "run_order_memos": b.run_memos, "work_items": b.work_items,
-           "cuda_graph": graph_ok, "rebuild_ms": ms_rebuild, "enumerate_ms": ms_enum,
+           "cuda_graph": graph_ok, "ms_per_step_serial": ms_serial, "pipelined": pipe,
+           "rebuild_ms": ms_rebuild, "enumerate_ms": ms_enum,
            "per_instance_ms_per_step": ms_pi,
            "per_instance_value": b.total_rows / (ms_pi / 1e3) if ms_pi else None,
            "speedup_vs_per_instance": ms_pi / ms if ms_pi else None,
@@ -753,7 +808,8 @@ def measure_batch(torch, fz, steps, warmup, count=4096, only_d=0, pi_steps=5, au
 def run_batch_workload(args):
     torch, fz = _gpu_env()
     r = measure_batch(torch, fz, args.steps, args.warmup, args.batch_count, args.batch_d,
-                      pi_steps=args.batch_pi_steps, autotune=not args.no_autotune)
+                      pi_steps=args.batch_pi_steps, autotune=not args.no_autotune,
+                      pipeline=not args.no_pipeline)
     rec = {"metric": "Factorizations/s, batched (%d instances, one persistent launch)"
                      % r["instances"],
            "value": r["value"], "unit": UNIT, "n_gpus": 1, "steps": args.steps,

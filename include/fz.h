@@ -367,6 +367,11 @@ int fz_batch_layout(fz_batch_t batch, uint64_t *rows, uint64_t *word_offsets,
                     int32_t *k, int32_t *top);
 /* Recompute every table and memo in place.  Asynchronous (capturable). */
 int fz_batch_rebuild(fz_batch_t batch, void *stream);
+/* Cap the batch's enumeration kernel at `ctas` blocks per SM (0 = as many
+ * as fit; it fits 4), leaving room for other kernels beside it, e.g. the
+ * rebuild of another batch overlapping this enumeration.
+ * Errors: FZ_EINVAL. */
+int fz_batch_set_enum_ctas_per_sm(fz_batch_t batch, int32_t ctas);
 /* All instances' rows into out_dev (capacity in int32 words).  Asynchronous,
  * one persistent kernel.  Errors: FZ_EINVAL, FZ_ENOSPC, FZ_ECUDA. */
 int fz_batch_enumerate(fz_batch_t batch, int32_t *out_dev,

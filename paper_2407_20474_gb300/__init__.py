@@ -49,6 +49,7 @@ EXPORTS = (
     "fz_plan_unrank", "fz_plan_sync", "fz_plan_destroy",
     "fz_enumerate", "fz_enumerate_host", "fz_enumerate_host_chunks",
     "fz_batch_create", "fz_batch_info", "fz_batch_layout", "fz_batch_rebuild",
+    "fz_batch_set_enum_ctas_per_sm",
     "fz_batch_enumerate", "fz_batch_sync", "fz_batch_destroy", "fz_enumerate_batch",
     "fz_plan_batch", "fz_batch_autotune", "fz_batch_policy", "fz_batch_policy_reset",
     "fz_serve_create", "fz_serve_register", "fz_serve_submit", "fz_serve_poll",
@@ -189,6 +190,7 @@ _SIGS = {
     "fz_batch_info": (ctypes.c_int, [_P, ctypes.POINTER(fz_batch_info_t)]),
     "fz_batch_layout": (ctypes.c_int, [_P, _U64P, _U64P, _I32P, _I32P]),
     "fz_batch_rebuild": (ctypes.c_int, [_P, _P]),
+    "fz_batch_set_enum_ctas_per_sm": (ctypes.c_int, [_P, ctypes.c_int32]),
     "fz_batch_enumerate": (ctypes.c_int, [_P, _P, ctypes.c_uint64, _P]),
     "fz_batch_sync": (ctypes.c_int, [_P, _P]),
     "fz_batch_destroy": (ctypes.c_int, [_P]),
@@ -632,6 +634,10 @@ class Batch:
 
     def rebuild(self, stream=None):
         _check(lib().fz_batch_rebuild(self._h, _stream(stream)))
+
+    def set_enum_ctas_per_sm(self, ctas: int):
+        """Cap the enumeration kernel's blocks per SM (0 = no cap)."""
+        _check(lib().fz_batch_set_enum_ctas_per_sm(self._h, int(ctas)))
 
     def enumerate(self, out, capacity_words: Optional[int] = None, stream=None):
         if capacity_words is None:

@@ -99,6 +99,7 @@ struct fz_batch_s {
     RunJob *run_jobs_dev = nullptr;
     int nrun = 0, run_inst = 0;
     uint64_t run_blocks = 0;  // blocks of the run-row kernel
+    int ctas_per_sm = 0;      // cap of the enumeration kernel (0: as many as fit)
     void *params_dev = nullptr;       // EnumParams images (out = word offset)
     uint64_t *item0_dev = nullptr;
     unsigned long long *counter_dev = nullptr;
@@ -902,6 +903,13 @@ int fz_batch_layout(fz_batch_t b, uint64_t *rows, uint64_t *word_offsets, int32_
     return FZ_OK;
 }
 
+int fz_batch_set_enum_ctas_per_sm(fz_batch_t b, int32_t ctas) {
+    if (!b) return set_error(FZ_EINVAL, "batch: null pointer");
+    if (ctas < 0) return set_error(FZ_EINVAL, "ctas must be >= 0");
+    b->ctas_per_sm = ctas;
+    return FZ_OK;
+}
+
 int fz_batch_rebuild(fz_batch_t b, void *stream) {
     if (!b) return set_error(FZ_EINVAL, "batch: null pointer");
     return batch_enqueue_rebuild(b, static_cast<cudaStream_t>(stream));
@@ -915,7 +923,8 @@ int fz_batch_enumerate(fz_batch_t b, int32_t *out_dev, uint64_t out_capacity_wor
     if (((uintptr_t)out_dev & 3u) != 0) return set_error(FZ_EINVAL, "out must be 4-byte aligned");
     if (out_capacity_words < b->total_words) return set_error(FZ_ENOSPC, "output capacity too small");
     return launch_enumerate_batch(b->params_dev, b->item0_dev, b->count, b->nitems,
-                                  b->counter_dev, out_dev, static_cast<cudaStream_t>(stream));
+                                  b->counter_dev, out_dev, static_cast<cudaStream_t>(stream),
+                                  b->ctas_per_sm);
 }
 
 int fz_batch_sync(fz_batch_t b, void *stream) {

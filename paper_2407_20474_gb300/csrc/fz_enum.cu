@@ -1669,7 +1669,7 @@ void fill_batch_params(const EnumLaunch &L, int32_t *out, uint64_t count, uint64
 
 int launch_enumerate_batch(const void *params_dev, const uint64_t *item0_dev, int count,
                            uint64_t nitems, unsigned long long *item_counter, int32_t *out_base,
-                           cudaStream_t s) {
+                           cudaStream_t s, int ctas_per_sm) {
     if (nitems == 0) return FZ_OK;
     DeviceProps dp;
     int rc = device_props(&dp);
@@ -1685,6 +1685,7 @@ int launch_enumerate_batch(const void *params_dev, const uint64_t *item0_dev, in
     FZ_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fz_enum_batch_kernel,
                                                               ENUM_THREADS, smem));
     if (per_sm < 1) per_sm = 1;
+    if (ctas_per_sm > 0 && ctas_per_sm < per_sm) per_sm = ctas_per_sm;
     uint64_t grid = (uint64_t)per_sm * dp.sms;
     const uint64_t want = (nitems + ENUM_WARPS - 1) / ENUM_WARPS;
     if (want < grid) grid = want;

@@ -410,7 +410,7 @@ void fill_batch_params(const EnumLaunch &L, int32_t *out, uint64_t count, uint64
                        uint64_t slice_cost, void *dst);
 int launch_enumerate_batch(const void *params_dev, const uint64_t *item0_dev, int count,
                            uint64_t nitems, unsigned long long *item_counter, int32_t *out_base,
-                           cudaStream_t s);
+                           cudaStream_t s, int ctas_per_sm = 0);
 
 // Plans as seen by the batch and serve layers (fz_api.cu): the launch
 // description of a plan for an element n <= its n, and host copies of row 0
