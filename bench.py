@@ -9,12 +9,20 @@ counting table, the memo build (elementwise batches of copy-and-increment),
 and the rank-sliced enumeration writing every tuple to HBM.
 
 Printed: one JSON line (rank 0).  `value` is factorizations/s with the
-generators already on the device side; `e2e` is the same metric through
-fz_enumerate_host (plan, enumeration and the device->host copy of every tuple
-into pinned host memory inside the timed region); `roofline` is the
-enumeration kernel's written bytes per launch over its CUDA-event time
-against the measured HBM copy bandwidth; `cpu_baseline` is the oracle (plain
-C recursion) on a bounded sample of the same workload on the host cores.
+generators already on the device side, the memo depth and work-item size
+chosen by the library's tuner in the warm-up (`config.k_choice` lists every
+timed candidate); `e2e` is the same metric through fz_enumerate_host (plan,
+enumeration and the device->host copy of every tuple into pinned host memory
+inside the timed region; `e2e.pageable` and `e2e.pageable_staged` into a
+plain numpy array); `roofline` is the enumeration kernel's written bytes per
+launch over its CUDA-event time against the measured HBM copy bandwidth,
+with the DRAM traffic of a committed ncu record; `cpu_baseline` is the
+oracle (plain C recursion) on a bounded sample of the same workload on the
+host cores; `secondary` holds bounded records of the other workloads: the
+config-3 memo build, the config-4 batch (measured memo policy, pipelined
+steps, against per-instance plans) and config-5 serving (grouped and
+per-request launches and one request at a time, with a sweep of offered
+rates).
 
 `--impl reference` times that oracle alone, on the same workload and metric.
 Under torchrun each rank runs its own replica of the workload (weak scaling,
