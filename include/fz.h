@@ -476,7 +476,9 @@ typedef struct fz_serve_cfg {
  * groups.  By default (flags 0) the requests admitted in one pass of the
  * server loop are launched together: one launch of the batch enumeration
  * kernel with a range of work items per request, one transfer of their
- * parameters and one completion callback per group. */
+ * parameters and one completion callback per group; requests of 2^22 rows
+ * or more, whose plan's own kernel writes them faster, are launched with it
+ * right after the group's kernel on the same stream. */
 #define FZ_SERVE_PER_REQUEST 1
 
 typedef struct fz_server_s *fz_server_t;

@@ -26,6 +26,7 @@
 
 #include <atomic>
 #include <chrono>
+#include <cstdlib>
 #include <condition_variable>
 #include <deque>
 #include <map>
@@ -260,6 +261,18 @@ void CUDART_CB on_group_done(void *p) {
     s->done_cv.notify_all();
 }
 
+// Requests of at least this many rows are launched with their plan's own
+// kernel after the group's batch kernel (FZ_SERVE_DIRECT_ROWS overrides it;
+// tuning only).
+uint64_t serve_direct_rows() {
+    static const uint64_t v = [] {
+        const char *e = std::getenv("FZ_SERVE_DIRECT_ROWS");
+        const long long x = e ? std::atoll(e) : -1;
+        return x >= 0 ? (uint64_t)x : (uint64_t)(1u << 22);
+    }();
+    return v;
+}
+
 // Whether the batch kernel serves a launch of this shape (its run-order
 // copy takes widths up to 8 with at least one walked coordinate).
 bool batch_kernel_serves(const EnumLaunch &L) {
@@ -296,7 +309,10 @@ int launch_group(fz_server_s *s, Group &G) {
             L.total_cost = r->count + L.W * S.runs_row[r->n];
             cost[j] = L.total_cost;
         }
-        direct[j] = batch_kernel_serves(L) ? 0 : 1;
+        // large requests take their plan's own kernel (its compiled-in walk
+        // or run copy writes faster than the batch kernel's generic one);
+        // so do those the batch kernel does not serve
+        direct[j] = (!batch_kernel_serves(L) || r->count >= serve_direct_rows()) ? 1 : 0;
         if (!direct[j]) total_cost += cost[j];
     }
     const uint64_t warps = (uint64_t)dp.sms * 16;
