@@ -353,6 +353,10 @@ typedef struct fz_batch_info {
     uint64_t work_items;   /* (instance, slice) items of one enumeration */
     int32_t run_order;     /* instances whose full memo is copied in run order */
     int32_t run_memos;     /* distinct run-order memos */
+    int32_t coop_memos;    /* memos built by a thread-block cluster (the
+                              longest, when one alone would outlast an even
+                              share of the build) */
+    int32_t reserved;
 } fz_batch_info_t;
 
 /* Validate, count every instance (device), choose each memo depth (opts->k

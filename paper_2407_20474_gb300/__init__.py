@@ -105,7 +105,8 @@ class fz_batch_info_t(ctypes.Structure):
     _fields_ = [("count", ctypes.c_int32), ("memos", ctypes.c_int32),
                 ("total_rows", ctypes.c_uint64), ("total_words", ctypes.c_uint64),
                 ("device_bytes", ctypes.c_uint64), ("work_items", ctypes.c_uint64),
-                ("run_order", ctypes.c_int32), ("run_memos", ctypes.c_int32)]
+                ("run_order", ctypes.c_int32), ("run_memos", ctypes.c_int32),
+                ("coop_memos", ctypes.c_int32), ("reserved", ctypes.c_int32)]
 
 
 class fz_serve_cfg_t(ctypes.Structure):
@@ -624,6 +625,7 @@ class Batch:
         self.work_items = int(info.work_items)
         self.run_order = int(info.run_order)
         self.run_memos = int(info.run_memos)
+        self.coop_memos = int(info.coop_memos)
         self.rows = np.zeros(self.count, dtype=np.uint64)
         self.word_offsets = np.zeros(self.count + 1, dtype=np.uint64)
         self.k = np.zeros(self.count, dtype=np.int32)

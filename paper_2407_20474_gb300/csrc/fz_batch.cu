@@ -95,6 +95,8 @@ struct fz_batch_s {
     ScanTask *tasks_dev = nullptr;
     MemoJob *memo_jobs_dev = nullptr;
     int nmemo = 0;
+    int memo_ncoop = 0;              // memos built by a cluster
+    unsigned *memo_claim = nullptr;  // claim counter of the memo build
     std::vector<MemoJob> memo_jobs;
     RunJob *run_jobs_dev = nullptr;
     int nrun = 0, run_inst = 0;
@@ -285,7 +287,8 @@ int batch_enqueue_rebuild(fz_batch_s *b, cudaStream_t s) {
         int rc = launch_scan_tasks(b->jobs_dev, b->tasks_dev + L.first, L.second, s);
         if (rc != FZ_OK) return rc;
     }
-    int rc = launch_memo_cta_build(b->memo_jobs_dev, b->nmemo, b->status_dev, s);
+    int rc = launch_memo_cta_build(b->memo_jobs_dev, b->nmemo, b->memo_ncoop, b->memo_claim,
+                                   b->status_dev, s);
     if (rc != FZ_OK) return rc;
     return launch_run_memo_batch(b->run_jobs_dev, b->nrun, b->run_blocks, b->status_dev, s);
 }
@@ -609,6 +612,7 @@ int batch_create_impl(const fz_instance_t *inst, int count, const fz_opts_t *opt
     b->item0_dev = reinterpret_cast<uint64_t *>(mb + o_item0);
     b->counter_dev = reinterpret_cast<unsigned long long *>(mb + o_misc);
     b->status_dev = reinterpret_cast<int *>(mb + o_misc + 64);
+    b->memo_claim = reinterpret_cast<unsigned *>(mb + o_misc + 128);
     uint64_t *mrows_dev = reinterpret_cast<uint64_t *>(mb + o_mrows);
     FZ_CUDA_TRY(cudaMemsetAsync(mb + o_misc, 0, 256, s));
     if (!jobs.empty())
@@ -665,7 +669,9 @@ int batch_create_impl(const fz_instance_t *inst, int count, const fz_opts_t *opt
         FZ_CUDA_TRY(cudaMemcpyAsync(b->memo_jobs_dev, by_work.data(),
                                     by_work.size() * sizeof(MemoJob), cudaMemcpyHostToDevice, s));
         FZ_CUDA_TRY(cudaStreamSynchronize(s));  // by_work is a host temporary
-        rc = launch_memo_cta_build(b->memo_jobs_dev, b->nmemo, b->status_dev, s);
+        b->memo_ncoop = memo_coop_count(by_work.data(), b->nmemo);
+        rc = launch_memo_cta_build(b->memo_jobs_dev, b->nmemo, b->memo_ncoop, b->memo_claim,
+                                   b->status_dev, s);
         if (rc != FZ_OK) return fail(rc);
     }
     // run-order memos, one per distinct (g_lam, tail) and source (memo or
@@ -887,6 +893,8 @@ int fz_batch_info(fz_batch_t b, fz_batch_info_t *info) {
     info->work_items = b->nitems;
     info->run_order = b->run_inst;
     info->run_memos = b->nrun;
+    info->coop_memos = b->memo_ncoop;
+    info->reserved = 0;
     return FZ_OK;
 }
 

@@ -316,7 +316,13 @@ int launch_memo_sizes(const MemoJob *jobs, int njobs, uint64_t *rows_out, cudaSt
 int launch_run_memo(const uint64_t *C, int64_t cs, int lam, int32_t n, int32_t g_lam,
                     const uint64_t *O, const int32_t *rows, int k, uint64_t memo_rows,
                     uint64_t *cls_beg, int4 *run_memo, int *status, cudaStream_t s);
-int launch_memo_cta_build(const MemoJob *jobs, int njobs, int *status, cudaStream_t s);
+// The memos of a batch, one per job (jobs sorted longest first): the first
+// ncoop jobs each by a thread-block cluster, the rest one per CTA (claim: a
+// device counter the launch zeroes).  memo_coop_count picks ncoop (0: the
+// one-CTA launch for every job).
+int memo_coop_count(const MemoJob *sorted, int njobs);
+int launch_memo_cta_build(const MemoJob *jobs, int njobs, int ncoop, unsigned *claim,
+                          int *status, cudaStream_t s);
 
 // One run-order memo of a batch (the layout of launch_run_memo) for the
 // elements 0..n: its rows come from an element-order memo of depth k <= 3

@@ -559,11 +559,9 @@ constexpr int MB_CTA_THREADS_DEFAULT = 512;
 // PAR: lanes 0..k-1 load the lengths and source offsets of an element's k
 // blocks at once (one round of loads per element) instead of each block's
 // before its copy (two dependent rounds per block).
-template <int T, bool PAR>
-__global__ void __launch_bounds__(T, 1024 / T) memo_cta_build_kernel(
-    const MemoJob *__restrict__ jobs, int *status) {
-    __shared__ uint64_t sums[33];
-    const MemoJob J = jobs[blockIdx.x];
+template <bool PAR>
+__device__ __forceinline__ void memo_cta_build_body(const MemoJob &J, uint64_t *sums,
+                                                    int *status) {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int nwarps = blockDim.x >> 5;
     const int k = J.k;
@@ -639,6 +637,132 @@ __global__ void __launch_bounds__(T, 1024 / T) memo_cta_build_kernel(
             }
         }
         __syncthreads();
+    }
+}
+
+template <int T, bool PAR>
+__global__ void __launch_bounds__(T, 1024 / T) memo_cta_build_kernel(
+    const MemoJob *__restrict__ jobs, int *status) {
+    __shared__ uint64_t sums[33];
+    const MemoJob J = jobs[blockIdx.x];
+    memo_cta_build_body<PAR>(J, sums, status);
+}
+
+// One memo built by all CTAs of a thread-block cluster: the same elementwise
+// batches as the one-CTA build, with the elements of a batch spread over the
+// warps of the whole cluster (wpe warps to an element, interleaving its words,
+// when a batch has fewer elements than the cluster has warps) and the
+// hardware cluster barrier (release/acquire) between batches.  Every CTA
+// computes the offsets; rank 0 stores them.  Offsets and sources, stored by
+// other CTAs, are read from L2 (ld.global.cg): a line of L1 could hold rows
+// of a batch that another CTA was still writing.  All CTAs of the cluster
+// pass the same sequence of barriers: the batch loop and the one early
+// return depend only on the job.
+__device__ __forceinline__ void memo_coop_build_body(const MemoJob &J, unsigned part,
+                                                     unsigned nparts, uint64_t *sums,
+                                                     int *status) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int nwarps = blockDim.x >> 5;
+    const int k = J.k;
+    uint64_t carry = 0;
+    for (int base = 0; base < J.top; base += blockDim.x) {
+        const int m = base + threadIdx.x;
+        const uint64_t v = m < J.top ? __ldg(J.Ct + m) : 0ull;
+        uint64_t tot;
+        const uint64_t ex = block_exclusive_scan(v, sums, &tot);
+        if (part == 0 && m < J.top) J.O[m] = carry + ex;
+        carry += tot;
+    }
+    if (part == 0 && threadIdx.x == 0) J.O[J.top] = carry;
+    __syncthreads();
+    if (carry != J.rows) {
+        if (part == 0 && threadIdx.x == 0) atomicExch(status, (int)DEV_INTERNAL);
+        return;
+    }
+    cluster_arrive_release();
+    cluster_wait_acquire();
+    const int tw = (int)nparts * nwarps;  // warps of the cluster
+    const int gw = (int)part * nwarps + warp;
+    for (int m0 = 0; m0 < J.top; m0 += J.b) {
+        const int m1 = m0 + J.b < J.top ? m0 + J.b : J.top;
+        const int ne = m1 - m0;
+        const int wpe = tw >= 2 * ne ? tw / ne : 1;
+        const int groups = tw / wpe;
+        const int sub = gw % wpe;
+        const uint32_t stride = 32u * (uint32_t)wpe;
+        const uint32_t step = stride % (uint32_t)k;
+        for (int e = gw / wpe; e < ne && gw < groups * wpe; e += groups) {
+            const int m = m0 + e;
+            uint64_t dst = __ldcg(J.O + m);
+            if (m == 0) {
+                if (sub == 0 && lane < k) J.R[lane] = 0;
+                continue;
+            }
+            uint64_t plen = 0, psrc = 0;
+            if (lane < k) {
+                const int sm = m - J.t[lane];
+                if (sm >= 0) {
+                    plen = __ldg(J.Ct + (int64_t)lane * J.cs + sm);
+                    psrc = __ldcg(J.O + sm + 1) - plen;  // suffix Z_{>=lane}(sm)
+                }
+            }
+            for (int i = 0; i < k; ++i) {
+                const uint64_t len = shfl_u64(plen, i);
+                const uint64_t src = shfl_u64(psrc, i);
+                if (len == 0) continue;
+                const uint64_t W = len * (uint64_t)k;
+                const int32_t *a = J.R + src * (uint64_t)k;
+                int32_t *b = J.R + dst * (uint64_t)k;
+                const uint64_t first = (uint64_t)sub * 32u + (uint64_t)lane;
+                uint32_t c0 = (uint32_t)(first % (uint64_t)k);
+                for (uint64_t w0 = first; w0 < W; w0 += (uint64_t)stride * MB_ILP) {
+                    int32_t v[MB_ILP];
+#pragma unroll
+                    for (int u = 0; u < MB_ILP; ++u)
+                        if (w0 + (uint64_t)stride * u < W) v[u] = __ldcg(a + w0 + (uint64_t)stride * u);
+                    uint32_t c = c0;
+#pragma unroll
+                    for (int u = 0; u < MB_ILP; ++u) {
+                        if (w0 + (uint64_t)stride * u < W)
+                            b[w0 + (uint64_t)stride * u] = v[u] + (c == (uint32_t)i ? 1 : 0);
+                        c += step;
+                        if (c >= (uint32_t)k) c -= (uint32_t)k;
+                    }
+                    c0 = c;
+                }
+                dst += len;
+            }
+        }
+        cluster_arrive_release();
+        cluster_wait_acquire();
+    }
+}
+
+// Persistent build of a batch's memos, jobs sorted longest first: cluster c
+// < ncoop builds job c cooperatively, then every CTA claims the remaining
+// jobs one at a time (claim counter zeroed before the launch), so the short
+// memos fill in behind the long ones as in the one-CTA launch.  Clusters
+// need not be co-resident with one another: a CTA waits only on its own
+// cluster's barrier.
+template <int T>
+__global__ void __launch_bounds__(T, 1024 / T) memo_cluster_build_kernel(
+    const MemoJob *__restrict__ jobs, int njobs, int ncoop, unsigned *claim, int *status) {
+    __shared__ uint64_t sums[33];
+    __shared__ int s_job;
+    const unsigned nparts = cluster_size();
+    const int cl = (int)(blockIdx.x / nparts);
+    if (cl < ncoop) {
+        const MemoJob J = jobs[cl];
+        memo_coop_build_body(J, cluster_rank(), nparts, sums, status);
+    }
+    for (;;) {
+        __syncthreads();  // s_job of the previous claim has been read
+        if (threadIdx.x == 0) s_job = ncoop + (int)atomicAdd(claim, 1u);
+        __syncthreads();
+        const int j = s_job;
+        if (j >= njobs) break;
+        const MemoJob J = jobs[j];
+        memo_cta_build_body<true>(J, sums, status);
     }
 }
 
@@ -890,8 +1014,106 @@ static int memo_cta_threads() {
     return t;
 }
 
-int launch_memo_cta_build(const MemoJob *jobs, int njobs, int *status, cudaStream_t s) {
+// Cluster size of the cooperative batch memo build: FZ_MEMO_COOP=0 turns it
+// off, 2|4|8 set the size (tuning only).
+constexpr int MEMO_COOP_CL_DEFAULT = 2;
+static int memo_coop_cluster() {
+    static const int c = [] {
+        const char *e = getenv("FZ_MEMO_COOP");
+        if (!e) return MEMO_COOP_CL_DEFAULT;
+        const int v = atoi(e);
+        return (v == 0 || v == 2 || v == 4 || v == 8) ? v : MEMO_COOP_CL_DEFAULT;
+    }();
+    return c;
+}
+
+static cudaLaunchConfig_t coop_config(int grid, int csize, cudaLaunchAttribute *attr,
+                                      cudaStream_t s) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(grid);
+    cfg.blockDim = dim3(MB_CTA_THREADS_DEFAULT);
+    cfg.dynamicSmemBytes = 0;
+    cfg.stream = s;
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = csize;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cfg;
+}
+
+// Clusters of the cooperative build that fit on the device at once (0 if
+// the shape does not fit).
+static int coop_resident_clusters(int csize) {
+    static DeviceOnce done[3];
+    static int cached[3][64];
+    const int slot = csize == 2 ? 0 : csize == 4 ? 1 : 2;
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return 0;
+    if (!done[slot].is_set(dev)) {
+        cudaLaunchAttribute attr[1];
+        cudaLaunchConfig_t cfg = coop_config(csize, csize, attr, 0);
+        int n = 0;
+        if (cudaOccupancyMaxActiveClusters(&n, memo_cluster_build_kernel<MB_CTA_THREADS_DEFAULT>,
+                                           &cfg) != cudaSuccess) {
+            cudaGetLastError();
+            n = 0;
+        }
+        cached[slot][dev] = n;
+        done[slot].set(dev);
+    }
+    return cached[slot][dev];
+}
+
+// The build takes as long as its longest memo when that memo alone outlasts
+// an even share of all the work: a one-CTA memo costs about its words plus
+// MEMO_BATCH_WORDS per elementwise batch (the dependent round trips and the
+// barrier).  Jobs sorted longest first; every job above the even share over
+// the device's CTA slots is built by a cluster, at most half the clusters
+// that fit at once.
+constexpr double MEMO_BATCH_WORDS = 16000.0;
+
+int memo_coop_count(const MemoJob *sorted, int njobs) {
+    const int csize = memo_coop_cluster();
+    if (csize == 0 || njobs < 2) return 0;
+    const int clusters = coop_resident_clusters(csize);
+    if (clusters < 2) return 0;
+    const double slots = (double)clusters * csize;
+    std::vector<double> w((size_t)njobs);
+    double sum = 0;
+    for (int j = 0; j < njobs; ++j) {
+        const MemoJob &J = sorted[j];
+        const double nbatch = ((double)J.top + J.b - 1) / (double)J.b;
+        w[(size_t)j] = (double)J.rows * J.k + MEMO_BATCH_WORDS * nbatch;
+        sum += w[(size_t)j];
+    }
+    const double share = sum / slots;
+    int n = 0;
+    while (n < njobs && n < clusters / 2 && w[(size_t)n] > share) ++n;
+    return n;
+}
+
+int launch_memo_cta_build(const MemoJob *jobs, int njobs, int ncoop, unsigned *claim,
+                          int *status, cudaStream_t s) {
     if (njobs <= 0) return FZ_OK;
+    const int csize = memo_coop_cluster();
+    if (ncoop > 0 && csize > 0) {
+        const int clusters = coop_resident_clusters(csize);
+        if (ncoop > clusters) return set_error(FZ_EINTERNAL, "memo build: too many clusters");
+        // enough CTAs for every slot, none beyond the jobs they can take
+        int grid_cl = clusters;
+        const int need = ncoop + (njobs - ncoop + csize - 1) / csize;
+        if (grid_cl > need) grid_cl = need;
+        FZ_CUDA_TRY(cudaMemsetAsync(claim, 0, sizeof(unsigned), s));
+        cudaLaunchAttribute attr[1];
+        cudaLaunchConfig_t cfg = coop_config(grid_cl * csize, csize, attr, s);
+        cudaError_t e = cudaLaunchKernelEx(&cfg, memo_cluster_build_kernel<MB_CTA_THREADS_DEFAULT>,
+                                           jobs, njobs, ncoop, claim, status);
+        if (e != cudaSuccess) return cuda_error(e, "memo build (cluster) launch");
+        note_launch();
+        return FZ_OK;
+    }
     const bool par = memo_desc_parallel();
     switch (memo_cta_threads()) {
         case 256:

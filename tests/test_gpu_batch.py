@@ -154,6 +154,32 @@ def test_batch_every_memo_depth(fz):
             assert np.array_equal(got, oracle.enumerate_desc(g, n)), (g, n, k)
 
 
+def test_batch_cluster_memo_build(fz):
+    """The longest memos built by thread-block clusters: a few elements per
+    batch (small tail generators: several warps share an element's words),
+    batches of more elements than the cluster has warps (tail minimum 140),
+    and many short memos claimed one per CTA after them.  Rebuilt twice (the
+    claim counter starts over)."""
+    inst = [((2, 3, 5, 7), 400), ((2, 3, 5, 7, 11), 200), ((33, 37, 41, 43, 47), 2500),
+            ((34, 39, 41, 45), 3000), ((5, 8, 11, 14), 900), ((3, 4, 5, 6, 7, 8), 60),
+            ((70, 75, 80, 85), 5000), ((130, 140, 150, 160), 9000)]
+    inst += small_instances(36, 80)
+    with fz.Batch(inst) as b:
+        assert b.coop_memos > 0, b.coop_memos
+        out = torch.full((int(b.total_words) + 16,), CANARY, dtype=torch.int32, device="cuda")
+        for _ in range(2):
+            out.fill_(CANARY)
+            b.rebuild()
+            b.enumerate(out)
+            b.sync()
+        host = out.cpu().numpy()
+        assert (host[int(b.total_words):] == CANARY).all()
+        for i, (g, n) in enumerate(inst):
+            a, r = int(b.word_offsets[i]), int(b.rows[i])
+            got = host[a:a + r * len(g)].reshape(r, len(g))
+            assert np.array_equal(got, oracle.enumerate_desc(g, n)), (g, n)
+
+
 def test_batch_shared_tails_and_rebuild(fz):
     rng = np.random.Generator(np.random.PCG64(33))
     pool = [workloads.draw_generators(rng, int(rng.integers(3, 8)), 5, 60) for _ in range(6)]
