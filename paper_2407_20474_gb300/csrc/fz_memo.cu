@@ -648,6 +648,159 @@ __global__ void __launch_bounds__(T, 1024 / T) memo_cta_build_kernel(
     memo_cta_build_body<PAR>(J, sums, status);
 }
 
+// Element groups.  Most elements of a batch memo are a few rows (config 4:
+// 95 % of 1.7e7 elements hold at most 256 words), and a warp that takes them
+// one at a time pays a chain of dependent loads (the element's offset, then
+// its blocks' lengths and sources, then the copy) for a handful of words.
+// Here each warp owns a contiguous run of the batch's elements and takes
+// them G = floor(32 / k) at a time: lane j loads the length and source of
+// block j mod k of element j div k, all in one round; a warp scan of the
+// lengths gives every block its first row (the group's rows are contiguous,
+// so the scan total must meet the next element's offset).  A group of at
+// most MG_FLAT_WORDS words is then copied as one flat range: each word finds
+// its block by a binary search over the lanes' first rows (shuffles; empty
+// blocks share their successor's first row and are never the last block
+// starting at or before a row).  Larger groups copy block by block, as the
+// one-element build does.  One __syncthreads per elementwise batch, as
+// before: a warp's groups never read rows of its own batch.
+constexpr uint64_t MG_FLAT_WORDS = 4 * 32 * MB_ILP;
+
+__device__ __forceinline__ uint32_t warp_incl_scan_u32(uint32_t v, int lane) {
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t t = __shfl_up_sync(FULL, v, o);
+        if (lane >= o) v += t;
+    }
+    return v;
+}
+
+__device__ __forceinline__ void memo_group_build_body(const MemoJob &J, uint64_t *sums,
+                                                      int32_t *s_t, int *status) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int nwarps = blockDim.x >> 5;
+    const int k = J.k;
+    uint64_t carry = 0;
+    for (int base = 0; base < J.top; base += blockDim.x) {
+        const int m = base + threadIdx.x;
+        const uint64_t v = m < J.top ? __ldg(J.Ct + m) : 0ull;
+        uint64_t tot;
+        const uint64_t ex = block_exclusive_scan(v, sums, &tot);
+        if (m < J.top) J.O[m] = carry + ex;
+        carry += tot;
+    }
+    if (threadIdx.x == 0) J.O[J.top] = carry;
+    if (threadIdx.x < FZ_MAX_D) s_t[threadIdx.x] = (int)threadIdx.x < k ? J.t[threadIdx.x] : 0;
+    __syncthreads();
+    if (carry != J.rows || k < 1 || k > FZ_MAX_D) {
+        if (threadIdx.x == 0) atomicExch(status, (int)DEV_INTERNAL);
+        return;
+    }
+    const int G = 32 / k;                          // elements per group
+    const int je = lane / k, ji = lane - je * k;   // lane's (element, block) in a group
+    const uint32_t uk = (uint32_t)k, rstep = 32u / uk, cstep = 32u % uk;
+    int32_t *R = J.R;
+    for (int m0 = 0; m0 < J.top; m0 += J.b) {
+        const int m1 = m0 + J.b < J.top ? m0 + J.b : J.top;
+        const int ne = m1 - m0;
+        const int e_lo = m0 + (int)(((int64_t)warp * ne) / nwarps);
+        const int e_hi = m0 + (int)(((int64_t)(warp + 1) * ne) / nwarps);
+        for (int eb = e_lo; eb < e_hi; eb += G) {
+            const int ge = e_hi - eb < G ? e_hi - eb : G;
+            const int npair = ge * k;
+            uint32_t len = 0, src = 0;
+            if (lane < npair) {
+                const int sm = eb + je - s_t[ji];
+                if (sm >= 0) {
+                    const uint64_t l = __ldg(J.Ct + (int64_t)ji * J.cs + sm);
+                    len = (uint32_t)l;
+                    src = (uint32_t)(J.O[sm + 1] - l);  // suffix Z_{>=ji}(sm)
+                }
+            }
+            const uint32_t ob = (uint32_t)J.O[eb], oe = (uint32_t)J.O[eb + ge];
+            const uint32_t z = eb == 0 ? 1u : 0u;  // Z(0): one zero row before the blocks
+            const uint32_t incl = warp_incl_scan_u32(len, lane);
+            const uint32_t rbeg = ob + z;
+            const uint32_t dst = rbeg + incl - len;
+            if (rbeg + __shfl_sync(FULL, incl, 31) != oe) {
+                if (lane == 0) atomicExch(status, (int)DEV_INTERNAL);
+                continue;
+            }
+            if (z && lane < k) R[lane] = 0;
+            const uint64_t W = (uint64_t)(oe - rbeg) * uk;
+            if (W <= MG_FLAT_WORDS) {
+                const uint32_t key = lane < npair ? dst : 0xffffffffu;
+                const uint64_t obase = (uint64_t)rbeg * uk;
+                for (uint32_t w0 = 0; w0 < (uint32_t)W; w0 += 32u * MB_ILP) {
+                    const uint32_t wl = w0 + (uint32_t)lane;
+                    uint32_t r = rbeg + wl / uk, c = wl % uk;
+                    int32_t v[MB_ILP];
+                    uint32_t inc = 0;
+#pragma unroll
+                    for (int u = 0; u < MB_ILP; ++u) {
+                        int p = 0;  // the last block starting at or before row r
+#pragma unroll
+                        for (int st = 16; st >= 1; st >>= 1)
+                            if (__shfl_sync(FULL, key, p + st) <= r) p += st;
+                        const uint32_t sp = __shfl_sync(FULL, src, p);
+                        const uint32_t dp = __shfl_sync(FULL, dst, p);
+                        const int ip = __shfl_sync(FULL, ji, p);
+                        if (wl + 32u * u < (uint32_t)W) {
+                            v[u] = R[(uint64_t)(sp + (r - dp)) * uk + c];
+                            if (c == (uint32_t)ip) inc |= 1u << u;
+                        }
+                        r += rstep;
+                        c += cstep;
+                        if (c >= uk) {
+                            c -= uk;
+                            ++r;
+                        }
+                    }
+#pragma unroll
+                    for (int u = 0; u < MB_ILP; ++u)
+                        if (wl + 32u * u < (uint32_t)W)
+                            R[obase + wl + 32u * u] = v[u] + (int32_t)((inc >> u) & 1u);
+                }
+            } else {
+                for (int j = 0; j < npair; ++j) {
+                    const uint32_t l = __shfl_sync(FULL, len, j);
+                    if (l == 0) continue;
+                    const uint32_t sj = __shfl_sync(FULL, src, j);
+                    const uint32_t dj = __shfl_sync(FULL, dst, j);
+                    const uint32_t i = (uint32_t)(j % k);
+                    const uint64_t Wb = (uint64_t)l * uk;
+                    const int32_t *a = R + (uint64_t)sj * uk;
+                    int32_t *b = R + (uint64_t)dj * uk;
+                    uint32_t c0 = (uint32_t)lane % uk;
+                    for (uint64_t w0 = lane; w0 < Wb; w0 += 32 * MB_ILP) {
+                        int32_t v[MB_ILP];
+#pragma unroll
+                        for (int u = 0; u < MB_ILP; ++u)
+                            if (w0 + 32 * u < Wb) v[u] = a[w0 + 32 * u];
+                        uint32_t c = c0;
+#pragma unroll
+                        for (int u = 0; u < MB_ILP; ++u) {
+                            if (w0 + 32 * u < Wb) b[w0 + 32 * u] = v[u] + (c == i ? 1 : 0);
+                            c += cstep;
+                            if (c >= uk) c -= uk;
+                        }
+                        c0 = c;
+                    }
+                }
+            }
+        }
+        __syncthreads();
+    }
+}
+
+template <int T>
+__global__ void __launch_bounds__(T, 1024 / T) memo_group_cta_kernel(
+    const MemoJob *__restrict__ jobs, int *status) {
+    __shared__ uint64_t sums[33];
+    __shared__ int32_t s_t[FZ_MAX_D];
+    const MemoJob J = jobs[blockIdx.x];
+    memo_group_build_body(J, sums, s_t, status);
+}
+
 // One memo built by all CTAs of a thread-block cluster: the same elementwise
 // batches as the one-CTA build, with the elements of a batch spread over the
 // warps of the whole cluster (wpe warps to an element, interleaving its words,
@@ -744,10 +897,11 @@ __device__ __forceinline__ void memo_coop_build_body(const MemoJob &J, unsigned 
 // memos fill in behind the long ones as in the one-CTA launch.  Clusters
 // need not be co-resident with one another: a CTA waits only on its own
 // cluster's barrier.
-template <int T>
+template <int T, bool GROUP>
 __global__ void __launch_bounds__(T, 1024 / T) memo_cluster_build_kernel(
     const MemoJob *__restrict__ jobs, int njobs, int ncoop, unsigned *claim, int *status) {
     __shared__ uint64_t sums[33];
+    __shared__ int32_t s_t[FZ_MAX_D];
     __shared__ int s_job;
     const unsigned nparts = cluster_size();
     const int cl = (int)(blockIdx.x / nparts);
@@ -762,7 +916,8 @@ __global__ void __launch_bounds__(T, 1024 / T) memo_cluster_build_kernel(
         const int j = s_job;
         if (j >= njobs) break;
         const MemoJob J = jobs[j];
-        memo_cta_build_body<true>(J, sums, status);
+        if (GROUP) memo_group_build_body(J, sums, s_t, status);
+        else memo_cta_build_body<true>(J, sums, status);
     }
 }
 
@@ -1014,6 +1169,16 @@ static int memo_cta_threads() {
     return t;
 }
 
+// The one-CTA batch memo build: element groups (default) or
+// FZ_MEMO_BUILD=element, one element per warp at a time (tuning only).
+static bool memo_build_groups() {
+    static const bool on = [] {
+        const char *e = getenv("FZ_MEMO_BUILD");
+        return !(e && strcmp(e, "element") == 0);
+    }();
+    return on;
+}
+
 // Cluster size of the cooperative batch memo build: FZ_MEMO_COOP=0 turns it
 // off, 2|4|8 set the size (tuning only).
 constexpr int MEMO_COOP_CL_DEFAULT = 2;
@@ -1055,8 +1220,9 @@ static int coop_resident_clusters(int csize) {
         cudaLaunchAttribute attr[1];
         cudaLaunchConfig_t cfg = coop_config(csize, csize, attr, 0);
         int n = 0;
-        if (cudaOccupancyMaxActiveClusters(&n, memo_cluster_build_kernel<MB_CTA_THREADS_DEFAULT>,
-                                           &cfg) != cudaSuccess) {
+        if (cudaOccupancyMaxActiveClusters(
+                &n, memo_cluster_build_kernel<MB_CTA_THREADS_DEFAULT, true>, &cfg) !=
+            cudaSuccess) {
             cudaGetLastError();
             n = 0;
         }
@@ -1108,10 +1274,21 @@ int launch_memo_cta_build(const MemoJob *jobs, int njobs, int ncoop, unsigned *c
         FZ_CUDA_TRY(cudaMemsetAsync(claim, 0, sizeof(unsigned), s));
         cudaLaunchAttribute attr[1];
         cudaLaunchConfig_t cfg = coop_config(grid_cl * csize, csize, attr, s);
-        cudaError_t e = cudaLaunchKernelEx(&cfg, memo_cluster_build_kernel<MB_CTA_THREADS_DEFAULT>,
-                                           jobs, njobs, ncoop, claim, status);
+        cudaError_t e =
+            memo_build_groups()
+                ? cudaLaunchKernelEx(&cfg, memo_cluster_build_kernel<MB_CTA_THREADS_DEFAULT, true>,
+                                     jobs, njobs, ncoop, claim, status)
+                : cudaLaunchKernelEx(&cfg, memo_cluster_build_kernel<MB_CTA_THREADS_DEFAULT, false>,
+                                     jobs, njobs, ncoop, claim, status);
         if (e != cudaSuccess) return cuda_error(e, "memo build (cluster) launch");
         note_launch();
+        return FZ_OK;
+    }
+    if (memo_build_groups()) {
+        memo_group_cta_kernel<MB_CTA_THREADS_DEFAULT>
+            <<<njobs, MB_CTA_THREADS_DEFAULT, 0, s>>>(jobs, status);
+        note_launch();
+        FZ_CUDA_TRY(cudaGetLastError());
         return FZ_OK;
     }
     const bool par = memo_desc_parallel();
