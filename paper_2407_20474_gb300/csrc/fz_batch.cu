@@ -128,6 +128,7 @@ void chain_view(ScanJob &J, const Inst &I) {
 int build_scan_plan(fz_batch_s *b, uint64_t *table_base, std::vector<ScanJob> &jobs,
                     std::vector<ScanTask> &tasks, size_t *scratch_words) {
     const int64_t DIRECT = scan_direct_limit();
+    const int64_t LANE_LIMIT = scan_lane_limit();
     const int RBk = scan_block_rows();
     int maxlev = 0;
     for (const Inst &I : b->inst) maxlev = std::max(maxlev, std::max(I.d, I.lam_r));
@@ -253,8 +254,15 @@ int build_scan_plan(fz_batch_s *b, uint64_t *table_base, std::vector<ScanJob> &j
             const ScanJob &J = jobs[ji];
             if (!J.slen) {
                 const int64_t chains = std::min<int64_t>(J.g, J.len);
-                for (int64_t a = 0; a < chains; a += 8)
-                    tasks.push_back({ji, TK_DIRECT, a, std::min(chains, a + 8)});
+                const int64_t T = (J.len + J.g - 1) / J.g;
+                if (chains >= 32 && T <= LANE_LIMIT) {
+                    // 256 chains a task, one a lane
+                    for (int64_t a = 0; a < chains; a += 256)
+                        tasks.push_back({ji, TK_LANES, a, std::min(chains, a + 256)});
+                } else {
+                    for (int64_t a = 0; a < chains; a += 8)
+                        tasks.push_back({ji, TK_DIRECT, a, std::min(chains, a + 8)});
+                }
             } else {
                 for (int64_t a = 0; a < J.slen; a += 2048)
                     tasks.push_back({ji, TK_BSUM, a, std::min(J.slen, a + 2048)});

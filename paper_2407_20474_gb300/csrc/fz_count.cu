@@ -15,6 +15,7 @@
 // same routine (they form a strided array of the same shape), and the blocks
 // are then re-walked with their carries.  All sums saturate at 2^64 - 1.
 #include <cstdlib>
+#include <cstring>
 
 #include "fz_internal.cuh"
 
@@ -23,6 +24,8 @@ namespace fz {
 namespace {
 
 constexpr int64_t DIRECT_T = 4096;  // chains up to this length: one warp each
+constexpr int64_t LANE_T = 1024;    // chains up to this length, 32 or more: one lane each
+constexpr int LANE_ILP = 8;
 constexpr int RB = 32;              // entries per block in the blocked scan
 constexpr int THREADS = 256;
 
@@ -256,6 +259,32 @@ __global__ void __launch_bounds__(THREADS, MINB) scan_tasks_kernel(const ScanJob
             for (int64_t rho = t.begin + warp; rho < t.end; rho += nwarps)
                 chain_scan_warp(J.in, J.out, J.len, J.g, rho, lane, J.ones_below, off, es);
             break;
+        case TK_LANES: {
+            // lane l of warp w: chain rho = begin + 32 w + l, walked down with
+            // its own running sum; a warp's loads and stores cover 32
+            // neighbouring entries of a row (one 256-byte span when es = 1)
+            const int64_t rho = t.begin + (int64_t)warp * 32 + lane;
+            if (rho >= t.end) break;
+            const uint64_t *__restrict__ in = J.in;
+            uint64_t *__restrict__ out = J.out;
+            const int64_t T = (J.len - rho + J.g - 1) / J.g;
+            uint64_t acc = 0;
+            for (int64_t t0 = 0; t0 < T; t0 += LANE_ILP) {
+                uint64_t v[LANE_ILP];
+#pragma unroll
+                for (int u = 0; u < LANE_ILP; ++u)
+                    v[u] = t0 + u < T ? __ldg(in + off + (rho + (t0 + u) * J.g) * es) : 0ull;
+#pragma unroll
+                for (int u = 0; u < LANE_ILP; ++u) {
+                    if (t0 + u < T) {
+                        const int64_t x = off + (rho + (t0 + u) * J.g) * es;
+                        acc = sat_add(acc, v[u]);
+                        out[x] = x < J.ones_below ? 1ull : acc;
+                    }
+                }
+            }
+            break;
+        }
         case TK_SSCAN:
             for (int64_t rho = t.begin + warp; rho < t.end; rho += nwarps)
                 chain_scan_warp(J.S, J.Sincl, J.slen, J.g, rho, lane);
@@ -318,23 +347,32 @@ __global__ void __launch_bounds__(THREADS, MINB) scan_tasks_kernel(const ScanJob
             // |Z(r, (g, h))|: the a with g a = r (mod h) in [0, r / g] are
             // a = a* (mod h1), a* = (r / e) inv (mod h1), when e divides r
             // (row d-1 is written only for whole rows: es == 1)
-            for (int64_t i = t.begin + threadIdx.x; i < t.end; i += blockDim.x) {
-                const int64_t r = off + i * es;
-                uint64_t c = 0;
-                if (r % J.e == 0) {
-                    const int64_t re = r / J.e;
-                    const int64_t astar = (re % J.h1) * J.inv % J.h1;
-                    const int64_t q = re / J.g1;
-                    c = q >= astar ? (uint64_t)((q - astar) / J.h1 + 1) : 0ull;
+            // (32-bit: entries, generators and their quotients are below
+            // 2^31; the product (re mod h1) inv needs 64 bits when h1 >= 2^16)
+            {
+                const uint32_t e = (uint32_t)J.e, h1 = (uint32_t)J.h1, g1 = (uint32_t)J.g1;
+                const uint32_t h = (uint32_t)J.h, inv = (uint32_t)J.inv;
+                const bool small = h1 < 65536u;
+                for (int64_t i = t.begin + threadIdx.x; i < t.end; i += blockDim.x) {
+                    const uint32_t r = (uint32_t)(off + i * es);
+                    uint64_t c = 0;
+                    if (r % e == 0) {
+                        const uint32_t re = r / e;
+                        const uint32_t astar =
+                            small ? (re % h1) * inv % h1
+                                  : (uint32_t)((uint64_t)(re % h1) * inv % h1);
+                        const uint32_t q = re / g1;
+                        c = q >= astar ? (uint64_t)((q - astar) / h1 + 1) : 0ull;
+                    }
+                    J.out[r] = c;
+                    if (J.ones_below && es == 1) J.out[J.len + r] = (r % h == 0) ? 1ull : 0ull;
                 }
-                J.out[r] = c;
-                if (J.ones_below && es == 1) J.out[J.len + r] = (r % J.h == 0) ? 1ull : 0ull;
             }
             break;
         case TK_LINEAR:
             for (int64_t i = t.begin + threadIdx.x; i < t.end; i += blockDim.x) {
                 const int64_t x = off + i * es;
-                J.out[x] = x < J.ones_below ? 1ull : (uint64_t)(x / J.g + 1);
+                J.out[x] = x < J.ones_below ? 1ull : (uint64_t)((uint32_t)x / (uint32_t)J.g + 1u);
             }
             break;
         default:
@@ -365,6 +403,14 @@ int launch_scan_tasks(const ScanJob *jobs, const ScanTask *tasks, int ntasks, cu
 }
 
 int64_t scan_direct_limit() { return DIRECT_T; }
+// FZ_SCAN_LANES=0 scans every short chain with a warp (tuning only).
+int64_t scan_lane_limit() {
+    static const int64_t v = [] {
+        const char *e = getenv("FZ_SCAN_LANES");
+        return (e && strcmp(e, "0") == 0) ? (int64_t)0 : LANE_T;
+    }();
+    return v;
+}
 int scan_block_rows() { return RB; }
 
 int launch_count_rolling(const int32_t *g, int d, int32_t n, uint64_t *a, uint64_t *b,

@@ -259,7 +259,8 @@ enum ScanTaskKind : int {
     TK_DELTA = 4,   // out[begin..end) = [i == 0]
     TK_ONES = 5,    // out[begin..end) = 1
     TK_PAIR = 6,    // rows d-2 and d-1 of a count table in closed form
-    TK_LINEAR = 7   // out[x] = x / g + 1 (a runs-table row above the ones row)
+    TK_LINEAR = 7,  // out[x] = x / g + 1 (a runs-table row above the ones row)
+    TK_LANES = 8    // chains [begin, end) of in -> out, 32 neighbouring chains a warp
 };
 struct ScanTask {
     int job;
@@ -268,6 +269,7 @@ struct ScanTask {
 };
 int launch_scan_tasks(const ScanJob *jobs, const ScanTask *tasks, int ntasks, cudaStream_t s);
 int64_t scan_direct_limit();  // chains up to this length are scanned directly
+int64_t scan_lane_limit();    // chains up to this length, 32 or more of them: a lane each
 int scan_block_rows();        // entries per block of a blocked scan
 
 // out[0] = 0, out[r + 1] = in[0] + ... + in[r] for r < len (saturating).
