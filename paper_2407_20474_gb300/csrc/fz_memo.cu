@@ -1077,7 +1077,18 @@ __global__ void __launch_bounds__(THREADS) run_rows_batch_kernel(const RunJob *_
                 }
                 const int k = J.k;
                 const int32_t *s = J.rows + o0 * (uint64_t)k;
-                for (uint64_t r = 0; r < len; ++r, s += k)
+                // four rows' loads before their stores
+                uint64_t r = 0;
+                for (; r + 4 <= len; r += 4, s += 4 * k) {
+                    int4 v[4];
+#pragma unroll
+                    for (int u = 0; u < 4; ++u)
+                        v[u] = make_int4((int)q, __ldg(s + u * k), k > 1 ? __ldg(s + u * k + 1) : 0,
+                                         k > 2 ? __ldg(s + u * k + 2) : 0);
+#pragma unroll
+                    for (int u = 0; u < 4; ++u) o[r + u] = v[u];
+                }
+                for (; r < len; ++r, s += k)
                     o[r] = make_int4((int)q, __ldg(s), k > 1 ? __ldg(s + 1) : 0,
                                      k > 2 ? __ldg(s + 2) : 0);
             } else if (J.k == 1) {
@@ -1094,9 +1105,13 @@ __global__ void __launch_bounds__(THREADS) run_rows_batch_kernel(const RunJob *_
                     atomicExch(status, (int)DEV_INTERNAL);
                     return;
                 }
-                for (uint64_t r = 0; r < want; ++r) {
-                    const int64_t a0 = atop - (int64_t)r * J.h1;
-                    o[r] = make_int4((int)q, (int)a0, (int)((p - a0 * J.t0) / J.t1), 0);
+                // a0 falls by h1 = t1 / e a row, so the last coordinate
+                // (p - a0 t0) / t1 rises by t0 / e: one division an element
+                if (want > 0) {
+                    int64_t a0 = atop, b0 = (p - atop * J.t0) / J.t1;
+                    const int64_t bstep = J.t0 / J.e;
+                    for (uint64_t r = 0; r < want; ++r, a0 -= J.h1, b0 += bstep)
+                        o[r] = make_int4((int)q, (int)a0, (int)b0, 0);
                 }
             }
         }
