@@ -129,6 +129,7 @@ int build_scan_plan(fz_batch_s *b, uint64_t *table_base, std::vector<ScanJob> &j
                     std::vector<ScanTask> &tasks, size_t *scratch_words) {
     const int64_t DIRECT = scan_direct_limit();
     const int64_t LANE_LIMIT = scan_lane_limit();
+    const int64_t BS_TASK = scan_blocks_per_task();
     const int RBk = scan_block_rows();
     int maxlev = 0;
     for (const Inst &I : b->inst) maxlev = std::max(maxlev, std::max(I.d, I.lam_r));
@@ -264,8 +265,9 @@ int build_scan_plan(fz_batch_s *b, uint64_t *table_base, std::vector<ScanJob> &j
                         tasks.push_back({ji, TK_DIRECT, a, std::min(chains, a + 8)});
                 }
             } else {
-                for (int64_t a = 0; a < J.slen; a += 2048)
-                    tasks.push_back({ji, TK_BSUM, a, std::min(J.slen, a + 2048)});
+                // one block sum a thread: a block is rb strided entries
+                for (int64_t a = 0; a < J.slen; a += BS_TASK)
+                    tasks.push_back({ji, TK_BSUM, a, std::min(J.slen, a + BS_TASK)});
             }
         }
         b->scan_launches.push_back({first, (int)tasks.size() - first});
@@ -281,8 +283,8 @@ int build_scan_plan(fz_batch_s *b, uint64_t *table_base, std::vector<ScanJob> &j
         for (int ji : step_jobs) {
             const ScanJob &J = jobs[ji];
             if (J.slen)
-                for (int64_t a = 0; a < J.slen; a += 2048)
-                    tasks.push_back({ji, TK_APPLY, a, std::min(J.slen, a + 2048)});
+                for (int64_t a = 0; a < J.slen; a += BS_TASK)
+                    tasks.push_back({ji, TK_APPLY, a, std::min(J.slen, a + BS_TASK)});
         }
         b->scan_launches.push_back({first, (int)tasks.size() - first});
     }

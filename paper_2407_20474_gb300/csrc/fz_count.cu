@@ -403,6 +403,17 @@ int launch_scan_tasks(const ScanJob *jobs, const ScanTask *tasks, int ntasks, cu
 }
 
 int64_t scan_direct_limit() { return DIRECT_T; }
+// Block sums a task of a blocked scan covers: one a thread (256).
+// FZ_SCAN_BS_TASK=2048 gives a thread eight (tuning only).
+int64_t scan_blocks_per_task() {
+    static const int64_t v = [] {
+        const char *e = getenv("FZ_SCAN_BS_TASK");
+        const long x = e ? atol(e) : 0;
+        return (x >= 256 && x <= 65536 && x % 256 == 0) ? (int64_t)x : (int64_t)THREADS;
+    }();
+    return v;
+}
+
 // FZ_SCAN_LANES=0 scans every short chain with a warp (tuning only).
 int64_t scan_lane_limit() {
     static const int64_t v = [] {

@@ -270,6 +270,7 @@ struct ScanTask {
 int launch_scan_tasks(const ScanJob *jobs, const ScanTask *tasks, int ntasks, cudaStream_t s);
 int64_t scan_direct_limit();  // chains up to this length are scanned directly
 int64_t scan_lane_limit();    // chains up to this length, 32 or more of them: a lane each
+int64_t scan_blocks_per_task();  // block sums a TK_BSUM / TK_APPLY task covers
 int scan_block_rows();        // entries per block of a blocked scan
 
 // out[0] = 0, out[r + 1] = in[0] + ... + in[r] for r < len (saturating).
