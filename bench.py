@@ -19,8 +19,8 @@ launch over its CUDA-event time against the measured HBM copy bandwidth,
 with the DRAM traffic of a committed ncu record; `cpu_baseline` is the
 oracle (plain C recursion) on a bounded sample of the same workload on the
 host cores; `secondary` holds bounded records of the other workloads: the
-config-3 memo build, the config-4 batch (measured memo policy, pipelined
-steps, against per-instance plans) and config-5 serving (grouped and
+d = 5 memo build of all Z(0..1500), the 4096-instance batch (measured memo
+policy, pipelined steps, against per-instance plans) and serving (grouped and
 per-request launches and one request at a time, with a sweep of offered
 rates).
 
@@ -535,7 +535,7 @@ def run_ours(args):
         del page
 
     # the secondary workloads, bounded (about a minute together): batch,
-    # serving (with a sweep of offered rates) and the config-3 memo build
+    # serving (with a sweep of offered rates) and the d = 5 memo build
     secondary = None
     if rank == 0 and world == 1 and not args.no_secondary:
         secondary = {}
@@ -666,7 +666,7 @@ def _event_time(torch, fn, steps, warmup):
 
 def measure_batch(torch, fz, steps, warmup, count=4096, only_d=0, pi_steps=5, autotune=True,
                   pipeline=True):
-    """Config 4: ``count`` instances (d 3..8, generators in [2,300], |Z|
+    """The batch: ``count`` instances (d 3..8, generators in [2,300], |Z|
     log-uniform in [1e2,1e6]) in one persistent launch -- the step (batched
     counting tables, memos and enumeration) replayed as a captured CUDA
     graph -- against the same instances launched one plan at a time.
@@ -722,8 +722,8 @@ def measure_batch(torch, fz, steps, warmup, count=4096, only_d=0, pi_steps=5, au
     ms_serial = ms
     pipe = None
     if pipeline:
-        # Pipelined steps, as for config 2: two batches of the same instances
-        # take turns; one's rebuild (tables and memos, latency-bound) runs on
+        # Pipelined steps, as for the single large set: two batches of the
+        # same instances take turns; one's rebuild (tables and memos, latency-bound) runs on
         # its own stream while the other's enumeration runs on another, the
         # enumeration capped at 4, 3 or 2 blocks per SM (chosen in the
         # warm-up) so the rebuild's blocks fit beside it.  Every step still
@@ -838,7 +838,7 @@ def _hbm_peak():
 
 def measure_serve(torch, fz, seconds=10.0, sweep_rates=(), sweep_requests=4000,
                   serial=True):
-    """Config 5: an open-loop Poisson stream (2000 req/s) of queries over 64
+    """Serving: an open-loop Poisson stream (2000 req/s) of queries over 64
     resident generator sets (d 4..7, generators in [5,500]), |Z| log-uniform
     in [1e3,1e7]; continuous batching against one-request-at-a-time serving.
     ``sweep_rates`` replays the same query mix at higher offered rates,
@@ -950,7 +950,7 @@ def run_serve_workload(args):
 
 
 def measure_memo(torch, fz, steps, warmup):
-    """Config 3: dynamic FactorizationsUpToElement build of all Z(0..1500) for
+    """The memo build: dynamic FactorizationsUpToElement build of all Z(0..1500) for
     d = 5 generators in [3,40] (seed 1): the full CSR, elementwise in batches
     of min(g) elements.  Timed on the device as the rebuild of a plan whose
     memo is that CSR (k = d, top = N + 1: count table, offsets, gather map and

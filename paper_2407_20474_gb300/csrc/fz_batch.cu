@@ -337,7 +337,8 @@ int gather(const std::vector<const uint64_t *> &ptrs, std::vector<uint64_t> &out
 // prod g)) -- the deeper the memo, the fewer prefixes the walk visits.  Otherwise, for
 // d >= 5, a partial memo of depth 3 within BATCH_MEMO_MAX_ROWS rows (the
 // pair memo's leaves, prefixes of length d - 2, would be mostly empty
-// there: config 4's d = 5 instances took 11.3 ms with it, 2 ms with depth
+// there: the d = 5 instances of a 4096-instance batch took 11.3 ms with it,
+// 2 ms with depth
 // 3).  Otherwise the pair memo: depth 2, full, as the closed form of
 // Z(p, (g_{d-2}, g_{d-1})) -- no table to build, and its leaves are
 // evaluated 32 at a time.
@@ -379,8 +380,8 @@ BatchPolicy default_policy() {
     for (int d = 0; d <= FZ_MAX_D; ++d) {
         // the batch walk pays per memo leaf, so deeper memos (fewer, larger
         // leaves) repaid their build at d >= 6 up to ~4x the instance's rows
-        // (config 4: d = 6..8 enumeration 11.9 -> 4.1 ms for 1.6 ms more
-        // build); at d <= 5 they did not
+        // (4096 mixed instances: d = 6..8 enumeration 11.9 -> 4.1 ms for
+        // 1.6 ms more build); at d <= 5 they did not
         P.cap_rows[d] = d >= 6 ? 4.0 : 1.0;
         P.run_order[d] = true;
     }

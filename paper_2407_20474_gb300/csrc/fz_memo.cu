@@ -648,8 +648,9 @@ __global__ void __launch_bounds__(T, 1024 / T) memo_cta_build_kernel(
     memo_cta_build_body<PAR>(J, sums, status);
 }
 
-// Element groups.  Most elements of a batch memo are a few rows (config 4:
-// 95 % of 1.7e7 elements hold at most 256 words), and a warp that takes them
+// Element groups.  Most elements of a batch memo are a few rows (a batch of
+// 4096 instances of widths 3..8: 95 % of 1.7e7 elements hold at most 256
+// words), and a warp that takes them
 // one at a time pays a chain of dependent loads (the element's offset, then
 // its blocks' lengths and sources, then the copy) for a handful of words.
 // Here each warp owns a contiguous run of the batch's elements and takes

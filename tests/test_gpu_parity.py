@@ -4,7 +4,7 @@ Exact integer work: the comparison is bit-exact, tuple for tuple and in
 order, with no tolerance.  Small and medium cases are compared element by
 element; the full-size workloads are checked by properties that prove
 equality (sorted, valid, right count; see gpu_checks.py) plus sampled ranks
-the oracle computes one by one, and config 2 also by an order-sensitive
+the oracle computes one by one, and the 5e8-row set also by an order-sensitive
 digest of every row against the oracle's (its walk split over host cores).
 """
 import os
