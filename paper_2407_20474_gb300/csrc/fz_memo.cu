@@ -39,6 +39,7 @@ struct MapParams {
     int *status;
     int top;
     int k;
+    int skip0;  // leave block 0's entries out (the phase fill never reads them)
     int t[FZ_MAX_D];
 };
 
@@ -65,8 +66,9 @@ __global__ void __launch_bounds__(THREADS) memo_map_kernel(MapParams P) {
                 if (lane == 0) atomicExch(P.status, (int)DEV_INTERNAL);
                 break;
             }
-            for (uint64_t r = lane; r < len; r += 32)
-                P.map[dst + r] = ((src + r) << 4) | (uint64_t)i;
+            if (i > 0 || !P.skip0)
+                for (uint64_t r = lane; r < len; r += 32)
+                    P.map[dst + r] = ((src + r) << 4) | (uint64_t)i;
             dst += len;
         }
         if (lane == 0 && dst != end) atomicExch(P.status, (int)DEV_INTERNAL);
@@ -83,6 +85,7 @@ struct FillParams {
     int k;
     int b;        // elements per batch
     int nbatch;
+    int L;        // phase fill: elements a phase (the least of t_1..t_{k-1})
 };
 
 // The copies run over memo WORDS: word w is coordinate w % k of row w / k.
@@ -219,6 +222,65 @@ __global__ void __launch_bounds__(GRID_THREADS) memo_fill_kernel(FillParams P) {
             if (!grid_barrier_mono(P.bar, nbar++, P.status)) return;
         }
         R0 = R1;
+    }
+}
+
+// Phase fill.  Block 0 of Z(m) is Z(m - t_0) with coordinate 0 raised by
+// one, row for row (Corollary "resultislex" orders the blocks by i), so word
+// w of element m, while w < |Z(m - t_0)| k, is word w of element m - t_0 plus
+// one when w is coordinate 0; every other word's source lies at least L =
+// min(t_1..t_{k-1}) elements back.  A phase of L consecutive elements
+// therefore needs no barrier inside it when one thread owns the chain (class
+// e = m mod t_0 within the phase, word w) through all the phase's elements of
+// class e: it keeps the chain's last word in a register, reads the word
+// before the phase through L2 (another thread wrote it in an earlier phase),
+// and takes every other word from the gather map.  Along a class the
+// element sizes never shrink (block 0 is the previous element), so a chain
+// is born once and stays.  With t_1 >= 2 t_0 this needs L / t_0 times fewer
+// grid barriers than the batches of t_0 elements (the d = 5 memo with tail
+// (4, 20, 22, 31, 39): 76 instead of 376).
+__global__ void __launch_bounds__(GRID_THREADS) memo_fill_phase_kernel(FillParams P) {
+    const uint64_t tid = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const uint64_t nthreads = (uint64_t)gridDim.x * blockDim.x;
+    const uint32_t uk = (uint32_t)P.k;
+    const int64_t t0 = P.b;
+    unsigned nbar = 0;
+    for (int64_t ma = 0; ma < P.top; ma += P.L) {
+        const int64_t mb = ma + P.L < P.top ? ma + P.L : P.top;
+        const uint64_t R0 = __ldg(P.O + ma);
+        uint64_t wp = 0;  // the phase's widest element, in words
+        for (int64_t m = ma; m < mb; ++m) {
+            const uint64_t sz = __ldg(P.O + m + 1) - __ldg(P.O + m);
+            if (sz > wp) wp = sz;
+        }
+        wp *= uk;
+        const int64_t ncls = mb - ma < t0 ? mb - ma : t0;
+        const uint64_t nchains = (uint64_t)ncls * wp;
+        for (uint64_t ch = tid; ch < nchains; ch += nthreads) {
+            const int64_t e = (int64_t)(ch / wp);
+            const uint64_t w = ch - (uint64_t)e * wp;
+            const uint32_t c = (uint32_t)(w % uk);
+            int32_t prev = 0;
+            bool have = false;  // prev holds word w of element m - t_0
+            for (int64_t m = ma + e; m < mb; m += t0) {
+                const uint64_t o = __ldg(P.O + m);
+                if (w >= (__ldg(P.O + m + 1) - o) * uk) continue;  // not born yet
+                int32_t v;
+                const uint64_t op = m >= t0 ? __ldg(P.O + m - t0) : 0;
+                const uint64_t szp = m >= t0 ? (__ldg(P.O + m - t0 + 1) - op) * uk : 0;
+                if (w < szp) {
+                    if (!have) prev = ld_cg_s32(P.rows + op * uk + w);
+                    v = prev + (c == 0 ? 1 : 0);
+                } else if (!word_value<false>(P, __ldg(P.map + o + w / uk), c, R0, v)) {
+                    atomicExch(P.status, (int)DEV_INTERNAL);
+                    v = 0;
+                }
+                P.rows[o * uk + w] = v;
+                prev = v;
+                have = true;
+            }
+        }
+        if (mb < P.top && !grid_barrier_mono(P.bar, nbar++, P.status)) return;
     }
 }
 
@@ -1386,14 +1448,6 @@ int launch_memo_build(const int32_t *tail, int k, int32_t top, uint64_t rows,
         mp.t[i] = tail[i];
         if (tail[i] < tmin) tmin = tail[i];
     }
-    {
-        int64_t warps = top;
-        int64_t blocks = (warps * 32 + THREADS - 1) / THREADS;
-        if (blocks > 4096) blocks = 4096;
-        memo_map_kernel<<<(int)blocks, THREADS, 0, s>>>(mp);
-        note_launch();
-        FZ_CUDA_TRY(cudaGetLastError());
-    }
     FillParams fp{};
     fp.O = mb.O;
     fp.map = mb.map;
@@ -1404,22 +1458,39 @@ int launch_memo_build(const int32_t *tail, int k, int32_t top, uint64_t rows,
     fp.k = k;
     fp.b = tmin;
     fp.nbatch = (int)(((int64_t)top + tmin - 1) / tmin);
-    // Batches small enough for one cluster run there (hardware barrier);
-    // larger ones use the whole GPU with the bounded grid barrier.
-    // variant: one cluster (hardware barrier, sources through L2) for batches
-    // of modest size, else the whole GPU with the bounded grid barrier;
-    // FZ_MEMO_FILL=cta|cluster|grid forces one (tuning only)
+    // FZ_MEMO_FILL=cta|cluster|grid|phase forces one fill (tuning only)
     static const int forced = [] {
         const char *e = getenv("FZ_MEMO_FILL");
         if (!e) return 0;
         if (!strcmp(e, "cta")) return 1;
         if (!strcmp(e, "cluster")) return 2;
         if (!strcmp(e, "grid")) return 3;
+        if (!strcmp(e, "phase")) return 4;
         return 0;
     }();
+    // phases of L elements when block 0's generator is the tail's first and
+    // every other generator is at least twice it (a phase spans >= 2 batches)
+    {
+        int L = top;
+        for (int i = 1; i < k; ++i) L = tail[i] < L ? tail[i] : L;
+        fp.L = (tail[0] == tmin && L >= 2 * tail[0]) ? L : 0;
+    }
+    // the gather map: every memo row's source row and incremented coordinate
+    auto launch_map = [&](int skip0) -> int {
+        mp.skip0 = skip0;
+        int64_t warps = top;
+        int64_t blocks = (warps * 32 + THREADS - 1) / THREADS;
+        if (blocks > 4096) blocks = 4096;
+        memo_map_kernel<<<(int)blocks, THREADS, 0, s>>>(mp);
+        note_launch();
+        FZ_CUDA_TRY(cudaGetLastError());
+        return FZ_OK;
+    };
     if (schedule == FZ_MEMO_PER_BATCH) {
         DeviceProps dp;
         int rc = device_props(&dp);
+        if (rc != FZ_OK) return rc;
+        rc = launch_map(0);
         if (rc != FZ_OK) return rc;
         for (int q = 0; q < fp.nbatch; ++q) {
             memo_batch_kernel<<<dp.sms * 4, THREADS, 0, s>>>(fp, q);
@@ -1429,19 +1500,29 @@ int launch_memo_build(const int32_t *tail, int k, int32_t top, uint64_t rows,
         return FZ_OK;
     }
     const uint64_t avg_batch_rows = rows / (uint64_t)fp.nbatch;
-    // a few rows per batch: one CTA (its barrier and L1 beat a cluster's)
-    if ((forced == 0 && avg_batch_rows * (uint64_t)k <= ONE_CTA_MAX_WORDS) || forced == 1)
-        return launch_fill_one_cta(fp, s);
-    if ((forced == 0 && avg_batch_rows <= (uint64_t)64 * 1024) || forced == 2) {
+    // a few rows per batch: one CTA (its barrier and L1 beat a cluster's);
+    // batches of modest size: one cluster; else the whole GPU, in phases
+    // when the tail allows them (then block 0 needs no map entries)
+    const bool one_cta =
+        (forced == 0 && avg_batch_rows * (uint64_t)k <= ONE_CTA_MAX_WORDS) || forced == 1;
+    const bool cluster = !one_cta &&
+                         ((forced == 0 && avg_batch_rows <= (uint64_t)64 * 1024) || forced == 2);
+    const bool phase = !one_cta && !cluster && fp.L > 0 && forced != 3;
+    {
+        int rc = launch_map(phase ? 1 : 0);
+        if (rc != FZ_OK) return rc;
+    }
+    if (one_cta) return launch_fill_one_cta(fp, s);
+    if (cluster) {
         int rc = launch_fill_cluster(fp, mb.small_ctas, s);
         if (rc == FZ_OK) return rc;
     }
-    int grid = coop_grid((const void *)memo_fill_kernel, GRID_THREADS);
+    const void *kern = phase ? (const void *)memo_fill_phase_kernel : (const void *)memo_fill_kernel;
+    int grid = coop_grid(kern, GRID_THREADS);
     if (grid <= 0) return set_error(FZ_ECUDA, "memo build: no cooperative occupancy");
     FZ_CUDA_TRY(cudaMemsetAsync(mb.bar, 0, sizeof(unsigned), s));
     void *args[] = {&fp};
-    FZ_CUDA_TRY(cudaLaunchCooperativeKernel((const void *)memo_fill_kernel, dim3(grid),
-                                            dim3(GRID_THREADS), args, 0, s));
+    FZ_CUDA_TRY(cudaLaunchCooperativeKernel(kern, dim3(grid), dim3(GRID_THREADS), args, 0, s));
     note_launch();
     return FZ_OK;
 }

@@ -8,6 +8,8 @@ the oracle computes one by one, and the 5e8-row set also by an order-sensitive
 digest of every row against the oracle's (its walk split over host cores).
 """
 import os
+import subprocess
+import sys
 
 import numpy as np
 import pytest
@@ -535,6 +537,42 @@ def test_config2_full_size(fz):
                 assert torch.equal(out2, out), cap
             plan.set_enum_ctas_per_sm(0)
         del out, out2
+
+
+_FORCED_FILL = r"""
+import sys, numpy as np, torch
+sys.path.insert(0, sys.argv[1])
+import oracle
+import paper_2407_20474_gb300 as fz
+torch.cuda.set_device(0)
+for tail, top in (((4, 9, 10), 300), ((3, 7, 8, 20), 200), ((2, 5), 200), ((5,), 40),
+                  ((4, 20, 22, 31, 39), 240), ((2, 4), 80), ((3, 6, 6), 90), ((11, 14), 501)):
+    rows = fz.fz_memo_rows(tail, top)
+    off = torch.zeros(top + 1, dtype=torch.int64, device="cuda")
+    buf = torch.full(((rows + 4) * len(tail),), -7, dtype=torch.int32, device="cuda")
+    assert fz.fz_build_memo_into(tail, top, off, buf, rows) == rows
+    torch.cuda.synchronize()
+    host = buf.cpu().numpy()
+    assert (host[rows * len(tail):] == -7).all(), tail
+    ref_off, ref_rows = oracle.memo_csr(tail, top)
+    assert np.array_equal(off.cpu().numpy().view(np.uint64), ref_off), tail
+    assert np.array_equal(host[:rows * len(tail)].reshape(rows, len(tail)), ref_rows), tail
+print("forced fill ok")
+"""
+
+
+@pytest.mark.parametrize("variant", ["phase", "grid"])
+def test_memo_fill_forced_variant(fz, variant):
+    """The whole-GPU fills forced on small memos (FZ_MEMO_FILL is read once
+    per process, so each runs in a child): phases of min(t_1..) elements
+    where the tail allows them (t_1 >= 2 t_0), batches of t_0 elements
+    otherwise, both equal to the oracle's memo."""
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    env = dict(os.environ, FZ_MEMO_FILL=variant)
+    r = subprocess.run([sys.executable, "-c", _FORCED_FILL, root], env=env, capture_output=True,
+                       text=True, timeout=600)
+    assert r.returncode == 0, r.stdout[-2000:] + r.stderr[-2000:]
+    assert "forced fill ok" in r.stdout
 
 
 def test_config3_full_memo_build(fz):
