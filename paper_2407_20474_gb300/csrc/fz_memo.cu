@@ -712,9 +712,9 @@ __global__ void __launch_bounds__(T, 1024 / T) memo_cta_build_kernel(
 
 // Element groups.  Most elements of a batch memo are a few rows (a batch of
 // 4096 instances of widths 3..8: 95 % of 1.7e7 elements hold at most 256
-// words), and a warp that takes them
-// one at a time pays a chain of dependent loads (the element's offset, then
-// its blocks' lengths and sources, then the copy) for a handful of words.
+// words), and a warp that takes them one at a time pays a chain of
+// dependent loads (the element's offset, then its blocks' lengths and
+// sources, then the copy) for a handful of words.
 // Here each warp owns a contiguous run of the batch's elements and takes
 // them G = floor(32 / k) at a time: lane j loads the length and source of
 // block j mod k of element j div k, all in one round; a warp scan of the
@@ -724,8 +724,8 @@ __global__ void __launch_bounds__(T, 1024 / T) memo_cta_build_kernel(
 // its block by a binary search over the lanes' first rows (shuffles; empty
 // blocks share their successor's first row and are never the last block
 // starting at or before a row).  Larger groups copy block by block, as the
-// one-element build does.  One __syncthreads per elementwise batch, as
-// before: a warp's groups never read rows of its own batch.
+// one-element build does.  One __syncthreads per elementwise batch: a
+// warp's groups never read rows of its own batch.
 constexpr uint64_t MG_FLAT_WORDS = 4 * 32 * MB_ILP;
 
 __device__ __forceinline__ uint32_t warp_incl_scan_u32(uint32_t v, int lane) {
