@@ -158,11 +158,14 @@ def test_batch_cluster_memo_build(fz):
     """The longest memos built by thread-block clusters: a few elements per
     batch (small tail generators: several warps share an element's words),
     batches of more elements than the cluster has warps (tail minimum 140),
-    and many short memos claimed one per CTA after them.  Rebuilt twice (the
-    claim counter starts over)."""
+    and many short memos claimed one per CTA after them, some filled in
+    phases (tails whose other generators are at least twice the first).
+    Rebuilt twice (the claim counter starts over)."""
     inst = [((2, 3, 5, 7), 400), ((2, 3, 5, 7, 11), 200), ((33, 37, 41, 43, 47), 2500),
             ((34, 39, 41, 45), 3000), ((5, 8, 11, 14), 900), ((3, 4, 5, 6, 7, 8), 60),
-            ((70, 75, 80, 85), 5000), ((130, 140, 150, 160), 9000)]
+            ((70, 75, 80, 85), 5000), ((130, 140, 150, 160), 9000),
+            ((2, 3, 9, 10), 300), ((4, 5, 12, 30), 900), ((3, 4, 9, 20, 23), 250),
+            ((2, 5, 40, 41), 2000)]
     inst += small_instances(36, 80)
     with fz.Batch(inst) as b:
         assert b.coop_memos > 0, b.coop_memos
