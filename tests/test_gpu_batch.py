@@ -158,9 +158,9 @@ def test_batch_cluster_memo_build(fz):
     """The longest memos built by thread-block clusters: a few elements per
     batch (small tail generators: several warps share an element's words),
     batches of more elements than the cluster has warps (tail minimum 140),
-    and many short memos claimed one per CTA after them, some filled in
-    phases (tails whose other generators are at least twice the first).
-    Rebuilt twice (the claim counter starts over)."""
+    and many short memos claimed one per CTA after them, among them tails
+    whose other generators are at least twice the first.  Rebuilt twice (the
+    claim counter starts over)."""
     inst = [((2, 3, 5, 7), 400), ((2, 3, 5, 7, 11), 200), ((33, 37, 41, 43, 47), 2500),
             ((34, 39, 41, 45), 3000), ((5, 8, 11, 14), 900), ((3, 4, 5, 6, 7, 8), 60),
             ((70, 75, 80, 85), 5000), ((130, 140, 150, 160), 9000),
