@@ -192,6 +192,41 @@ __device__ __forceinline__ bool grid_barrier_mono(unsigned *count, unsigned inde
 }
 
 
+// The two halves of grid_barrier_mono, for a block that has work needing no
+// other block's writes to do between them: grid_arrive releases the block's
+// writes (ordered before thread 0 by the __syncthreads) with one add to the
+// count; grid_wait polls (thread 0, bounded like grid_barrier_mono) until
+// the count reaches (index + 1) x blocks, then orders the block after it.
+__device__ __forceinline__ void grid_arrive(unsigned *count) {
+    __syncthreads();
+    if (threadIdx.x == 0)
+        asm volatile("red.release.gpu.global.add.u32 [%0], 1;" ::"l"(count) : "memory");
+}
+
+__device__ __forceinline__ bool grid_wait(unsigned *count, unsigned index, int *status,
+                                          uint64_t timeout_ns = BARRIER_TIMEOUT_NS) {
+    __shared__ int ok_flag_w;
+    if (threadIdx.x == 0) {
+        int ok = 1;
+        const unsigned target = (index + 1u) * (gridDim.x * gridDim.y * gridDim.z);
+        uint64_t t0 = 0;
+        uint32_t polls = 0;
+        while (ld_acquire_u32(count) < target) {
+            if (polls == 0) t0 = globaltimer_ns();
+            if (++polls >= BARRIER_MAX_POLLS ||
+                ((polls & 255u) == 0 && globaltimer_ns() - t0 > timeout_ns)) {
+                atomicExch(status, (int)DEV_TIMEOUT);
+                ok = 0;
+                break;
+            }
+            __nanosleep(20);
+        }
+        ok_flag_w = ok;
+    }
+    __syncthreads();
+    return ok_flag_w != 0;
+}
+
 // ---------------------------------------------------------------------------
 // Host helpers.
 // ---------------------------------------------------------------------------

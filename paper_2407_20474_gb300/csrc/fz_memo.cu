@@ -229,48 +229,98 @@ __global__ void __launch_bounds__(GRID_THREADS) memo_fill_kernel(FillParams P) {
 // one, row for row (Corollary "resultislex" orders the blocks by i), so word
 // w of element m, while w < |Z(m - t_0)| k, is word w of element m - t_0 plus
 // one when w is coordinate 0; every other word's source lies at least L =
-// min(t_1..t_{k-1}) elements back.  A phase of L consecutive elements
-// therefore needs no barrier inside it when one thread owns the chain (class
-// e = m mod t_0 within the phase, word w) through all the phase's elements of
-// class e: it keeps the chain's last word in a register, reads the word
-// before the phase through L2 (another thread wrote it in an earlier phase),
-// and takes every other word from the gather map.  Along a class the
-// element sizes never shrink (block 0 is the previous element), so a chain
-// is born once and stays.  With t_1 >= 2 t_0 this needs L / t_0 times fewer
-// grid barriers than the batches of t_0 elements (the d = 5 memo with tail
-// (4, 20, 22, 31, 39): 76 instead of 376).
+// min(t_1..t_{k-1}) elements back.  Along a class m mod t_0 the element sizes
+// never shrink (block 0 is the previous element), so a (class, word) chain is
+// born once and stays.  Each chain belongs to one thread for the whole fill
+// (a fixed bound per class: its last element's words), and the memo is
+// filled in phases of L elements:
+//   pass A: the chains alive when the phase starts hold only block-0 words
+//     in it, computed from the thread's own last word of the chain (kept for
+//     its first PH_J chains, else re-read from its own store);
+//   wait at the grid barrier of the previous phase;
+//   pass B: the chains born in the phase, their first word from the gather
+//     map (sources L or more elements back, so in earlier phases), the rest
+//     block 0;
+//   arrive at this phase's barrier.
+// Pass A needs no other thread's writes, so it overlaps the barrier.  With
+// t_1 >= 2 t_0 there are L / t_0 times fewer barriers than batches of t_0
+// elements (the d = 5 memo with tail (4, 20, 22, 31, 39): 75 instead of 375).
+constexpr int PH_J = 32;
+
 __global__ void __launch_bounds__(GRID_THREADS) memo_fill_phase_kernel(FillParams P) {
     const uint64_t tid = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
     const uint64_t nthreads = (uint64_t)gridDim.x * blockDim.x;
     const uint32_t uk = (uint32_t)P.k;
     const int64_t t0 = P.b;
+    const int64_t ncl = P.top < t0 ? P.top : t0;
+    uint64_t wc = 0;  // words of the widest class's last element
+    for (int64_t e = 0; e < ncl; ++e) {
+        const int64_t ml = e + ((P.top - 1 - e) / t0) * t0;
+        const uint64_t sz = __ldg(P.O + ml + 1) - __ldg(P.O + ml);
+        if (sz > wc) wc = sz;
+    }
+    wc *= uk;
+    // chain ch: word w = 32 (ch / 32 div ncl) + ch mod 32 of class (ch / 32)
+    // mod ncl -- a warp's lanes take 32 neighbouring words of one class, and
+    // a thread's chains (ch = tid + j nthreads) grow in w with j, so a phase
+    // stops at its widest element
+    const uint64_t nblk = (wc + 31) / 32;
+    const uint64_t nch = (uint64_t)ncl * nblk * 32;
+    const uint64_t J = (nch + nthreads - 1) / nthreads;
+    int32_t last[PH_J];
     unsigned nbar = 0;
     for (int64_t ma = 0; ma < P.top; ma += P.L) {
         const int64_t mb = ma + P.L < P.top ? ma + P.L : P.top;
-        const uint64_t R0 = __ldg(P.O + ma);
+        const int64_t mr = ma % t0;
         uint64_t wp = 0;  // the phase's widest element, in words
         for (int64_t m = ma; m < mb; ++m) {
             const uint64_t sz = __ldg(P.O + m + 1) - __ldg(P.O + m);
             if (sz > wp) wp = sz;
         }
         wp *= uk;
-        const int64_t ncls = mb - ma < t0 ? mb - ma : t0;
-        const uint64_t nchains = (uint64_t)ncls * wp;
-        for (uint64_t ch = tid; ch < nchains; ch += nthreads) {
-            const int64_t e = (int64_t)(ch / wp);
-            const uint64_t w = ch - (uint64_t)e * wp;
+        // pass A
+        for (uint64_t j = 0; j < J; ++j) {
+            const uint64_t ch = tid + j * nthreads;
+            if (ch >= nch) break;
+            const uint64_t q = ch >> 5;
+            const int64_t e = (int64_t)(q % (uint64_t)ncl);
+            const uint64_t w = (q / (uint64_t)ncl) * 32 + (ch & 31);
+            if (w >= wp) break;
+            const int64_t m1 = ma + (e - mr + t0) % t0;  // the class's first element here
+            if (m1 >= mb || m1 < t0) continue;
+            const uint64_t op = __ldg(P.O + m1 - t0);
+            if (w >= (__ldg(P.O + m1 - t0 + 1) - op) * uk) continue;  // not alive yet
+            int32_t prev = j < PH_J ? last[j] : P.rows[op * uk + w];
+            const int32_t inc = (w % uk) == 0 ? 1 : 0;
+            for (int64_t m = m1; m < mb; m += t0) {
+                prev += inc;
+                P.rows[__ldg(P.O + m) * uk + w] = prev;
+            }
+            if (j < PH_J) last[j] = prev;
+        }
+        if (ma > 0 && !grid_wait(P.bar, nbar - 1, P.status)) return;
+        // pass B
+        const uint64_t R0 = __ldg(P.O + ma);
+        for (uint64_t j = 0; j < J; ++j) {
+            const uint64_t ch = tid + j * nthreads;
+            if (ch >= nch) break;
+            const uint64_t q = ch >> 5;
+            const int64_t e = (int64_t)(q % (uint64_t)ncl);
+            const uint64_t w = (q / (uint64_t)ncl) * 32 + (ch & 31);
+            if (w >= wp) break;
+            const int64_t m1 = ma + (e - mr + t0) % t0;
+            if (m1 >= mb) continue;
+            if (m1 >= t0 && w < (__ldg(P.O + m1 - t0 + 1) - __ldg(P.O + m1 - t0)) * uk)
+                continue;  // alive: done in pass A
             const uint32_t c = (uint32_t)(w % uk);
             int32_t prev = 0;
-            bool have = false;  // prev holds word w of element m - t_0
-            for (int64_t m = ma + e; m < mb; m += t0) {
+            bool have = false;
+            for (int64_t m = m1; m < mb; m += t0) {
                 const uint64_t o = __ldg(P.O + m);
                 if (w >= (__ldg(P.O + m + 1) - o) * uk) continue;  // not born yet
                 int32_t v;
-                const uint64_t op = m >= t0 ? __ldg(P.O + m - t0) : 0;
-                const uint64_t szp = m >= t0 ? (__ldg(P.O + m - t0 + 1) - op) * uk : 0;
-                if (w < szp) {
-                    if (!have) prev = ld_cg_s32(P.rows + op * uk + w);
-                    v = prev + (c == 0 ? 1 : 0);
+                if (have) {
+                    v = prev + (c == 0 ? 1 : 0);  // block 0 after the birth
                 } else if (!word_value<false>(P, __ldg(P.map + o + w / uk), c, R0, v)) {
                     atomicExch(P.status, (int)DEV_INTERNAL);
                     v = 0;
@@ -279,8 +329,12 @@ __global__ void __launch_bounds__(GRID_THREADS) memo_fill_phase_kernel(FillParam
                 prev = v;
                 have = true;
             }
+            if (have && j < PH_J) last[j] = prev;
         }
-        if (mb < P.top && !grid_barrier_mono(P.bar, nbar++, P.status)) return;
+        if (mb < P.top) {
+            grid_arrive(P.bar);
+            ++nbar;
+        }
     }
 }
 
