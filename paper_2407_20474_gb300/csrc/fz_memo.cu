@@ -264,34 +264,43 @@ __global__ void __launch_bounds__(GRID_THREADS) memo_fill_phase_kernel(FillParam
     // mod ncl -- a warp's lanes take 32 neighbouring words of one class, and
     // a thread's chains (ch = tid + j nthreads) grow in w with j, so a phase
     // stops at its widest element
-    const uint64_t nblk = (wc + 31) / 32;
-    const uint64_t nch = (uint64_t)ncl * nblk * 32;
-    const uint64_t J = (nch + nthreads - 1) / nthreads;
+    // (32-bit chain indices: the host launches this fill only when
+    // t_0 x rows x k stays below 2^31)
+    const uint32_t nblk = (uint32_t)((wc + 31) / 32);
+    const uint32_t ucl = (uint32_t)ncl, ut0 = (uint32_t)t0;
+    const uint32_t nch = ucl * nblk * 32u;
+    const uint32_t nth = (uint32_t)nthreads, utid = (uint32_t)tid;
+    const uint32_t J = (nch + nth - 1) / nth;
     int32_t last[PH_J];
     unsigned nbar = 0;
     for (int64_t ma = 0; ma < P.top; ma += P.L) {
         const int64_t mb = ma + P.L < P.top ? ma + P.L : P.top;
-        const int64_t mr = ma % t0;
-        uint64_t wp = 0;  // the phase's widest element, in words
-        for (int64_t m = ma; m < mb; ++m) {
-            const uint64_t sz = __ldg(P.O + m + 1) - __ldg(P.O + m);
+        const uint32_t mr = (uint32_t)(ma % t0);
+        // the phase's widest element: sizes never shrink along a class, so
+        // it is one of the classes' last elements in the phase
+        uint64_t wp = 0;
+        for (int64_t e = 0; e < ncl; ++e) {
+            const int64_t ml = mb - 1 - (int64_t)(((uint32_t)((mb - 1) % t0) - (uint32_t)e + ut0) % ut0);
+            if (ml < ma) continue;
+            const uint64_t sz = __ldg(P.O + ml + 1) - __ldg(P.O + ml);
             if (sz > wp) wp = sz;
         }
         wp *= uk;
         // pass A
-        for (uint64_t j = 0; j < J; ++j) {
-            const uint64_t ch = tid + j * nthreads;
+        for (uint32_t j = 0; j < J; ++j) {
+            const uint32_t ch = utid + j * nth;
             if (ch >= nch) break;
-            const uint64_t q = ch >> 5;
-            const int64_t e = (int64_t)(q % (uint64_t)ncl);
-            const uint64_t w = (q / (uint64_t)ncl) * 32 + (ch & 31);
+            const uint32_t q = ch >> 5;
+            const uint32_t qd = q / ucl;
+            const int64_t e = (int64_t)(q - qd * ucl);
+            const uint64_t w = (uint64_t)qd * 32u + (ch & 31u);
             if (w >= wp) break;
-            const int64_t m1 = ma + (e - mr + t0) % t0;  // the class's first element here
+            const int64_t m1 = ma + (int64_t)(((uint32_t)e - mr + ut0) % ut0);  // the class's first element here
             if (m1 >= mb || m1 < t0) continue;
             const uint64_t op = __ldg(P.O + m1 - t0);
             if (w >= (__ldg(P.O + m1 - t0 + 1) - op) * uk) continue;  // not alive yet
             int32_t prev = j < PH_J ? last[j] : P.rows[op * uk + w];
-            const int32_t inc = (w % uk) == 0 ? 1 : 0;
+            const int32_t inc = ((uint32_t)w % uk) == 0 ? 1 : 0;
             for (int64_t m = m1; m < mb; m += t0) {
                 prev += inc;
                 P.rows[__ldg(P.O + m) * uk + w] = prev;
@@ -301,18 +310,19 @@ __global__ void __launch_bounds__(GRID_THREADS) memo_fill_phase_kernel(FillParam
         if (ma > 0 && !grid_wait(P.bar, nbar - 1, P.status)) return;
         // pass B
         const uint64_t R0 = __ldg(P.O + ma);
-        for (uint64_t j = 0; j < J; ++j) {
-            const uint64_t ch = tid + j * nthreads;
+        for (uint32_t j = 0; j < J; ++j) {
+            const uint32_t ch = utid + j * nth;
             if (ch >= nch) break;
-            const uint64_t q = ch >> 5;
-            const int64_t e = (int64_t)(q % (uint64_t)ncl);
-            const uint64_t w = (q / (uint64_t)ncl) * 32 + (ch & 31);
+            const uint32_t q = ch >> 5;
+            const uint32_t qd = q / ucl;
+            const int64_t e = (int64_t)(q - qd * ucl);
+            const uint64_t w = (uint64_t)qd * 32u + (ch & 31u);
             if (w >= wp) break;
-            const int64_t m1 = ma + (e - mr + t0) % t0;
+            const int64_t m1 = ma + (int64_t)(((uint32_t)e - mr + ut0) % ut0);
             if (m1 >= mb) continue;
             if (m1 >= t0 && w < (__ldg(P.O + m1 - t0 + 1) - __ldg(P.O + m1 - t0)) * uk)
                 continue;  // alive: done in pass A
-            const uint32_t c = (uint32_t)(w % uk);
+            const uint32_t c = (uint32_t)w % uk;
             int32_t prev = 0;
             bool have = false;
             for (int64_t m = m1; m < mb; m += t0) {
@@ -1527,7 +1537,8 @@ int launch_memo_build(const int32_t *tail, int k, int32_t top, uint64_t rows,
     {
         int L = top;
         for (int i = 1; i < k; ++i) L = tail[i] < L ? tail[i] : L;
-        fp.L = (tail[0] == tmin && L >= 2 * tail[0]) ? L : 0;
+        const bool fits32 = (double)tail[0] * (double)(rows + 32) * k < 2147483648.0;
+        fp.L = (tail[0] == tmin && L >= 2 * tail[0] && fits32) ? L : 0;
     }
     // the gather map: every memo row's source row and incremented coordinate
     auto launch_map = [&](int skip0) -> int {
